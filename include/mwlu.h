@@ -1,0 +1,214 @@
+/*
+ * mwlu.h -- C ABI of the multiword (DD/TD/QD) direct solver and
+ * mixed-precision iterative refinement library (libmwlu.so, sm_103a).
+ *
+ * Method: Kouya, "Accelerated Multiple Precision Direct Method and Mixed
+ * Precision Iterative Refinement on Python Programming Environment"
+ * (arXiv 2107.12550).  The calls follow the paper's problem statement
+ * A x = b (Section 3, Eq. (1)) and the calls of its refinement listing
+ * (Section 2, Listing 1): TDLUdecompPM(af, af_ch) -> mw_ludecomp,
+ * SolveTDLSPM(xf, af, bf, af_ch) -> mw_solve, the long-precision residual
+ * b - a*x -> mw_residual, and the whole loop -> mw_refine.
+ *
+ * Numbers.  A multiword value of precision w is w binary64 words whose sum
+ * is the value: w = 2 double-double (DD), 3 triple-double (TD), 4
+ * quad-double (QD); the long precision of the refinement is 8 words
+ * (8 x 53 = 424 bits, the paper's 424-bit mpmath precision).
+ *
+ * Layout (all matrix/vector pointers are DEVICE pointers unless stated):
+ *   matrix: w planes of lda*n doubles, column-major, plane = lda*n;
+ *           word c of A(i,j) is A[c*lda*n + j*lda + i];  lda >= max(1, n).
+ *   vector: w planes of n doubles; word c of v(i) is v[c*n + i].
+ *   pivots: int64 (the paper's ctypes c_long array), 0-based, LAPACK swap
+ *           sequence: at step k rows k and piv[k] were exchanged.
+ * The caller owns every buffer; no call allocates device memory.  Work
+ * buffers are caller-provided (size from mw_workspace_size), 256-byte
+ * aligned, and must not be shared by calls that may run concurrently.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ * enqueue work and return without synchronising, except mw_refine, which
+ * reads a few status words back once per refinement step.
+ *
+ * Return codes: MW_OK (0); a negative value -i when argument i (1-based) is
+ * invalid; MW_ECUDA when a CUDA call failed (mw_last_cuda_error gives the
+ * cudaError_t); MW_ETIMEOUT when a bounded device wait gave up;
+ * MW_ESINGULAR / MW_ENOTCONV as documented per call.  Inputs with NaN or
+ * Inf give unspecified (but memory-safe) results.
+ */
+#ifndef MWLU_H
+#define MWLU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* precisions: the number of binary64 words */
+#define MW_DD 2
+#define MW_TD 3
+#define MW_QD 4
+#define MW_LONG_WORDS 8
+
+/* trailing-update forms of the blocked LU */
+#define MW_UPDATE_PLAIN 0 /* multiword GEMM on the FP64 pipe, bitwise equal to unblocked LU */
+#define MW_UPDATE_SPLIT 1 /* split-precision (Ozaki-style) tensor-core update (DD only) */
+
+/* status codes */
+#define MW_OK 0
+#define MW_ESINGULAR 1
+#define MW_ENOTCONV 2
+#define MW_ECUDA 3
+#define MW_ETIMEOUT 4
+#define MW_EUNSUPPORTED 5
+
+/* operations for mw_workspace_size */
+#define MW_OP_LUDECOMP 0
+#define MW_OP_SOLVE 1
+#define MW_OP_REFINE 2
+
+/* stopping tests of mw_refine */
+#define MW_STOP_EQ2 0  /* Eq. (2): ||r||_2 <= sqrt(n) rtol ||A||_F ||x||_2 + atol */
+#define MW_STOP_BITS 1 /* applied correction <= 2^-(target_bits+2) ||x||_inf */
+
+/*
+ * mw_workspace_size -- bytes of work buffer needed by `op` at precision
+ * `prec` (for MW_OP_REFINE: the inner precision), trailing-update form
+ * `update` and order n.  Writes *bytes (host pointer).  Returns MW_OK or
+ * -i for an invalid argument.  Pure host function; no GPU is touched.
+ */
+int mw_workspace_size(int op, int prec, int update, int64_t n, size_t* bytes);
+
+/*
+ * mw_ludecomp -- LU decomposition with partial pivoting in place
+ * (Section 2, Listing 1: TDLUdecompPM(af, af_ch)).
+ *   prec    MW_DD, MW_TD or MW_QD; the first `prec` planes of A are used.
+ *   update  MW_UPDATE_PLAIN (any prec) or MW_UPDATE_SPLIT (MW_DD only).
+ *   n       order, n >= 0.
+ *   A       device, prec planes (lda, n); overwritten by L\U with the unit
+ *           lower factor L implicit.
+ *   lda     leading dimension, lda >= max(1, n).
+ *   piv     device int64[n]: the swap sequence (0-based).
+ *   info    device int64[1]: 0, or k+1 for the first exactly zero pivot
+ *           u_kk (the factorisation still completes, as in LAPACK getrf).
+ *   work    device work buffer of at least mw_workspace_size(MW_OP_LUDECOMP)
+ *           bytes; work_bytes its size.
+ * Pivot rule: p = the first row i >= k with the largest |a_ik| under the
+ * lexicographic order of the sign-adjusted words (ties take the smallest
+ * row).  The plain form is bitwise identical to unblocked right-looking
+ * elimination with a rounded multiword multiply and subtraction per element
+ * update.  Returns MW_OK, -i, MW_ECUDA, MW_ETIMEOUT or MW_EUNSUPPORTED.
+ */
+int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t lda, int64_t* piv,
+                int64_t* info, void* work, size_t work_bytes, void* stream);
+
+/*
+ * mw_solve -- forward/back substitution with the factors of mw_ludecomp
+ * (Section 2, Listing 1: SolveTDLSPM(xf, af, bf, af_ch)).
+ *   LU, lda, piv  as produced by mw_ludecomp at precision prec (device).
+ *   b             device, prec planes of n (right-hand side).
+ *   x             device, prec planes of n (solution); x may equal b.
+ * Order of operations per entry: y = P b; y_i -= l_ij y_j for j ascending;
+ * x_j = y_j / u_jj, then y_i -= u_ij x_j for j descending.  A zero u_jj gives
+ * Inf/NaN entries (check mw_ludecomp's info).  Returns MW_OK, -i, MW_ECUDA or
+ * MW_ETIMEOUT.
+ */
+int mw_solve(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
+             const double* b, double* x, void* work, size_t work_bytes, void* stream);
+
+/*
+ * mw_residual -- r = b - A x computed exactly (every product of two words is
+ * accumulated in a fixed-point integer covering the whole binary64 product
+ * range) and then rounded greedily to r_words words: r_0 = RN(r),
+ * r_c = RN(r - r_0 - ... - r_{c-1}).  This is the long-precision residual
+ * of Listing 1 (`res = b - a * x`), computed exactly instead of in 424-bit
+ * arithmetic.  A: a_words planes (lda, n); b: b_words planes of n; x:
+ * x_words planes of n; r: r_words planes of n (all device, 1..8 words).
+ * Returns MW_OK, -i or MW_ECUDA.
+ */
+int mw_residual(int64_t n, const double* A, int64_t lda, int a_words, const double* b,
+                int b_words, const double* x, int x_words, double* r, int r_words,
+                void* stream);
+
+/*
+ * mw_refine -- mixed precision iterative refinement (Section 2, Listing 1).
+ *   A, lda, a_words  device matrix (1..8 words; its first `inner` words are
+ *                    factored).
+ *   b, b_words       device right-hand side (1..8 words).
+ *   inner            MW_DD, MW_TD or MW_QD: precision of the LU and solves.
+ *   update           trailing-update form for the inner LU.
+ *   target_bits      MW_STOP_BITS: stop when the applied correction is below
+ *                    2^-(target_bits+2) ||x||_inf.
+ *   max_iter         maximum number of corrections (>= 0).
+ *   stop_mode        MW_STOP_EQ2 (uses rtol, atol) or MW_STOP_BITS.
+ *   x, x_words       device output, x_words planes of n (inner <= x_words
+ *                    <= 8; 8 = the paper's 424 bits).
+ *   stats            HOST int64[4]: corrections applied, residuals evaluated,
+ *                    LU info, final status.
+ *   work             device work buffer, mw_workspace_size(MW_OP_REFINE,
+ *                    inner, update, n) bytes.
+ * Steps: LU of A's first `inner` words; x = solve(b rounded to inner)
+ * padded with zero words; loop: r = RN_xw(b - A x) exactly; stop test;
+ * e = ilogb(max_i |r_0(i)|); z = solve(first `inner` words of 2^-e r);
+ * x = RN_xw(x + 2^e z) exactly.  The MW_STOP_BITS mode also stops (as not
+ * converged) when a correction exceeds half the previous one.
+ * Returns MW_OK (converged), MW_ESINGULAR (zero pivot; stats[2] = info),
+ * MW_ENOTCONV (max_iter reached or stagnation; x holds the last iterate),
+ * -i, MW_ECUDA or MW_ETIMEOUT.  Synchronises `stream` once per step.
+ */
+int mw_refine(int64_t n, const double* A, int64_t lda, int a_words, const double* b,
+              int b_words, int inner, int update, int target_bits, int max_iter, int stop_mode,
+              double rtol, double atol, double* x, int x_words, int64_t* stats, void* work,
+              size_t work_bytes, void* stream);
+
+/*
+ * mw_peak_fp64 -- project microbenchmark of the FP64 pipe: runs an
+ * independent fused multiply-add stream on every SM and writes the measured
+ * rate in FP64 instructions per second to *instr_per_s (host pointer).
+ * Synchronous.  Returns MW_OK or MW_ECUDA.
+ */
+int mw_peak_fp64(double* instr_per_s, void* stream);
+
+/*
+ * mw_arith -- element-wise multiword arithmetic on device arrays (the
+ * DD/TD/QD building blocks of Section 1, as used inside every kernel):
+ *   op 0: z = x + y   1: z = x - y   2: z = x * y   3: z = x / y
+ *   op 4: z plane 0 = sign(|x| - |y|) in the pivot order (-1, 0, +1),
+ *         other planes 0.
+ * x, y, z: device, prec planes of cnt doubles.  Asynchronous on `stream`.
+ * Returns MW_OK, -i or MW_ECUDA.
+ */
+int mw_arith(int op, int prec, int64_t cnt, const double* x, const double* y, double* z,
+             void* stream);
+
+/*
+ * Launch accounting and per-phase timing.  Phases: 0 panel factorisation,
+ * 1 row interchanges, 2 triangular solve of U12, 3 plain trailing update,
+ * 4 split trailing update (tensor-core GEMMs), 5 substitution, 6 pivot
+ * permutation, 7 exact residual, 8 refinement bookkeeping, 9 split-update
+ * slicing and recombination.
+ * mw_profile_enable(1) brackets every later kernel launch of the library with
+ * two CUDA events on its stream (0 turns this off; launches are counted
+ * either way).  mw_profile_read synchronises on the recorded events and
+ * writes, for phases 0..nphase-1, the summed device time in ms (ms, host
+ * array, may be NULL) and the launch count (launches, host array, may be
+ * NULL); reset != 0 clears both afterwards.  Returns MW_OK or MW_ECUDA.
+ */
+int mw_profile_enable(int on);
+int mw_profile_read(double* ms, long long* launches, int nphase, int reset);
+
+/* mw_strerror -- static text for a status code. */
+const char* mw_strerror(int code);
+
+/* mw_last_cuda_error -- the cudaError_t behind the last MW_ECUDA. */
+int mw_last_cuda_error(void);
+
+/* mw_version -- library version string. */
+const char* mw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MWLU_H */

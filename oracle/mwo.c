@@ -824,7 +824,7 @@ int mwo_refine(int64_t n, const double *A, int64_t lda, int wa,
         }
     }
     for (;;) {
-        double rmax = 0.0, scale;
+        double rmax = 0.0;
         int er;
         mwo_residual(n, A, lda, wa, b, wb, x, wx, r, wx);
         residuals++;
@@ -844,10 +844,9 @@ int mwo_refine(int64_t n, const double *A, int64_t lda, int wa,
             if (nr <= rhs) { status = 0; break; }
         }
         if (corrections >= max_iter) { status = 2; break; }
-        scale = ldexp(1.0, -er);
         for (c = 0; c < w_in; ++c)
             for (i = 0; i < n; ++i)
-                rh[c * n + i] = r[c * n + i] * scale;
+                rh[c * n + i] = ldexp(r[c * n + i], -er);
         mwo_solve(w_in, n, LU, lda, piv, rh, z);
         /* x = RN_wx(x + 2^er z), exactly */
         for (i = 0; i < n; ++i) {

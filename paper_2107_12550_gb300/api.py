@@ -1,0 +1,161 @@
+"""Python binding of the C ABI with the paper's call names: ``ludecomp``,
+``solve``, ``residual`` and ``refine`` (Section 2, Listing 1).
+
+Argument marshalling only: every step runs in the CUDA library.  Tensors are
+torch float64 CUDA tensors in the component-planar layout of
+``include/mwlu.h``: a matrix is (w, n, lda) with ``A[c, j, i]`` = word c of
+A(i, j), a vector is (w, n).  Work buffers are allocated here with torch and
+passed down; the library itself never allocates.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import _lib as L
+
+PREC = {"dd": L.MW_DD, "td": L.MW_TD, "qd": L.MW_QD, 2: L.MW_DD, 3: L.MW_TD, 4: L.MW_QD}
+UPDATE = {"plain": L.MW_UPDATE_PLAIN, "split": L.MW_UPDATE_SPLIT, 0: 0, 1: 1}
+
+
+def _prec(p) -> int:
+    return PREC[p.lower() if isinstance(p, str) else p]
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check_mat(A: torch.Tensor, name: str):
+    if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 3 and A.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape (w, n, lda)")
+
+
+def _check_vec(v: torch.Tensor, name: str):
+    if not (v.is_cuda and v.dtype == torch.float64 and v.dim() == 2 and v.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape (w, n)")
+
+
+def workspace(op: int, prec: int, update: int, n: int, device=None) -> torch.Tensor:
+    nbytes = max(L.workspace_size(op, prec, update, n), 256)
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def ludecomp(A: torch.Tensor, prec="dd", update="plain", *, work: Optional[torch.Tensor] = None,
+             stream=None, inplace: bool = False):
+    """LU with partial pivoting (TDLUdecompPM).  Returns (LU, piv, info_tensor);
+    LU has `prec` planes.  ``info`` is a device int64 tensor of one element
+    (0, or k+1 for the first exactly zero pivot)."""
+    _check_mat(A, "A")
+    w = _prec(prec)
+    u = UPDATE[update]
+    n, lda = A.shape[1], A.shape[2]
+    if inplace:
+        if A.shape[0] != w:
+            raise ValueError("in-place factorisation needs exactly `prec` planes")
+        LU = A
+    else:
+        LU = torch.zeros((w, n, lda), dtype=torch.float64, device=A.device)
+        k = min(w, A.shape[0])
+        LU[:k].copy_(A[:k])
+    piv = torch.empty(max(n, 1), dtype=torch.int64, device=A.device)
+    info = torch.zeros(1, dtype=torch.int64, device=A.device)
+    if work is None:
+        work = workspace(L.MW_OP_LUDECOMP, w, u, n, A.device)
+    L.check("mw_ludecomp", L.lib().mw_ludecomp(w, u, n, _ptr(LU), lda, _ptr(piv), _ptr(info),
+                                               _ptr(work), work.numel(), _stream(stream)))
+    return LU, piv[:n], info
+
+
+def solve(LU: torch.Tensor, piv: torch.Tensor, b: torch.Tensor, prec=None, *,
+          work: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None, stream=None):
+    """Forward/back substitution (SolveTDLSPM).  b: (>=1, n); uses its first
+    `prec` words (missing words are zero).  Returns x of shape (prec, n)."""
+    _check_mat(LU, "LU")
+    w = _prec(prec) if prec is not None else LU.shape[0]
+    n, lda = LU.shape[1], LU.shape[2]
+    _check_vec(b, "b")
+    if b.shape[0] != w:
+        bb = torch.zeros((w, n), dtype=torch.float64, device=LU.device)
+        k = min(w, b.shape[0])
+        bb[:k].copy_(b[:k])
+        b = bb
+    x = out if out is not None else torch.empty((w, n), dtype=torch.float64, device=LU.device)
+    if work is None:
+        work = workspace(L.MW_OP_SOLVE, w, 0, n, LU.device)
+    L.check("mw_solve", L.lib().mw_solve(w, n, _ptr(LU), lda, _ptr(piv), _ptr(b), _ptr(x),
+                                         _ptr(work), work.numel(), _stream(stream)))
+    return x
+
+
+def residual(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, r_words: int = 8, *, stream=None,
+             out: Optional[torch.Tensor] = None):
+    """r = b - A x exactly, rounded greedily to r_words words."""
+    _check_mat(A, "A")
+    _check_vec(b, "b")
+    _check_vec(x, "x")
+    n, lda = A.shape[1], A.shape[2]
+    r = out if out is not None else torch.empty((r_words, n), dtype=torch.float64, device=A.device)
+    L.check("mw_residual", L.lib().mw_residual(n, _ptr(A), lda, A.shape[0], _ptr(b), b.shape[0],
+                                               _ptr(x), x.shape[0], _ptr(r), r_words, _stream(stream)))
+    return r
+
+
+@dataclass
+class RefineResult:
+    x: torch.Tensor
+    status: int
+    corrections: int
+    residuals: int
+    info: int
+
+    @property
+    def converged(self) -> bool:
+        return self.status == L.MW_OK
+
+
+def refine(A: torch.Tensor, b: torch.Tensor, inner_prec="td", target_bits: int = 200, *,
+           update="plain", max_iter: int = 30, stop_mode: int = L.MW_STOP_BITS, rtol: float = 1e-100,
+           atol: float = 0.0, x_words: int = 8, work: Optional[torch.Tensor] = None,
+           out: Optional[torch.Tensor] = None, stream=None) -> RefineResult:
+    """Mixed precision iterative refinement (Listing 1).  Returns a
+    RefineResult; x has x_words planes (8 = 424 bits)."""
+    _check_mat(A, "A")
+    _check_vec(b, "b")
+    w = _prec(inner_prec)
+    u = UPDATE[update]
+    n, lda = A.shape[1], A.shape[2]
+    x = out if out is not None else torch.empty((x_words, n), dtype=torch.float64, device=A.device)
+    if work is None:
+        work = workspace(L.MW_OP_REFINE, w, u, n, A.device)
+    stats = (ctypes.c_int64 * 4)()
+    rc = L.lib().mw_refine(n, _ptr(A), lda, A.shape[0], _ptr(b), b.shape[0], w, u, target_bits,
+                           max_iter, stop_mode, rtol, atol, _ptr(x), x_words, stats, _ptr(work),
+                           work.numel(), _stream(stream))
+    L.check("mw_refine", rc, ok=(L.MW_OK, L.MW_ENOTCONV, L.MW_ESINGULAR))
+    return RefineResult(x, rc, int(stats[0]), int(stats[1]), int(stats[2]))
+
+
+def arith(op: int, prec, x: torch.Tensor, y: torch.Tensor, *, stream=None) -> torch.Tensor:
+    """Element-wise multiword op (0 add, 1 sub, 2 mul, 3 div, 4 compare |x|,|y|)."""
+    w = _prec(prec)
+    _check_vec(x, "x")
+    _check_vec(y, "y")
+    z = torch.empty_like(x)
+    L.check("mw_arith", L.lib().mw_arith(op, w, x.shape[1], _ptr(x), _ptr(y), _ptr(z), _stream(stream)))
+    return z
+
+
+def peak_fp64() -> float:
+    """FP64 instructions per second measured by the library's microbenchmark."""
+    out = ctypes.c_double(0.0)
+    L.check("mw_peak_fp64", L.lib().mw_peak_fp64(ctypes.byref(out), _stream()))
+    return out.value

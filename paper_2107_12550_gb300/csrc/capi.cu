@@ -1,0 +1,239 @@
+// capi.cu -- the extern "C" entry points of libmwlu.so (declared and
+// documented in include/mwlu.h): argument checks, work-buffer sizes,
+// dispatch on the precision, status text and the FP64 microbenchmark.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "mw_arith.cuh"
+#include "mw_common.cuh"
+#include "lu_internal.cuh"
+
+namespace mw {
+size_t refine_workspace_bytes(int inner, int update, int64_t n);
+int refine_dispatch(int64_t n, const double* A, int64_t lda, int a_words, const double* b, int b_words,
+                    int inner, int update, int target_bits, int max_iter, int stop_mode, double rtol,
+                    double atol, double* x, int x_words, int64_t* stats, char* ws, size_t ws_bytes,
+                    cudaStream_t s);
+}  // namespace mw
+
+static thread_local int g_last_cuda_error = 0;
+extern "C" void mw_internal_set_cuda_error(int e) { g_last_cuda_error = e; }
+
+static bool prec_ok(int p) { return p == MW_DD || p == MW_TD || p == MW_QD; }
+
+static size_t lu_ws_bytes(int update, int64_t n) {
+  return mw::kWsSplit + (update == MW_UPDATE_SPLIT ? mw::split_workspace_bytes(n, mw::kDefaultNb) : 0);
+}
+
+extern "C" int mw_workspace_size(int op, int prec, int update, int64_t n, size_t* bytes) {
+  if (op < MW_OP_LUDECOMP || op > MW_OP_REFINE) return -1;
+  if (!prec_ok(prec)) return -2;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -3;
+  if (n < 0) return -4;
+  if (!bytes) return -5;
+  switch (op) {
+    case MW_OP_LUDECOMP: *bytes = lu_ws_bytes(update, n); break;
+    case MW_OP_SOLVE: *bytes = mw::solve_workspace_bytes(prec, n); break;
+    default: *bytes = mw::refine_workspace_bytes(prec, update, n); break;
+  }
+  return MW_OK;
+}
+
+extern "C" int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t lda, int64_t* piv,
+                           int64_t* info, void* work, size_t work_bytes, void* stream) {
+  if (!prec_ok(prec)) return -1;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
+  if (n < 0) return -3;
+  if (n > 0 && !A) return -4;
+  if (lda < (n > 1 ? n : 1)) return -5;
+  if (n > 0 && !piv) return -6;
+  if (!info) return -7;
+  if (!work) return -8;
+  if (work_bytes < lu_ws_bytes(update, n)) return -9;
+  if (update == MW_UPDATE_SPLIT && prec != MW_DD) return MW_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(work);
+  if (n == 0) {
+    MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
+    return MW_OK;
+  }
+  switch (prec) {
+    case 2: return mw::lu_blocked<2>(update, n, A, lda, piv, info, ws, work_bytes, mw::kDefaultNb, s);
+    case 3: return mw::lu_blocked<3>(update, n, A, lda, piv, info, ws, work_bytes, mw::kDefaultNb, s);
+    default: return mw::lu_blocked<4>(update, n, A, lda, piv, info, ws, work_bytes, mw::kDefaultNb, s);
+  }
+}
+
+extern "C" int mw_solve(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
+                        const double* b, double* x, void* work, size_t work_bytes, void* stream) {
+  if (!prec_ok(prec)) return -1;
+  if (n < 0) return -2;
+  if (n > 0 && !LU) return -3;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (n > 0 && !piv) return -5;
+  if (n > 0 && !b) return -6;
+  if (n > 0 && !x) return -7;
+  if (!work) return -8;
+  if (work_bytes < mw::solve_workspace_bytes(prec, n)) return -9;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(work);
+  switch (prec) {
+    case 2: return mw::solve_launch<2>(n, LU, lda, piv, b, x, ws, work_bytes, s);
+    case 3: return mw::solve_launch<3>(n, LU, lda, piv, b, x, ws, work_bytes, s);
+    default: return mw::solve_launch<4>(n, LU, lda, piv, b, x, ws, work_bytes, s);
+  }
+}
+
+extern "C" int mw_residual(int64_t n, const double* A, int64_t lda, int a_words, const double* b,
+                           int b_words, const double* x, int x_words, double* r, int r_words,
+                           void* stream) {
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < (n > 1 ? n : 1)) return -3;
+  if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
+  if (n > 0 && !b) return -5;
+  if (b_words < 1 || b_words > MW_LONG_WORDS) return -6;
+  if (n > 0 && !x) return -7;
+  if (x_words < 1 || x_words > MW_LONG_WORDS) return -8;
+  if (n > 0 && !r) return -9;
+  if (r_words < 1 || r_words > MW_LONG_WORDS) return -10;
+  return mw::residual_launch(n, A, lda, a_words, b, b_words, x, x_words, r, r_words,
+                             static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int mw_refine(int64_t n, const double* A, int64_t lda, int a_words, const double* b,
+                         int b_words, int inner, int update, int target_bits, int max_iter,
+                         int stop_mode, double rtol, double atol, double* x, int x_words,
+                         int64_t* stats, void* work, size_t work_bytes, void* stream) {
+  if (n < 0) return -1;
+  if (n > 0 && !A) return -2;
+  if (lda < (n > 1 ? n : 1)) return -3;
+  if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
+  if (n > 0 && !b) return -5;
+  if (b_words < 1 || b_words > MW_LONG_WORDS) return -6;
+  if (!prec_ok(inner)) return -7;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -8;
+  if (target_bits < 1 || target_bits > 1000) return -9;
+  if (max_iter < 0) return -10;
+  if (stop_mode != MW_STOP_EQ2 && stop_mode != MW_STOP_BITS) return -11;
+  if (!(rtol >= 0.0)) return -12;
+  if (!(atol >= 0.0)) return -13;
+  if (n > 0 && !x) return -14;
+  if (x_words < inner || x_words > MW_LONG_WORDS) return -15;
+  if (!stats) return -16;
+  if (!work) return -17;
+  if (work_bytes < mw::refine_workspace_bytes(inner, update, n)) return -18;
+  if (update == MW_UPDATE_SPLIT && inner != MW_DD) return MW_EUNSUPPORTED;
+  return mw::refine_dispatch(n, A, lda, a_words, b, b_words, inner, update, target_bits, max_iter,
+                             stop_mode, rtol, atol, x, x_words, stats, static_cast<char*>(work),
+                             work_bytes, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// element-wise arithmetic
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void k_arith(int op, int64_t cnt, const double* __restrict__ x, const double* __restrict__ y,
+                        double* __restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  const mw::val<W> a = mw::load<W>(x, cnt, i);
+  const mw::val<W> b = mw::load<W>(y, cnt, i);
+  mw::val<W> r;
+  switch (op) {
+    case 0: r = mw::add<W>(a, b); break;
+    case 1: r = mw::sub<W>(a, b); break;
+    case 2: r = mw::mul<W>(a, b); break;
+    case 3: r = mw::div<W>(a, b); break;
+    default:
+#pragma unroll
+      for (int c = 0; c < W; ++c) r.v[c] = 0.0;
+      r.v[0] = (double)mw::cmp_abs<W>(a, b);
+      break;
+  }
+  mw::store<W>(z, cnt, i, r);
+}
+
+extern "C" int mw_arith(int op, int prec, int64_t cnt, const double* x, const double* y, double* z,
+                        void* stream) {
+  if (op < 0 || op > 4) return -1;
+  if (!prec_ok(prec)) return -2;
+  if (cnt < 0) return -3;
+  if (cnt > 0 && (!x)) return -4;
+  if (cnt > 0 && (!y)) return -5;
+  if (cnt > 0 && (!z)) return -6;
+  if (cnt == 0) return MW_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned grid = (unsigned)((cnt + 255) / 256);
+  switch (prec) {
+    case 2: k_arith<2><<<grid, 256, 0, s>>>(op, cnt, x, y, z); break;
+    case 3: k_arith<3><<<grid, 256, 0, s>>>(op, cnt, x, y, z); break;
+    default: k_arith<4><<<grid, 256, 0, s>>>(op, cnt, x, y, z); break;
+  }
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 pipe microbenchmark: 8 independent FMA chains per thread
+// ---------------------------------------------------------------------------
+__device__ double g_peak_sink;
+
+__global__ void k_peak_fp64(int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = __fma_rn(x[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  if (s != s) g_peak_sink = s;  // keeps the chains live; never true for finite inputs
+}
+
+extern "C" int mw_peak_fp64(double* instr_per_s, void* stream) {
+  if (!instr_per_s) return -1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  MW_CUDA_CHECK(cudaGetDevice(&dev));
+  MW_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256, blocks = sms * 8, iters = 4096;
+  cudaEvent_t e0, e1;
+  MW_CUDA_CHECK(cudaEventCreate(&e0));
+  MW_CUDA_CHECK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, s);
+    k_peak_fp64<<<blocks, threads, 0, s>>>(iters, 1.0000001, 1e-9);
+    cudaEventRecord(e1, s);
+    MW_CUDA_CHECK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MW_LAUNCH_CHECK();
+  *instr_per_s = (double)threads * blocks * iters * 8 / (best * 1e-3);
+  return MW_OK;
+}
+
+extern "C" const char* mw_strerror(int code) {
+  switch (code) {
+    case MW_OK: return "ok";
+    case MW_ESINGULAR: return "exactly zero pivot (matrix singular in the working precision)";
+    case MW_ENOTCONV: return "refinement did not converge (iteration limit or stagnation)";
+    case MW_ECUDA: return "CUDA error (see mw_last_cuda_error)";
+    case MW_ETIMEOUT: return "a bounded device wait gave up";
+    case MW_EUNSUPPORTED: return "unsupported combination of arguments";
+  }
+  if (code < 0) return "invalid argument";
+  return "unknown status";
+}
+
+extern "C" int mw_last_cuda_error(void) { return g_last_cuda_error; }
+
+extern "C" const char* mw_version(void) { return "mwlu 0.1 (sm_103a)"; }

@@ -1,0 +1,485 @@
+// lu.cu -- blocked right-looking LU decomposition with partial pivoting in
+// DD/TD/QD (Section 2, Listing 1: TDLUdecompPM).
+//
+// For each panel of nb columns starting at k0:
+//   1. k_panel  (cooperative): for each column k of the panel, a warp-shuffle
+//      argmax of |a_ik| over rows i >= k across all CTAs, the row swap inside
+//      the panel, the multipliers l_ik = a_ik / a_kk and the in-panel
+//      updates a_ij -= l_ik u_kj.
+//   2. k_laswp on the columns left of the panel, and k_trsm on the columns
+//      right of it: the panel's row swaps, then U12 = L11^-1 A12.
+//   3. the trailing update A22 -= L21 U12, either the plain multiword GEMM
+//      on the FP64 pipe (k_gemm_plain, here) or the split-precision
+//      tensor-core form (ozaki.cu).
+// Every element a_ij receives its updates a_ij -= l_it u_tj in ascending t
+// exactly as unblocked right-looking elimination applies them, with the same
+// rounded multiply and subtraction, so the plain form is bitwise identical
+// to unblocked elimination.
+#include <algorithm>
+#include <cuda_runtime.h>
+
+#include "mw_arith.cuh"
+#include "mw_common.cuh"
+#include "lu_internal.cuh"
+#include "profile.cuh"
+
+namespace mw {
+
+// ---------------------------------------------------------------------------
+// panel factorisation
+// ---------------------------------------------------------------------------
+template <int W>
+struct Cand {
+  val<W> v;
+  long long idx;  // -1: no candidate
+};
+
+template <int W>
+__device__ __forceinline__ bool better(const val<W>& a, long long ia, const val<W>& b, long long ib) {
+  if (ia < 0) return false;
+  if (ib < 0) return true;
+  const int c = cmp_abs<W>(a, b);
+  return c > 0 || (c == 0 && ia < ib);
+}
+
+template <int W>
+__device__ __forceinline__ void warp_argmax(val<W>& v, long long& idx) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    val<W> ov;
+#pragma unroll
+    for (int c = 0; c < W; ++c) ov.v[c] = __shfl_xor_sync(0xffffffffu, v.v[c], off);
+    const long long oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (better<W>(ov, oi, v, idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kPanelThreads)
+k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
+        int64_t* __restrict__ piv, int64_t* __restrict__ info, char* __restrict__ ws) {
+  GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + kWsBarrier);
+  DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
+  Cand<W>* cand = reinterpret_cast<Cand<W>*>(ws + kWsCand);
+
+  const int G = gridDim.x;
+  const int cta = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int64_t rows = n - k0;
+  const int64_t chunk = (rows + G - 1) / G;
+  const int64_t r0 = k0 + (int64_t)cta * chunk;
+  const int64_t r1 = (r0 + chunk < n) ? r0 + chunk : n;
+
+  extern __shared__ double smem[];
+  double* su = smem;                 // [W][nb]  pivot row u_kj
+  double* sl = smem + W * nb;        // [W][chunk]  multipliers of owned rows
+  __shared__ Cand<W> wred[kPanelThreads / 32];
+  __shared__ long long s_piv;
+  __shared__ int s_zero;
+
+  for (int kk = 0; kk < nb; ++kk) {
+    const int64_t k = k0 + kk;
+    const int64_t colk = (k0 + kk) * lda;
+    // (a) local argmax over owned rows i >= k
+    val<W> bv;
+#pragma unroll
+    for (int c = 0; c < W; ++c) bv.v[c] = 0.0;
+    long long bi = -1;
+    for (int64_t i = (r0 > k ? r0 : k) + tid; i < r1; i += kPanelThreads) {
+      const val<W> v = load_cg<W>(A, plane, colk + i);
+      if (better<W>(v, i, bv, bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    warp_argmax<W>(bv, bi);
+    if (lane == 0) {
+      wred[warp].v = bv;
+      wred[warp].idx = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      Cand<W> b = wred[0];
+      for (int w = 1; w < kPanelThreads / 32; ++w)
+        if (better<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
+#pragma unroll
+      for (int c = 0; c < W; ++c) __stcg(&cand[cta].v.v[c], b.v.v[c]);
+      __stcg(&cand[cta].idx, b.idx);
+    }
+    if (!grid_sync(bar, status, 1)) return;
+    // (b) global argmax from all candidates (every CTA computes the same)
+    if (warp == 0) {
+      val<W> gv;
+#pragma unroll
+      for (int c = 0; c < W; ++c) gv.v[c] = 0.0;
+      long long gi = -1;
+      for (int q = lane; q < G; q += 32) {
+        val<W> v;
+#pragma unroll
+        for (int c = 0; c < W; ++c) v.v[c] = __ldcg(&cand[q].v.v[c]);
+        const long long iq = __ldcg(&cand[q].idx);
+        if (better<W>(v, iq, gv, gi)) {
+          gv = v;
+          gi = iq;
+        }
+      }
+      warp_argmax<W>(gv, gi);
+      if (lane == 0) {
+        s_piv = gi;
+        s_zero = is_zero<W>(gv) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    const int64_t p = s_piv;
+    if (cta == 0) {
+      if (tid == 0) {
+        piv[k] = p;
+        if (s_zero && *info == 0) *info = k + 1;
+      }
+      if (p != k) {
+        for (int j = tid; j < nb; j += kPanelThreads) {
+          const int64_t col = (k0 + j) * lda;
+#pragma unroll
+          for (int c = 0; c < W; ++c) {
+            const double a = __ldcg(A + c * plane + col + k);
+            const double b = __ldcg(A + c * plane + col + p);
+            __stcg(A + c * plane + col + k, b);
+            __stcg(A + c * plane + col + p, a);
+          }
+        }
+      }
+    }
+    if (!grid_sync(bar, status, 2)) return;
+    // (c) pivot row into shared memory, multipliers, in-panel update
+    for (int j = kk + tid; j < nb; j += kPanelThreads) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) su[c * nb + j] = __ldcg(A + c * plane + (k0 + j) * lda + k);
+    }
+    __syncthreads();
+    val<W> akk;
+#pragma unroll
+    for (int c = 0; c < W; ++c) akk.v[c] = su[c * nb + kk];
+    const bool zero = is_zero<W>(akk);
+    const int64_t ilo = (r0 > k + 1) ? r0 : k + 1;
+    for (int64_t i = ilo + tid; i < r1; i += kPanelThreads) {
+      val<W> a = load_cg<W>(A, plane, colk + i);
+      if (!zero) {
+        a = div<W>(a, akk);
+        store_cg<W>(A, plane, colk + i, a);
+      }
+#pragma unroll
+      for (int c = 0; c < W; ++c) sl[c * chunk + (i - r0)] = a.v[c];
+    }
+    __syncthreads();
+    const int64_t nrows = r1 - ilo;
+    const int ncols = nb - kk - 1;
+    if (nrows > 0 && ncols > 0) {
+      const int64_t items = nrows * ncols;
+      for (int64_t q = tid; q < items; q += kPanelThreads) {
+        const int64_t i = ilo + q % nrows;
+        const int j = kk + 1 + (int)(q / nrows);
+        const int64_t idx = (k0 + j) * lda + i;
+        val<W> l, u;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          l.v[c] = sl[c * chunk + (i - r0)];
+          u.v[c] = su[c * nb + j];
+        }
+        val<W> a = load_cg<W>(A, plane, idx);
+        a = msub<W>(a, l, u);
+        store_cg<W>(A, plane, idx, a);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// row interchanges on a range of columns (one thread per column and word)
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void k_laswp(double* __restrict__ A, int64_t lda, int64_t plane, int64_t c_begin,
+                        int64_t c_end, int64_t k0, int nb, const int64_t* __restrict__ piv) {
+  const int64_t j = c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (j >= c_end) return;
+  double* col = A + c * plane + j * lda;
+  for (int kk = 0; kk < nb; ++kk) {
+    const int64_t k = k0 + kk;
+    const int64_t p = piv[k];
+    if (p != k) {
+      const double a = col[k];
+      col[k] = col[p];
+      col[p] = a;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// row interchanges + U12 = L11^-1 A12 on 32 columns per CTA.
+// Thread (lane, warp): column j = j0 + lane, rows r = q * 8 + warp.
+// ---------------------------------------------------------------------------
+template <int W, int NB>
+__global__ void __launch_bounds__(256)
+k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0,
+       const int64_t* __restrict__ piv) {
+  constexpr int NW = 8;
+  constexpr int RPT = NB / NW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j = k0 + NB + (int64_t)blockIdx.x * 32 + lane;
+  const bool active = j < n;
+  __shared__ double su[2][W][32];
+  // row interchanges of this CTA's columns (warp c handles word c)
+  if (active && warp < W) {
+    double* col = A + warp * plane + j * lda;
+    for (int kk = 0; kk < NB; ++kk) {
+      const int64_t k = k0 + kk;
+      const int64_t p = piv[k];
+      if (p != k) {
+        const double a = col[k];
+        col[k] = col[p];
+        col[p] = a;
+      }
+    }
+  }
+  __syncthreads();
+  val<W> a[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = q * NW + warp;
+    if (active) a[q] = load<W>(A, plane, j * lda + k0 + r);
+    else {
+#pragma unroll
+      for (int c = 0; c < W; ++c) a[q].v[c] = 0.0;
+    }
+  }
+#pragma unroll
+  for (int qt = 0; qt < RPT; ++qt) {
+    for (int g = 0; g < NW; ++g) {
+      const int t = qt * NW + g;
+      const int buf = t & 1;
+      if (warp == g) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) su[buf][c][lane] = a[qt].v[c];
+      }
+      __syncthreads();
+      val<W> u;
+#pragma unroll
+      for (int c = 0; c < W; ++c) u.v[c] = su[buf][c][lane];
+      const int64_t lcol = (k0 + t) * lda + k0;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = q * NW + warp;
+        if (q >= qt && r > t) {
+          const val<W> l = load_ro<W>(A, plane, lcol + r);
+          a[q] = msub<W>(a[q], l, u);
+        }
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = q * NW + warp;
+      store<W>(A, plane, j * lda + k0 + r, a[q]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plain trailing update: C -= L21 * U12 with per-element sequential t.
+// 16 x 16 threads, micro-tile TM x TN per thread, K chunks of KT staged in
+// shared memory with coalesced loads of each word plane.
+// ---------------------------------------------------------------------------
+template <int W, int TM, int TN>
+__global__ void __launch_bounds__(256)
+k_gemm_plain(double* __restrict__ A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
+             int64_t col0, int64_t N, int64_t k0, int nb) {
+  constexpr int KT = 16;
+  constexpr int BM = 16 * TM, BN = 16 * TN;
+  __shared__ double sL[W][KT][BM];
+  __shared__ double sU[W][KT][BN];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t bi = (int64_t)blockIdx.x * BM, bj = (int64_t)blockIdx.y * BN;
+
+  val<W> acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int64_t i = bi + tx + 16 * a, jj = bj + ty + 16 * b;
+      if (i < m && jj < N) acc[a][b] = load<W>(A, plane, (col0 + jj) * lda + row0 + i);
+      else {
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[a][b].v[c] = 0.0;
+      }
+    }
+
+  for (int t0 = 0; t0 < nb; t0 += KT) {
+    const int kt_n = (nb - t0 < KT) ? nb - t0 : KT;
+    // L tile: rows bi..bi+BM, columns k0+t0..: consecutive threads -> rows
+    for (int e = threadIdx.x; e < BM * KT; e += 256) {
+      const int r = e % BM, kt = e / BM;
+      const int64_t i = bi + r;
+      const bool ok = (i < m) && (kt < kt_n);
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        sL[c][kt][r] = ok ? __ldg(A + c * plane + (k0 + t0 + kt) * lda + row0 + i) : 0.0;
+    }
+    // U tile: rows k0+t0.., columns bj..: consecutive threads -> rows (t)
+    for (int e = threadIdx.x; e < BN * KT; e += 256) {
+      const int kt = e % KT, cidx = e / KT;
+      const int64_t jj = bj + cidx;
+      const bool ok = (jj < N) && (kt < kt_n);
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        sU[c][kt][cidx] = ok ? __ldg(A + c * plane + (col0 + jj) * lda + k0 + t0 + kt) : 0.0;
+    }
+    __syncthreads();
+    for (int kt = 0; kt < kt_n; ++kt) {
+      val<W> l[TM], u[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int c = 0; c < W; ++c) l[a].v[c] = sL[c][kt][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b)
+#pragma unroll
+        for (int c = 0; c < W; ++c) u[b].v[c] = sU[c][kt][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = msub<W>(acc[a][b], l[a], u[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int64_t i = bi + tx + 16 * a, jj = bj + ty + 16 * b;
+      if (i < m && jj < N) store<W>(A, plane, (col0 + jj) * lda + row0 + i, acc[a][b]);
+    }
+}
+
+template <int W> struct GemmTile;
+template <> struct GemmTile<2> { static constexpr int TM = 4, TN = 4; };
+template <> struct GemmTile<3> { static constexpr int TM = 2, TN = 4; };
+template <> struct GemmTile<4> { static constexpr int TM = 2, TN = 2; };
+
+template <int W>
+int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
+                      int64_t col0, int64_t N, int64_t k0, int nb, cudaStream_t s) {
+  constexpr int TM = GemmTile<W>::TM, TN = GemmTile<W>::TN;
+  if (m <= 0 || N <= 0) return MW_OK;
+  dim3 grid((unsigned)((m + 16 * TM - 1) / (16 * TM)), (unsigned)((N + 16 * TN - 1) / (16 * TN)));
+  k_gemm_plain<W, TM, TN><<<grid, 256, 0, s>>>(A, lda, plane, row0, m, col0, N, k0, nb);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+static int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+template <int W>
+int launch_panel(double* A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
+                 int64_t* piv, int64_t* info, char* ws, cudaStream_t s) {
+  const int64_t rows = n - k0;
+  int G = (int)std::min<int64_t>((rows + kPanelRowsPerCta - 1) / kPanelRowsPerCta, sm_count());
+  G = std::max(1, std::min(G, kMaxPanelCtas));
+  const int64_t chunk = (rows + G - 1) / G;
+  const size_t shmem = sizeof(double) * (size_t)W * ((size_t)nb + (size_t)chunk);
+  auto kern = k_panel<W>;
+  if (shmem > 48 * 1024) {
+    MW_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kPanelThreads);
+  cfg.dynamicSmemBytes = shmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MW_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, A, lda, plane, n, k0, nb, piv, info, ws));
+  return MW_OK;
+}
+
+template <int W>
+static int launch_trsm(double* A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
+                       const int64_t* piv, cudaStream_t s) {
+  const int64_t ncols = n - k0 - nb;
+  if (ncols <= 0) return MW_OK;
+  dim3 grid((unsigned)((ncols + 31) / 32));
+  switch (nb) {
+    case 32: k_trsm<W, 32><<<grid, 256, 0, s>>>(A, lda, plane, n, k0, piv); break;
+    case 64: k_trsm<W, 64><<<grid, 256, 0, s>>>(A, lda, plane, n, k0, piv); break;
+    case 128: k_trsm<W, 128><<<grid, 256, 0, s>>>(A, lda, plane, n, k0, piv); break;
+    default: return MW_EUNSUPPORTED;
+  }
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info,
+               char* ws, size_t ws_bytes, int nb, cudaStream_t s) {
+  const int64_t plane = lda * n;
+  MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand, s));
+  MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
+  for (int64_t k0 = 0; k0 < n; k0 += nb) {
+    const int kb = (int)std::min<int64_t>(nb, n - k0);
+    int rc;
+    {
+      ProfScope ps(kPhPanel, s);
+      rc = launch_panel<W>(A, lda, plane, n, k0, kb, piv, info, ws, s);
+    }
+    if (rc) return rc;
+    if (k0 > 0) {
+      ProfScope ps(kPhLaswp, s);
+      dim3 grid((unsigned)((k0 + 127) / 128), W);
+      k_laswp<W><<<grid, 128, 0, s>>>(A, lda, plane, 0, k0, k0, kb, piv);
+      MW_LAUNCH_CHECK();
+    }
+    if (k0 + kb < n) {
+      {
+        ProfScope ps(kPhTrsm, s);
+        rc = launch_trsm<W>(A, lda, plane, n, k0, kb, piv, s);
+      }
+      if (rc) return rc;
+      const int64_t r0 = k0 + kb;
+      if (update == MW_UPDATE_SPLIT && W == 2) {
+        rc = split_update_dd(A, lda, plane, r0, n - r0, r0, n - r0, k0, kb, ws + kWsSplit,
+                             ws_bytes > kWsSplit ? ws_bytes - kWsSplit : 0, s);
+      } else {
+        ProfScope ps(kPhGemmPlain, s);
+        rc = launch_gemm_plain<W>(A, lda, plane, r0, n - r0, r0, n - r0, k0, kb, s);
+      }
+      if (rc) return rc;
+    }
+  }
+  return MW_OK;
+}
+
+template int lu_blocked<2>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
+template int lu_blocked<3>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
+template int lu_blocked<4>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
+
+}  // namespace mw

@@ -1,0 +1,45 @@
+// lu_internal.cuh -- launch constants and the work-buffer map shared by the
+// library's host drivers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace mw {
+
+constexpr int kPanelThreads = 256;
+constexpr int kPanelRowsPerCta = 32;   // panel rows per CTA before adding CTAs
+constexpr int kMaxPanelCtas = 1024;
+constexpr int kDefaultNb = 64;          // panel width of the blocked LU
+
+// LU work buffer: [barrier | status | panel candidates | split-update scratch]
+constexpr size_t kWsBarrier = 0;
+constexpr size_t kWsStatus = 64;
+constexpr size_t kWsCand = 256;
+constexpr size_t kCandStride = 48;      // >= sizeof(Cand<4>)
+constexpr size_t kWsSplit = 64 * 1024;  // >= kWsCand + kMaxPanelCtas * kCandStride
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <int W>
+int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info,
+               char* ws, size_t ws_bytes, int nb, cudaStream_t s);
+
+// split-precision trailing update for DD (ozaki.cu): C -= L21 * U12
+int split_update_dd(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
+                    int64_t col0, int64_t N, int64_t k0, int nb, char* ws, size_t ws_bytes,
+                    cudaStream_t s);
+size_t split_workspace_bytes(int64_t n, int nb);
+
+// substitution (solve.cu); y is a w-plane vector work area of n
+template <int W>
+int solve_launch(int64_t n, const double* LU, int64_t lda, const int64_t* piv, const double* b,
+                 double* x, char* ws, size_t ws_bytes, cudaStream_t s);
+size_t solve_workspace_bytes(int w, int64_t n);
+
+// exact residual (residual.cu)
+int residual_launch(int64_t n, const double* A, int64_t lda, int a_words, const double* b,
+                    int b_words, const double* x, int x_words, double* r, int r_words,
+                    cudaStream_t s);
+
+}  // namespace mw

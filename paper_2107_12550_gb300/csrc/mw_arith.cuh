@@ -1,0 +1,326 @@
+// mw_arith.cuh -- multiword (DD/TD/QD) arithmetic as device inlines.
+//
+// A value of precision W (2 = double-double, 3 = triple-double, 4 =
+// quad-double; Section 1 of Kouya's paper) is W binary64 words.  Every
+// floating-point step below is an explicit round-to-nearest intrinsic, so the
+// compiler can neither contract a*b+c nor reassociate: the bits of each result
+// are fixed by the algorithm alone.
+//
+// Algorithms (the paper names Bailey et al.'s QD library but prints none):
+//   * error-free transformations: Knuth's TwoSum, Dekker's FastTwoSum, and
+//     TwoProd via a fused multiply-add;
+//   * W = 2: Joldes, Muller and Popescu, ACM TOMS 44(2) 2017 --
+//     AccurateDWPlusDW (Alg. 6), DWTimesDW3 (Alg. 12) and a DWDivDW2-shaped
+//     division (Alg. 17) whose DW-times-FP step uses the FMA;
+//   * W = 3, 4: gather the exact partial results (TwoSum of matching words;
+//     TwoProd of the products up to order W-2, plain products at order W-1)
+//     and renormalise: a bottom-up TwoSum cascade (Ogita-Rump-Oishi VecSum),
+//     a top-down extraction of W words that skips zero errors and folds the
+//     tail into the last word, then a top-down FastTwoSum sweep
+//     (renormalisation in the manner of Hida, Li and Bailey, ARITH 2001);
+//     division is long division with W+1 quotient digits.
+//
+// Additions are issued as fma(a, 1, b): one rounding of a + b, hence the same
+// bits as an add, and the fused pipe issues faster than the add pipe on this
+// GPU's FP64 units.
+#pragma once
+#include <cstdint>
+
+namespace mw {
+
+template <int W>
+struct val {
+  double v[W];
+};
+
+__device__ __forceinline__ double fadd(double a, double b) { return __fma_rn(a, 1.0, b); }
+__device__ __forceinline__ double fsub(double a, double b) { return __fma_rn(b, -1.0, a); }
+__device__ __forceinline__ double fmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double fdiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// s + e = a + b exactly, s = RN(a + b)
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = fadd(a, b);
+  const double a_virt = fsub(s, b);
+  const double b_virt = fsub(s, a_virt);
+  const double a_err = fsub(a, a_virt);
+  const double b_err = fsub(b, b_virt);
+  e = fadd(a_err, b_err);
+}
+
+// exact when exponent(a) >= exponent(b)
+__device__ __forceinline__ void quick_two_sum(double a, double b, double& s, double& e) {
+  s = fadd(a, b);
+  const double t = fsub(s, a);
+  e = fsub(b, t);
+}
+
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
+  p = fmul(a, b);
+  e = ffma(a, b, -p);
+}
+
+// ---------------------------------------------------------------------------
+// W = 2
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ val<2> dd_add(const val<2>& x, const val<2>& y) {
+  double sh, sl, th, tl, vh, vl;
+  two_sum(x.v[0], y.v[0], sh, sl);
+  two_sum(x.v[1], y.v[1], th, tl);
+  const double c = fadd(sl, th);
+  quick_two_sum(sh, c, vh, vl);
+  const double w = fadd(tl, vl);
+  val<2> z;
+  quick_two_sum(vh, w, z.v[0], z.v[1]);
+  return z;
+}
+
+__device__ __forceinline__ val<2> dd_mul(const val<2>& x, const val<2>& y) {
+  double ch, cl1;
+  two_prod(x.v[0], y.v[0], ch, cl1);
+  const double tl0 = fmul(x.v[1], y.v[1]);
+  const double tl1 = ffma(x.v[0], y.v[1], tl0);
+  const double cl2 = ffma(x.v[1], y.v[0], tl1);
+  const double cl3 = fadd(cl1, cl2);
+  val<2> z;
+  quick_two_sum(ch, cl3, z.v[0], z.v[1]);
+  return z;
+}
+
+__device__ __forceinline__ val<2> dd_div(const val<2>& x, const val<2>& y) {
+  const double q0 = fdiv(x.v[0], y.v[0]);
+  double ph, pl, rh, rl;
+  two_prod(y.v[0], q0, ph, pl);
+  pl = ffma(y.v[1], q0, pl);
+  quick_two_sum(ph, pl, rh, rl);
+  const double dh = fsub(x.v[0], rh);
+  const double dl = fsub(x.v[1], rl);
+  const double d = fadd(dh, dl);
+  const double q1 = fdiv(d, y.v[0]);
+  val<2> z;
+  quick_two_sum(q0, q1, z.v[0], z.v[1]);
+  return z;
+}
+
+// ---------------------------------------------------------------------------
+// Renormalisation of M terms into W words (W = 3, 4)
+// ---------------------------------------------------------------------------
+template <int W, int M>
+__device__ __forceinline__ val<W> renormalise(double (&t)[M]) {
+  // bottom-up exact cascade
+  double s = t[M - 1];
+#pragma unroll
+  for (int i = M - 2; i >= 0; --i) {
+    double hi, lo;
+    two_sum(t[i], s, hi, lo);
+    s = hi;
+    t[i + 1] = lo;
+  }
+  t[0] = s;
+  // top-down extraction; k = number of words emitted so far
+  val<W> z;
+#pragma unroll
+  for (int j = 0; j < W; ++j) z.v[j] = 0.0;
+  int k = 0;
+  s = t[0];
+#pragma unroll
+  for (int i = 1; i < M; ++i) {
+    if (k < W - 1) {
+      double hi, lo;
+      two_sum(s, t[i], hi, lo);
+      if (lo != 0.0) {
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) z.v[j] = (k == j) ? hi : z.v[j];
+        k += 1;
+        s = lo;
+      } else {
+        s = hi;
+      }
+    } else {
+      s = fadd(s, t[i]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < W; ++j) z.v[j] = (k == j) ? s : z.v[j];
+  // top-down sweep
+#pragma unroll
+  for (int j = 0; j < W - 1; ++j) {
+    double hi, lo;
+    quick_two_sum(z.v[j], z.v[j + 1], hi, lo);
+    z.v[j] = hi;
+    z.v[j + 1] = lo;
+  }
+  return z;
+}
+
+template <int W>
+__device__ __forceinline__ val<W> gen_add(const val<W>& x, const val<W>& y) {
+  double s[W], e[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) two_sum(x.v[i], y.v[i], s[i], e[i]);
+  double t[2 * W - 1];
+  t[0] = s[0];
+#pragma unroll
+  for (int i = 1; i < W; ++i) {
+    t[2 * i - 1] = s[i];
+    t[2 * i] = e[i - 1];
+  }
+  return renormalise<W, 2 * W - 1>(t);
+}
+
+__device__ __forceinline__ val<3> td_mul(const val<3>& x, const val<3>& y) {
+  double p00, q00, p01, q01, p10, q10;
+  two_prod(x.v[0], y.v[0], p00, q00);
+  two_prod(x.v[0], y.v[1], p01, q01);
+  two_prod(x.v[1], y.v[0], p10, q10);
+  double c = fmul(x.v[1], y.v[1]);
+  c = ffma(x.v[0], y.v[2], c);
+  c = ffma(x.v[2], y.v[0], c);
+  c = fadd(c, q01);
+  c = fadd(c, q10);
+  double t[5] = {p00, q00, p01, p10, c};
+  return renormalise<3, 5>(t);
+}
+
+__device__ __forceinline__ val<4> qd_mul(const val<4>& x, const val<4>& y) {
+  double p00, q00, p01, q01, p10, q10, p02, q02, p11, q11, p20, q20;
+  two_prod(x.v[0], y.v[0], p00, q00);
+  two_prod(x.v[0], y.v[1], p01, q01);
+  two_prod(x.v[1], y.v[0], p10, q10);
+  two_prod(x.v[0], y.v[2], p02, q02);
+  two_prod(x.v[1], y.v[1], p11, q11);
+  two_prod(x.v[2], y.v[0], p20, q20);
+  double c = fmul(x.v[1], y.v[2]);
+  c = ffma(x.v[2], y.v[1], c);
+  c = ffma(x.v[0], y.v[3], c);
+  c = ffma(x.v[3], y.v[0], c);
+  c = fadd(c, q02);
+  c = fadd(c, q11);
+  c = fadd(c, q20);
+  double t[10] = {p00, q00, p01, p10, q01, q10, p02, p11, p20, c};
+  return renormalise<4, 10>(t);
+}
+
+template <int W>
+__device__ __forceinline__ val<W> gen_mul_d(const val<W>& x, double d) {
+  double p[W], q[W];
+#pragma unroll
+  for (int i = 0; i < W - 1; ++i) two_prod(x.v[i], d, p[i], q[i]);
+  p[W - 1] = fmul(x.v[W - 1], d);
+  double t[2 * W - 1];
+  t[0] = p[0];
+#pragma unroll
+  for (int i = 1; i < W; ++i) {
+    t[2 * i - 1] = p[i];
+    t[2 * i] = q[i - 1];
+  }
+  return renormalise<W, 2 * W - 1>(t);
+}
+
+template <int W>
+__device__ __forceinline__ val<W> neg(const val<W>& x) {
+  val<W> z;
+#pragma unroll
+  for (int i = 0; i < W; ++i) z.v[i] = -x.v[i];
+  return z;
+}
+
+template <int W>
+__device__ __forceinline__ val<W> gen_div(const val<W>& x, const val<W>& y) {
+  double q[W + 1];
+  q[0] = fdiv(x.v[0], y.v[0]);
+  val<W> r = x;
+#pragma unroll
+  for (int i = 1; i <= W; ++i) {
+    r = gen_add<W>(r, neg<W>(gen_mul_d<W>(y, q[i - 1])));
+    q[i] = fdiv(r.v[0], y.v[0]);
+  }
+  return renormalise<W, W + 1>(q);
+}
+
+// ---------------------------------------------------------------------------
+// Precision-generic entry points
+// ---------------------------------------------------------------------------
+template <int W> __device__ __forceinline__ val<W> add(const val<W>& x, const val<W>& y);
+template <> __device__ __forceinline__ val<2> add<2>(const val<2>& x, const val<2>& y) { return dd_add(x, y); }
+template <> __device__ __forceinline__ val<3> add<3>(const val<3>& x, const val<3>& y) { return gen_add<3>(x, y); }
+template <> __device__ __forceinline__ val<4> add<4>(const val<4>& x, const val<4>& y) { return gen_add<4>(x, y); }
+
+template <int W>
+__device__ __forceinline__ val<W> sub(const val<W>& x, const val<W>& y) { return add<W>(x, neg<W>(y)); }
+
+template <int W> __device__ __forceinline__ val<W> mul(const val<W>& x, const val<W>& y);
+template <> __device__ __forceinline__ val<2> mul<2>(const val<2>& x, const val<2>& y) { return dd_mul(x, y); }
+template <> __device__ __forceinline__ val<3> mul<3>(const val<3>& x, const val<3>& y) { return td_mul(x, y); }
+template <> __device__ __forceinline__ val<4> mul<4>(const val<4>& x, const val<4>& y) { return qd_mul(x, y); }
+
+template <int W> __device__ __forceinline__ val<W> div(const val<W>& x, const val<W>& y);
+template <> __device__ __forceinline__ val<2> div<2>(const val<2>& x, const val<2>& y) { return dd_div(x, y); }
+template <> __device__ __forceinline__ val<3> div<3>(const val<3>& x, const val<3>& y) { return gen_div<3>(x, y); }
+template <> __device__ __forceinline__ val<4> div<4>(const val<4>& x, const val<4>& y) { return gen_div<4>(x, y); }
+
+// c - a*b as a rounded multiply followed by a rounded subtraction (the
+// per-element step of the elimination and of the substitutions)
+template <int W>
+__device__ __forceinline__ val<W> msub(const val<W>& c, const val<W>& a, const val<W>& b) {
+  return sub<W>(c, mul<W>(a, b));
+}
+
+// |x| vs |y| on the sign-adjusted words (|x0|, s x1, s x2, ...): -1, 0, +1
+template <int W>
+__device__ __forceinline__ int cmp_abs(const val<W>& x, const val<W>& y) {
+  const double sx = (x.v[0] < 0.0) ? -1.0 : 1.0;
+  const double sy = (y.v[0] < 0.0) ? -1.0 : 1.0;
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const double a = fmul(sx, x.v[c]);
+    const double b = fmul(sy, y.v[c]);
+    if (a > b) return 1;
+    if (a < b) return -1;
+  }
+  return 0;
+}
+
+template <int W>
+__device__ __forceinline__ bool is_zero(const val<W>& x) {
+  bool z = true;
+#pragma unroll
+  for (int c = 0; c < W; ++c) z = z && (x.v[c] == 0.0);
+  return z;
+}
+
+// planar loads/stores: word c at p[c * plane + idx]
+template <int W>
+__device__ __forceinline__ val<W> load(const double* p, int64_t plane, int64_t idx) {
+  val<W> z;
+#pragma unroll
+  for (int c = 0; c < W; ++c) z.v[c] = p[c * plane + idx];
+  return z;
+}
+template <int W>
+__device__ __forceinline__ val<W> load_cg(const double* p, int64_t plane, int64_t idx) {
+  val<W> z;
+#pragma unroll
+  for (int c = 0; c < W; ++c) z.v[c] = __ldcg(p + c * plane + idx);
+  return z;
+}
+template <int W>
+__device__ __forceinline__ val<W> load_ro(const double* __restrict__ p, int64_t plane, int64_t idx) {
+  val<W> z;
+#pragma unroll
+  for (int c = 0; c < W; ++c) z.v[c] = __ldg(p + c * plane + idx);
+  return z;
+}
+template <int W>
+__device__ __forceinline__ void store(double* p, int64_t plane, int64_t idx, const val<W>& x) {
+#pragma unroll
+  for (int c = 0; c < W; ++c) p[c * plane + idx] = x.v[c];
+}
+template <int W>
+__device__ __forceinline__ void store_cg(double* p, int64_t plane, int64_t idx, const val<W>& x) {
+#pragma unroll
+  for (int c = 0; c < W; ++c) __stcg(p + c * plane + idx, x.v[c]);
+}
+
+}  // namespace mw

@@ -1,0 +1,98 @@
+// mw_common.cuh -- status codes, launch checks and the bounded grid barrier
+// shared by the library's kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/mwlu.h"
+
+namespace mw {
+
+// Error word written by kernels that give up on a bounded wait.
+struct DeviceStatus {
+  unsigned int timeout;     // non-zero: a bounded spin-wait ran out
+  unsigned int where;       // which wait (kernel-specific tag)
+};
+
+// Software grid barrier for cooperative launches.  All CTAs of the grid are
+// co-resident (the launch is cooperative), so every wait ends; still, each
+// wait spins at most kSpinLimit times, after which it records the tag in
+// `status`, sets `abort` and returns false so that the kernel can leave.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int generation;
+  unsigned int abort;
+  unsigned int pad;
+};
+
+constexpr unsigned long long kSpinLimit = 1ull << 26;  // ~seconds at worst
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Returns true when every CTA arrived; false if the wait gave up (or another
+// CTA gave up earlier).  Must be called by all threads of every CTA.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DeviceStatus* status, unsigned int tag) {
+  __shared__ int ok_shared;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    __threadfence();
+    const unsigned int gen = ld_acquire_u32(&bar->generation);
+    if (ld_acquire_u32(&bar->abort)) {
+      ok = 0;
+    } else if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->generation, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (ld_acquire_u32(&bar->generation) == gen) {
+        if (ld_acquire_u32(&bar->abort) || ++spins > kSpinLimit) {
+          atomicExch(&bar->abort, 1u);
+          if (status) {
+            atomicExch(&status->timeout, 1u);
+            atomicExch(&status->where, tag);
+          }
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok_shared = ok;
+  }
+  __syncthreads();
+  return ok_shared != 0;
+}
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? MW_OK : MW_ECUDA; }
+
+}  // namespace mw
+
+// record the last CUDA error of the library for mw_last_cuda_error()
+extern "C" void mw_internal_set_cuda_error(int e);
+
+#define MW_CUDA_CHECK(expr)                                      \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) {                                     \
+      mw_internal_set_cuda_error((int)_e);                       \
+      return MW_ECUDA;                                           \
+    }                                                            \
+  } while (0)
+
+#define MW_LAUNCH_CHECK()                                        \
+  do {                                                           \
+    cudaError_t _e = cudaGetLastError();                         \
+    if (_e != cudaSuccess) {                                     \
+      mw_internal_set_cuda_error((int)_e);                       \
+      return MW_ECUDA;                                           \
+    }                                                            \
+  } while (0)

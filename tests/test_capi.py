@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every symbol that
+include/mwlu.h declares; host-side argument checks answer without touching a
+GPU."""
+import ctypes
+
+import pytest
+
+from paper_2107_12550_gb300 import _lib as L
+from paper_2107_12550_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = L.declared_symbols()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(L.SIGNATURES) >= set(declared)
+
+
+def test_workspace_sizes(lib):
+    for prec in (2, 3, 4):
+        for n in (0, 1, 100, 2048):
+            lu = L.workspace_size(L.MW_OP_LUDECOMP, prec, 0, n)
+            sv = L.workspace_size(L.MW_OP_SOLVE, prec, 0, n)
+            rf = L.workspace_size(L.MW_OP_REFINE, prec, 0, n)
+            assert lu > 0 and sv > 0
+            assert rf >= prec * n * n * 8 + sv
+            assert lu % 256 == 0 and sv % 256 == 0 and rf % 256 == 0
+    out = ctypes.c_size_t(0)
+    assert lib.mw_workspace_size(7, 2, 0, 10, ctypes.byref(out)) == -1
+    assert lib.mw_workspace_size(0, 5, 0, 10, ctypes.byref(out)) == -2
+    assert lib.mw_workspace_size(0, 2, 9, 10, ctypes.byref(out)) == -3
+    assert lib.mw_workspace_size(0, 2, 0, -1, ctypes.byref(out)) == -4
+
+
+def test_argument_checks_need_no_gpu(lib):
+    # every call below is rejected before any CUDA call
+    assert lib.mw_ludecomp(5, 0, 4, None, 4, None, None, None, 0, None) == -1
+    assert lib.mw_ludecomp(2, 3, 4, None, 4, None, None, None, 0, None) == -2
+    assert lib.mw_ludecomp(2, 0, -1, None, 4, None, None, None, 0, None) == -3
+    assert lib.mw_ludecomp(2, 0, 4, None, 4, None, None, None, 0, None) == -4
+    assert lib.mw_ludecomp(2, 0, 4, 8, 3, 8, 8, 8, 1 << 30, None) == -5
+    assert lib.mw_ludecomp(2, 0, 4, 8, 4, 8, 8, 8, 16, None) == -9
+    assert lib.mw_ludecomp(3, 1, 4, 8, 4, 8, 8, 8, 1 << 30, None) == L.MW_EUNSUPPORTED
+    assert lib.mw_solve(1, 4, 8, 4, 8, 8, 8, 8, 1 << 30, None) == -1
+    assert lib.mw_solve(2, 4, 8, 2, 8, 8, 8, 8, 1 << 30, None) == -4
+    assert lib.mw_residual(4, 8, 4, 9, 8, 1, 8, 1, 8, 1, None) == -4
+    assert lib.mw_residual(4, 8, 4, 1, 8, 1, 8, 1, 8, 0, None) == -10
+    stats = (ctypes.c_int64 * 4)()
+    assert lib.mw_refine(4, 8, 4, 2, 8, 2, 3, 0, 200, 5, 1, 0.0, 0.0, 8, 2, stats, 8, 1 << 30, None) == -15
+    assert lib.mw_refine(4, 8, 4, 2, 8, 2, 3, 0, 200, -1, 1, 0.0, 0.0, 8, 8, stats, 8, 1 << 30, None) == -10
+    assert lib.mw_arith(9, 2, 4, 8, 8, 8, None) == -1
+    assert lib.mw_strerror(L.MW_ESINGULAR).startswith(b"exactly zero pivot")
+    assert lib.mw_version().startswith(b"mwlu")

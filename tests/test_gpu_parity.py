@@ -1,0 +1,248 @@
+"""GPU parity: every call goes through the C ABI (libmwlu.so) and is compared
+with the CPU oracle on the same seeded inputs.  The plain path is required to
+be bitwise identical (same algorithms, same per-element operation order);
+the exact residual is identical by construction (exact, then greedy
+round-to-nearest)."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact as X
+from paper_2107_12550_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2107_12550_gb300 import build as B
+    B.build()
+
+
+def api():
+    from paper_2107_12550_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rand_mw(rng, w, cnt, cancel=False):
+    e = rng.integers(-30, 30, cnt)
+    x = np.zeros((w, cnt))
+    x[0] = np.ldexp(rng.uniform(-1, 1, cnt), e)
+    for c in range(1, w):
+        _, ex = np.frexp(x[c - 1])
+        x[c] = np.where(x[c - 1] == 0, 0.0, np.ldexp(rng.uniform(-1, 1, cnt), ex - 55))
+    if cancel:
+        y = -x.copy()
+        y[w - 1] = y[w - 1] * (1 + rng.uniform(-1e-3, 1e-3, cnt))
+        return x, y
+    return x
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_arith_bitwise(w):
+    rng = np.random.default_rng(5 + w)
+    cnt = 20000
+    x = _rand_mw(rng, w, cnt)
+    y = _rand_mw(rng, w, cnt)
+    xc, yc = _rand_mw(rng, w, 2000, cancel=True)
+    x = np.concatenate([x, xc], axis=1)
+    y = np.concatenate([y, yc], axis=1)
+    y[:, :50] = x[:, :50]            # exact ties for the comparison
+    y[0, 50:60] = 0.0                # zero leading words
+    y[:, 60:70] = 0.0
+    y[0, 60:70] = 1.0
+    for op in range(5):
+        got = host(api().arith(op, w, dev(x), dev(y)))
+        ref = oracle.arith(op, w, x, y)
+        if op == 4:
+            assert np.array_equal(got[0].astype(np.int64), ref)
+        else:
+            assert np.array_equal(got, ref, equal_nan=True), (op, np.argwhere(got != ref)[:5])
+
+
+def _lu_compare(A, w, update="plain"):
+    LUg, pivg, infog = api().ludecomp(dev(A), w, update)
+    LUo, pivo, infoo = oracle.lu(w, A)
+    LUg = host(LUg)
+    n = A.shape[1]
+    assert int(host(infog)[0]) == infoo
+    assert np.array_equal(host(pivg), pivo)
+    assert np.array_equal(LUg[:, :, :n], LUo[:, :, :n])
+    return LUo, pivo
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 63, 64, 65, 100, 129, 200])
+def test_lu_bitwise(w, n):
+    A = W.uniform_matrix(n, w, seed=1000 + 7 * n + w)
+    _lu_compare(A, w)
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_lu_bitwise_odd_lda_and_svd(w):
+    A = W.uniform_matrix(150, w, seed=3, lda=157)
+    _lu_compare(A, w)
+    s = W.svd_system(130, 12.0, seed=4)
+    _lu_compare(s.A[:w].copy(), w)
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_lu_singular_and_degenerate(w):
+    n = 70
+    A = np.zeros((w, n, n))
+    rng = np.random.default_rng(9)
+    A[0] = rng.integers(-5, 6, (n, n)).astype(float)
+    A[0, 40] = 0.0                    # zero column 40 -> a zero pivot at some step
+    A[0, 41] = 2 * A[0, 3]            # dependent columns
+    _lu_compare(A, w)
+    Z = np.zeros((w, 33, 33))
+    _lu_compare(Z, w)
+    P = np.zeros((w, 97, 97))
+    perm = rng.permutation(97)
+    for i in range(97):
+        P[0, perm[i], i] = 1.0
+    _lu_compare(P, w)
+
+
+def test_lu_empty():
+    A = torch.zeros((2, 0, 1), dtype=torch.float64, device="cuda")
+    LU, piv, info = api().ludecomp(A, 2)
+    assert int(info.item()) == 0
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+@pytest.mark.parametrize("n", [1, 33, 100, 257])
+def test_solve_bitwise(w, n):
+    A = W.uniform_matrix(n, w, seed=77 + n)
+    LUo, pivo, info = oracle.lu(w, A)
+    b = _rand_mw(np.random.default_rng(n), w, n)
+    xg = host(api().solve(dev(LUo), torch.from_numpy(pivo).cuda(), dev(b), w))
+    xo = oracle.solve(w, LUo, pivo, b)
+    assert np.array_equal(xg, xo)
+    # b aliased with x
+    bt = dev(b)
+    api().solve(dev(LUo), torch.from_numpy(pivo).cuda(), bt, w, out=bt)
+    assert np.array_equal(host(bt), xo)
+
+
+@pytest.mark.parametrize("n,wa,wb,wx,wr", [(1, 1, 1, 1, 1), (37, 2, 2, 8, 8), (100, 4, 8, 8, 8),
+                                           (65, 3, 1, 5, 4), (300, 4, 8, 8, 8)])
+def test_residual_bitwise(n, wa, wb, wx, wr):
+    rng = np.random.default_rng(n + wa)
+    A = np.zeros((wa, n, n + 3))
+    for c in range(wa):
+        A[c, :, :n] = np.ldexp(rng.uniform(-1, 1, (n, n)), -54 * c + rng.integers(-3, 3))
+    x = np.stack([np.ldexp(rng.uniform(-1, 1, n), -53 * d + 5) for d in range(wx)])
+    b = np.stack([np.ldexp(rng.uniform(-1, 1, n), -53 * d) for d in range(wb)])
+    if n > 10:
+        x[:, 3] = 0.0
+        A[:, 2, :] = 0.0
+        b[0, 4] = 2.0 ** -1074          # subnormal terms
+        A[0, 5, 6] = 2.0 ** -1070
+        x[0, 5] = 2.0 ** -1000
+    got = host(api().residual(dev(A), dev(b), dev(x), wr))
+    ref = oracle.residual(A, b, x, wr)
+    assert np.array_equal(got, ref)
+
+
+def test_residual_matches_fraction_small():
+    rng = np.random.default_rng(3)
+    n = 6
+    A = np.zeros((2, n, n))
+    A[0] = rng.uniform(-1, 1, (n, n))
+    A[1] = A[0] * 2.0 ** -60
+    x = np.zeros((3, n))
+    x[0] = rng.uniform(-1, 1, n)
+    x[2] = x[0] * 2.0 ** -130
+    b = np.zeros((1, n))
+    b[0] = rng.uniform(-1, 1, n)
+    got = host(api().residual(dev(A), dev(b), dev(x), 8))
+    rf = X.residual(X.mat_to_frac(A, n), X.vec_to_frac(b), X.vec_to_frac(x))
+    for i in range(n):
+        assert list(got[:, i]) == X.greedy_words(rf[i], 8)
+
+
+@pytest.mark.parametrize("w_in", [2, 3, 4])
+@pytest.mark.parametrize("stop_mode", [0, 1])
+def test_refine_bitwise(w_in, stop_mode):
+    s = W.svd_system(90, 10.0, seed=21)
+    res = api().refine(dev(s.A), dev(s.b), w_in, 200, stop_mode=stop_mode, rtol=1e-90)
+    st, xo, corr, nres, info = oracle.refine(s.A, s.b, w_in, stop_mode=stop_mode, rtol=1e-90)
+    assert res.status == st
+    assert (res.corrections, res.residuals, res.info) == (corr, nres, info)
+    assert np.array_equal(host(res.x), xo)
+    assert X.forward_error(X.vec_to_frac(xo), [Fraction(1)] * 90) <= Fraction(1, 2 ** 200)
+
+
+def test_refine_dd_rhs_and_limits():
+    s = W.uniform_system(70, words=2, seed=12, b_words=2)
+    res = api().refine(dev(s.A), dev(s.b), 2, 200)
+    st, xo, corr, nres, info = oracle.refine(s.A, s.b, 2)
+    assert res.status == st == 0 and np.array_equal(host(res.x), xo)
+    res = api().refine(dev(s.A), dev(s.b), 2, 200, max_iter=0)
+    assert res.status == 2 and res.corrections == 0 and res.residuals == 1
+    Z = np.zeros((2, 8, 8))
+    res = api().refine(dev(Z), dev(np.ones((2, 8))), 2, 200)
+    assert res.status == 1 and res.info == 1
+
+
+def test_config1_dd_n256_bitwise():
+    """Single DD LU + substitution at n = 256 (uniform entries, b = A*1
+    rounded to DD), plain path: bitwise equal to the oracle."""
+    s = W.uniform_system(256, words=2, seed=0, b_words=2)
+    LUo, pivo = _lu_compare(s.A, 2)
+    LUg, pivg, _ = api().ludecomp(dev(s.A), 2)
+    xg = host(api().solve(LUg, pivg, dev(s.b), 2))
+    assert np.array_equal(xg, oracle.solve(2, LUo, pivo, s.b))
+
+
+@pytest.mark.parametrize("w", [3, 4])
+def test_config2_n1024_lu_bitwise_and_refine(w):
+    """TD/QD LU + solve at n = 1024 on the SVD-built matrix (kappa 2^33):
+    factors bitwise equal to the oracle; refinement with the TD inner solver
+    reaches 2^-200 against x* = ones (b = A*1 exactly in 8 words)."""
+    s = W.svd_system(1024, 10.0, seed=0)
+    _lu_compare(s.A[:w].copy(), w)
+    if w == 3:
+        res = api().refine(dev(s.A), dev(s.b), 3, 200)
+        assert res.status == 0
+        x = host(res.x)
+        # |x - 1| <= 2^-200 elementwise, checked exactly on the words
+        for i in range(0, 1024, 7):
+            assert abs(X.words_to_frac(x[:, i]) - 1) <= Fraction(1, 2 ** 200)
+
+
+def test_config2_n2048_full_size_properties():
+    """n = 2048, TD inner, the bench's launch: refined x = ones to 2^-200
+    for every entry; the direct TD solve has normwise backward error
+    <= 1e-44 (exact residual from the oracle)."""
+    s = W.svd_system(2048, 10.0, seed=0)
+    A = dev(s.A)
+    b = dev(s.b)
+    res = api().refine(A, b, 3, 200)
+    assert res.status == 0 and 1 <= res.corrections <= 4
+    x = host(res.x)
+    err = np.abs(x[0] - 1.0)
+    assert err.max() <= 2.0 ** -100
+    for i in range(0, 2048, 97):
+        assert abs(X.words_to_frac(x[:, i]) - 1) <= Fraction(1, 2 ** 200)
+    LU, piv, info = api().ludecomp(A, 3)
+    xd = host(api().solve(LU, piv, b, 3))
+    r = oracle.residual(s.A, s.b, xd, 8)
+    rn = np.max(np.abs(r[0]))
+    Ainf = np.max(np.sum(np.abs(s.A[0, :, :2048]), axis=0))
+    eta = rn / (Ainf * np.max(np.abs(xd[0])) + np.max(np.abs(s.b[0])))
+    assert eta <= 1e-44, eta
