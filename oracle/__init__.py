@@ -56,13 +56,14 @@ def _bind(path: str) -> ctypes.CDLL:
     L.mwo_eft.argtypes = [I, I64, P, P, P, P]
     L.mwo_arith.argtypes = [I, I, I64, P, P, P]
     L.mwo_lu.argtypes = [I, I64, P, I64, P, P]
+    L.mwo_lu_steps.argtypes = [I, I64, P, I64, P, P, I64]
     L.mwo_solve.argtypes = [I, I64, P, I64, P, P, P]
     L.mwo_residual.argtypes = [I64, P, I64, I, P, I, P, I, P, I]
     L.mwo_exact_sum.argtypes = [I64, P, I, P]
     L.mwo_exact_dot.argtypes = [I64, P, P, I, P]
     L.mwo_refine.argtypes = [I64, P, I64, I, P, I, I, I, I, D, D, I, P, I, P]
     L.mwo_set_threads.argtypes = [I]
-    for f in ("mwo_eft", "mwo_arith", "mwo_lu", "mwo_solve", "mwo_residual",
+    for f in ("mwo_eft", "mwo_arith", "mwo_lu", "mwo_lu_steps", "mwo_solve", "mwo_residual",
               "mwo_exact_sum", "mwo_exact_dot", "mwo_refine", "mwo_set_threads"):
         getattr(L, f).restype = I
     return L
@@ -168,6 +169,20 @@ def lu(w: int, A):
     piv = np.zeros(max(n, 1), dtype=np.int64)
     info = np.zeros(1, dtype=np.int64)
     rc = lib().mwo_lu(w, n, _p(LU), lda, _p(piv), _p(info))
+    assert rc == 0, rc
+    return LU, piv[:n], int(info[0])
+
+
+def lu_steps(w: int, A, ksteps: int):
+    """The first ksteps elimination steps of ``lu`` (for timing samples)."""
+    A = _f64(A)
+    n, lda = A.shape[1], A.shape[2]
+    LU = np.zeros((w, n, lda))
+    k = min(w, A.shape[0])
+    LU[:k] = A[:k]
+    piv = np.zeros(max(n, 1), dtype=np.int64)
+    info = np.zeros(1, dtype=np.int64)
+    rc = lib().mwo_lu_steps(w, n, _p(LU), lda, _p(piv), _p(info), int(ksteps))
     assert rc == 0, rc
     return LU, piv[:n], int(info[0])
 

@@ -395,15 +395,19 @@ int mwo_arith(int op, int w, int64_t cnt, const double *x, const double *y, doub
 /* In place: A <- L\U, unit lower L implicit.  piv is 0-based.              */
 /* ------------------------------------------------------------------------ */
 
-int mwo_lu(int w, int64_t n, double *A, int64_t lda, int64_t *piv, int64_t *info)
+/* The first `ksteps` elimination steps only (ksteps >= n: the whole
+ * factorisation).  Used to time a bounded sample of a large factorisation. */
+int mwo_lu_steps(int w, int64_t n, double *A, int64_t lda, int64_t *piv, int64_t *info,
+                 int64_t ksteps)
 {
-    int64_t plane, k;
+    int64_t plane, k, kend;
     if (w < 2 || w > 4) return -1;
     if (n < 0) return -2;
     if (lda < (n > 1 ? n : 1)) return -4;
     plane = lda * n;
     *info = 0;
-    for (k = 0; k < n; ++k) {
+    kend = ksteps < n ? ksteps : n;
+    for (k = 0; k < kend; ++k) {
         double best[4], v[4], akk[4];
         int64_t p = k, i, j;
         ld_m(w, A, plane, k * lda + k, best);
@@ -455,6 +459,11 @@ int mwo_lu(int w, int64_t n, double *A, int64_t lda, int64_t *piv, int64_t *info
         }
     }
     return 0;
+}
+
+int mwo_lu(int w, int64_t n, double *A, int64_t lda, int64_t *piv, int64_t *info)
+{
+    return mwo_lu_steps(w, n, A, lda, piv, info, n);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,59 @@
+"""Run one library operation on a synthetic case, for profilers.
+
+    python -m paper_2107_12550_gb300.prof_case --op lu --prec 3 --n 4096
+
+Ops: lu (ludecomp), solve, residual, refine.  Uniform matrices for lu/solve/
+residual, the kappa = 1e10 SVD-built matrix for refine.  Exits non-zero if
+the library reports an error.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+import time
+
+
+def main(argv=None) -> int:
+    p = argparse.ArgumentParser()
+    p.add_argument("--op", default="lu", choices=["lu", "solve", "residual", "refine"])
+    p.add_argument("--prec", type=int, default=3)
+    p.add_argument("--n", type=int, default=2048)
+    p.add_argument("--update", default="plain", choices=["plain", "split"])
+    p.add_argument("--repeat", type=int, default=1)
+    a = p.parse_args(argv)
+    import numpy as np
+    import torch
+    from . import api, build, workloads as W
+    build.build()
+    if a.op == "refine":
+        s = W.svd_system(a.n, 10.0, seed=0)
+        A, b = s.A, s.b
+    else:
+        A = W.uniform_matrix(a.n, max(a.prec, 2), seed=0)
+        b = W.uniform_matrix(1, 1, seed=1)[:, 0, :1]
+        b = np.ones((a.prec, a.n))
+    Ad = torch.from_numpy(A).cuda()
+    bd = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    t0 = time.perf_counter()
+    for _ in range(a.repeat):
+        if a.op == "lu":
+            LU, piv, info = api.ludecomp(Ad, a.prec, a.update)
+        elif a.op == "solve":
+            LU, piv, info = api.ludecomp(Ad, a.prec)
+            api.solve(LU, piv, bd, a.prec)
+        elif a.op == "residual":
+            x = torch.ones((8, a.n), dtype=torch.float64, device="cuda")
+            api.residual(Ad, bd, x, 8)
+        else:
+            r = api.refine(Ad, bd, a.prec, 200, update=a.update)
+            if not r.converged:
+                print("refinement did not converge", file=sys.stderr)
+                return 1
+    torch.cuda.synchronize()
+    print(f"{a.op} prec={a.prec} n={a.n} update={a.update} x{a.repeat}: "
+          f"{(time.perf_counter() - t0) / a.repeat * 1e3:.1f} ms per call")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
