@@ -198,6 +198,34 @@ int mw_arith(int op, int prec, int64_t cnt, const double* x, const double* y, do
 int mw_profile_enable(int on);
 int mw_profile_read(double* ms, long long* launches, int nphase, int reset);
 
+/*
+ * mw_solve_noalloc -- the substitution of mw_solve for callers that cannot
+ * allocate device memory and so cannot pass a work buffer: code inside a
+ * framework whose memory pool owns the whole GPU and forbids outside
+ * allocations, plugins or hooks that are not allowed to allocate, and
+ * latency-critical loops that must stay away from the allocator.  The paper
+ * has no counterpart; this is an interface convenience of this library.
+ *   Arguments and results are those of mw_solve without work/work_bytes:
+ *   the caller still passes LU, lda, piv, b and x (device pointers).
+ *   Scratch: a fixed array of MW_NOALLOC_SCRATCH_BYTES in the library's own
+ *   device memory, held on every GPU that loads the library until exit.  n
+ *   is limited to the orders whose scratch fits (mw_workspace_size(
+ *   MW_OP_SOLVE, prec, 0, n) <= MW_NOALLOC_SCRATCH_BYTES: n <= 58240 for QD,
+ *   74880 for TD, 104832 for DD); larger n returns -2 before any GPU work.
+ *   Nothing is allocated or freed by this call.
+ *   Set-up: the first call on each device looks up the scratch address with
+ *   cudaGetSymbolAddress (with that device current) and caches it; make that
+ *   first call outside any stream capture.
+ *   Sharing: all calls on a device use the same scratch, which keeps the last
+ *   call's contents (the parts that must start at zero are cleared by each
+ *   call); calls that overlap on the GPU, e.g. on two streams at once, race
+ *   on it and must be serialised by the caller.
+ * Returns MW_OK, -i or MW_ECUDA, as mw_solve.
+ */
+#define MW_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
+                     const double* b, double* x, void* stream);
+
 /* mw_strerror -- static text for a status code. */
 const char* mw_strerror(int code);
 

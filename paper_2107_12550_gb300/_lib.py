@@ -33,6 +33,7 @@ SIGNATURES = {
     "mw_refine": (_I, [_I64, _P, _I64, _I, _P, _I, _I, _I, _I, _I, _I, _D, _D, _P, _I, _P, _P, _SZ, _P]),
     "mw_arith": (_I, [_I, _I, _I64, _P, _P, _P, _P]),
     "mw_peak_fp64": (_I, [ctypes.POINTER(_D), _P]),
+    "mw_solve_noalloc": (_I, [_I, _I64, _P, _I64, _P, _P, _P, _P]),
     "mw_profile_enable": (_I, [_I]),
     "mw_profile_read": (_I, [ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I, _I]),
     "mw_strerror": (ctypes.c_char_p, [_I]),
