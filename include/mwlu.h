@@ -67,6 +67,7 @@ extern "C" {
 #define MW_OP_LUDECOMP 0
 #define MW_OP_SOLVE 1
 #define MW_OP_REFINE 2
+#define MW_OP_GEMM 3 /* n = max(m, N) of mw_gemm_sub */
 
 /* stopping tests of mw_refine */
 #define MW_STOP_EQ2 0  /* Eq. (2): ||r||_2 <= sqrt(n) rtol ||A||_F ||x||_2 + atol */
@@ -171,6 +172,29 @@ int mw_refine(int64_t n, const double* A, int64_t lda, int a_words, const double
 int mw_peak_fp64(double* instr_per_s, void* stream);
 
 /*
+ * mw_gemm_sub -- C -= A * B in multiword arithmetic: the block matrix product
+ * of the paper's BNCmatmul (Section 2), in the form the blocked LU's
+ * trailing update uses.
+ *   prec    MW_DD, MW_TD or MW_QD (MW_DD only for MW_UPDATE_SPLIT).
+ *   update  MW_UPDATE_PLAIN: each entry applies c -= a_t * b_t for t = 0..K-1
+ *           in order with a rounded multiword multiply and subtraction (the
+ *           elimination's operation order).  MW_UPDATE_SPLIT: the Ozaki-style
+ *           bf16 tensor-core product, per 64-wide slab of K: the slab product is
+ *           formed exactly from 15 base-256 digits per operand (pairs of digit
+ *           order <= 16), rounded once to DD and subtracted; K must be a
+ *           multiple of 64.  Per entry and slab the product error is at most
+ *           2^-107 max_t|a_it| max_t|b_tj|.
+ *   C       device, prec planes (ldc, N): m x N, updated in place.
+ *   A       device, prec planes (lda, K): m x K.   B: prec planes (ldb, N): K x N.
+ *   work    device work buffer, mw_workspace_size(MW_OP_GEMM, prec, update,
+ *           max(m, N)) bytes.
+ * Returns MW_OK, -i, MW_ECUDA or MW_EUNSUPPORTED.
+ */
+int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K, double* C, int64_t ldc,
+                const double* A, int64_t lda, const double* B, int64_t ldb, void* work,
+                size_t work_bytes, void* stream);
+
+/*
  * mw_arith -- element-wise multiword arithmetic on device arrays (the
  * DD/TD/QD building blocks of Section 1, as used inside every kernel):
  *   op 0: z = x + y   1: z = x - y   2: z = x * y   3: z = x / y
@@ -210,8 +234,8 @@ int mw_profile_read(double* ms, long long* launches, int nphase, int reset);
  *   Scratch: a fixed array of MW_NOALLOC_SCRATCH_BYTES in the library's own
  *   device memory, held on every GPU that loads the library until exit.  n
  *   is limited to the orders whose scratch fits (mw_workspace_size(
- *   MW_OP_SOLVE, prec, 0, n) <= MW_NOALLOC_SCRATCH_BYTES: n <= 58240 for QD,
- *   74880 for TD, 104832 for DD); larger n returns -2 before any GPU work.
+ *   MW_OP_SOLVE, prec, 0, n) <= MW_NOALLOC_SCRATCH_BYTES: n <= 58040 for QD,
+ *   74549 for TD, 104192 for DD); larger n returns -2 before any GPU work.
  *   Nothing is allocated or freed by this call.
  *   Set-up: the first call on each device looks up the scratch address with
  *   cudaGetSymbolAddress (with that device current) and caches it; make that

@@ -16,7 +16,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "mwlu.h")
 MW_DD, MW_TD, MW_QD, MW_LONG_WORDS = 2, 3, 4, 8
 MW_UPDATE_PLAIN, MW_UPDATE_SPLIT = 0, 1
 MW_OK, MW_ESINGULAR, MW_ENOTCONV, MW_ECUDA, MW_ETIMEOUT, MW_EUNSUPPORTED = 0, 1, 2, 3, 4, 5
-MW_OP_LUDECOMP, MW_OP_SOLVE, MW_OP_REFINE = 0, 1, 2
+MW_OP_LUDECOMP, MW_OP_SOLVE, MW_OP_REFINE, MW_OP_GEMM = 0, 1, 2, 3
 MW_STOP_EQ2, MW_STOP_BITS = 0, 1
 
 _P = ctypes.c_void_p
@@ -32,6 +32,7 @@ SIGNATURES = {
     "mw_residual": (_I, [_I64, _P, _I64, _I, _P, _I, _P, _I, _P, _I, _P]),
     "mw_refine": (_I, [_I64, _P, _I64, _I, _P, _I, _I, _I, _I, _I, _I, _D, _D, _P, _I, _P, _P, _SZ, _P]),
     "mw_arith": (_I, [_I, _I, _I64, _P, _P, _P, _P]),
+    "mw_gemm_sub": (_I, [_I, _I, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ, _P]),
     "mw_peak_fp64": (_I, [ctypes.POINTER(_D), _P]),
     "mw_solve_noalloc": (_I, [_I, _I64, _P, _I64, _P, _P, _P, _P]),
     "mw_profile_enable": (_I, [_I]),

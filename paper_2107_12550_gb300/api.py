@@ -144,6 +144,25 @@ def refine(A: torch.Tensor, b: torch.Tensor, inner_prec="td", target_bits: int =
     return RefineResult(x, rc, int(stats[0]), int(stats[1]), int(stats[2]))
 
 
+def gemm_sub(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, prec=None, update="plain", *,
+             work: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """C -= A B in multiword arithmetic on the leading m rows (in place;
+    returns C).  C: (w, N, ldc), A: (w, K, lda), B: (w, N, ldb), component
+    planes, column-major."""
+    for t, nm in ((C, "C"), (A, "A"), (B, "B")):
+        _check_mat(t, nm)
+    w = _prec(prec) if prec is not None else C.shape[0]
+    u = UPDATE[update]
+    N, ldc = C.shape[1], C.shape[2]
+    K, lda = A.shape[1], A.shape[2]
+    ldb = B.shape[2]
+    if work is None:
+        work = workspace(L.MW_OP_GEMM, w, u, max(m, N), C.device)
+    L.check("mw_gemm_sub", L.lib().mw_gemm_sub(w, u, m, N, K, _ptr(C), ldc, _ptr(A), lda, _ptr(B), ldb,
+                                               _ptr(work), work.numel(), _stream(stream)))
+    return C
+
+
 def arith(op: int, prec, x: torch.Tensor, y: torch.Tensor, *, stream=None) -> torch.Tensor:
     """Element-wise multiword op (0 add, 1 sub, 2 mul, 3 div, 4 compare |x|,|y|)."""
     w = _prec(prec)

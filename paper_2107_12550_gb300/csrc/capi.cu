@@ -27,7 +27,7 @@ static size_t lu_ws_bytes(int update, int64_t n) {
 }
 
 extern "C" int mw_workspace_size(int op, int prec, int update, int64_t n, size_t* bytes) {
-  if (op < MW_OP_LUDECOMP || op > MW_OP_REFINE) return -1;
+  if (op < MW_OP_LUDECOMP || op > MW_OP_GEMM) return -1;
   if (!prec_ok(prec)) return -2;
   if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -3;
   if (n < 0) return -4;
@@ -35,7 +35,8 @@ extern "C" int mw_workspace_size(int op, int prec, int update, int64_t n, size_t
   switch (op) {
     case MW_OP_LUDECOMP: *bytes = lu_ws_bytes(update, n); break;
     case MW_OP_SOLVE: *bytes = mw::solve_workspace_bytes(prec, n); break;
-    default: *bytes = mw::refine_workspace_bytes(prec, update, n); break;
+    case MW_OP_REFINE: *bytes = mw::refine_workspace_bytes(prec, update, n); break;
+    default: *bytes = 256 + (update == MW_UPDATE_SPLIT ? mw::split_workspace_bytes(n, mw::kDefaultNb) : 0); break;
   }
   return MW_OK;
 }
@@ -128,6 +129,43 @@ extern "C" int mw_refine(int64_t n, const double* A, int64_t lda, int a_words, c
   return mw::refine_dispatch(n, A, lda, a_words, b, b_words, inner, update, target_bits, max_iter,
                              stop_mode, rtol, atol, x, x_words, stats, static_cast<char*>(work),
                              work_bytes, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K, double* C, int64_t ldc,
+                           const double* A, int64_t lda, const double* B, int64_t ldb, void* work,
+                           size_t work_bytes, void* stream) {
+  if (!prec_ok(prec)) return -1;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
+  if (m < 0) return -3;
+  if (N < 0) return -4;
+  if (K < 0) return -5;
+  if (m > 0 && N > 0 && !C) return -6;
+  if (ldc < (m > 1 ? m : 1)) return -7;
+  if (m > 0 && K > 0 && !A) return -8;
+  if (lda < (m > 1 ? m : 1)) return -9;
+  if (K > 0 && N > 0 && !B) return -10;
+  if (ldb < (K > 1 ? K : 1)) return -11;
+  const int64_t nmax = m > N ? m : N;
+  const size_t need = 256 + (update == MW_UPDATE_SPLIT ? mw::split_workspace_bytes(nmax, mw::kDefaultNb) : 0);
+  if (update == MW_UPDATE_SPLIT && !work) return -12;
+  if (update == MW_UPDATE_SPLIT && work_bytes < need) return -13;
+  if (update == MW_UPDATE_SPLIT && (prec != MW_DD || K % 64 != 0)) return MW_EUNSUPPORTED;
+  if (m == 0 || N == 0 || K == 0) return MW_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t pc = ldc * N, pa = lda * K, pb = ldb * N;
+  if (update == MW_UPDATE_PLAIN) {
+    switch (prec) {
+      case 2: return mw::launch_gemm_plain_ptr<2>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s);
+      case 3: return mw::launch_gemm_plain_ptr<3>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s);
+      default: return mw::launch_gemm_plain_ptr<4>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s);
+    }
+  }
+  for (int64_t k0 = 0; k0 < K; k0 += 64) {
+    const int rc = mw::split_gemm_sub_dd(m, N, C, ldc, pc, A + k0 * lda, lda, pa, B + k0, ldb, pb,
+                                         static_cast<char*>(work), work_bytes, s);
+    if (rc) return rc;
+  }
+  return MW_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -220,22 +220,24 @@ __global__ void k_laswp(double* __restrict__ A, int64_t lda, int64_t plane, int6
 }
 
 // ---------------------------------------------------------------------------
-// row interchanges + U12 = L11^-1 A12 on 32 columns per CTA.
-// Thread (lane, warp): column j = j0 + lane, rows r = q * 8 + warp.
+// row interchanges + U12 = L11^-1 A12 on 8 columns per CTA.
+// Thread (c, g): column j = j0 + c (c = tid % 8), rows r = q * 32 + g
+// (g = tid / 8).  Step t: the owner of row t publishes u_tj through shared
+// memory; every thread then updates its rows r > t.
 // ---------------------------------------------------------------------------
 template <int W, int NB>
 __global__ void __launch_bounds__(256)
 k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0,
        const int64_t* __restrict__ piv) {
-  constexpr int NW = 8;
-  constexpr int RPT = NB / NW;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t j = k0 + NB + (int64_t)blockIdx.x * 32 + lane;
+  constexpr int TC = 8;
+  constexpr int NG = 256 / TC;
+  constexpr int RPT = (NB + NG - 1) / NG;
+  const int c = threadIdx.x % TC, g = threadIdx.x / TC;
+  const int64_t j = k0 + NB + (int64_t)blockIdx.x * TC + c;
   const bool active = j < n;
-  __shared__ double su[2][W][32];
-  // row interchanges of this CTA's columns (warp c handles word c)
-  if (active && warp < W) {
-    double* col = A + warp * plane + j * lda;
+  __shared__ double su[2][W][TC];
+  if (active && g < W) {
+    double* col = A + g * plane + j * lda;
     for (int kk = 0; kk < NB; ++kk) {
       const int64_t k = k0 + kk;
       const int64_t p = piv[k];
@@ -250,31 +252,32 @@ k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0
   val<W> a[RPT];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
-    const int r = q * NW + warp;
-    if (active) a[q] = load<W>(A, plane, j * lda + k0 + r);
+    const int r = q * NG + g;
+    if (active && r < NB) a[q] = load<W>(A, plane, j * lda + k0 + r);
     else {
 #pragma unroll
-      for (int c = 0; c < W; ++c) a[q].v[c] = 0.0;
+      for (int cc = 0; cc < W; ++cc) a[q].v[cc] = 0.0;
     }
   }
 #pragma unroll
   for (int qt = 0; qt < RPT; ++qt) {
-    for (int g = 0; g < NW; ++g) {
-      const int t = qt * NW + g;
+    for (int gg = 0; gg < NG; ++gg) {
+      const int t = qt * NG + gg;
+      if (t >= NB) break;
       const int buf = t & 1;
-      if (warp == g) {
+      if (g == gg) {
 #pragma unroll
-        for (int c = 0; c < W; ++c) su[buf][c][lane] = a[qt].v[c];
+        for (int cc = 0; cc < W; ++cc) su[buf][cc][c] = a[qt].v[cc];
       }
       __syncthreads();
       val<W> u;
 #pragma unroll
-      for (int c = 0; c < W; ++c) u.v[c] = su[buf][c][lane];
+      for (int cc = 0; cc < W; ++cc) u.v[cc] = su[buf][cc][c];
       const int64_t lcol = (k0 + t) * lda + k0;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
-        const int r = q * NW + warp;
-        if (q >= qt && r > t) {
+        const int r = q * NG + g;
+        if (q >= qt && r > t && r < NB) {
           const val<W> l = load_ro<W>(A, plane, lcol + r);
           a[q] = msub<W>(a[q], l, u);
         }
@@ -284,8 +287,8 @@ k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0
   if (active) {
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-      const int r = q * NW + warp;
-      store<W>(A, plane, j * lda + k0 + r, a[q]);
+      const int r = q * NG + g;
+      if (r < NB) store<W>(A, plane, j * lda + k0 + r, a[q]);
     }
   }
 }
@@ -297,8 +300,9 @@ k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0
 // ---------------------------------------------------------------------------
 template <int W, int TM, int TN>
 __global__ void __launch_bounds__(256)
-k_gemm_plain(double* __restrict__ A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
-             int64_t col0, int64_t N, int64_t k0, int nb) {
+k_gemm_plain(double* __restrict__ C, int64_t ldc, int64_t planeC, const double* __restrict__ L,
+             int64_t ldl, int64_t planeL, const double* __restrict__ U, int64_t ldu, int64_t planeU,
+             int64_t m, int64_t N, int K) {
   constexpr int KT = 16;
   constexpr int BM = 16 * TM, BN = 16 * TN;
   __shared__ double sL[W][KT][BM];
@@ -312,32 +316,30 @@ k_gemm_plain(double* __restrict__ A, int64_t lda, int64_t plane, int64_t row0, i
 #pragma unroll
     for (int b = 0; b < TN; ++b) {
       const int64_t i = bi + tx + 16 * a, jj = bj + ty + 16 * b;
-      if (i < m && jj < N) acc[a][b] = load<W>(A, plane, (col0 + jj) * lda + row0 + i);
+      if (i < m && jj < N) acc[a][b] = load<W>(C, planeC, jj * ldc + i);
       else {
 #pragma unroll
         for (int c = 0; c < W; ++c) acc[a][b].v[c] = 0.0;
       }
     }
 
-  for (int t0 = 0; t0 < nb; t0 += KT) {
-    const int kt_n = (nb - t0 < KT) ? nb - t0 : KT;
-    // L tile: rows bi..bi+BM, columns k0+t0..: consecutive threads -> rows
+  for (int t0 = 0; t0 < K; t0 += KT) {
+    const int kt_n = (K - t0 < KT) ? K - t0 : KT;
+    // L tile: rows bi..bi+BM, columns t0..: consecutive threads -> rows
     for (int e = threadIdx.x; e < BM * KT; e += 256) {
       const int r = e % BM, kt = e / BM;
       const int64_t i = bi + r;
       const bool ok = (i < m) && (kt < kt_n);
 #pragma unroll
-      for (int c = 0; c < W; ++c)
-        sL[c][kt][r] = ok ? __ldg(A + c * plane + (k0 + t0 + kt) * lda + row0 + i) : 0.0;
+      for (int c = 0; c < W; ++c) sL[c][kt][r] = ok ? __ldg(L + c * planeL + (t0 + kt) * ldl + i) : 0.0;
     }
-    // U tile: rows k0+t0.., columns bj..: consecutive threads -> rows (t)
+    // U tile: rows t0.., columns bj..: consecutive threads -> rows (t)
     for (int e = threadIdx.x; e < BN * KT; e += 256) {
       const int kt = e % KT, cidx = e / KT;
       const int64_t jj = bj + cidx;
       const bool ok = (jj < N) && (kt < kt_n);
 #pragma unroll
-      for (int c = 0; c < W; ++c)
-        sU[c][kt][cidx] = ok ? __ldg(A + c * plane + (col0 + jj) * lda + k0 + t0 + kt) : 0.0;
+      for (int c = 0; c < W; ++c) sU[c][kt][cidx] = ok ? __ldg(U + c * planeU + jj * ldu + t0 + kt) : 0.0;
     }
     __syncthreads();
     for (int kt = 0; kt < kt_n; ++kt) {
@@ -362,7 +364,7 @@ k_gemm_plain(double* __restrict__ A, int64_t lda, int64_t plane, int64_t row0, i
 #pragma unroll
     for (int b = 0; b < TN; ++b) {
       const int64_t i = bi + tx + 16 * a, jj = bj + ty + 16 * b;
-      if (i < m && jj < N) store<W>(A, plane, (col0 + jj) * lda + row0 + i, acc[a][b]);
+      if (i < m && jj < N) store<W>(C, planeC, jj * ldc + i, acc[a][b]);
     }
 }
 
@@ -372,14 +374,25 @@ template <> struct GemmTile<3> { static constexpr int TM = 2, TN = 4; };
 template <> struct GemmTile<4> { static constexpr int TM = 2, TN = 2; };
 
 template <int W>
-int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
-                      int64_t col0, int64_t N, int64_t k0, int nb, cudaStream_t s) {
+int launch_gemm_plain_ptr(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
+                          const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
+                          int64_t planeU, cudaStream_t s) {
   constexpr int TM = GemmTile<W>::TM, TN = GemmTile<W>::TN;
-  if (m <= 0 || N <= 0) return MW_OK;
+  if (m <= 0 || N <= 0 || K <= 0) return MW_OK;
   dim3 grid((unsigned)((m + 16 * TM - 1) / (16 * TM)), (unsigned)((N + 16 * TN - 1) / (16 * TN)));
-  k_gemm_plain<W, TM, TN><<<grid, 256, 0, s>>>(A, lda, plane, row0, m, col0, N, k0, nb);
+  k_gemm_plain<W, TM, TN><<<grid, 256, 0, s>>>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K);
   MW_LAUNCH_CHECK();
   return MW_OK;
+}
+template int launch_gemm_plain_ptr<2>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t);
+template int launch_gemm_plain_ptr<3>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t);
+template int launch_gemm_plain_ptr<4>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t);
+
+template <int W>
+int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
+                      int64_t col0, int64_t N, int64_t k0, int nb, cudaStream_t s) {
+  return launch_gemm_plain_ptr<W>(m, N, nb, A + col0 * lda + row0, lda, plane, A + k0 * lda + row0, lda,
+                                  plane, A + col0 * lda + k0, lda, plane, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -427,7 +440,7 @@ static int launch_trsm(double* A, int64_t lda, int64_t plane, int64_t n, int64_t
                        const int64_t* piv, cudaStream_t s) {
   const int64_t ncols = n - k0 - nb;
   if (ncols <= 0) return MW_OK;
-  dim3 grid((unsigned)((ncols + 31) / 32));
+  dim3 grid((unsigned)((ncols + 7) / 8));
   switch (nb) {
     case 32: k_trsm<W, 32><<<grid, 256, 0, s>>>(A, lda, plane, n, k0, piv); break;
     case 64: k_trsm<W, 64><<<grid, 256, 0, s>>>(A, lda, plane, n, k0, piv); break;

@@ -8,7 +8,7 @@
 namespace mw {
 
 constexpr int kPanelThreads = 256;
-constexpr int kPanelRowsPerCta = 32;   // panel rows per CTA before adding CTAs
+constexpr int kPanelRowsPerCta = 8;    // panel rows per CTA before adding CTAs
 constexpr int kMaxPanelCtas = 1024;
 constexpr int kDefaultNb = 64;          // panel width of the blocked LU
 
@@ -30,6 +30,13 @@ int split_update_dd(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t
                     int64_t col0, int64_t N, int64_t k0, int nb, char* ws, size_t ws_bytes,
                     cudaStream_t s);
 size_t split_workspace_bytes(int64_t n, int nb);
+int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
+                      int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
+                      char* ws, size_t ws_bytes, cudaStream_t s);
+template <int W>
+int launch_gemm_plain_ptr(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
+                          const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
+                          int64_t planeU, cudaStream_t s);
 
 // substitution (solve.cu); y is a w-plane vector work area of n
 template <int W>

@@ -49,6 +49,11 @@ __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e
   e = fadd(a_err, b_err);
 }
 
+// x != 0 (either sign) tested on the bit pattern, off the FP64 pipe
+__device__ __forceinline__ bool nonzero(double x) {
+  return (((unsigned long long)__double_as_longlong(x)) << 1) != 0ull;
+}
+
 // exact when exponent(a) >= exponent(b)
 __device__ __forceinline__ void quick_two_sum(double a, double b, double& s, double& e) {
   s = fadd(a, b);
@@ -129,7 +134,7 @@ __device__ __forceinline__ val<W> renormalise(double (&t)[M]) {
     if (k < W - 1) {
       double hi, lo;
       two_sum(s, t[i], hi, lo);
-      if (lo != 0.0) {
+      if (nonzero(lo)) {
 #pragma unroll
         for (int j = 0; j < W - 1; ++j) z.v[j] = (k == j) ? hi : z.v[j];
         k += 1;

@@ -1,21 +1,562 @@
-// ozaki.cu -- split-precision (Ozaki-style) trailing update for DD.
+// ozaki.cu -- split-precision (Ozaki scheme I) trailing update for DD on the
+// Blackwell tensor cores: C -= L21 * U12 with C, L21, U12 double-double.
+//
+// The paper's trailing update is a DD block matrix product (Section 2,
+// BNCmatmul).  Here it is reshaped for bf16 tcgen05 MMAs with FP32
+// accumulation in tensor memory:
+//
+//  1. Scaling.  Row i of L21 is scaled by 2^-e_i and column j of U12 by 2^-f_j
+//     (powers of two, e = ilogb(row/column max) + 2), so every scaled entry
+//     lies in (-1/2, 1/2).
+//  2. Slicing.  A scaled entry x is rounded toward minus infinity on the grid
+//     2^-120 and written as 15 balanced base-256 digits,
+//     x ~ sum_{p=1..15} a_p 2^(-8p), a_p in [-128, 127].  Each digit is a bf16
+//     (exact: 8 significant bits).  Slices are stored per 128-row (L21) or
+//     32-column (U12) tile in the 128-byte-swizzled K-major layout the MMA
+//     reads, K = nb = 64.
+//  3. Products.  For every pair (p, q) with p + q <= 16 one 128 x 32 x 64 MMA
+//     accumulates A_p B_q^T into the FP32 accumulator of diagonal d = p + q
+//     (15 accumulators x 32 columns = 480 TMEM columns).  A diagonal gathers
+//     at most 8 pairs x 64 products of magnitude <= 2^14, so every partial
+//     sum is an integer below 2^23 and the FP32 accumulation is exact.
+//  4. Recombination.  Per output entry the 15 exact diagonal sums D_d are
+//     combined in a 192-bit integer R = sum_d D_d 2^(8(16-d)); R 2^(e_i+f_j-128)
+//     is the (truncated-digit) product L21 U12 exactly.  R is rounded greedily
+//     to a double-double and subtracted from C with the DD subtraction.
+//
+// Error per entry (stated per result in the tests): the dropped pairs
+// p + q > 16 and the digit truncation give
+// |dC_ij| <= 2^-111 * 2^(e_i + f_j) <= 2^-107 max_t|l_it| max_t|u_tj|,
+// below the rounding of one DD multiply-subtract step.
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "mw_arith.cuh"
 #include "mw_common.cuh"
 #include "lu_internal.cuh"
+#include "profile.cuh"
+#include "tc.cuh"
 
 namespace mw {
 
+// exact power-of-two scaling, at most one rounding (defined below)
+__device__ double scale2_exact(double x, int e);
+
+namespace {
+
+constexpr int kS = 15;                 // digits per operand
+constexpr int kDiag = 15;              // diagonals d = 2..16
+constexpr int kK = 64;                 // panel width (K of the update)
+constexpr int kTileM = 128;            // rows per MMA tile
+constexpr int kTileN = 32;             // columns per MMA tile
+constexpr int kASliceBytes = kTileM * kK * 2;   // 16 KB
+constexpr int kBSliceBytes = kTileN * kK * 2;   // 4 KB
+constexpr uint32_t kTmemCols = 512;
+
+// byte offset of element (row r, k) inside a K-major 128B-swizzled tile
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ int exp_of_max(double mx) {  // ilogb(mx) + 2, mx > 0
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(mx);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  int lg;
+  if (ex) lg = ex - 1023;
+  else lg = -1074 + (63 - __clzll((long long)(bits & ((1ull << 52) - 1))));
+  return lg + 2;
+}
+
+// floor(v * 2^sh) as a signed 128-bit integer (|result| < 2^126)
+__device__ __forceinline__ __int128 scaled_floor(double v, int sh) {
+  if (v == 0.0) return 0;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const bool neg = (bits >> 63) != 0;
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  int e;
+  if (ex) {
+    m |= (1ull << 52);
+    e = ex - 1075;
+  } else {
+    e = -1074;
+  }
+  const int s = e + sh;  // value = m * 2^s
+  __int128 r;
+  if (s >= 0) {
+    r = (__int128)m << s;  // m 2^s < 2^119 by the choice of the scale, so s < 119
+  } else if (s <= -64) {
+    r = 0;  // |value| < 1 on the grid: floor gives 0 or -1
+    if (neg) return -1;
+    return 0;
+  } else {
+    const int rs = -s;
+    const unsigned long long q = m >> rs;
+    const bool rem = (m & ((1ull << rs) - 1)) != 0;
+    r = (__int128)q;
+    if (neg) return -(r) - (rem ? 1 : 0);
+    return r;
+  }
+  return neg ? -r : r;
+}
+
+// 15 base-256 digits of X (|X| < 2^119), most significant first: the 14
+// low digits balanced in [-128, 127], the top digit the exact remainder,
+// within [-128, 128]
+__device__ __forceinline__ void digits15(__int128 X, int (&a)[kS]) {
+#pragma unroll
+  for (int p = kS - 1; p >= 1; --p) {
+    int d = (int)(X & 0xff);
+    if (d >= 128) d -= 256;
+    a[p] = d;
+    X = (X - d) >> 8;
+  }
+  a[0] = (int)X;
+}
+
+__device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
+  const __nv_bfloat16 h = __float2bfloat16_rn((float)d);  // exact for |d| <= 256
+  return *reinterpret_cast<const unsigned short*>(&h);
+}
+
+// ---------------------------------------------------------------------------
+// slicing: L21 rows -> A slices [tile][p][128 x 64], row exponents e_i
+// one thread per row; 8 consecutive k at a time -> one 16-byte store per slice
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_slice_rows(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t m,
+             unsigned char* __restrict__ aslices, int* __restrict__ ea) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // padded row index
+  const int64_t tile = r / kTileM;
+  const int rr = (int)(r % kTileM);
+  const bool ok = r < m;
+  double mx = 0.0;
+  if (ok) {
+    for (int k = 0; k < kK; ++k) mx = fmax(mx, fabs(L[k * ldl + r]));
+  }
+  const int e = (mx > 0.0) ? exp_of_max(mx) : 0;
+  ea[r] = e;
+  unsigned char* base = aslices + tile * (int64_t)kS * kASliceBytes;
+  for (int kc = 0; kc < kK / 8; ++kc) {
+    uint32_t packed[kS][4];
+#pragma unroll
+    for (int p = 0; p < kS; ++p)
+#pragma unroll
+      for (int h = 0; h < 4; ++h) packed[p][h] = 0u;
+#pragma unroll
+    for (int k8 = 0; k8 < 8; ++k8) {
+      const int k = kc * 8 + k8;
+      int a[kS];
+      if (ok && mx > 0.0) {
+        const int64_t idx = k * ldl + r;
+        const __int128 X = scaled_floor(L[idx], 120 - e) + scaled_floor(L[planeL + idx], 120 - e);
+        digits15(X, a);
+      } else {
+#pragma unroll
+        for (int p = 0; p < kS; ++p) a[p] = 0;
+      }
+#pragma unroll
+      for (int p = 0; p < kS; ++p)
+        packed[p][k8 >> 1] |= (uint32_t)bf16_bits_of_int(a[p]) << (16 * (k8 & 1));
+    }
+#pragma unroll
+    for (int p = 0; p < kS; ++p) {
+      uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
+      *reinterpret_cast<uint4*>(base + (int64_t)p * kASliceBytes + sw128_offset(rr, kc * 8)) = v;
+    }
+  }
+}
+
+// U12 columns -> B slices [tile][q][32 x 64] (column j is a K-major row), f_j
+__global__ void __launch_bounds__(128)
+k_slice_cols(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t N, int64_t npad,
+             unsigned char* __restrict__ bslices, int* __restrict__ fb) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // padded column index
+  if (j >= npad) return;
+  const int64_t tile = j / kTileN;
+  const int jj = (int)(j % kTileN);
+  const bool ok = j < N;
+  const double* col = U + (ok ? j : 0) * ldu;
+  double mx = 0.0;
+  if (ok) {
+    for (int k = 0; k < kK; ++k) mx = fmax(mx, fabs(col[k]));
+  }
+  const int f = (mx > 0.0) ? exp_of_max(mx) : 0;
+  fb[j] = f;
+  unsigned char* base = bslices + tile * (int64_t)kS * kBSliceBytes;
+  for (int kc = 0; kc < kK / 8; ++kc) {
+    uint32_t packed[kS][4];
+#pragma unroll
+    for (int p = 0; p < kS; ++p)
+#pragma unroll
+      for (int h = 0; h < 4; ++h) packed[p][h] = 0u;
+#pragma unroll
+    for (int k8 = 0; k8 < 8; ++k8) {
+      const int k = kc * 8 + k8;
+      int a[kS];
+      if (ok && mx > 0.0) {
+        const __int128 X = scaled_floor(col[k], 120 - f) + scaled_floor(col[planeU + k], 120 - f);
+        digits15(X, a);
+      } else {
+#pragma unroll
+        for (int p = 0; p < kS; ++p) a[p] = 0;
+      }
+#pragma unroll
+      for (int p = 0; p < kS; ++p)
+        packed[p][k8 >> 1] |= (uint32_t)bf16_bits_of_int(a[p]) << (16 * (k8 & 1));
+    }
+#pragma unroll
+    for (int p = 0; p < kS; ++p) {
+      uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
+      *reinterpret_cast<uint4*>(base + (int64_t)p * kBSliceBytes + sw128_offset(jj, kc * 8)) = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 192-bit two's-complement accumulator and greedy rounding to DD
+// ---------------------------------------------------------------------------
+struct I192 {
+  unsigned long long w0, w1, w2;
+};
+
+// R += D * 2^pos, |D| < 2^24, 0 <= pos <= 112
+__device__ __forceinline__ void i192_add_shifted(I192& R, int D, int pos) {
+  const __int128 v = (__int128)D << (pos & 63);          // |v| < 2^87
+  const unsigned __int128 uv = (unsigned __int128)v;
+  const unsigned long long vlo = (unsigned long long)uv;
+  const unsigned long long vhi = (unsigned long long)(uv >> 64);
+  const unsigned long long sext = (v < 0) ? ~0ull : 0ull;
+  if (pos < 64) {
+    const unsigned long long s0 = R.w0 + vlo;
+    const unsigned long long c0 = s0 < R.w0;
+    const unsigned long long t1 = R.w1 + vhi;
+    const unsigned long long c1a = t1 < R.w1;
+    const unsigned long long s1 = t1 + c0;
+    const unsigned long long c1b = s1 < t1;
+    R.w0 = s0;
+    R.w1 = s1;
+    R.w2 = R.w2 + sext + c1a + c1b;
+  } else {
+    const unsigned long long s1 = R.w1 + vlo;
+    const unsigned long long c1 = s1 < R.w1;
+    R.w1 = s1;
+    R.w2 = R.w2 + vhi + c1;
+  }
+}
+
+__device__ __forceinline__ int i192_bit(const I192& R, int b) {
+  const unsigned long long w = (b < 64) ? R.w0 : (b < 128 ? R.w1 : R.w2);
+  return (int)((w >> (b & 63)) & 1ull);
+}
+
+// bits [lo, lo+53) of a non-negative R (lo >= 0)
+__device__ __forceinline__ unsigned long long i192_bits53(const I192& R, int lo) {
+  unsigned __int128 x;
+  if (lo < 64) {
+    x = ((unsigned __int128)R.w1 << 64) | R.w0;
+    x >>= lo;
+    if (lo > 0) x |= (unsigned __int128)R.w2 << (128 - lo);
+  } else if (lo < 128) {
+    x = ((unsigned __int128)R.w2 << 64) | R.w1;
+    x >>= (lo - 64);
+  } else {
+    x = (unsigned __int128)(R.w2 >> (lo - 128));
+  }
+  return (unsigned long long)x & ((1ull << 53) - 1);
+}
+
+__device__ __forceinline__ bool i192_any_below(const I192& R, int b) {  // any bit < b set
+  if (b <= 0) return false;
+  if (b >= 128) return R.w0 || R.w1 || (b > 128 && (R.w2 & ((1ull << (b - 128)) - 1)));
+  if (b >= 64) return R.w0 || (b > 64 && (R.w1 & ((1ull << (b - 64)) - 1)));
+  return (R.w0 & ((1ull << b) - 1)) != 0;
+}
+
+__device__ __forceinline__ int i192_top(const I192& R) {  // index of highest set bit, -1 if 0
+  if (R.w2) return 128 + 63 - __clzll((long long)R.w2);
+  if (R.w1) return 64 + 63 - __clzll((long long)R.w1);
+  if (R.w0) return 63 - __clzll((long long)R.w0);
+  return -1;
+}
+
+__device__ __forceinline__ void i192_neg(I192& R) {
+  R.w0 = ~R.w0;
+  R.w1 = ~R.w1;
+  R.w2 = ~R.w2;
+  R.w0 += 1;
+  const unsigned long long c0 = (R.w0 == 0);
+  R.w1 += c0;
+  R.w2 += (c0 && R.w1 == 0);
+}
+
+// subtract q * 2^lo from a non-negative R (q <= 2^53, result may go negative)
+__device__ __forceinline__ void i192_sub_shifted(I192& R, unsigned long long q, int lo) {
+  unsigned __int128 v = (unsigned __int128)q << (lo & 63);
+  const unsigned long long vlo = (unsigned long long)v, vhi = (unsigned long long)(v >> 64);
+  if (lo < 64) {
+    const unsigned long long b0 = R.w0 < vlo;
+    R.w0 -= vlo;
+    const unsigned long long t = R.w1 - vhi;
+    const unsigned long long b1a = R.w1 < vhi;
+    const unsigned long long b1b = t < b0;
+    R.w1 = t - b0;
+    R.w2 -= (b1a + b1b);
+  } else if (lo < 128) {
+    const unsigned long long b1 = R.w1 < vlo;
+    R.w1 -= vlo;
+    R.w2 -= vhi + b1;
+  } else {
+    R.w2 -= vlo;
+  }
+}
+
+// q * 2^e as a double (q <= 2^53 integer, e within the normal range)
+__device__ __forceinline__ double make_double(unsigned long long q, int e) {
+  if (q == 0) return 0.0;
+  return scale2_exact(__ull2double_rn(q), e);
+}
+
+
+// RN of R (signed) -> double, R -= it; R * 2^scale is the value
+__device__ __forceinline__ double i192_take_rn(I192& R, int scale) {
+  const bool neg = (long long)R.w2 < 0;
+  if (neg) i192_neg(R);
+  const int top = i192_top(R);
+  double res = 0.0;
+  if (top >= 0) {
+    const int lo = (top >= 52) ? top - 52 : 0;
+    unsigned long long q = (top >= 52) ? i192_bits53(R, lo) : R.w0;
+    if (lo > 0 && i192_bit(R, lo - 1) && (i192_any_below(R, lo - 1) || (q & 1ull))) q += 1;
+    i192_sub_shifted(R, q, lo);
+    res = make_double(q, lo + scale);
+  }
+  if (neg) {
+    i192_neg(R);
+    res = -res;
+  }
+  return res;
+}
+
+// ---------------------------------------------------------------------------
+// the tensor-core kernel: one CTA per 128 x 32 output tile
+// warp 0: bulk-copy producer; warp 1: TMEM owner + MMA issuer;
+// warps 2..5: epilogue (TMEM lane quarter = warp % 4)
+// ---------------------------------------------------------------------------
+struct SplitSmem {
+  unsigned char b[kS][kBSliceBytes];       // all B slices of the tile (60 KB)
+  unsigned char a[2][kASliceBytes];        // double-buffered A slice (32 KB)
+  uint64_t full_b;
+  uint64_t full_a[2];
+  uint64_t empty_a[2];
+  uint64_t mma_done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+constexpr int kSplitThreads = 192;
+
+__global__ void __launch_bounds__(kSplitThreads, 1)
+k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int64_t N,
+             const unsigned char* __restrict__ aslices,
+             const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
+             const int* __restrict__ fb, DeviceStatus* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzle atoms
+  SplitSmem& sm = *reinterpret_cast<SplitSmem*>(
+      (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tm = blockIdx.x, tn = blockIdx.y;
+
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&sm.full_b, 1);
+    tc::mbar_init(&sm.full_a[0], 1);
+    tc::mbar_init(&sm.full_a[1], 1);
+    tc::mbar_init(&sm.empty_a[0], 1);
+    tc::mbar_init(&sm.empty_a[1], 1);
+    tc::mbar_init(&sm.mma_done, 1);
+    sm.abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(&sm.tmem_base, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+
+  int issued = 0;   // A slices whose copies the producer started
+  if (warp == 0) {
+    if (lane == 0) {
+      const unsigned char* bsrc = bslices + tn * (int64_t)kS * kBSliceBytes;
+      tc::mbar_arrive_expect_tx(&sm.full_b, kS * kBSliceBytes);
+      tc::bulk_g2s(&sm.b[0][0], bsrc, kS * kBSliceBytes, &sm.full_b);
+      const unsigned char* asrc = aslices + tm * (int64_t)kS * kASliceBytes;
+      for (int p = 0; p < kS; ++p) {
+        const int buf = p & 1;
+        if (p >= 2) {
+          if (!tc::mbar_wait(&sm.empty_a[buf], ((p >> 1) - 1) & 1)) {
+            atomicExch(&sm.abort, 1);
+            break;
+          }
+        }
+        tc::mbar_arrive_expect_tx(&sm.full_a[buf], kASliceBytes);
+        tc::bulk_g2s(&sm.a[buf][0], asrc + (int64_t)p * kASliceBytes, kASliceBytes, &sm.full_a[buf]);
+        issued = p + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
+      bool ok = tc::mbar_wait(&sm.full_b, 0);
+      for (int p = 0; p < kS && ok; ++p) {
+        const int buf = p & 1;
+        if (!tc::mbar_wait(&sm.full_a[buf], (p >> 1) & 1)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t a_addr = tc::smem_u32(&sm.a[buf][0]);
+        for (int q = 0; q + p + 2 <= 16; ++q) {   // p+1 + q+1 <= 16
+          const int d = (p + 1) + (q + 1);        // 2..16
+          const uint32_t dcol = tmem + (uint32_t)((d - 2) * kTileN);
+          const uint32_t b_addr = tc::smem_u32(&sm.b[q][0]);
+#pragma unroll
+          for (int kk = 0; kk < kK / 16; ++kk) {
+            const uint64_t adesc = tc::sdesc_sw128_kmajor(a_addr + kk * 32);
+            const uint64_t bdesc = tc::sdesc_sw128_kmajor(b_addr + kk * 32);
+            tc::mma_bf16(dcol, adesc, bdesc, idesc, (p > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&sm.empty_a[buf]);   // frees the A buffer when these MMAs finish
+      }
+      if (!ok) atomicExch(&sm.abort, 1);
+      tc::mma_commit(&sm.mma_done);
+    }
+  } else {
+    // epilogue: thread <-> row (TMEM lane) of the tile
+    const int quarter = warp & 3;
+    const int rr = quarter * 32 + lane;
+    const int64_t i = tm * kTileM + rr;
+    bool ok = tc::mbar_wait(&sm.mma_done, 0);
+    tc::tc_fence_after();
+    // one decision per warp: the TMEM loads below are warp-collective
+    ok = __all_sync(0xffffffffu, ok && (*(volatile int*)&sm.abort == 0));
+    if (!ok) {
+      if (threadIdx.x == 64) atomicExch(&status->timeout, 1u);
+    } else {
+      const int ei = (i < m) ? ea[i] : 0;
+      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+      for (int c4 = 0; c4 < kTileN; c4 += 4) {
+        uint32_t v[kDiag][4];
+#pragma unroll
+        for (int d = 0; d < kDiag; ++d) tc::tmem_ld_x4(lane_base + (uint32_t)(d * kTileN + c4), v[d]);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int64_t j = tn * kTileN + c4 + cc;
+          if (i >= m || j >= N) continue;
+          I192 R = {0ull, 0ull, 0ull};
+#pragma unroll
+          for (int d = 0; d < kDiag; ++d) {
+            const int D = __float2int_rn(__uint_as_float(v[d][cc]));
+            if (D) i192_add_shifted(R, D, 8 * (kDiag - 1 - d));   // diagonal d+2: weight 2^(8(16-(d+2)))
+          }
+          const int scale = ei + fb[j] - 128;
+          val<2> pr;
+          pr.v[0] = i192_take_rn(R, scale);
+          pr.v[1] = i192_take_rn(R, scale);
+          const int64_t idx = j * ldc + i;
+          val<2> cv = load<2>(C, planeC, idx);
+          cv = sub<2>(cv, pr);
+          store<2>(C, planeC, idx, cv);
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0 && lane == 0 && sm.abort) {
+    // after an aborted tile, let the copies this thread started land before
+    // the CTA's shared memory is released (bounded waits)
+    tc::mbar_wait(&sm.full_b, 0);
+    for (int p = (issued > 2 ? issued - 2 : 0); p < issued; ++p) tc::mbar_wait(&sm.full_a[p & 1], (p >> 1) & 1);
+  }
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace
+
+__device__ double scale2_exact(double x, int e) {
+  while (e > 1000) {
+    x = __dmul_rn(x, 0x1p+1000);
+    e -= 1000;
+  }
+  while (e < -1000) {
+    x = __dmul_rn(x, 0x1p-1000);
+    e += 1000;
+  }
+  return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
+}
+
+// workspace: [status 256 | A slices | B slices | ea | fb]
 size_t split_workspace_bytes(int64_t n, int nb) {
-  (void)n;
   (void)nb;
-  return 0;
+  const int64_t mt = (n + kTileM - 1) / kTileM, nt = (n + kTileN - 1) / kTileN;
+  return 256 + align256((size_t)mt * kS * kASliceBytes) + align256((size_t)nt * kS * kBSliceBytes) +
+         align256(sizeof(int) * (size_t)mt * kTileM) + align256(sizeof(int) * (size_t)nt * kTileN);
+}
+
+// C (m x N) -= L (m x 64) * U (64 x N), all DD component-planar column-major
+int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
+                      int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
+                      char* ws, size_t ws_bytes, cudaStream_t s) {
+  if (m <= 0 || N <= 0) return MW_OK;
+  const int64_t mt = (m + kTileM - 1) / kTileM, nt = (N + kTileN - 1) / kTileN;
+  size_t off = 256;
+  unsigned char* aslices = reinterpret_cast<unsigned char*>(ws + off);
+  off += align256((size_t)mt * kS * kASliceBytes);
+  unsigned char* bslices = reinterpret_cast<unsigned char*>(ws + off);
+  off += align256((size_t)nt * kS * kBSliceBytes);
+  int* ea = reinterpret_cast<int*>(ws + off);
+  off += align256(sizeof(int) * (size_t)mt * kTileM);
+  int* fb = reinterpret_cast<int*>(ws + off);
+  off += align256(sizeof(int) * (size_t)nt * kTileN);
+  if (off > ws_bytes) return MW_EUNSUPPORTED;
+  DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
+  {
+    ProfScope ps(kPhSplitAux, s);
+    k_slice_rows<<<(unsigned)mt, 128, 0, s>>>(L, ldl, planeL, m, aslices, ea);
+    MW_LAUNCH_CHECK();
+    k_slice_cols<<<(unsigned)((nt * kTileN + 127) / 128), 128, 0, s>>>(U, ldu, planeU, N, nt * kTileN,
+                                                                          bslices, fb);
+    MW_LAUNCH_CHECK();
+  }
+  {
+    ProfScope ps(kPhGemmSplit, s);
+    // more than half of the SM's shared memory: one CTA per SM, which owns
+    // all 512 TMEM columns
+    const size_t shmem = (sizeof(SplitSmem) + 1024 > 120 * 1024) ? sizeof(SplitSmem) + 1024 : 120 * 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+      MW_CUDA_CHECK(cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+      attr_set = true;
+    }
+    dim3 grid((unsigned)mt, (unsigned)nt);
+    k_split_gemm<<<grid, kSplitThreads, shmem, s>>>(C, ldc, planeC, m, N, aslices, bslices, ea, fb, status);
+    MW_LAUNCH_CHECK();
+  }
+  return MW_OK;
 }
 
 int split_update_dd(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m, int64_t col0,
                     int64_t N, int64_t k0, int nb, char* ws, size_t ws_bytes, cudaStream_t s) {
-  (void)A; (void)lda; (void)plane; (void)row0; (void)m; (void)col0; (void)N; (void)k0; (void)nb;
-  (void)ws; (void)ws_bytes; (void)s;
-  return MW_EUNSUPPORTED;
+  if (nb != kK) return MW_EUNSUPPORTED;
+  return split_gemm_sub_dd(m, N, A + col0 * lda + row0, lda, plane, A + k0 * lda + row0, lda, plane,
+                           A + col0 * lda + k0, lda, plane, ws, ws_bytes, s);
 }
 
 }  // namespace mw

@@ -2,12 +2,15 @@
 // (Section 2, Listing 1: SolveTDLSPM).
 //
 // y = P b; y_i -= l_ij y_j (j ascending); x_j = y_j / u_jj and
-// y_i -= u_ij x_j (j descending).  One cooperative launch walks the columns
-// in blocks of 32: warp 0 of CTA 0 solves the 32 x 32 diagonal block with
-// shuffles, then every CTA applies the block's 32 updates, in order, to the
-// rows below (forward) or above (back) it.  Each entry sees the same
-// sequence of rounded multiply-subtract steps as the column-by-column
-// algorithm, so the result is bitwise identical to it.
+// y_i -= u_ij x_j (j descending).  One cooperative launch runs a wavefront
+// over block-rows of 32: each warp owns block-rows (lane = row) and keeps
+// their values in registers.  For block-row I it waits, block by block, for
+// the ready flag of every block J < I (forward) or J > I (back), applies that
+// block's 32 updates in order with the published values, then solves its own
+// diagonal block with shuffles, publishes the result and raises its flag.
+// No grid-wide barrier is needed.  Each entry sees the same sequence of
+// rounded multiply-subtract steps as the column-by-column algorithm, so the
+// result is bitwise identical to it.
 #include <algorithm>
 #include <cuda_runtime.h>
 
@@ -18,14 +21,18 @@
 
 namespace mw {
 
-constexpr int kSolveThreads = 256;
 constexpr int kSolveBlock = 32;
+constexpr int kSolveMaxOwned = 8;              // block-rows per warp kept in registers
 constexpr int64_t kPermSmemMax = 26 * 1024;   // pivots handled in shared memory up to here
 
-// solve work buffer: [barrier | status | perm (int32 n) | y (w planes of n)]
+// solve work buffer: [status | perm (int32 n) | ready flags (int32 per block) | y (w planes of n)]
 constexpr size_t kSolveWsPerm = 256;
-__host__ __device__ inline size_t solve_ws_y(int64_t n) {
+__host__ __device__ inline size_t solve_ws_flags(int64_t n) {
   return (kSolveWsPerm + 4 * (size_t)n + 255) & ~(size_t)255;
+}
+__host__ __device__ inline int64_t solve_nblk(int64_t n) { return (n + kSolveBlock - 1) / kSolveBlock; }
+__host__ __device__ inline size_t solve_ws_y(int64_t n) {
+  return solve_ws_flags(n) + ((4 * (size_t)solve_nblk(n) + 255) & ~(size_t)255);
 }
 
 size_t solve_workspace_bytes(int w, int64_t n) {
@@ -67,119 +74,142 @@ __device__ __forceinline__ val<W> shfl_val(const val<W>& v, int src) {
   return z;
 }
 
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// lane 0 waits (bounded) until flags[J] >= level; false if it gave up
+__device__ __forceinline__ bool wait_flag(const int* flags, int64_t J, int level, DeviceStatus* status, int tag) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long spins = 0;
+    while (ld_acquire_i32(flags + J) < level) {
+      if (++spins > kSpinLimit) {
+        atomicExch(&status->timeout, 1u);
+        atomicExch(&status->where, (unsigned)tag);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  return ok != 0;
+}
+
+// One warp per CTA; warp b owns block-rows b, b + G, b + 2G, ...
 template <int W>
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(32)
 k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
         const double* b, double* x, char* __restrict__ ws) {
-  GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + kWsBarrier);
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
   const int* perm = reinterpret_cast<const int*>(ws + kSolveWsPerm);
+  int* flags = reinterpret_cast<int*>(ws + solve_ws_flags(n));
   double* y = reinterpret_cast<double*>(ws + solve_ws_y(n));
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ double sblk[W][kSolveBlock];
+  const int lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x;
+  const int64_t nblk = solve_nblk(n);
 
-  // y = P b
-  for (int64_t i = gtid; i < n; i += gthreads) {
-    const int src = perm[i];
+  // gather y = P b for every owned block-row (before any flag is raised, so
+  // b may alias x)
+  val<W> yr[kSolveMaxOwned];
 #pragma unroll
-    for (int c = 0; c < W; ++c) __stcg(y + c * n + i, b[c * n + src]);
-  }
-  if (!grid_sync(bar, status, 11)) return;
-
-  // forward: unit lower L
-  for (int64_t J0 = 0; J0 < n; J0 += kSolveBlock) {
-    const int jb = (int)((n - J0 < kSolveBlock) ? n - J0 : kSolveBlock);
-    if (blockIdx.x == 0 && warp == 0) {
-      const int64_t i = J0 + lane;
-      val<W> yv;
-      if (lane < jb) yv = load_cg<W>(y, n, i);
-      else {
+  for (int q = 0; q < kSolveMaxOwned; ++q) {
+    const int64_t I = blockIdx.x + q * G;
+    const int64_t i = I * kSolveBlock + lane;
 #pragma unroll
-        for (int c = 0; c < W; ++c) yv.v[c] = 0.0;
-      }
-      for (int jj = 0; jj < jb; ++jj) {
-        const val<W> yj = shfl_val<W>(yv, jj);
-        if (lane > jj && lane < jb) {
-          const val<W> l = load_ro<W>(LU, plane, (J0 + jj) * lda + i);
-          yv = msub<W>(yv, l, yj);
-        }
-      }
-      if (lane < jb) store_cg<W>(y, n, i, yv);
+    for (int c = 0; c < W; ++c) yr[q].v[c] = 0.0;
+    if (I < nblk && i < n) {
+      const int src = perm[i];
+#pragma unroll
+      for (int c = 0; c < W; ++c) yr[q].v[c] = b[c * n + src];
     }
-    if (!grid_sync(bar, status, 12)) return;
-    const int64_t below = J0 + jb;
-    if (below < n) {
-      for (int e = threadIdx.x; e < W * jb; e += blockDim.x)
-        sblk[e / jb][e % jb] = __ldcg(y + (e / jb) * n + J0 + (e % jb));
-      __syncthreads();
-      for (int64_t i = below + gtid; i < n; i += gthreads) {
-        val<W> acc = load_cg<W>(y, n, i);
-        for (int jj = 0; jj < jb; ++jj) {
-          val<W> yj;
+  }
+
+  // forward: unit lower L, block-rows in increasing order
 #pragma unroll
-          for (int c = 0; c < W; ++c) yj.v[c] = sblk[c][jj];
-          const val<W> l = load_ro<W>(LU, plane, (J0 + jj) * lda + i);
+  for (int q = 0; q < kSolveMaxOwned; ++q) {
+    const int64_t I = blockIdx.x + q * G;
+    if (I >= nblk) break;
+    const int64_t i = I * kSolveBlock + lane;
+    const bool row_ok = i < n;
+    val<W> acc = yr[q];
+    for (int64_t J = 0; J < I; ++J) {
+      if (!wait_flag(flags, J, 1, status, 21)) return;
+      const val<W> yJ = load_cg<W>(y, n, J * kSolveBlock + lane);
+      for (int jj = 0; jj < kSolveBlock; ++jj) {
+        const val<W> yj = shfl_val<W>(yJ, jj);
+        if (row_ok) {
+          const val<W> l = load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i);
           acc = msub<W>(acc, l, yj);
         }
-        store_cg<W>(y, n, i, acc);
       }
-      __syncthreads();
-      if (!grid_sync(bar, status, 13)) return;
     }
+    const int jb = (int)((n - I * kSolveBlock < kSolveBlock) ? n - I * kSolveBlock : kSolveBlock);
+    for (int jj = 0; jj < jb; ++jj) {
+      const val<W> yj = shfl_val<W>(acc, jj);
+      if (lane > jj && lane < jb) {
+        const val<W> l = load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i);
+        acc = msub<W>(acc, l, yj);
+      }
+    }
+    if (row_ok) store_cg<W>(y, n, i, acc);
+    yr[q] = acc;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release_i32(flags + I, 1);
   }
 
-  // back: upper U
-  for (int64_t J1 = n; J1 > 0;) {
-    const int64_t J0 = (J1 > kSolveBlock) ? J1 - kSolveBlock : 0;
-    const int jb = (int)(J1 - J0);
-    if (blockIdx.x == 0 && warp == 0) {
-      const int64_t i = J0 + lane;
-      val<W> yv;
-      if (lane < jb) yv = load_cg<W>(y, n, i);
+  // back: upper U, block-rows in decreasing order
+#pragma unroll
+  for (int q = kSolveMaxOwned - 1; q >= 0; --q) {
+    const int64_t I = blockIdx.x + q * G;
+    if (I >= nblk) continue;
+    const int64_t i = I * kSolveBlock + lane;
+    const bool row_ok = i < n;
+    val<W> acc = yr[q];
+    for (int64_t J = nblk - 1; J > I; --J) {
+      if (!wait_flag(flags, J, 2, status, 22)) return;
+      const int jbJ = (int)((n - J * kSolveBlock < kSolveBlock) ? n - J * kSolveBlock : kSolveBlock);
+      val<W> xJ;
+      if (lane < jbJ) xJ = load_cg<W>(y, n, J * kSolveBlock + lane);
       else {
 #pragma unroll
-        for (int c = 0; c < W; ++c) yv.v[c] = 0.0;
+        for (int c = 0; c < W; ++c) xJ.v[c] = 0.0;
       }
-      for (int jj = jb - 1; jj >= 0; --jj) {
-        if (lane == jj) {
-          const val<W> ujj = load_ro<W>(LU, plane, (J0 + jj) * lda + i);
-          yv = div<W>(yv, ujj);
-        }
-        const val<W> xj = shfl_val<W>(yv, jj);
-        if (lane < jj) {
-          const val<W> u = load_ro<W>(LU, plane, (J0 + jj) * lda + i);
-          yv = msub<W>(yv, u, xj);
-        }
-      }
-      if (lane < jb) store_cg<W>(y, n, i, yv);
-    }
-    if (!grid_sync(bar, status, 14)) return;
-    if (J0 > 0) {
-      for (int e = threadIdx.x; e < W * jb; e += blockDim.x)
-        sblk[e / jb][e % jb] = __ldcg(y + (e / jb) * n + J0 + (e % jb));
-      __syncthreads();
-      for (int64_t i = gtid; i < J0; i += gthreads) {
-        val<W> acc = load_cg<W>(y, n, i);
-        for (int jj = jb - 1; jj >= 0; --jj) {
-          val<W> xj;
-#pragma unroll
-          for (int c = 0; c < W; ++c) xj.v[c] = sblk[c][jj];
-          const val<W> u = load_ro<W>(LU, plane, (J0 + jj) * lda + i);
+      for (int jj = jbJ - 1; jj >= 0; --jj) {
+        const val<W> xj = shfl_val<W>(xJ, jj);
+        if (row_ok) {
+          const val<W> u = load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i);
           acc = msub<W>(acc, u, xj);
         }
-        store_cg<W>(y, n, i, acc);
       }
-      __syncthreads();
-      if (!grid_sync(bar, status, 15)) return;
     }
-    J1 = J0;
-  }
-
-  for (int64_t i = gtid; i < n; i += gthreads) {
+    const int jb = (int)((n - I * kSolveBlock < kSolveBlock) ? n - I * kSolveBlock : kSolveBlock);
+    for (int jj = jb - 1; jj >= 0; --jj) {
+      if (lane == jj) {
+        const val<W> ujj = load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i);
+        acc = div<W>(acc, ujj);
+      }
+      const val<W> xj = shfl_val<W>(acc, jj);
+      if (lane < jj) {
+        const val<W> u = load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i);
+        acc = msub<W>(acc, u, xj);
+      }
+    }
+    if (row_ok) store_cg<W>(y, n, i, acc);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release_i32(flags + I, 2);
+    if (row_ok) {
 #pragma unroll
-    for (int c = 0; c < W; ++c) x[c * n + i] = __ldcg(y + c * n + i);
+      for (int c = 0; c < W; ++c) x[c * n + i] = acc.v[c];
+    }
   }
 }
 
@@ -211,12 +241,15 @@ int solve_with_perm(int64_t n, const double* LU, int64_t lda, const double* b, d
                     char* ws, cudaStream_t s) {
   const int64_t plane = lda * n;
   ProfScope ps(kPhSolve, s);
-  int G = (int)std::min<int64_t>((n + kSolveThreads - 1) / kSolveThreads, sm_count_solve());
-  G = std::max(G, 1);
+  const int64_t nblk = solve_nblk(n);
+  int64_t G = std::min<int64_t>(nblk, 4 * (int64_t)sm_count_solve());
+  if (nblk > G * kSolveMaxOwned) return MW_EUNSUPPORTED;
+  G = std::max<int64_t>(G, (nblk + kSolveMaxOwned - 1) / kSolveMaxOwned);
   MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kSolveWsPerm, s));
+  MW_CUDA_CHECK(cudaMemsetAsync(ws + solve_ws_flags(n), 0, 4 * (size_t)nblk, s));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(G);
-  cfg.blockDim = dim3(kSolveThreads);
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(32);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

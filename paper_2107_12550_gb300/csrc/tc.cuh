@@ -10,7 +10,7 @@
 namespace mw {
 namespace tc {
 
-constexpr unsigned long long kWaitLimit = 1ull << 24;
+constexpr unsigned long long kWaitLimit = 1ull << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

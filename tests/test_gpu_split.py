@@ -1,0 +1,150 @@
+"""The split-precision (Ozaki-style, bf16 tcgen05) trailing update for DD and
+the standalone multiword GEMM (C -= A B, the paper's BNCmatmul block product,
+Section 2), through the C ABI.
+
+The plain GEMM is bitwise equal to the elimination's per-entry order.  The
+split form is not bitwise: each 64-wide slab product is exact up to the
+digit truncation and is rounded once, so its error is stated per result
+against the exact product (error / (max_t|a_it| max_t|b_tj|) <= 2^-104 is
+required; the bound of the method is 2^-107 plus the final DD rounding)."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact as X
+from paper_2107_12550_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2107_12550_gb300 import build as B
+    B.build()
+
+
+def api():
+    from paper_2107_12550_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _mat(w, rows, cols, seed, ld=None, scale_rows=False):
+    g = np.random.default_rng(seed)
+    ld = ld or rows + 3
+    M = np.zeros((w, cols, ld))
+    M[0, :, :rows] = g.uniform(-1, 1, (cols, rows))
+    if scale_rows:
+        M[0, :, :rows] *= np.ldexp(1.0, g.integers(-20, 20, rows))[None, :]
+    for c in range(1, w):
+        _, ex = np.frexp(M[c - 1, :, :rows])
+        M[c, :, :rows] = np.where(M[c - 1, :, :rows] == 0, 0.0,
+                                  np.ldexp(g.uniform(-1, 1, (cols, rows)), ex - 55))
+    return M
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_gemm_sub_plain_bitwise(w):
+    m, N, K = 70, 45, 21
+    C = _mat(w, m, N, 1)
+    A = _mat(w, m, K, 2)
+    B = _mat(w, K, N, 3)
+    got = host(api().gemm_sub(dev(C), dev(A), dev(B), m, w, "plain"))
+    ref = C[:, :, :m].copy()
+    for t in range(K):
+        a = np.repeat(A[:, t, :m][:, None, :], N, axis=1).reshape(w, -1)      # (w, N*m)
+        b = np.repeat(B[:, :, t][:, :, None], m, axis=2).reshape(w, -1)
+        prod = oracle.arith(oracle.OP_MUL, w, a, b)
+        ref = oracle.arith(oracle.OP_SUB, w, ref.reshape(w, -1), prod).reshape(w, N, m)
+    assert np.array_equal(got[:, :, :m], ref)
+
+
+@pytest.mark.parametrize("m,N,scaled", [(130, 70, False), (257, 33, True), (64, 32, False)])
+def test_gemm_sub_split_error_per_result(m, N, scaled):
+    K = 64
+    C = _mat(2, m, N, 11)
+    A = _mat(2, m, K, 12, scale_rows=scaled)
+    B = _mat(2, K, N, 13)
+    got = host(api().gemm_sub(dev(C), dev(A), dev(B), m, 2, "split"))
+    worst = 0.0
+    for i in range(0, m, 3):
+        amax = np.max(np.abs(A[0, :, i]))
+        for j in range(0, N, 2):
+            bmax = np.max(np.abs(B[0, j, :K]))
+            xs = np.concatenate([A[0, :, i], A[0, :, i], A[1, :, i], A[1, :, i]])
+            ys = np.concatenate([B[0, j, :K], B[1, j, :K], B[0, j, :K], B[1, j, :K]])
+            P = oracle.exact_dot(xs, ys, 4)
+            exact = X.words_to_frac(C[:, j, i]) - X.words_to_frac(P)
+            err = abs(X.words_to_frac(got[:, j, i]) - exact)
+            # the final DD rounding of the result is allowed on top
+            allowed_rounding = Fraction(3, 2 ** 106) * abs(exact)
+            ratio = max(err - allowed_rounding, Fraction(0)) / (Fraction(amax) * Fraction(bmax))
+            worst = max(worst, float(ratio))
+    print(f"split GEMM m={m} N={N}: max |dC|/(max|a| max|b|) = 2^{math.log2(worst) if worst else -math.inf:.1f}")
+    assert worst <= 2.0 ** -104
+
+
+def test_gemm_sub_split_matches_plain_closely():
+    m, N, K = 300, 200, 128
+    C = _mat(2, m, N, 21)
+    A = _mat(2, m, K, 22)
+    B = _mat(2, K, N, 23)
+    gs = host(api().gemm_sub(dev(C), dev(A), dev(B), m, 2, "split"))
+    gp = host(api().gemm_sub(dev(C), dev(A), dev(B), m, 2, "plain"))
+    d = np.abs((gs[0, :, :m] - gp[0, :, :m]) + (gs[1, :, :m] - gp[1, :, :m]))
+    assert d.max() <= 2.0 ** -95 * K
+
+
+def _eta(s_A, s_b, x):
+    n = x.shape[1]
+    r = oracle.residual(s_A, s_b, x, 8)
+    Ainf = np.max(np.sum(np.abs(s_A[0, :, :n]), axis=0))
+    return np.max(np.abs(r[0])) / (Ainf * np.max(np.abs(x[0])) + np.max(np.abs(s_b[0])))
+
+
+@pytest.mark.parametrize("n", [65, 200, 300, 513])
+def test_lu_split_backward_error_and_pivots(n):
+    s = W.uniform_system(n, words=2, seed=40 + n, b_words=2)
+    A = dev(s.A)
+    LUs, pivs, infos = api().ludecomp(A, 2, "split")
+    LUp, pivp, infop = api().ludecomp(A, 2, "plain")
+    xs = host(api().solve(LUs, pivs, dev(s.b), 2))
+    eta = _eta(s.A, s.b, xs)
+    assert eta <= 1e-28, eta
+    diff = int((host(pivs) != host(pivp)).sum())
+    print(f"n={n}: split-vs-plain pivot differences {diff}, eta {eta:.2e}")
+    assert diff <= n // 50
+
+
+def test_lu_split_full_size_backward_error():
+    """n = 4096 DD (the large-LU configuration), split trailing update:
+    normwise backward error of the solution <= 1e-28 (exact CPU residual)."""
+    s = W.uniform_system(4096, words=2, seed=0, b_words=2)
+    LU, piv, info = api().ludecomp(dev(s.A), 2, "split")
+    assert int(info.item()) == 0
+    x = host(api().solve(LU, piv, dev(s.b), 2))
+    eta = _eta(s.A, s.b, x)
+    print(f"n=4096 split: eta {eta:.2e}")
+    assert eta <= 1e-28
+
+
+def test_refine_split_dd_inner():
+    s = W.svd_system(300, 10.0, seed=7)
+    res = api().refine(dev(s.A), dev(s.b), 2, 200, update="split")
+    assert res.status == 0
+    x = host(res.x)
+    for i in range(0, 300, 5):
+        assert abs(X.words_to_frac(x[:, i]) - 1) <= Fraction(1, 2 ** 200)
