@@ -195,6 +195,34 @@ int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K, double* C
                 size_t work_bytes, void* stream);
 
 /*
+ * Batches of independent systems of uneven order (one launch per step for
+ * the whole batch; SURVEY-style "batched persistent form" of the method).
+ *   count    number of systems; n_host: HOST int32[count], 1 <= n[s] <= 1024.
+ *   Layout (device): with moff[s] = sum_{s'<s} n[s']^2 and
+ *   voff[s] = sum_{s'<s} n[s'], system s's matrix of w words is at
+ *   M + w*moff[s] (word c of M_s(i,j) at M[w*moff[s] + c*n*n + j*n + i],
+ *   column-major, ld = n); a vector of w words at v + w*voff[s] (word c of
+ *   v_s(i) at v[w*voff[s] + c*n + i]); pivots at piv + voff[s]; info[s].
+ *   The library derives the offsets and a largest-first processing order
+ *   from n_host and uploads them into the work buffer on every call.
+ * Each system's results are bitwise identical to the single-system calls
+ * (mw_ludecomp/mw_solve/mw_refine with MW_UPDATE_PLAIN, MW_STOP_BITS).
+ * The persistent kernels give each system to one CTA, taken from an atomic
+ * counter: no CTA waits for another.
+ */
+int mw_batch_workspace_size(int op, int prec, int count, const int* n_host, size_t* bytes);
+int mw_ludecomp_batched(int prec, int count, const int* n_host, double* A, int64_t* piv, int64_t* info,
+                        void* work, size_t work_bytes, void* stream);
+int mw_solve_batched(int prec, int count, const int* n_host, const double* LU, const int64_t* piv,
+                     const double* b, double* x, void* work, size_t work_bytes, void* stream);
+/* stats: DEVICE int64[4*count]: corrections, residuals, LU info, status
+ * (MW_OK, MW_ENOTCONV or MW_ESINGULAR) per system.  x: x_words planes per
+ * system (inner <= x_words <= 8).  Reads one int back per refinement step. */
+int mw_refine_batched(int count, const int* n_host, const double* A, int a_words, const double* b,
+                      int b_words, int inner, int target_bits, int max_iter, double* x, int x_words,
+                      int64_t* stats, void* work, size_t work_bytes, void* stream);
+
+/*
  * mw_arith -- element-wise multiword arithmetic on device arrays (the
  * DD/TD/QD building blocks of Section 1, as used inside every kernel):
  *   op 0: z = x + y   1: z = x - y   2: z = x * y   3: z = x / y

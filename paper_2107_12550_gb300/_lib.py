@@ -35,6 +35,10 @@ SIGNATURES = {
     "mw_gemm_sub": (_I, [_I, _I, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ, _P]),
     "mw_peak_fp64": (_I, [ctypes.POINTER(_D), _P]),
     "mw_solve_noalloc": (_I, [_I, _I64, _P, _I64, _P, _P, _P, _P]),
+    "mw_batch_workspace_size": (_I, [_I, _I, _I, _P, ctypes.POINTER(_SZ)]),
+    "mw_ludecomp_batched": (_I, [_I, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "mw_solve_batched": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "mw_refine_batched": (_I, [_I, _P, _P, _I, _P, _I, _I, _I, _I, _P, _I, _P, _P, _SZ, _P]),
     "mw_profile_enable": (_I, [_I]),
     "mw_profile_read": (_I, [ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I, _I]),
     "mw_strerror": (ctypes.c_char_p, [_I]),
@@ -87,7 +91,7 @@ def workspace_size(op: int, prec: int, update: int, n: int) -> int:
 
 
 PHASES = ["panel", "laswp", "trsm", "gemm_plain", "gemm_split", "solve", "perm", "residual",
-          "refine_aux", "split_aux"]
+          "refine_aux", "split_aux", "batch_lu", "batch_solve"]
 
 
 def profile_enable(on: bool = True) -> None:

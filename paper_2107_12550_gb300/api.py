@@ -163,6 +163,117 @@ def gemm_sub(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, prec=Non
     return C
 
 
+# ---------------------------------------------------------------------------
+# batches of independent systems (layout: include/mwlu.h, "Batches")
+# ---------------------------------------------------------------------------
+
+def batch_offsets(n_list):
+    """(moff, voff) prefix offsets for the batch layout."""
+    import numpy as np
+    n = np.asarray(n_list, dtype=np.int64)
+    moff = np.concatenate([[0], np.cumsum(n * n)])
+    voff = np.concatenate([[0], np.cumsum(n)])
+    return moff, voff
+
+
+def pack_matrices(mats, w: int):
+    """Pack a list of (>=1, n, lda) float64 arrays into the batch layout with
+    w words per entry (missing words are zero).  Returns a numpy array."""
+    import numpy as np
+    n_list = [m.shape[1] for m in mats]
+    moff, _ = batch_offsets(n_list)
+    out = np.zeros(w * int(moff[-1]))
+    for s, M in enumerate(mats):
+        n = n_list[s]
+        base = w * int(moff[s])
+        for c in range(min(w, M.shape[0])):
+            out[base + c * n * n: base + (c + 1) * n * n] = M[c, :, :n].reshape(-1)
+    return out
+
+
+def pack_vectors(vecs, w: int):
+    import numpy as np
+    n_list = [v.shape[1] for v in vecs]
+    _, voff = batch_offsets(n_list)
+    out = np.zeros(w * int(voff[-1]))
+    for s, v in enumerate(vecs):
+        n = n_list[s]
+        base = w * int(voff[s])
+        for c in range(min(w, v.shape[0])):
+            out[base + c * n: base + (c + 1) * n] = v[c, :n]
+    return out
+
+
+def unpack_vectors(flat, n_list, w: int):
+    import numpy as np
+    _, voff = batch_offsets(n_list)
+    return [np.asarray(flat[w * int(voff[s]): w * int(voff[s]) + w * n]).reshape(w, n)
+            for s, n in enumerate(n_list)]
+
+
+def unpack_matrices(flat, n_list, w: int):
+    import numpy as np
+    moff, _ = batch_offsets(n_list)
+    return [np.asarray(flat[w * int(moff[s]): w * int(moff[s]) + w * n * n]).reshape(w, n, n)
+            for s, n in enumerate(n_list)]
+
+
+def _n_host(n_list):
+    arr = (ctypes.c_int * len(n_list))(*[int(v) for v in n_list])
+    return arr
+
+
+def batch_workspace(op: int, prec: int, n_list, device=None) -> torch.Tensor:
+    out = ctypes.c_size_t(0)
+    L.check("mw_batch_workspace_size",
+            L.lib().mw_batch_workspace_size(op, prec, len(n_list), _n_host(n_list), ctypes.byref(out)))
+    return torch.empty(max(int(out.value), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def ludecomp_batched(A: torch.Tensor, n_list, prec="dd", *, work=None, stream=None, inplace=False):
+    """Batched LU (packed layout, `prec` words).  Returns (LU, piv, info)."""
+    w = _prec(prec)
+    LU = A if inplace else A.clone()
+    total_n = int(sum(n_list))
+    piv = torch.empty(max(total_n, 1), dtype=torch.int64, device=A.device)
+    info = torch.zeros(max(len(n_list), 1), dtype=torch.int64, device=A.device)
+    if work is None:
+        work = batch_workspace(L.MW_OP_LUDECOMP, w, n_list, A.device)
+    L.check("mw_ludecomp_batched", L.lib().mw_ludecomp_batched(
+        w, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(info), _ptr(work), work.numel(),
+        _stream(stream)))
+    return LU, piv, info
+
+
+def solve_batched(LU: torch.Tensor, piv: torch.Tensor, b: torch.Tensor, n_list, prec="dd", *, work=None,
+                  out=None, stream=None):
+    w = _prec(prec)
+    x = out if out is not None else torch.empty_like(b)
+    if work is None:
+        work = batch_workspace(L.MW_OP_SOLVE, w, n_list, LU.device)
+    L.check("mw_solve_batched", L.lib().mw_solve_batched(
+        w, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(b), _ptr(x), _ptr(work), work.numel(),
+        _stream(stream)))
+    return x
+
+
+def refine_batched(A: torch.Tensor, a_words: int, b: torch.Tensor, b_words: int, n_list, inner_prec="dd",
+                   target_bits: int = 200, *, max_iter: int = 30, x_words: int = 8, work=None, out=None,
+                   stream=None):
+    """Batched refinement; returns (x, stats) with stats an int64 tensor
+    (count, 4): corrections, residuals, LU info, status."""
+    w = _prec(inner_prec)
+    total_n = int(sum(n_list))
+    x = out if out is not None else torch.empty(x_words * total_n, dtype=torch.float64, device=A.device)
+    stats = torch.zeros((len(n_list), 4), dtype=torch.int64, device=A.device)
+    if work is None:
+        work = batch_workspace(L.MW_OP_REFINE, w, n_list, A.device)
+    L.check("mw_refine_batched", L.lib().mw_refine_batched(
+        len(n_list), _n_host(n_list), _ptr(A), a_words, _ptr(b), b_words, w, target_bits, max_iter, _ptr(x),
+        x_words, _ptr(stats), _ptr(work), work.numel(), _stream(stream)))
+    return x, stats
+
+
 def arith(op: int, prec, x: torch.Tensor, y: torch.Tensor, *, stream=None) -> torch.Tensor:
     """Element-wise multiword op (0 add, 1 sub, 2 mul, 3 div, 4 compare |x|,|y|)."""
     w = _prec(prec)

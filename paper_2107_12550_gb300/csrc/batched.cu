@@ -1,0 +1,806 @@
+// batched.cu -- many independent systems of uneven order: LU with partial
+// pivoting, substitution, and the refinement loop of the paper (Section 2,
+// Listing 1), one launch per step for the whole batch.
+//
+// Layout of a batch (device arrays, caller-owned):
+//   n[s]     order of system s;
+//   moff[s]  sum_{s' < s} n[s']^2;  voff[s] = sum_{s' < s} n[s'];
+//   order    a permutation of the systems: the processing order (largest
+//            first balances the persistent CTAs);
+//   a matrix of w words for system s lives at M + w*moff[s] (word c of
+//   M_s(i,j) at M[w*moff[s] + c*n*n + j*n + i]); a vector of w words at
+//   v + w*voff[s] (word c of v_s(i) at v[w*voff[s] + c*n + i]); pivots at
+//   piv + voff[s].
+//
+// The LU and the substitution are persistent: each CTA takes the next system
+// from an atomic counter and processes it alone, so no CTA waits for another.
+// Within a system every entry receives exactly the operation sequence of the
+// unblocked algorithms (right-looking k-j-i elimination; column-oriented
+// substitution), so each system's results are bitwise identical to the
+// single-system calls.
+#include <algorithm>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "mw_arith.cuh"
+#include "mw_common.cuh"
+#include "lu_internal.cuh"
+#include "profile.cuh"
+#include "exact_acc.cuh"
+
+namespace mw {
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchMaxN = 1024;   // largest order in a batch (shared-memory caches)
+
+struct BatchCursor {
+  unsigned int next;
+  unsigned int pad[63];
+};
+
+struct BatchState {
+  int er;            // exponent of max |r_0|
+  int done;          // 0 running, 1 converged, 2 not converged, 3 singular
+  int corrections;
+  int residuals;
+  double prev_corr;
+};
+
+template <int W>
+struct BCand {
+  val<W> v;
+  int idx;
+};
+
+template <int W>
+__device__ __forceinline__ bool bbetter(const val<W>& a, int ia, const val<W>& b, int ib) {
+  if (ia < 0) return false;
+  if (ib < 0) return true;
+  const int c = cmp_abs<W>(a, b);
+  return c > 0 || (c == 0 && ia < ib);
+}
+
+__device__ __forceinline__ int next_system(BatchCursor* cur, int count) {
+  __shared__ int s_idx;
+  if (threadIdx.x == 0) s_idx = (int)atomicAdd(&cur->next, 1u);
+  __syncthreads();
+  const int v = s_idx;
+  __syncthreads();
+  return v < count ? v : -1;
+}
+
+// system containing flat index e, given prefix offsets off[0..count] (off[count] = total)
+__device__ __forceinline__ int find_system(const int64_t* off, int count, int64_t e) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// LU of one system per CTA (unblocked right-looking, LAPACK getf2 order).
+// dynamic shared memory: pivot row and multipliers, 2 * W * nmax doubles
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kBatchThreads)
+k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
+             const int64_t* __restrict__ moff, const int64_t* __restrict__ voff, double* __restrict__ A,
+             int64_t* __restrict__ piv, int64_t* __restrict__ info, BatchCursor* cur) {
+  extern __shared__ double bsm[];
+  double* su = bsm;               // [W][nmax]
+  double* sl = bsm + W * nmax;    // [W][nmax]
+  __shared__ BCand<W> wred[kBatchThreads / 32];
+  __shared__ int s_p;
+  __shared__ int s_zero;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    const int pos = next_system(cur, count);
+    if (pos < 0) break;
+    const int s = order[pos];
+    const int n = nn[s];
+    double* a = A + (int64_t)W * moff[s];
+    const int64_t plane = (int64_t)n * n;
+    int64_t* pv = piv + voff[s];
+    int64_t inf = 0;
+    for (int k = 0; k < n; ++k) {
+      val<W> bv;
+#pragma unroll
+      for (int c = 0; c < W; ++c) bv.v[c] = 0.0;
+      int bi = -1;
+      for (int i = k + tid; i < n; i += kBatchThreads) {
+        const val<W> v = load<W>(a, plane, (int64_t)k * n + i);
+        if (bbetter<W>(v, i, bv, bi)) {
+          bv = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        val<W> ov;
+#pragma unroll
+        for (int c = 0; c < W; ++c) ov.v[c] = __shfl_xor_sync(0xffffffffu, bv.v[c], off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (bbetter<W>(ov, oi, bv, bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        wred[warp].v = bv;
+        wred[warp].idx = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        BCand<W> b = wred[0];
+        for (int w = 1; w < kBatchThreads / 32; ++w)
+          if (bbetter<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
+        s_p = b.idx;
+        s_zero = is_zero<W>(b.v) ? 1 : 0;
+        pv[k] = b.idx;
+      }
+      __syncthreads();
+      const int p = s_p;
+      if (s_zero && inf == 0) inf = k + 1;
+      // swap rows k and p over all columns; cache the new row k (j >= k)
+      for (int j = tid; j < n; j += kBatchThreads) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          double* col = a + c * plane + (int64_t)j * n;
+          const double x = col[k];
+          const double y = col[p];
+          if (p != k) {
+            col[k] = y;
+            col[p] = x;
+          }
+          if (j >= k) su[c * nmax + j] = (p != k) ? y : x;
+        }
+      }
+      __syncthreads();
+      val<W> akk;
+#pragma unroll
+      for (int c = 0; c < W; ++c) akk.v[c] = su[c * nmax + k];
+      const bool zero = is_zero<W>(akk);
+      for (int i = k + 1 + tid; i < n; i += kBatchThreads) {
+        val<W> l = load<W>(a, plane, (int64_t)k * n + i);
+        if (!zero) {
+          l = div<W>(l, akk);
+          store<W>(a, plane, (int64_t)k * n + i, l);
+        }
+#pragma unroll
+        for (int c = 0; c < W; ++c) sl[c * nmax + i] = l.v[c];
+      }
+      __syncthreads();
+      const int m = n - k - 1;
+      const int items = m * m;
+      for (int q = tid; q < items; q += kBatchThreads) {
+        const int i = k + 1 + q % m;
+        const int j = k + 1 + q / m;
+        val<W> l, u;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          l.v[c] = sl[c * nmax + i];
+          u.v[c] = su[c * nmax + j];
+        }
+        const int64_t idx = (int64_t)j * n + i;
+        val<W> x = load<W>(a, plane, idx);
+        x = msub<W>(x, l, u);
+        store<W>(a, plane, idx, x);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) info[s] = inf;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// substitution of one system per CTA (column-oriented; x may alias b).
+// Systems whose state is not "running" are skipped when st is given.
+// dynamic shared memory: W * nmax doubles
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kBatchThreads)
+k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
+                const int64_t* __restrict__ moff, const int64_t* __restrict__ voff,
+                const double* __restrict__ LU, const int64_t* __restrict__ piv, const double* b,
+                double* x, const BatchState* __restrict__ st, BatchCursor* cur) {
+  extern __shared__ double bsm[];
+  const int tid = threadIdx.x;
+  for (;;) {
+    const int pos = next_system(cur, count);
+    if (pos < 0) break;
+    const int s = order[pos];
+    if (st && st[s].done) continue;
+    const int n = nn[s];
+    const double* a = LU + (int64_t)W * moff[s];
+    const int64_t plane = (int64_t)n * n;
+    const int64_t* pv = piv + voff[s];
+    const double* bs = b + (int64_t)W * voff[s];
+    double* xs = x + (int64_t)W * voff[s];
+    for (int i = tid; i < n; i += kBatchThreads)
+#pragma unroll
+      for (int c = 0; c < W; ++c) bsm[c * nmax + i] = bs[c * n + i];
+    __syncthreads();
+    if (tid == 0) {
+      for (int k = 0; k < n; ++k) {
+        const int p = (int)pv[k];
+        if (p != k)
+#pragma unroll
+          for (int c = 0; c < W; ++c) {
+            const double t = bsm[c * nmax + k];
+            bsm[c * nmax + k] = bsm[c * nmax + p];
+            bsm[c * nmax + p] = t;
+          }
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+      val<W> yj;
+#pragma unroll
+      for (int c = 0; c < W; ++c) yj.v[c] = bsm[c * nmax + j];
+      for (int i = j + 1 + tid; i < n; i += kBatchThreads) {
+        val<W> yi;
+#pragma unroll
+        for (int c = 0; c < W; ++c) yi.v[c] = bsm[c * nmax + i];
+        yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)j * n + i), yj);
+#pragma unroll
+        for (int c = 0; c < W; ++c) bsm[c * nmax + i] = yi.v[c];
+      }
+      __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+      if (tid == 0) {
+        val<W> yj;
+#pragma unroll
+        for (int c = 0; c < W; ++c) yj.v[c] = bsm[c * nmax + j];
+        yj = div<W>(yj, load_ro<W>(a, plane, (int64_t)j * n + j));
+#pragma unroll
+        for (int c = 0; c < W; ++c) bsm[c * nmax + j] = yj.v[c];
+      }
+      __syncthreads();
+      val<W> xj;
+#pragma unroll
+      for (int c = 0; c < W; ++c) xj.v[c] = bsm[c * nmax + j];
+      for (int i = tid; i < j; i += kBatchThreads) {
+        val<W> yi;
+#pragma unroll
+        for (int c = 0; c < W; ++c) yi.v[c] = bsm[c * nmax + i];
+        yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)j * n + i), xj);
+#pragma unroll
+        for (int c = 0; c < W; ++c) bsm[c * nmax + i] = yi.v[c];
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < n; i += kBatchThreads)
+#pragma unroll
+      for (int c = 0; c < W; ++c) xs[c * n + i] = bsm[c * nmax + i];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// refinement kernels (stop mode: correction below 2^-(tb+2) ||x||_inf)
+// ---------------------------------------------------------------------------
+
+// LU buffer (W words) <- first W words of A (a_words words), zero-padded
+__global__ void k_bt_take_mat(int count, const int64_t* __restrict__ moff, const int* __restrict__ nn,
+                              int64_t total, const double* __restrict__ A, int a_words, double* __restrict__ LU,
+                              int W) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int s = find_system(moff, count, e);
+  const int64_t loc = e - moff[s];
+  const int64_t nn2 = (int64_t)nn[s] * nn[s];
+  for (int c = 0; c < W; ++c)
+    LU[W * moff[s] + c * nn2 + loc] = (c < a_words) ? A[a_words * moff[s] + c * nn2 + loc] : 0.0;
+}
+
+// dst (dw words) <- first dw words of src (sw words), zero-padded
+__global__ void k_bt_take_vec(int count, const int64_t* __restrict__ voff, const int* __restrict__ nn,
+                              int64_t total, const double* __restrict__ src, int sw, double* __restrict__ dst,
+                              int dw) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int s = find_system(voff, count, e);
+  const int64_t loc = e - voff[s];
+  const int n = nn[s];
+  for (int c = 0; c < dw; ++c) dst[dw * voff[s] + c * n + loc] = (c < sw) ? src[sw * voff[s] + c * n + loc] : 0.0;
+}
+
+__global__ void k_bt_init_state(int count, const int64_t* __restrict__ info, BatchState* __restrict__ st) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= count) return;
+  BatchState z;
+  z.er = 0;
+  z.done = info[s] ? 3 : 0;
+  z.corrections = 0;
+  z.residuals = 0;
+  z.prev_corr = 0.0;
+  st[s] = z;
+}
+
+// r = b - A x exactly (running systems only); one CTA per 32-row block
+__global__ void __launch_bounds__(kResThreads)
+k_bt_residual(int count, const int* __restrict__ nn, const int64_t* __restrict__ moff,
+              const int64_t* __restrict__ voff, const int64_t* __restrict__ rbstart, const double* __restrict__ A,
+              int a_words, const double* __restrict__ b, int b_words, const double* __restrict__ x, int x_words,
+              double* __restrict__ r, int r_words, const BatchState* __restrict__ st) {
+  __shared__ u64 acc[kRowsPerCta][kNL];
+  const int s = find_system(rbstart, count, blockIdx.x);
+  if (st[s].done) return;
+  const int n = nn[s];
+  const int64_t plane = (int64_t)n * n;
+  const double* As = A + (int64_t)a_words * moff[s];
+  const double* bs = b + (int64_t)b_words * voff[s];
+  const double* xs = x + (int64_t)x_words * voff[s];
+  double* rs = r + (int64_t)r_words * voff[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = (int)(blockIdx.x - rbstart[s]) * kRowsPerCta + lane;
+  const bool row_ok = i < n;
+  for (int e = threadIdx.x; e < kRowsPerCta * kNL; e += blockDim.x) (&acc[0][0])[e] = 0ull;
+  __syncthreads();
+  if (warp < b_words && row_ok) deposit_double(acc[lane], bs[warp * n + i], 0, false);
+  constexpr int NWARP = kResThreads / 32;
+  for (int j = warp; j < n; j += NWARP) {
+    double xv[MW_LONG_WORDS];
+#pragma unroll
+    for (int d = 0; d < MW_LONG_WORDS; ++d) xv[d] = (d < x_words) ? __ldg(xs + d * n + j) : 0.0;
+    if (!row_ok) continue;
+    for (int c = 0; c < a_words; ++c) {
+      const double a = __ldg(As + c * plane + (int64_t)j * n + i);
+      if (a == 0.0) continue;
+#pragma unroll
+      for (int d = 0; d < MW_LONG_WORDS; ++d)
+        if (d < x_words && xv[d] != 0.0) deposit_product(acc[lane], a, xv[d], 0, true);
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && row_ok) {
+    for (int c = 0; c < r_words; ++c) rs[c * n + i] = acc_take(acc[lane]);
+  }
+}
+
+// per system (one CTA each): residual count, zero residual, iteration limit,
+// e = ilogb(max|r_0|) and r_hat = first W words of 2^-e r
+__global__ void __launch_bounds__(256)
+k_bt_check(int count, const int* __restrict__ nn, const int64_t* __restrict__ voff, const double* __restrict__ r,
+           int r_words, double* __restrict__ rhat, int W, int max_iter, BatchState* __restrict__ st) {
+  const int s = blockIdx.x;
+  if (st[s].done) return;
+  const int n = nn[s];
+  const double* rs = r + (int64_t)r_words * voff[s];
+  __shared__ double red[8];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(rs[i]));
+  for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double rmax = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rmax = fmax(rmax, red[w]);
+  __shared__ int s_go;
+  if (threadIdx.x == 0) {
+    BatchState q = st[s];
+    q.residuals += 1;
+    int go = 0;
+    if (rmax == 0.0) q.done = 1;
+    else if (q.corrections >= max_iter) q.done = 2;
+    else {
+      q.er = ilogb_pos(rmax);
+      go = 1;
+    }
+    st[s] = q;
+    s_go = go;
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const int er = st[s].er;
+  double* hs = rhat + (int64_t)W * voff[s];
+  for (int q = threadIdx.x; q < W * n; q += blockDim.x) hs[q] = scale2(rs[q], -er);
+}
+
+// x = RN_xw(x + 2^e z) exactly, one thread per entry (running systems)
+__global__ void __launch_bounds__(kRowsPerCta)
+k_bt_update(int count, const int* __restrict__ nn, const int64_t* __restrict__ voff, int64_t total,
+            double* __restrict__ x, int x_words, const double* __restrict__ z, int W,
+            const BatchState* __restrict__ st) {
+  __shared__ u64 acc[kRowsPerCta][kNL];
+  u64* a = acc[threadIdx.x];
+  for (int k = 0; k < kNL; ++k) a[k] = 0ull;
+  const int64_t e = (int64_t)blockIdx.x * kRowsPerCta + threadIdx.x;
+  if (e >= total) return;
+  const int s = find_system(voff, count, e);
+  if (st[s].done) return;
+  const int n = nn[s];
+  const int64_t i = e - voff[s];
+  double* xs = x + (int64_t)x_words * voff[s];
+  const double* zs = z + (int64_t)W * voff[s];
+  const int er = st[s].er;
+  for (int c = 0; c < x_words; ++c) deposit_double(a, xs[c * n + i], 0, false);
+  for (int c = 0; c < W; ++c) deposit_double(a, zs[c * n + i], er, false);
+  for (int c = 0; c < x_words; ++c) xs[c * n + i] = acc_take(a);
+}
+
+// per system after an update: correction size and the stopping tests
+__global__ void __launch_bounds__(256)
+k_bt_check2(int count, const int* __restrict__ nn, const int64_t* __restrict__ voff, const double* __restrict__ z,
+            int W, const double* __restrict__ x, int x_words, int target_bits, BatchState* __restrict__ st) {
+  const int s = blockIdx.x;
+  if (st[s].done) return;
+  const int n = nn[s];
+  const double* zs = z + (int64_t)W * voff[s];
+  const double* xs = x + (int64_t)x_words * voff[s];
+  __shared__ double rz[8], rx[8];
+  double mz = 0.0, mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    mz = fmax(mz, fabs(zs[i]));
+    mx = fmax(mx, fabs(xs[i]));
+  }
+  for (int off = 16; off; off >>= 1) {
+    mz = fmax(mz, __shfl_xor_sync(0xffffffffu, mz, off));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rz[threadIdx.x >> 5] = mz;
+    rx[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double zmax = 0.0, xmax = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      zmax = fmax(zmax, rz[w]);
+      xmax = fmax(xmax, rx[w]);
+    }
+    BatchState q = st[s];
+    q.corrections += 1;
+    const double corr = scale2(zmax, q.er);
+    const double lim = scale2(xmax, -target_bits - 2);
+    if (corr <= lim) q.done = 1;
+    else if (q.corrections >= 2 && corr > __dmul_rn(0.5, q.prev_corr)) q.done = 2;
+    q.prev_corr = corr;
+    st[s] = q;
+  }
+}
+
+__global__ void k_bt_count_running(int count, const BatchState* __restrict__ st, int* __restrict__ running) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int s = threadIdx.x; s < count; s += blockDim.x) c += (st[s].done == 0);
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) *running = cnt;
+}
+
+__global__ void k_bt_stats(int count, const BatchState* __restrict__ st, const int64_t* __restrict__ info,
+                           int64_t* __restrict__ stats) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= count) return;
+  const BatchState q = st[s];
+  stats[4 * s + 0] = q.corrections;
+  stats[4 * s + 1] = q.residuals;
+  stats[4 * s + 2] = info[s];
+  stats[4 * s + 3] = q.done == 1 ? MW_OK : (q.done == 3 ? MW_ESINGULAR : MW_ENOTCONV);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int sm_count_b() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+template <typename K>
+static int set_smem(K kern, size_t bytes) {
+  if (bytes > 48 * 1024) MW_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return MW_OK;
+}
+
+template <int W>
+static int lu_batched_launch(int count, int nmax, const int* order, const int* nn, const int64_t* moff,
+                             const int64_t* voff, double* A, int64_t* piv, int64_t* info, char* ws, cudaStream_t s) {
+  if (count <= 0) return MW_OK;
+  BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
+  MW_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(BatchCursor), s));
+  const size_t shmem = sizeof(double) * 2 * W * (size_t)nmax;
+  int rc = set_smem(k_lu_batched<W>, shmem);
+  if (rc) return rc;
+  ProfScope ps(kPhBatchLu, s);
+  const int grid = std::min(count, 2 * sm_count_b());
+  k_lu_batched<W><<<grid, kBatchThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, A, piv, info, cur);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+static int solve_batched_launch(int count, int nmax, const int* order, const int* nn, const int64_t* moff,
+                                const int64_t* voff, const double* LU, const int64_t* piv, const double* b,
+                                double* x, const void* st, char* ws, cudaStream_t s) {
+  if (count <= 0) return MW_OK;
+  BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
+  MW_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(BatchCursor), s));
+  const size_t shmem = sizeof(double) * W * (size_t)nmax;
+  int rc = set_smem(k_solve_batched<W>, shmem);
+  if (rc) return rc;
+  ProfScope ps(kPhBatchSolve, s);
+  const int grid = std::min(count, 4 * sm_count_b());
+  k_solve_batched<W><<<grid, kBatchThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x,
+                                                       static_cast<const BatchState*>(st), cur);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch plan: n, offsets, processing order and residual row-block prefix,
+// computed on the host from the host copy of n and uploaded into the work
+// buffer at the start of every call
+// ---------------------------------------------------------------------------
+struct BatchPlanHost {
+  std::vector<int> n, order;
+  std::vector<int64_t> moff, voff, rb;
+  int64_t sum_n = 0, sum_n2 = 0;
+  int nmax = 0;
+};
+
+static bool make_plan(int count, const int* n_host, BatchPlanHost& p) {
+  p.n.assign(n_host, n_host + count);
+  p.moff.resize(count + 1);
+  p.voff.resize(count + 1);
+  p.rb.resize(count + 1);
+  int64_t m = 0, v = 0, r = 0;
+  p.nmax = 1;
+  for (int s = 0; s < count; ++s) {
+    if (p.n[s] < 1 || p.n[s] > kBatchMaxN) return false;
+    p.moff[s] = m;
+    p.voff[s] = v;
+    p.rb[s] = r;
+    m += (int64_t)p.n[s] * p.n[s];
+    v += p.n[s];
+    r += (p.n[s] + kRowsPerCta - 1) / kRowsPerCta;
+    p.nmax = std::max(p.nmax, p.n[s]);
+  }
+  p.moff[count] = m;
+  p.voff[count] = v;
+  p.rb[count] = r;
+  p.sum_n = v;
+  p.sum_n2 = m;
+  p.order.resize(count);
+  for (int s = 0; s < count; ++s) p.order[s] = s;
+  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) { return p.n[a] > p.n[b]; });
+  return true;
+}
+
+struct BatchPlanDev {
+  int* n;
+  int64_t* moff;
+  int64_t* voff;
+  int* order;
+  int64_t* rb;
+};
+
+// [cursor 256 | n | moff | voff | order | rb]
+static size_t plan_bytes(int count) {
+  return 256 + align256(sizeof(int) * count) + 2 * align256(sizeof(int64_t) * (count + 1)) +
+         align256(sizeof(int) * count) + align256(sizeof(int64_t) * (count + 1));
+}
+
+static int upload_plan(const BatchPlanHost& p, int count, char* ws, BatchPlanDev& d, cudaStream_t s) {
+  size_t off = 256;
+  d.n = reinterpret_cast<int*>(ws + off);
+  off += align256(sizeof(int) * count);
+  d.moff = reinterpret_cast<int64_t*>(ws + off);
+  off += align256(sizeof(int64_t) * (count + 1));
+  d.voff = reinterpret_cast<int64_t*>(ws + off);
+  off += align256(sizeof(int64_t) * (count + 1));
+  d.order = reinterpret_cast<int*>(ws + off);
+  off += align256(sizeof(int) * count);
+  d.rb = reinterpret_cast<int64_t*>(ws + off);
+  MW_CUDA_CHECK(cudaMemcpyAsync(d.n, p.n.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+  MW_CUDA_CHECK(cudaMemcpyAsync(d.moff, p.moff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  MW_CUDA_CHECK(cudaMemcpyAsync(d.voff, p.voff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  MW_CUDA_CHECK(cudaMemcpyAsync(d.order, p.order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+  MW_CUDA_CHECK(cudaMemcpyAsync(d.rb, p.rb.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  return MW_OK;
+}
+
+// refinement work buffer map (after the plan)
+struct BatchRefineMap {
+  size_t lu, piv, info, r, z, rhat, st, running, total;
+};
+
+static BatchRefineMap batch_refine_map(int W, int count, int64_t sum_n, int64_t sum_n2) {
+  BatchRefineMap m;
+  size_t off = plan_bytes(count);
+  m.lu = off;
+  off += align256(sizeof(double) * W * (size_t)sum_n2);
+  m.piv = off;
+  off += align256(sizeof(int64_t) * (size_t)sum_n);
+  m.info = off;
+  off += align256(sizeof(int64_t) * (size_t)count);
+  m.r = off;
+  off += align256(sizeof(double) * MW_LONG_WORDS * (size_t)sum_n);
+  m.z = off;
+  off += align256(sizeof(double) * W * (size_t)sum_n);
+  m.rhat = off;
+  off += align256(sizeof(double) * W * (size_t)sum_n);
+  m.st = off;
+  off += align256(sizeof(BatchState) * (size_t)count);
+  m.running = off;
+  off += 256;
+  m.total = off;
+  return m;
+}
+
+template <int W>
+static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPlanDev& d, const double* A, int a_words,
+                               const double* b, int b_words, int target_bits, int max_iter, double* x, int x_words,
+                               int64_t* stats, char* ws, size_t ws_bytes, cudaStream_t s) {
+  const BatchRefineMap mp = batch_refine_map(W, count, p.sum_n, p.sum_n2);
+  if (ws_bytes < mp.total) return -15;
+  double* LU = reinterpret_cast<double*>(ws + mp.lu);
+  int64_t* piv = reinterpret_cast<int64_t*>(ws + mp.piv);
+  int64_t* info = reinterpret_cast<int64_t*>(ws + mp.info);
+  double* r = reinterpret_cast<double*>(ws + mp.r);
+  double* z = reinterpret_cast<double*>(ws + mp.z);
+  double* rhat = reinterpret_cast<double*>(ws + mp.rhat);
+  BatchState* st = reinterpret_cast<BatchState*>(ws + mp.st);
+  int* running_d = reinterpret_cast<int*>(ws + mp.running);
+  char* cur = ws;
+  const int64_t nrb = p.rb[count];
+  prof_count(kPhRefineAux);
+  k_bt_take_mat<<<(unsigned)((p.sum_n2 + 255) / 256), 256, 0, s>>>(count, d.moff, d.n, p.sum_n2, A, a_words, LU, W);
+  MW_LAUNCH_CHECK();
+  int rc = lu_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, info, cur, s);
+  if (rc) return rc;
+  prof_count(kPhRefineAux);
+  k_bt_init_state<<<(count + 255) / 256, 256, 0, s>>>(count, info, st);
+  prof_count(kPhRefineAux);
+  k_bt_take_vec<<<(unsigned)((p.sum_n + 255) / 256), 256, 0, s>>>(count, d.voff, d.n, p.sum_n, b, b_words, rhat, W);
+  MW_LAUNCH_CHECK();
+  rc = solve_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, rhat, z, st, cur, s);
+  if (rc) return rc;
+  prof_count(kPhRefineAux);
+  k_bt_take_vec<<<(unsigned)((p.sum_n + 255) / 256), 256, 0, s>>>(count, d.voff, d.n, p.sum_n, z, W, x, x_words);
+  MW_LAUNCH_CHECK();
+  for (int it = 0; it <= max_iter; ++it) {
+    {
+      ProfScope ps(kPhResidual, s);
+      k_bt_residual<<<(unsigned)nrb, kResThreads, 0, s>>>(count, d.n, d.moff, d.voff, d.rb, A, a_words, b, b_words,
+                                                          x, x_words, r, x_words, st);
+      MW_LAUNCH_CHECK();
+    }
+    prof_count(kPhRefineAux);
+    k_bt_check<<<count, 256, 0, s>>>(count, d.n, d.voff, r, x_words, rhat, W, max_iter, st);
+    prof_count(kPhRefineAux);
+    k_bt_count_running<<<1, 256, 0, s>>>(count, st, running_d);
+    MW_LAUNCH_CHECK();
+    int running = 0;
+    MW_CUDA_CHECK(cudaMemcpyAsync(&running, running_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MW_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (running == 0) break;
+    rc = solve_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, rhat, z, st, cur, s);
+    if (rc) return rc;
+    prof_count(kPhRefineAux);
+    k_bt_update<<<(unsigned)((p.sum_n + kRowsPerCta - 1) / kRowsPerCta), kRowsPerCta, 0, s>>>(
+        count, d.n, d.voff, p.sum_n, x, x_words, z, W, st);
+    prof_count(kPhRefineAux);
+    k_bt_check2<<<count, 256, 0, s>>>(count, d.n, d.voff, z, W, x, x_words, target_bits, st);
+    MW_LAUNCH_CHECK();
+  }
+  prof_count(kPhRefineAux);
+  k_bt_stats<<<(count + 255) / 256, 256, 0, s>>>(count, st, info, stats);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+}  // namespace mw
+
+// ---------------------------------------------------------------------------
+// C ABI (declared in include/mwlu.h)
+// ---------------------------------------------------------------------------
+static bool bprec_ok(int p) { return p == MW_DD || p == MW_TD || p == MW_QD; }
+
+extern "C" int mw_batch_workspace_size(int op, int prec, int count, const int* n_host, size_t* bytes) {
+  if (op != MW_OP_LUDECOMP && op != MW_OP_SOLVE && op != MW_OP_REFINE) return -1;
+  if (!bprec_ok(prec)) return -2;
+  if (count < 0) return -3;
+  if (count > 0 && !n_host) return -4;
+  if (!bytes) return -5;
+  mw::BatchPlanHost p;
+  if (!mw::make_plan(count, n_host, p)) return -4;
+  if (op == MW_OP_REFINE) *bytes = mw::batch_refine_map(prec, count, p.sum_n, p.sum_n2).total;
+  else *bytes = mw::plan_bytes(count);
+  return MW_OK;
+}
+
+extern "C" int mw_ludecomp_batched(int prec, int count, const int* n_host, double* A, int64_t* piv,
+                                   int64_t* info, void* work, size_t work_bytes, void* stream) {
+  if (!bprec_ok(prec)) return -1;
+  if (count < 0) return -2;
+  if (count == 0) return MW_OK;
+  if (!n_host) return -3;
+  if (!A) return -4;
+  if (!piv) return -5;
+  if (!info) return -6;
+  if (!work) return -7;
+  mw::BatchPlanHost p;
+  if (!mw::make_plan(count, n_host, p)) return -3;
+  if (work_bytes < mw::plan_bytes(count)) return -8;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(work);
+  mw::BatchPlanDev d;
+  int rc = mw::upload_plan(p, count, ws, d, s);
+  if (rc) return rc;
+  switch (prec) {
+    case 2: return mw::lu_batched_launch<2>(count, p.nmax, d.order, d.n, d.moff, d.voff, A, piv, info, ws, s);
+    case 3: return mw::lu_batched_launch<3>(count, p.nmax, d.order, d.n, d.moff, d.voff, A, piv, info, ws, s);
+    default: return mw::lu_batched_launch<4>(count, p.nmax, d.order, d.n, d.moff, d.voff, A, piv, info, ws, s);
+  }
+}
+
+extern "C" int mw_solve_batched(int prec, int count, const int* n_host, const double* LU, const int64_t* piv,
+                                const double* b, double* x, void* work, size_t work_bytes, void* stream) {
+  if (!bprec_ok(prec)) return -1;
+  if (count < 0) return -2;
+  if (count == 0) return MW_OK;
+  if (!n_host) return -3;
+  if (!LU) return -4;
+  if (!piv) return -5;
+  if (!b) return -6;
+  if (!x) return -7;
+  if (!work) return -8;
+  mw::BatchPlanHost p;
+  if (!mw::make_plan(count, n_host, p)) return -3;
+  if (work_bytes < mw::plan_bytes(count)) return -9;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(work);
+  mw::BatchPlanDev d;
+  int rc = mw::upload_plan(p, count, ws, d, s);
+  if (rc) return rc;
+  switch (prec) {
+    case 2: return mw::solve_batched_launch<2>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, b, x, nullptr, ws, s);
+    case 3: return mw::solve_batched_launch<3>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, b, x, nullptr, ws, s);
+    default: return mw::solve_batched_launch<4>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, b, x, nullptr, ws, s);
+  }
+}
+
+extern "C" int mw_refine_batched(int count, const int* n_host, const double* A, int a_words, const double* b,
+                                 int b_words, int inner, int target_bits, int max_iter, double* x, int x_words,
+                                 int64_t* stats, void* work, size_t work_bytes, void* stream) {
+  if (count < 0) return -1;
+  if (count == 0) return MW_OK;
+  if (!n_host) return -2;
+  if (!A) return -3;
+  if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
+  if (!b) return -5;
+  if (b_words < 1 || b_words > MW_LONG_WORDS) return -6;
+  if (!bprec_ok(inner)) return -7;
+  if (target_bits < 1 || target_bits > 1000) return -8;
+  if (max_iter < 0) return -9;
+  if (!x) return -10;
+  if (x_words < inner || x_words > MW_LONG_WORDS) return -11;
+  if (!stats) return -12;
+  if (!work) return -13;
+  mw::BatchPlanHost p;
+  if (!mw::make_plan(count, n_host, p)) return -2;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(work);
+  if (work_bytes < mw::batch_refine_map(inner, count, p.sum_n, p.sum_n2).total) return -14;
+  mw::BatchPlanDev d;
+  int rc = mw::upload_plan(p, count, ws, d, s);
+  if (rc) return rc;
+  switch (inner) {
+    case 2: return mw::refine_batched_impl<2>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, work_bytes, s);
+    case 3: return mw::refine_batched_impl<3>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, work_bytes, s);
+    default: return mw::refine_batched_impl<4>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, work_bytes, s);
+  }
+}

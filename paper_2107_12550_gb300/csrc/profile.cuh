@@ -15,7 +15,9 @@ enum Phase {
   kPhResidual = 7,
   kPhRefineAux = 8,
   kPhSplitAux = 9,
-  kNumPhases = 10
+  kPhBatchLu = 10,
+  kPhBatchSolve = 11,
+  kNumPhases = 12
 };
 
 bool prof_enabled();
