@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--impl", default="mwlu", choices=["mwlu", "reference"])
     p.add_argument("--n", type=int, default=N)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the split / large-LU / batched comparison measurements")
     return p.parse_args()
 
 
@@ -212,6 +214,109 @@ def run_reference(args, world, rank):
     return 0
 
 
+def _time(fn, reps, stream):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def extras(A, b, n, steps, peak_fp64):
+    """Comparison measurements beside the headline (same GPU, same run):
+    the split-precision DD inner solver on the same system, the large DD LU
+    (n = 4096) plain vs split, and a 4096-system batch (n in [16, 256])."""
+    import numpy as np
+    import torch
+    from paper_2107_12550_gb300 import _lib as L
+    from paper_2107_12550_gb300 import api
+    from paper_2107_12550_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    out = {}
+    # split DD inner refinement of the same n = 2048 system
+    x = torch.empty((X_WORDS, n), dtype=torch.float64, device="cuda")
+    work = api.workspace(L.MW_OP_REFINE, 2, 1, n)
+    f = lambda: api.refine(A, b, 2, TARGET_BITS, update="split", x_words=X_WORDS, work=work, out=x)
+    r = f()
+    ms, r = _time(f, max(steps, 3), stream)
+    ok = r.converged and exact_ok(x.cpu().numpy(), n)
+    out["split_dd_inner_refine"] = {"solves_per_s": (1.0 if ok else 0.0) / (ms * 1e-3), "ms_per_solve": ms,
+                                    "corrections": r.corrections, "target_met": ok,
+                                    "workload": "same system as the headline, DD inner LU with the split update"}
+    # large DD LU, n = 4096, plain vs split (LU DD-Gop/s = (2/3) n^3 / t)
+    n3 = 4096
+    Au = torch.from_numpy(W.uniform_matrix(n3, 2, seed=0)).cuda()
+    lu = {}
+    for upd, reps in (("plain", 1), ("split", 3)):
+        wk = api.workspace(L.MW_OP_LUDECOMP, 2, 1 if upd == "split" else 0, n3)
+        g = lambda: api.ludecomp(Au, 2, upd, work=wk)
+        g()
+        L.profile_read(reset=True)
+        L.profile_enable(True)
+        t, _ = _time(g, reps, stream)
+        L.profile_enable(False)
+        prof = L.profile_read(reset=True)
+        lu[upd] = {"ms": t, "dd_gops": (2.0 / 3.0) * n3 ** 3 / (t * 1e-3) / 1e9,
+                   "phase_ms": {k: v[0] / reps for k, v in prof.items() if v[1]}}
+    # tensor-pipe roofline of the split GEMM: bf16 MMA flops issued per LU
+    mma_flops = 0
+    for k0 in range(0, n3, 64):
+        r0 = k0 + 64
+        if r0 >= n3:
+            break
+        m_t = -(-(n3 - r0) // 128)
+        n_t = -(-(n3 - r0) // 32)
+        mma_flops += m_t * n_t * 120 * 2 * 128 * 32 * 64
+    split_gemm_ms = lu["split"]["phase_ms"].get("gemm_split", 0.0)
+    out["lu_dd_n4096"] = {
+        "plain_dd_gops": lu["plain"]["dd_gops"], "split_dd_gops": lu["split"]["dd_gops"],
+        "plain_ms": lu["plain"]["ms"], "split_ms": lu["split"]["ms"],
+        "split_phase_ms": lu["split"]["phase_ms"],
+        "split_gemm_roofline": {"bound": "tensor", "kernel": "k_split_gemm (bf16 tcgen05, TMEM)",
+                                "achieved": mma_flops / (split_gemm_ms * 1e-3) / 1e12 if split_gemm_ms else None,
+                                "peak": None, "unit": "TFLOP/s",
+                                "note": "MMA flops over the kernel time including its exact-recombination epilogue"},
+        "plain_gemm_fp64_frac": None,
+    }
+    pg = lu["plain"]["phase_ms"].get("gemm_plain", 0.0)
+    if pg:
+        instr = panel_sum_sq(n3) * FP64_PER_MSUB[2]
+        out["lu_dd_n4096"]["plain_gemm_fp64_frac"] = instr / (pg * 1e-3) / peak_fp64
+    # batch of 4096 DD systems, n in [16, 256], one RHS (x_true = ones)
+    n_list = [int(v) for v in W.batch_sizes(4096, 16, 256, seed=0)]
+    mats = [W.uniform_matrix(m, 2, seed=W.system_seed(0, s), lda=m) for s, m in enumerate(n_list)]
+    Ab = torch.from_numpy(api.pack_matrices(mats, 2)).cuda()
+    del mats
+    vb = np.zeros(2 * int(sum(n_list)))
+    _, voff = api.batch_offsets(n_list)
+    for s, m in enumerate(n_list):
+        vb[2 * voff[s]: 2 * voff[s] + m] = 1.0
+    bb = torch.from_numpy(vb).cuda()
+    wk = api.batch_workspace(L.MW_OP_LUDECOMP, 2, n_list)
+    LUb = torch.empty_like(Ab)
+    pivb = torch.empty(int(sum(n_list)), dtype=torch.int64, device="cuda")
+
+    def batch_step():
+        LUb.copy_(Ab)
+        LU_, piv_, info_ = api.ludecomp_batched(LUb, n_list, 2, work=wk, inplace=True)
+        return api.solve_batched(LU_, piv_, bb, n_list, 2, work=wk)
+
+    batch_step()
+    tb, _ = _time(batch_step, 2, stream)
+    ops = sum((2.0 / 3.0) * m ** 3 for m in n_list)
+    out["batched_config4_dd"] = {"systems": 4096, "n_range": [16, 256], "ms_per_batch": tb,
+                                 "systems_per_s": 4096 / (tb * 1e-3),
+                                 "lu_dd_gops": ops / (tb * 1e-3) / 1e9,
+                                 "workload": "uniform DD systems, one launch each for LU and solve"}
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -348,6 +453,8 @@ def main():
                 "h2d_bytes_per_step": int(s.A.nbytes + s.b.nbytes),
                 "d2h_bytes_per_step": int(x.numel() * 8)},
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["extras"] = extras(A, b, n, args.steps, peak_fp64)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(n, s.A, s.b, corrections, residuals)
     if rank == 0:
