@@ -278,6 +278,25 @@ int mw_profile_read(double* ms, long long* launches, int nphase, int reset);
 int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
                      const double* b, double* x, void* stream);
 
+/*
+ * Tuning knobs (process-wide, per precision; read at each launch).  They
+ * change the blocking only: every result is bitwise the same for any value.
+ *   MW_TUNE_PANEL_WIDTH          panel width nb of the plain blocked LU:
+ *                                32, 64 (default) or 128 (the split update
+ *                                always uses 64)
+ *   MW_TUNE_PANEL_ROWS_PER_CTA   panel rows per CTA before the panel kernel
+ *                                adds CTAs: 1..4096 (default 8)
+ *   MW_TUNE_BATCH_CTAS_PER_SM    persistent CTAs per SM of the batched LU:
+ *                                1..8 (default 2)
+ * mw_set_tuning returns the previous value, or -1 (param), -2 (prec) or
+ * -3 (value) when invalid; mw_get_tuning returns the value or -1/-2.
+ */
+#define MW_TUNE_PANEL_WIDTH 0
+#define MW_TUNE_PANEL_ROWS_PER_CTA 1
+#define MW_TUNE_BATCH_CTAS_PER_SM 2
+int mw_set_tuning(int param, int prec, int value);
+int mw_get_tuning(int param, int prec);
+
 /* mw_strerror -- static text for a status code. */
 const char* mw_strerror(int code);
 

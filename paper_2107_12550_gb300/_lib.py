@@ -18,6 +18,7 @@ MW_UPDATE_PLAIN, MW_UPDATE_SPLIT = 0, 1
 MW_OK, MW_ESINGULAR, MW_ENOTCONV, MW_ECUDA, MW_ETIMEOUT, MW_EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 MW_OP_LUDECOMP, MW_OP_SOLVE, MW_OP_REFINE, MW_OP_GEMM = 0, 1, 2, 3
 MW_STOP_EQ2, MW_STOP_BITS = 0, 1
+MW_TUNE_PANEL_WIDTH, MW_TUNE_PANEL_ROWS_PER_CTA, MW_TUNE_BATCH_CTAS_PER_SM = 0, 1, 2
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -41,6 +42,8 @@ SIGNATURES = {
     "mw_refine_batched": (_I, [_I, _P, _P, _I, _P, _I, _I, _I, _I, _P, _I, _P, _P, _SZ, _P]),
     "mw_profile_enable": (_I, [_I]),
     "mw_profile_read": (_I, [ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I, _I]),
+    "mw_set_tuning": (_I, [_I, _I, _I]),
+    "mw_get_tuning": (_I, [_I, _I]),
     "mw_strerror": (ctypes.c_char_p, [_I]),
     "mw_last_cuda_error": (_I, []),
     "mw_version": (ctypes.c_char_p, []),

@@ -515,7 +515,7 @@ static int lu_batched_launch(int count, int nmax, const int* order, const int* n
   int rc = set_smem(k_lu_batched<W>, shmem);
   if (rc) return rc;
   ProfScope ps(kPhBatchLu, s);
-  const int grid = std::min(count, 2 * sm_count_b());
+  const int grid = std::min(count, std::max(1, tune_get(MW_TUNE_BATCH_CTAS_PER_SM, W)) * sm_count_b());
   k_lu_batched<W><<<grid, kBatchThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, A, piv, info, cur);
   MW_LAUNCH_CHECK();
   return MW_OK;

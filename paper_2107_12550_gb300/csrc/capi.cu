@@ -22,6 +22,35 @@ extern "C" void mw_internal_set_cuda_error(int e) { g_last_cuda_error = e; }
 
 static bool prec_ok(int p) { return p == MW_DD || p == MW_TD || p == MW_QD; }
 
+// tuning table: [param][prec - 2]
+static int g_tune[3][3] = {{64, 64, 64}, {8, 8, 8}, {2, 2, 2}};
+
+int mw::tune_get(int param, int prec) {
+  if (param < 0 || param > 2 || !prec_ok(prec)) return -1;
+  return g_tune[param][prec - 2];
+}
+
+extern "C" int mw_set_tuning(int param, int prec, int value) {
+  if (param < MW_TUNE_PANEL_WIDTH || param > MW_TUNE_BATCH_CTAS_PER_SM) return -1;
+  if (!prec_ok(prec)) return -2;
+  bool ok = false;
+  switch (param) {
+    case MW_TUNE_PANEL_WIDTH: ok = value == 32 || value == 64 || value == 128; break;
+    case MW_TUNE_PANEL_ROWS_PER_CTA: ok = value >= 1 && value <= 4096; break;
+    default: ok = value >= 1 && value <= 8; break;
+  }
+  if (!ok) return -3;
+  const int prev = g_tune[param][prec - 2];
+  g_tune[param][prec - 2] = value;
+  return prev;
+}
+
+extern "C" int mw_get_tuning(int param, int prec) {
+  if (param < MW_TUNE_PANEL_WIDTH || param > MW_TUNE_BATCH_CTAS_PER_SM) return -1;
+  if (!prec_ok(prec)) return -2;
+  return g_tune[param][prec - 2];
+}
+
 static size_t lu_ws_bytes(int update, int64_t n) {
   return mw::kWsSplit + (update == MW_UPDATE_SPLIT ? mw::split_workspace_bytes(n, mw::kDefaultNb) : 0);
 }
@@ -59,10 +88,11 @@ extern "C" int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t l
     MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
     return MW_OK;
   }
+  const int nb = (update == MW_UPDATE_SPLIT) ? mw::kDefaultNb : mw::tune_get(MW_TUNE_PANEL_WIDTH, prec);
   switch (prec) {
-    case 2: return mw::lu_blocked<2>(update, n, A, lda, piv, info, ws, work_bytes, mw::kDefaultNb, s);
-    case 3: return mw::lu_blocked<3>(update, n, A, lda, piv, info, ws, work_bytes, mw::kDefaultNb, s);
-    default: return mw::lu_blocked<4>(update, n, A, lda, piv, info, ws, work_bytes, mw::kDefaultNb, s);
+    case 2: return mw::lu_blocked<2>(update, n, A, lda, piv, info, ws, work_bytes, nb, s);
+    case 3: return mw::lu_blocked<3>(update, n, A, lda, piv, info, ws, work_bytes, nb, s);
+    default: return mw::lu_blocked<4>(update, n, A, lda, piv, info, ws, work_bytes, nb, s);
   }
 }
 

@@ -413,7 +413,8 @@ template <int W>
 int launch_panel(double* A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
                  int64_t* piv, int64_t* info, char* ws, cudaStream_t s) {
   const int64_t rows = n - k0;
-  int G = (int)std::min<int64_t>((rows + kPanelRowsPerCta - 1) / kPanelRowsPerCta, sm_count());
+  const int rpc = std::max(1, tune_get(MW_TUNE_PANEL_ROWS_PER_CTA, W));
+  int G = (int)std::min<int64_t>((rows + rpc - 1) / rpc, sm_count());
   G = std::max(1, std::min(G, kMaxPanelCtas));
   const int64_t chunk = (rows + G - 1) / G;
   const size_t shmem = sizeof(double) * (size_t)W * ((size_t)nb + (size_t)chunk);

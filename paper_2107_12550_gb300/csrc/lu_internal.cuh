@@ -21,6 +21,9 @@ constexpr size_t kWsSplit = 64 * 1024;  // >= kWsCand + kMaxPanelCtas * kCandStr
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// tuning knobs (capi.cu): value of `param` (MW_TUNE_*) for precision prec
+int tune_get(int param, int prec);
+
 template <int W>
 int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info,
                char* ws, size_t ws_bytes, int nb, cudaStream_t s);

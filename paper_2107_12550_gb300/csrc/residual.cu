@@ -334,7 +334,8 @@ static int refine_impl(int64_t n, const double* A, int64_t lda, int a_words, con
     }
   }
   MW_CUDA_CHECK(cudaMemsetAsync(st, 0, sizeof(RefineState), s));
-  int rc = lu_blocked<W>(update, n, LU, ldl, piv, info_d, ws + m.lu_ws, m.solve_ws - m.lu_ws, kDefaultNb, s);
+  const int nb = (update == MW_UPDATE_SPLIT) ? kDefaultNb : tune_get(MW_TUNE_PANEL_WIDTH, W);
+  int rc = lu_blocked<W>(update, n, LU, ldl, piv, info_d, ws + m.lu_ws, m.solve_ws - m.lu_ws, nb, s);
   if (rc) return rc;
   int64_t info = 0;
   MW_CUDA_CHECK(cudaMemcpyAsync(&info, info_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
