@@ -111,9 +111,9 @@ int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t lda, int64_t
  *   b             device, prec planes of n (right-hand side).
  *   x             device, prec planes of n (solution); x may equal b.
  * Order of operations per entry: y = P b; y_i -= l_ij y_j for j ascending;
- * x_j = y_j / u_jj, then y_i -= u_ij x_j for j descending.  A zero u_jj gives
- * Inf/NaN entries (check mw_ludecomp's info).  Returns MW_OK, -i, MW_ECUDA or
- * MW_ETIMEOUT.
+ * d_j = 1 / u_jj (multiword division) for every j, then x_j = y_j * d_j and
+ * y_i -= u_ij x_j for j descending.  A zero u_jj gives Inf/NaN entries (check
+ * mw_ludecomp's info).  Returns MW_OK, -i, MW_ECUDA or MW_ETIMEOUT.
  */
 int mw_solve(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
              const double* b, double* x, void* work, size_t work_bytes, void* stream);
@@ -262,8 +262,8 @@ int mw_profile_read(double* ms, long long* launches, int nphase, int reset);
  *   Scratch: a fixed array of MW_NOALLOC_SCRATCH_BYTES in the library's own
  *   device memory, held on every GPU that loads the library until exit.  n
  *   is limited to the orders whose scratch fits (mw_workspace_size(
- *   MW_OP_SOLVE, prec, 0, n) <= MW_NOALLOC_SCRATCH_BYTES: n <= 58040 for QD,
- *   74549 for TD, 104192 for DD); larger n returns -2 before any GPU work.
+ *   MW_OP_SOLVE, prec, 0, n) <= MW_NOALLOC_SCRATCH_BYTES: n <= 20968 for QD,
+ *   27584 for TD, 40320 for DD); larger n returns -2 before any GPU work.
  *   Nothing is allocated or freed by this call.
  *   Set-up: the first call on each device looks up the scratch address with
  *   cudaGetSymbolAddress (with that device current) and caches it; make that

@@ -470,7 +470,8 @@ int mwo_lu(int w, int64_t n, double *A, int64_t lda, int64_t *piv, int64_t *info
 /* Forward/back substitution (Section 2, Listing 1: SolveTDLSPM).           */
 /*   y = P b (swaps in order k = 0..n-1);                                   */
 /*   y_i = y_i - l_ij * y_j   for j ascending (unit lower L);               */
-/*   x_j = y_j / u_jj, then y_i = y_i - u_ij * x_j for j descending.        */
+/*   d_j = 1 / u_jj (a multiword division, for every j first), then        */
+/*   x_j = y_j * d_j and y_i = y_i - u_ij * x_j for j descending.           */
 /* b and x are w planes of n; b may alias x.                                */
 /* ------------------------------------------------------------------------ */
 
@@ -478,12 +479,13 @@ int mwo_solve(int w, int64_t n, const double *LU, int64_t lda, const int64_t *pi
               const double *b, double *x)
 {
     int64_t plane, i, j, k;
-    double *y;
+    double *y, *d;
     if (w < 2 || w > 4) return -1;
     if (n == 0) return 0;
     plane = lda * n;
     y = (double *)malloc(sizeof(double) * (size_t)(w * n));
-    if (!y) return -100;
+    d = (double *)malloc(sizeof(double) * (size_t)(w * n));
+    if (!y || !d) { free(y); free(d); return -100; }
     memcpy(y, b, sizeof(double) * (size_t)(w * n));
     for (k = 0; k < n; ++k) {
         int64_t p = piv[k];
@@ -508,11 +510,17 @@ int mwo_solve(int w, int64_t n, const double *LU, int64_t lda, const int64_t *pi
             st_m(w, y, n, i, res);
         }
     }
-    for (j = n - 1; j >= 0; --j) {
-        double yj[4], ujj[4], xj[4];
-        ld_m(w, y, n, j, yj);
+    for (j = 0; j < n; ++j) {
+        double one[4] = {1.0, 0.0, 0.0, 0.0}, ujj[4], dj[4];
         ld_m(w, LU, plane, j * lda + j, ujj);
-        mw_div(w, yj, ujj, xj);
+        mw_div(w, one, ujj, dj);
+        st_m(w, d, n, j, dj);
+    }
+    for (j = n - 1; j >= 0; --j) {
+        double yj[4], dj[4], xj[4];
+        ld_m(w, y, n, j, yj);
+        ld_m(w, d, n, j, dj);
+        mw_mul(w, yj, dj, xj);
         st_m(w, y, n, j, xj);
         for (i = 0; i < j; ++i) {
             double u[4], yi[4], prod[4], res[4];
@@ -525,6 +533,7 @@ int mwo_solve(int w, int64_t n, const double *LU, int64_t lda, const int64_t *pi
     }
     memcpy(x, y, sizeof(double) * (size_t)(w * n));
     free(y);
+    free(d);
     return 0;
 }
 

@@ -196,9 +196,11 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 }
 
 // ---------------------------------------------------------------------------
-// substitution of one system per CTA (column-oriented; x may alias b).
+// substitution of one system per CTA (column-oriented; x may alias b):
+// y = P b, y_i -= l_ij y_j (j ascending), d_j = 1 / u_jj for all j, then
+// x_j = y_j d_j and y_i -= u_ij x_j (j descending).
 // Systems whose state is not "running" are skipped when st is given.
-// dynamic shared memory: W * nmax doubles
+// dynamic shared memory: 2 * W * nmax doubles
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(kBatchThreads)
@@ -250,12 +252,27 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
       }
       __syncthreads();
     }
+    // reciprocals of the diagonal, all j in parallel
+    double* dsm = bsm + W * nmax;
+    for (int j = tid; j < n; j += kBatchThreads) {
+      val<W> one;
+#pragma unroll
+      for (int c = 0; c < W; ++c) one.v[c] = 0.0;
+      one.v[0] = 1.0;
+      const val<W> dj = div<W>(one, load_ro<W>(a, plane, (int64_t)j * n + j));
+#pragma unroll
+      for (int c = 0; c < W; ++c) dsm[c * nmax + j] = dj.v[c];
+    }
+    __syncthreads();
     for (int j = n - 1; j >= 0; --j) {
       if (tid == 0) {
-        val<W> yj;
+        val<W> yj, dj;
 #pragma unroll
-        for (int c = 0; c < W; ++c) yj.v[c] = bsm[c * nmax + j];
-        yj = div<W>(yj, load_ro<W>(a, plane, (int64_t)j * n + j));
+        for (int c = 0; c < W; ++c) {
+          yj.v[c] = bsm[c * nmax + j];
+          dj.v[c] = dsm[c * nmax + j];
+        }
+        yj = mul<W>(yj, dj);
 #pragma unroll
         for (int c = 0; c < W; ++c) bsm[c * nmax + j] = yj.v[c];
       }
@@ -528,7 +545,7 @@ static int solve_batched_launch(int count, int nmax, const int* order, const int
   if (count <= 0) return MW_OK;
   BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
   MW_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(BatchCursor), s));
-  const size_t shmem = sizeof(double) * W * (size_t)nmax;
+  const size_t shmem = sizeof(double) * 2 * W * (size_t)nmax;
   int rc = set_smem(k_solve_batched<W>, shmem);
   if (rc) return rc;
   ProfScope ps(kPhBatchSolve, s);

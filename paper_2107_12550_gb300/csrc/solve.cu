@@ -1,16 +1,17 @@
 // solve.cu -- forward/back substitution with the factors of the blocked LU
 // (Section 2, Listing 1: SolveTDLSPM).
 //
-// y = P b; y_i -= l_ij y_j (j ascending); x_j = y_j / u_jj and
-// y_i -= u_ij x_j (j descending).  One cooperative launch runs a wavefront
-// over block-rows of 32: each warp owns block-rows (lane = row) and keeps
-// their values in registers.  For block-row I it waits, block by block, for
-// the ready flag of every block J < I (forward) or J > I (back), applies that
-// block's 32 updates in order with the published values, then solves its own
-// diagonal block with shuffles, publishes the result and raises its flag.
-// No grid-wide barrier is needed.  Each entry sees the same sequence of
-// rounded multiply-subtract steps as the column-by-column algorithm, so the
-// result is bitwise identical to it.
+// y = P b; y_i -= l_ij y_j (j ascending); d_j = 1 / u_jj for every j (a
+// parallel prologue), then x_j = y_j d_j and y_i -= u_ij x_j (j
+// descending).  One cooperative launch runs a row-granular wavefront over
+// block-rows of 32: each warp owns block-rows (lane = row) and keeps their
+// values in registers.  A row's value is published to a work buffer the moment
+// it is final; the buffers start filled with a NaN sentinel that no
+// computation produces, so a consumer knows a published value by its bits
+// alone and applies rows as soon as they appear.  The critical path is one
+// multiply-subtract per row.  Each entry sees the same sequence of rounded
+// steps as the column-by-column algorithm, so the result is bitwise
+// identical to it.
 #include <algorithm>
 #include <cuda_runtime.h>
 
@@ -24,20 +25,19 @@ namespace mw {
 constexpr int kSolveBlock = 32;
 constexpr int kSolveMaxOwned = 8;              // block-rows per warp kept in registers
 constexpr int64_t kPermSmemMax = 26 * 1024;   // pivots handled in shared memory up to here
+constexpr unsigned long long kSentinel = 0x7FF4DEADBEEF5EA1ull;   // a NaN payload no operation produces
 
-// solve work buffer: [status | perm (int32 n) | ready flags (int32 per block) | y (w planes of n)]
+// solve work buffer: [status | perm (int32 n) | y | x | d], y/x/d: w planes of n
 constexpr size_t kSolveWsPerm = 256;
-__host__ __device__ inline size_t solve_ws_flags(int64_t n) {
+__host__ __device__ inline size_t solve_ws_y(int64_t n) {
   return (kSolveWsPerm + 4 * (size_t)n + 255) & ~(size_t)255;
 }
+__host__ __device__ inline size_t solve_vec_bytes(int w, int64_t n) {
+  return (sizeof(double) * (size_t)w * (size_t)(n > 0 ? n : 1) + 255) & ~(size_t)255;
+}
 __host__ __device__ inline int64_t solve_nblk(int64_t n) { return (n + kSolveBlock - 1) / kSolveBlock; }
-__host__ __device__ inline size_t solve_ws_y(int64_t n) {
-  return solve_ws_flags(n) + ((4 * (size_t)solve_nblk(n) + 255) & ~(size_t)255);
-}
 
-size_t solve_workspace_bytes(int w, int64_t n) {
-  return solve_ws_y(n) + align256(sizeof(double) * (size_t)w * (size_t)(n > 0 ? n : 1));
-}
+size_t solve_workspace_bytes(int w, int64_t n) { return solve_ws_y(n) + 3 * solve_vec_bytes(w, n); }
 
 // perm[i] = index of b that lands in row i after the swaps piv[0..n-1]
 __global__ void __launch_bounds__(1024) k_perm(int64_t n, const int64_t* __restrict__ piv,
@@ -74,32 +74,59 @@ __device__ __forceinline__ val<W> shfl_val(const val<W>& v, int src) {
   return z;
 }
 
-__device__ __forceinline__ int ld_acquire_i32(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_i32(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// lane 0 waits (bounded) until flags[J] >= level; false if it gave up
-__device__ __forceinline__ bool wait_flag(const int* flags, int64_t J, int level, DeviceStatus* status, int tag) {
-  int ok = 1;
-  if ((threadIdx.x & 31) == 0) {
-    unsigned long long spins = 0;
-    while (ld_acquire_i32(flags + J) < level) {
-      if (++spins > kSpinLimit) {
-        atomicExch(&status->timeout, 1u);
-        atomicExch(&status->where, (unsigned)tag);
-        ok = 0;
-        break;
-      }
-      __nanosleep(20);
+// reciprocals of the diagonal and the sentinel fill of the y/x buffers
+template <int W>
+__global__ void k_solve_prep(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
+                             char* __restrict__ ws) {
+  double* y = reinterpret_cast<double*>(ws + solve_ws_y(n));
+  double* xb = y + solve_vec_bytes(W, n) / sizeof(double);
+  double* d = xb + solve_vec_bytes(W, n) / sizeof(double);
+  const double sent = __longlong_as_double((long long)kSentinel);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    val<W> one;
+#pragma unroll
+    for (int c = 0; c < W; ++c) one.v[c] = 0.0;
+    one.v[0] = 1.0;
+    const val<W> dj = div<W>(one, load_ro<W>(LU, plane, q * lda + q));
+    store<W>(d, n, q, dj);
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      y[c * n + q] = sent;
+      xb[c * n + q] = sent;
     }
   }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  return ok != 0;
+}
+
+__device__ __forceinline__ bool is_sent(double v) {
+  return (unsigned long long)__double_as_longlong(v) == kSentinel;
+}
+
+// lanes [lo, hi) load a published value; returns the ballot of ready lanes
+template <int W>
+__device__ __forceinline__ unsigned poll_block(const double* buf, int64_t n, int64_t base, int lo, int hi, val<W>& v) {
+  const int lane = threadIdx.x & 31;
+  bool ok = false;
+  if (lane >= lo && lane < hi) {
+    ok = true;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      v.v[c] = __ldcv(buf + c * n + base + lane);
+      ok = ok && !is_sent(v.v[c]);
+    }
+  }
+  return __ballot_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ bool spin_backoff(unsigned long long& spins, DeviceStatus* status, int tag) {
+  if (++spins > kSpinLimit) {
+    if ((threadIdx.x & 31) == 0) {
+      atomicExch(&status->timeout, 1u);
+      atomicExch(&status->where, (unsigned)tag);
+    }
+    return false;
+  }
+  __nanosleep(32);
+  return true;
 }
 
 // One warp per CTA; warp b owns block-rows b, b + G, b + 2G, ...
@@ -109,14 +136,15 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
         const double* b, double* x, char* __restrict__ ws) {
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
   const int* perm = reinterpret_cast<const int*>(ws + kSolveWsPerm);
-  int* flags = reinterpret_cast<int*>(ws + solve_ws_flags(n));
   double* y = reinterpret_cast<double*>(ws + solve_ws_y(n));
+  double* xb = y + solve_vec_bytes(W, n) / sizeof(double);
+  const double* d = xb + solve_vec_bytes(W, n) / sizeof(double);
   const int lane = threadIdx.x & 31;
   const int64_t G = gridDim.x;
   const int64_t nblk = solve_nblk(n);
 
-  // gather y = P b for every owned block-row (before any flag is raised, so
-  // b may alias x)
+  // gather y = P b for every owned block-row (before anything is published,
+  // so b may alias x)
   val<W> yr[kSolveMaxOwned];
 #pragma unroll
   for (int q = 0; q < kSolveMaxOwned; ++q) {
@@ -140,29 +168,34 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
     const bool row_ok = i < n;
     val<W> acc = yr[q];
     for (int64_t J = 0; J < I; ++J) {
-      if (!wait_flag(flags, J, 1, status, 21)) return;
-      const val<W> yJ = load_cg<W>(y, n, J * kSolveBlock + lane);
-      for (int jj = 0; jj < kSolveBlock; ++jj) {
-        const val<W> yj = shfl_val<W>(yJ, jj);
-        if (row_ok) {
-          const val<W> l = load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i);
-          acc = msub<W>(acc, l, yj);
+      int done = 0;
+      unsigned long long spins = 0;
+      while (done < kSolveBlock) {
+        val<W> v;
+        const unsigned mask = poll_block<W>(y, n, J * kSolveBlock, done, kSolveBlock, v);
+        const unsigned notready = ~(mask >> done);
+        const int k = notready ? __ffs(notready) - 1 : kSolveBlock - done;
+        if (k == 0) {
+          if (!spin_backoff(spins, status, 31)) return;
+          continue;
         }
+        for (int jj = done; jj < done + k; ++jj) {
+          const val<W> yj = shfl_val<W>(v, jj);
+          if (row_ok) acc = msub<W>(acc, load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i), yj);
+        }
+        done += k;
       }
     }
     const int jb = (int)((n - I * kSolveBlock < kSolveBlock) ? n - I * kSolveBlock : kSolveBlock);
     for (int jj = 0; jj < jb; ++jj) {
-      const val<W> yj = shfl_val<W>(acc, jj);
-      if (lane > jj && lane < jb) {
-        const val<W> l = load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i);
-        acc = msub<W>(acc, l, yj);
+      if (lane == jj) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) __stcg(y + c * n + i, acc.v[c]);
       }
+      const val<W> yj = shfl_val<W>(acc, jj);
+      if (lane > jj && lane < jb) acc = msub<W>(acc, load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i), yj);
     }
-    if (row_ok) store_cg<W>(y, n, i, acc);
     yr[q] = acc;
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release_i32(flags + I, 1);
   }
 
   // back: upper U, block-rows in decreasing order
@@ -174,38 +207,36 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
     const bool row_ok = i < n;
     val<W> acc = yr[q];
     for (int64_t J = nblk - 1; J > I; --J) {
-      if (!wait_flag(flags, J, 2, status, 22)) return;
       const int jbJ = (int)((n - J * kSolveBlock < kSolveBlock) ? n - J * kSolveBlock : kSolveBlock);
-      val<W> xJ;
-      if (lane < jbJ) xJ = load_cg<W>(y, n, J * kSolveBlock + lane);
-      else {
-#pragma unroll
-        for (int c = 0; c < W; ++c) xJ.v[c] = 0.0;
-      }
-      for (int jj = jbJ - 1; jj >= 0; --jj) {
-        const val<W> xj = shfl_val<W>(xJ, jj);
-        if (row_ok) {
-          const val<W> u = load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i);
-          acc = msub<W>(acc, u, xj);
+      int done = jbJ;   // rows [0, done) of block J still to apply, from done-1 down
+      unsigned long long spins = 0;
+      while (done > 0) {
+        val<W> v;
+        const unsigned mask = poll_block<W>(xb, n, J * kSolveBlock, 0, done, v);
+        const unsigned top = (done == 32) ? mask : (mask << (32 - done));
+        int k = __clz(~top);
+        if (k > done) k = done;
+        if (k == 0) {
+          if (!spin_backoff(spins, status, 32)) return;
+          continue;
         }
+        for (int jj = done - 1; jj >= done - k; --jj) {
+          const val<W> xj = shfl_val<W>(v, jj);
+          if (row_ok) acc = msub<W>(acc, load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i), xj);
+        }
+        done -= k;
       }
     }
     const int jb = (int)((n - I * kSolveBlock < kSolveBlock) ? n - I * kSolveBlock : kSolveBlock);
     for (int jj = jb - 1; jj >= 0; --jj) {
       if (lane == jj) {
-        const val<W> ujj = load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i);
-        acc = div<W>(acc, ujj);
+        acc = mul<W>(acc, load_ro<W>(d, n, i));
+#pragma unroll
+        for (int c = 0; c < W; ++c) __stcg(xb + c * n + i, acc.v[c]);
       }
       const val<W> xj = shfl_val<W>(acc, jj);
-      if (lane < jj) {
-        const val<W> u = load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i);
-        acc = msub<W>(acc, u, xj);
-      }
+      if (lane < jj) acc = msub<W>(acc, load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i), xj);
     }
-    if (row_ok) store_cg<W>(y, n, i, acc);
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) st_release_i32(flags + I, 2);
     if (row_ok) {
 #pragma unroll
       for (int c = 0; c < W; ++c) x[c * n + i] = acc.v[c];
@@ -246,7 +277,11 @@ int solve_with_perm(int64_t n, const double* LU, int64_t lda, const double* b, d
   if (nblk > G * kSolveMaxOwned) return MW_EUNSUPPORTED;
   G = std::max<int64_t>(G, (nblk + kSolveMaxOwned - 1) / kSolveMaxOwned);
   MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kSolveWsPerm, s));
-  MW_CUDA_CHECK(cudaMemsetAsync(ws + solve_ws_flags(n), 0, 4 * (size_t)nblk, s));
+  {
+    const int pg = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)sm_count_solve());
+    k_solve_prep<W><<<std::max(pg, 1), 256, 0, s>>>(LU, lda, plane, n, ws);
+    MW_LAUNCH_CHECK();
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(32);

@@ -15,7 +15,9 @@ import time
 
 def main(argv=None) -> int:
     p = argparse.ArgumentParser()
-    p.add_argument("--op", default="lu", choices=["lu", "solve", "residual", "refine"])
+    p.add_argument("--op", default="lu", choices=["lu", "solve", "residual", "refine", "batched_lu"])
+    p.add_argument("--count", type=int, default=512, help="systems in a batch (batched_lu)")
+    p.add_argument("--nmax", type=int, default=256, help="largest order in a batch (batched_lu)")
     p.add_argument("--prec", type=int, default=3)
     p.add_argument("--n", type=int, default=2048)
     p.add_argument("--update", default="plain", choices=["plain", "split"])
@@ -25,6 +27,17 @@ def main(argv=None) -> int:
     import torch
     from . import api, build, workloads as W
     build.build()
+    if a.op == "batched_lu":
+        n_list = [int(v) for v in W.batch_sizes(a.count, 16, a.nmax, seed=0)]
+        mats = [W.uniform_matrix(m, a.prec, seed=W.system_seed(0, i), lda=m) for i, m in enumerate(n_list)]
+        Ab = torch.from_numpy(api.pack_matrices(mats, a.prec)).cuda()
+        t0 = time.perf_counter()
+        for _ in range(a.repeat):
+            api.ludecomp_batched(Ab, n_list, a.prec)
+        torch.cuda.synchronize()
+        print(f"batched_lu prec={a.prec} count={a.count} n<={a.nmax} x{a.repeat}: "
+              f"{(time.perf_counter() - t0) / a.repeat * 1e3:.1f} ms per call")
+        return 0
     if a.op == "refine":
         s = W.svd_system(a.n, 10.0, seed=0)
         A, b = s.A, s.b

@@ -67,6 +67,6 @@ def test_noalloc_solve_matches_solve_twice(lib):
 
 def test_noalloc_rejects_orders_beyond_scratch(lib):
     # checked on the host before any GPU work: -2 (the order n is invalid)
-    assert lib.mw_solve_noalloc(4, 58041, 8, 58041, 8, 8, 8, None) == -2
-    assert lib.mw_solve_noalloc(2, 104193, 8, 104193, 8, 8, 8, None) == -2
+    assert lib.mw_solve_noalloc(4, 20969, 8, 20969, 8, 8, 8, None) == -2
+    assert lib.mw_solve_noalloc(2, 40321, 8, 40321, 8, 8, 8, None) == -2
     assert lib.mw_solve_noalloc(4, 10, 8, 5, 8, 8, 8, None) == -4
