@@ -43,6 +43,12 @@ WORKLOAD = "svd_kappa1e10_n2048_qd_stored_td_inner_refine_to_2^-200"
 # (all error terms non-zero) path
 FP64_PER_MSUB = {2: 29, 3: 117, 4: 196}
 
+# DRAM bytes (read + write) per launch of the TD plain trailing update in this
+# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum over the 124
+# launches of one bench run (warm-up, one step, the end-to-end steps),
+# averaged per launch.  Must be re-measured whenever k_gemm_plain changes.
+GEMM_TD_TRAFFIC_PER_LAUNCH = 40.45e6
+
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -445,7 +451,8 @@ def main():
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "flop": "one FP64 instruction (DADD/DMUL/DFMA)",
                      "peak_source": "measured: mw_peak_fp64 microbenchmark in this run",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None, "traffic": GEMM_TD_TRAFFIC_PER_LAUNCH,
+                     "traffic_unit": "bytes per launch (ncu)",
                      "algorithmic_per_launch": instr / max(gemm_launches, 1)},
         "gpu_launches": launches,
         "clocks": clk,

@@ -342,7 +342,8 @@ __device__ __forceinline__ double i192_take_rn(I192& R, int scale) {
 // ---------------------------------------------------------------------------
 // the tensor-core kernel: one CTA per 128 x 32 output tile
 // warp 0: bulk-copy producer; warp 1: TMEM owner + MMA issuer;
-// warps 2..5: epilogue (TMEM lane quarter = warp % 4)
+// warps 2..9: epilogue (TMEM lane quarter = warp % 4; warps 2..5 take
+// columns 0..15 of the tile, warps 6..9 columns 16..31)
 // ---------------------------------------------------------------------------
 struct SplitSmem {
   unsigned char b[kS][kBSliceBytes];       // all B slices of the tile (60 KB)
@@ -355,7 +356,8 @@ struct SplitSmem {
   int abort;
 };
 
-constexpr int kSplitThreads = 192;
+constexpr int kEpiWarps = 8;                       // two warpgroups over the 4 TMEM lane quarters
+constexpr int kSplitThreads = 64 + 32 * kEpiWarps;  // producer + MMA warps + epilogue
 
 __global__ void __launch_bounds__(kSplitThreads, 1)
 k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int64_t N,
@@ -434,8 +436,9 @@ k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int
       tc::mma_commit(&sm.mma_done);
     }
   } else {
-    // epilogue: thread <-> row (TMEM lane) of the tile
+    // epilogue: thread <-> row (TMEM lane) of the tile, half of the columns
     const int quarter = warp & 3;
+    const int chalf = (warp - 2) / 4;
     const int rr = quarter * 32 + lane;
     const int64_t i = tm * kTileM + rr;
     bool ok = tc::mbar_wait(&sm.mma_done, 0);
@@ -447,7 +450,7 @@ k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int
     } else {
       const int ei = (i < m) ? ea[i] : 0;
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-      for (int c4 = 0; c4 < kTileN; c4 += 4) {
+      for (int c4 = chalf * (kTileN / 2); c4 < (chalf + 1) * (kTileN / 2); c4 += 4) {
         uint32_t v[kDiag][4];
 #pragma unroll
         for (int d = 0; d < kDiag; ++d) tc::tmem_ld_x4(lane_base + (uint32_t)(d * kTileN + c4), v[d]);
