@@ -57,13 +57,21 @@ __device__ __forceinline__ void warp_argmax(val<W>& v, long long& idx) {
   }
 }
 
+// Candidate record (in the work buffer, per column parity and CTA):
+//   [0, W)          candidate value words
+//   [W]             candidate row index (as int64 bits)
+//   [W+1, W+1+W*nb) the candidate's whole panel row, word-major
+// After the single grid barrier of a column every CTA reads the winner's
+// record, so the pivot row never has to be read from the matrix while its
+// owner may be rewriting it.  The owner of row k also publishes row k's old
+// values (after the records) for the owner of the pivot row, which moves
+// them into its row; the owner of row k writes the pivot row into row k.
 template <int W>
 __global__ void __launch_bounds__(kPanelThreads)
 k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
         int64_t* __restrict__ piv, int64_t* __restrict__ info, char* __restrict__ ws) {
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + kWsBarrier);
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
-  Cand<W>* cand = reinterpret_cast<Cand<W>*>(ws + kWsCand);
 
   const int G = gridDim.x;
   const int cta = blockIdx.x;
@@ -75,15 +83,18 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
   const int64_t r1 = (r0 + chunk < n) ? r0 + chunk : n;
 
   extern __shared__ double smem[];
-  double* su = smem;                 // [W][nb]  pivot row u_kj
+  double* su = smem;                 // [W][nb]  pivot row u_kj (all panel columns)
   double* sl = smem + W * nb;        // [W][chunk]  multipliers of owned rows
   __shared__ Cand<W> wred[kPanelThreads / 32];
-  __shared__ long long s_piv;
-  __shared__ int s_zero;
+  __shared__ long long s_piv, s_best;
+  __shared__ int s_zero, s_wcta;
 
   for (int kk = 0; kk < nb; ++kk) {
     const int64_t k = k0 + kk;
     const int64_t colk = (k0 + kk) * lda;
+    double* rec_base = reinterpret_cast<double*>(ws + kWsCand + (size_t)(kk & 1) * kCandParity);
+    double* rec = rec_base + (size_t)cta * (kCandStride / 8);
+    double* oldk = rec_base + (size_t)kMaxPanelCtas * (kCandStride / 8);
     // (a) local argmax over owned rows i >= k
     val<W> bv;
 #pragma unroll
@@ -107,8 +118,20 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       for (int w = 1; w < kPanelThreads / 32; ++w)
         if (better<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
 #pragma unroll
-      for (int c = 0; c < W; ++c) __stcg(&cand[cta].v.v[c], b.v.v[c]);
-      __stcg(&cand[cta].idx, b.idx);
+      for (int c = 0; c < W; ++c) __stcg(rec + c, b.v.v[c]);
+      __stcg(reinterpret_cast<long long*>(rec + W), b.idx);
+      s_best = b.idx;
+    }
+    __syncthreads();
+    // publish the candidate's whole panel row, and old row k if this CTA owns it
+    {
+      const long long brow = s_best;
+      const bool own_k = (k >= r0 && k < r1);
+      for (int e = tid; e < W * nb; e += kPanelThreads) {
+        const int c = e / nb, j = e % nb;
+        if (brow >= 0) __stcg(rec + W + 1 + e, __ldcg(A + c * plane + (k0 + j) * lda + brow));
+        if (own_k) __stcg(oldk + e, __ldcg(A + c * plane + (k0 + j) * lda + k));
+      }
     }
     if (!grid_sync(bar, status, 1)) return;
     // (b) global argmax from all candidates (every CTA computes the same)
@@ -117,49 +140,61 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
 #pragma unroll
       for (int c = 0; c < W; ++c) gv.v[c] = 0.0;
       long long gi = -1;
+      int gc = -1;
       for (int q = lane; q < G; q += 32) {
+        const double* rq = rec_base + (size_t)q * (kCandStride / 8);
         val<W> v;
 #pragma unroll
-        for (int c = 0; c < W; ++c) v.v[c] = __ldcg(&cand[q].v.v[c]);
-        const long long iq = __ldcg(&cand[q].idx);
+        for (int c = 0; c < W; ++c) v.v[c] = __ldcg(rq + c);
+        const long long iq = __ldcg(reinterpret_cast<const long long*>(rq + W));
         if (better<W>(v, iq, gv, gi)) {
           gv = v;
           gi = iq;
+          gc = q;
         }
       }
-      warp_argmax<W>(gv, gi);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        val<W> ov;
+#pragma unroll
+        for (int c = 0; c < W; ++c) ov.v[c] = __shfl_xor_sync(0xffffffffu, gv.v[c], off);
+        const long long oi = __shfl_xor_sync(0xffffffffu, gi, off);
+        const int oc = __shfl_xor_sync(0xffffffffu, gc, off);
+        if (better<W>(ov, oi, gv, gi)) {
+          gv = ov;
+          gi = oi;
+          gc = oc;
+        }
+      }
       if (lane == 0) {
         s_piv = gi;
+        s_wcta = gc;
         s_zero = is_zero<W>(gv) ? 1 : 0;
       }
     }
     __syncthreads();
     const int64_t p = s_piv;
-    if (cta == 0) {
-      if (tid == 0) {
-        piv[k] = p;
-        if (s_zero && *info == 0) *info = k + 1;
-      }
+    if (cta == 0 && tid == 0) {
+      piv[k] = p;
+      if (s_zero && *info == 0) *info = k + 1;
+    }
+    // (c) pivot row from the winner's record; swap rows k and p
+    {
+      const double* wrec = rec_base + (size_t)s_wcta * (kCandStride / 8) + W + 1;
+      for (int e = tid; e < W * nb; e += kPanelThreads) su[e] = __ldcg(wrec + e);
+      __syncthreads();
       if (p != k) {
-        for (int j = tid; j < nb; j += kPanelThreads) {
-          const int64_t col = (k0 + j) * lda;
-#pragma unroll
-          for (int c = 0; c < W; ++c) {
-            const double a = __ldcg(A + c * plane + col + k);
-            const double b = __ldcg(A + c * plane + col + p);
-            __stcg(A + c * plane + col + k, b);
-            __stcg(A + c * plane + col + p, a);
-          }
+        const bool own_k = (k >= r0 && k < r1);
+        const bool own_p = (p >= r0 && p < r1);
+        for (int e = tid; e < W * nb; e += kPanelThreads) {
+          const int c = e / nb, j = e % nb;
+          if (own_k) __stcg(A + c * plane + (k0 + j) * lda + k, su[e]);
+          if (own_p) __stcg(A + c * plane + (k0 + j) * lda + p, __ldcg(oldk + e));
         }
       }
+      __syncthreads();
     }
-    if (!grid_sync(bar, status, 2)) return;
-    // (c) pivot row into shared memory, multipliers, in-panel update
-    for (int j = kk + tid; j < nb; j += kPanelThreads) {
-#pragma unroll
-      for (int c = 0; c < W; ++c) su[c * nb + j] = __ldcg(A + c * plane + (k0 + j) * lda + k);
-    }
-    __syncthreads();
+    // (d) multipliers and in-panel update of owned rows i > k
     val<W> akk;
 #pragma unroll
     for (int c = 0; c < W; ++c) akk.v[c] = su[c * nb + kk];

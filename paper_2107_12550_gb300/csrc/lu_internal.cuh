@@ -9,15 +9,20 @@ namespace mw {
 
 constexpr int kPanelThreads = 256;
 constexpr int kPanelRowsPerCta = 8;    // panel rows per CTA before adding CTAs
-constexpr int kMaxPanelCtas = 1024;
+constexpr int kMaxPanelCtas = 256;
 constexpr int kDefaultNb = 64;          // panel width of the blocked LU
+constexpr int kMaxNb = 128;
 
 // LU work buffer: [barrier | status | panel candidates | split-update scratch]
+// The candidate area holds, for two column parities, one record per CTA
+// (the candidate value, its row index and a copy of the whole candidate row
+// of the panel) and a copy of the old row k.
 constexpr size_t kWsBarrier = 0;
 constexpr size_t kWsStatus = 64;
 constexpr size_t kWsCand = 256;
-constexpr size_t kCandStride = 48;      // >= sizeof(Cand<4>)
-constexpr size_t kWsSplit = 64 * 1024;  // >= kWsCand + kMaxPanelCtas * kCandStride
+constexpr size_t kCandStride = 8 * (4 + 1 + 4 * kMaxNb);             // doubles of one record, in bytes
+constexpr size_t kCandParity = kCandStride * kMaxPanelCtas + 8 * 4 * kMaxNb;  // records + old row k
+constexpr size_t kWsSplit = (kWsCand + 2 * kCandParity + 65535) & ~(size_t)65535;
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
