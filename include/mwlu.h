@@ -196,7 +196,7 @@ int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K, double* C
 
 /*
  * Batches of independent systems of uneven order (one launch per step for
- * the whole batch; SURVEY-style "batched persistent form" of the method).
+ * the whole batch: the batched persistent form of the method).
  *   count    number of systems; n_host: HOST int32[count], 1 <= n[s] <= 1024.
  *   Layout (device): with moff[s] = sum_{s'<s} n[s']^2 and
  *   voff[s] = sum_{s'<s} n[s'], system s's matrix of w words is at
@@ -221,6 +221,35 @@ int mw_solve_batched(int prec, int count, const int* n_host, const double* LU, c
 int mw_refine_batched(int count, const int* n_host, const double* A, int a_words, const double* b,
                       int b_words, int inner, int target_bits, int max_iter, double* x, int x_words,
                       int64_t* stats, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Blocked batched LU (Section 2: the blocked LU with its block matrix
+ * product, applied to a whole batch at once).  Same packed layout, pivots,
+ * info and stats as above; n[s] <= 1024.  All systems advance one panel of
+ * 64 columns per step: the panels of the systems still active (one CTA
+ * each), their row swaps and U12 = L11^-1 A12, then ONE trailing-update
+ * launch over the tiles of every active system.
+ *   update   MW_UPDATE_PLAIN: the plain multiword GEMM; every system's
+ *            factors are bitwise identical to mw_ludecomp / the persistent
+ *            mw_ludecomp_batched.
+ *            MW_UPDATE_SPLIT (DD only, else MW_EUNSUPPORTED): the
+ *            split-precision tensor-core GEMM of mw_ludecomp, with its
+ *            per-entry error bound 2^-107 max|l| max|u| per update.
+ * mw_batch_blocked_workspace_size: op MW_OP_LUDECOMP or MW_OP_REFINE; the
+ *   work buffer holds the plan, the per-step tile lists and, for the split
+ *   update, the bf16 digit slices of the largest step.
+ * mw_refine_batched_blocked: mw_refine_batched with the inner LU factored by
+ *   the blocked batched LU (`update` as above; split needs inner = MW_DD).
+ * Returns MW_OK, -i, MW_ECUDA or MW_EUNSUPPORTED.
+ */
+int mw_batch_blocked_workspace_size(int op, int prec, int update, int count, const int* n_host,
+                                    size_t* bytes);
+int mw_ludecomp_batched_blocked(int prec, int update, int count, const int* n_host, double* A,
+                                int64_t* piv, int64_t* info, void* work, size_t work_bytes, void* stream);
+int mw_refine_batched_blocked(int count, const int* n_host, const double* A, int a_words,
+                              const double* b, int b_words, int inner, int update, int target_bits,
+                              int max_iter, double* x, int x_words, int64_t* stats, void* work,
+                              size_t work_bytes, void* stream);
 
 /*
  * mw_arith -- element-wise multiword arithmetic on device arrays (the

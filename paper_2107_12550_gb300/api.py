@@ -274,6 +274,59 @@ def refine_batched(A: torch.Tensor, a_words: int, b: torch.Tensor, b_words: int,
     return x, stats
 
 
+def _update(update) -> int:
+    if update in ("plain", L.MW_UPDATE_PLAIN):
+        return L.MW_UPDATE_PLAIN
+    if update in ("split", L.MW_UPDATE_SPLIT):
+        return L.MW_UPDATE_SPLIT
+    raise ValueError(f"update must be 'plain' or 'split', not {update!r}")
+
+
+def batch_blocked_workspace(op: int, prec: int, update, n_list, device=None) -> torch.Tensor:
+    out = ctypes.c_size_t(0)
+    L.check("mw_batch_blocked_workspace_size",
+            L.lib().mw_batch_blocked_workspace_size(op, prec, _update(update), len(n_list), _n_host(n_list),
+                                                    ctypes.byref(out)))
+    return torch.empty(max(int(out.value), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def ludecomp_batched_blocked(A: torch.Tensor, n_list, prec="dd", update="plain", *, work=None, stream=None,
+                             inplace=False):
+    """Blocked batched LU (packed layout): all systems advance one 64-column
+    panel per step; the trailing update of every active system is one launch
+    (plain multiword GEMM or, for DD, the split tensor-core form).
+    Returns (LU, piv, info)."""
+    w = _prec(prec)
+    u = _update(update)
+    LU = A if inplace else A.clone()
+    total_n = int(sum(n_list))
+    piv = torch.empty(max(total_n, 1), dtype=torch.int64, device=A.device)
+    info = torch.zeros(max(len(n_list), 1), dtype=torch.int64, device=A.device)
+    if work is None:
+        work = batch_blocked_workspace(L.MW_OP_LUDECOMP, w, u, n_list, A.device)
+    L.check("mw_ludecomp_batched_blocked", L.lib().mw_ludecomp_batched_blocked(
+        w, u, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(info), _ptr(work), work.numel(),
+        _stream(stream)))
+    return LU, piv, info
+
+
+def refine_batched_blocked(A: torch.Tensor, a_words: int, b: torch.Tensor, b_words: int, n_list,
+                           inner_prec="dd", update="split", target_bits: int = 200, *, max_iter: int = 30,
+                           x_words: int = 8, work=None, out=None, stream=None):
+    """refine_batched with the inner LU factored by the blocked batched LU."""
+    w = _prec(inner_prec)
+    u = _update(update)
+    total_n = int(sum(n_list))
+    x = out if out is not None else torch.empty(x_words * total_n, dtype=torch.float64, device=A.device)
+    stats = torch.zeros((len(n_list), 4), dtype=torch.int64, device=A.device)
+    if work is None:
+        work = batch_blocked_workspace(L.MW_OP_REFINE, w, u, n_list, A.device)
+    L.check("mw_refine_batched_blocked", L.lib().mw_refine_batched_blocked(
+        len(n_list), _n_host(n_list), _ptr(A), a_words, _ptr(b), b_words, w, u, target_bits, max_iter,
+        _ptr(x), x_words, _ptr(stats), _ptr(work), work.numel(), _stream(stream)))
+    return x, stats
+
+
 def arith(op: int, prec, x: torch.Tensor, y: torch.Tensor, *, stream=None) -> torch.Tensor:
     """Element-wise multiword op (0 add, 1 sub, 2 mul, 3 div, 4 compare |x|,|y|)."""
     w = _prec(prec)

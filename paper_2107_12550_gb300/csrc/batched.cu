@@ -629,6 +629,128 @@ static int upload_plan(const BatchPlanHost& p, int count, char* ws, BatchPlanDev
   return MW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// blocked batched LU: all systems advance one panel of kBatchNb columns per
+// step.  Step k0 factors the panels of the systems with n > k0 (one CTA
+// each), applies their swaps left of the panel, solves U12 = L11^-1 A12 and
+// runs the trailing update A22 -= L21 U12 as one launch over a tile list
+// that spans all active systems (plain multiword GEMM, or the split form for
+// DD).  The plan below holds, per step, the active count, the grid extents
+// and the tile lists; it is computed on the host from n and uploaded with
+// the batch plan.
+// ---------------------------------------------------------------------------
+struct BlockedPlanHost {
+  int update = MW_UPDATE_PLAIN;
+  int nsteps = 0;
+  std::vector<int> act, max_cb_trsm, max_mt, max_cb_slice;
+  std::vector<int64_t> toff, boff;   // per step: first tile, first base (nsteps + 1 entries)
+  std::vector<TileEntry> tiles;
+  std::vector<int2> bases;           // split: {first A-slice tile, first B-slice tile} per (step, pos)
+  int64_t a_tiles = 0, b_tiles = 0;  // split: slice tiles of the largest step
+};
+
+static void make_blocked_plan(const BatchPlanHost& p, int W, int update, BlockedPlanHost& bp) {
+  bp = BlockedPlanHost();
+  bp.update = update;
+  const bool split = update == MW_UPDATE_SPLIT;
+  int bm = 0, bn = 0;
+  gemm_plain_tile_shape(W, &bm, &bn);
+  if (split) {
+    bm = kSplitTileM;
+    bn = kSplitTileN;
+  }
+  const int count = (int)p.n.size();
+  bp.toff.push_back(0);
+  bp.boff.push_back(0);
+  if (count == 0) return;
+  int act = count;
+  for (int k0 = 0; k0 < p.nmax; k0 += kBatchNb) {
+    while (act > 0 && p.n[p.order[act - 1]] <= k0) --act;   // order is largest first
+    bp.act.push_back(act);
+    const int m0 = p.n[p.order[0]] - k0 - kBatchNb;          // largest trailing order
+    bp.max_cb_trsm.push_back(m0 > 0 ? (m0 + 7) / 8 : 0);
+    bp.max_mt.push_back(m0 > 0 ? (m0 + kSplitTileM - 1) / kSplitTileM : 0);
+    bp.max_cb_slice.push_back(m0 > 0 ? ((m0 + kSplitTileN - 1) / kSplitTileN * kSplitTileN + 127) / 128 : 0);
+    int64_t at = 0, btl = 0;
+    for (int pos = 0; pos < act; ++pos) {
+      const int m = p.n[p.order[pos]] - k0 - kBatchNb;
+      if (split) bp.bases.push_back(make_int2((int)at, (int)btl));
+      if (m <= 0) continue;
+      const int mt = (m + bm - 1) / bm, nt = (m + bn - 1) / bn;
+      for (int tj = 0; tj < nt; ++tj)
+        for (int ti = 0; ti < mt; ++ti) bp.tiles.push_back(TileEntry{pos, ti, tj, 0});
+      at += mt;
+      btl += nt;
+    }
+    if (split) {
+      bp.a_tiles = std::max(bp.a_tiles, at);
+      bp.b_tiles = std::max(bp.b_tiles, btl);
+    }
+    bp.toff.push_back((int64_t)bp.tiles.size());
+    bp.boff.push_back((int64_t)bp.bases.size());
+    ++bp.nsteps;
+  }
+}
+
+// [tiles | bases | split scratch]
+static size_t blocked_extra_bytes(const BlockedPlanHost& bp) {
+  size_t b = align256(sizeof(TileEntry) * std::max<size_t>(1, bp.tiles.size())) +
+             align256(sizeof(int2) * std::max<size_t>(1, bp.bases.size()));
+  if (bp.update == MW_UPDATE_SPLIT) b += split_batched_workspace_bytes(bp.a_tiles, bp.b_tiles);
+  return b;
+}
+
+struct BlockedDev {
+  TileEntry* tiles;
+  int2* bases;
+  char* split_ws;
+  size_t split_bytes;
+};
+
+static int upload_blocked(const BlockedPlanHost& bp, char* base, BlockedDev& d, cudaStream_t s) {
+  size_t off = 0;
+  d.tiles = reinterpret_cast<TileEntry*>(base + off);
+  off += align256(sizeof(TileEntry) * std::max<size_t>(1, bp.tiles.size()));
+  d.bases = reinterpret_cast<int2*>(base + off);
+  off += align256(sizeof(int2) * std::max<size_t>(1, bp.bases.size()));
+  d.split_ws = base + off;
+  d.split_bytes = bp.update == MW_UPDATE_SPLIT ? split_batched_workspace_bytes(bp.a_tiles, bp.b_tiles) : 0;
+  if (!bp.tiles.empty())
+    MW_CUDA_CHECK(cudaMemcpyAsync(d.tiles, bp.tiles.data(), sizeof(TileEntry) * bp.tiles.size(),
+                                  cudaMemcpyHostToDevice, s));
+  if (!bp.bases.empty())
+    MW_CUDA_CHECK(cudaMemcpyAsync(d.bases, bp.bases.data(), sizeof(int2) * bp.bases.size(),
+                                  cudaMemcpyHostToDevice, s));
+  if (d.split_bytes) MW_CUDA_CHECK(cudaMemsetAsync(d.split_ws, 0, 256, s));
+  return MW_OK;
+}
+
+template <int W>
+static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d, const BlockedPlanHost& bp,
+                                  const BlockedDev& bd, double* A, int64_t* piv, int64_t* info, cudaStream_t s) {
+  const BatchView bv{d.order, d.n, d.moff, d.voff};
+  for (int st = 0; st < bp.nsteps; ++st) {
+    const int k0 = st * kBatchNb;
+    const int act = bp.act[st];
+    int rc = launch_bpanel<W>(bv, act, p.nmax, k0, A, piv, info, s);
+    if (rc) return rc;
+    rc = launch_blaswp<W>(bv, act, k0, A, piv, s);
+    if (rc) return rc;
+    rc = launch_btrsm<W>(bv, act, bp.max_cb_trsm[st], k0, A, piv, s);
+    if (rc) return rc;
+    const int64_t ntiles = bp.toff[st + 1] - bp.toff[st];
+    if (bp.update == MW_UPDATE_SPLIT) {
+      if (W != 2) return MW_EUNSUPPORTED;
+      rc = split_bupdate_dd(bv, act, bp.max_mt[st], bp.max_cb_slice[st], bd.tiles + bp.toff[st], ntiles,
+                            bd.bases + bp.boff[st], bp.a_tiles, bp.b_tiles, k0, A, bd.split_ws, bd.split_bytes, s);
+    } else {
+      rc = launch_bgemm_plain<W>(bv, bd.tiles + bp.toff[st], ntiles, k0, A, s);
+    }
+    if (rc) return rc;
+  }
+  return MW_OK;
+}
+
 // refinement work buffer map (after the plan)
 struct BatchRefineMap {
   size_t lu, piv, info, r, z, rhat, st, running, total;
@@ -657,10 +779,12 @@ static BatchRefineMap batch_refine_map(int W, int count, int64_t sum_n, int64_t 
   return m;
 }
 
+// blk: null for the persistent one-CTA-per-system LU, else the blocked LU
 template <int W>
 static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPlanDev& d, const double* A, int a_words,
                                const double* b, int b_words, int target_bits, int max_iter, double* x, int x_words,
-                               int64_t* stats, char* ws, size_t ws_bytes, cudaStream_t s) {
+                               int64_t* stats, char* ws, size_t ws_bytes, cudaStream_t s,
+                               const BlockedPlanHost* blk = nullptr, const BlockedDev* blkd = nullptr) {
   const BatchRefineMap mp = batch_refine_map(W, count, p.sum_n, p.sum_n2);
   if (ws_bytes < mp.total) return -15;
   double* LU = reinterpret_cast<double*>(ws + mp.lu);
@@ -676,7 +800,8 @@ static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPla
   prof_count(kPhRefineAux);
   k_bt_take_mat<<<(unsigned)((p.sum_n2 + 255) / 256), 256, 0, s>>>(count, d.moff, d.n, p.sum_n2, A, a_words, LU, W);
   MW_LAUNCH_CHECK();
-  int rc = lu_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, info, cur, s);
+  int rc = blk ? lu_blocked_batched_run<W>(p, d, *blk, *blkd, LU, piv, info, s)
+               : lu_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, info, cur, s);
   if (rc) return rc;
   prof_count(kPhRefineAux);
   k_bt_init_state<<<(count + 255) / 256, 256, 0, s>>>(count, info, st);
@@ -819,5 +944,100 @@ extern "C" int mw_refine_batched(int count, const int* n_host, const double* A, 
     case 2: return mw::refine_batched_impl<2>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, work_bytes, s);
     case 3: return mw::refine_batched_impl<3>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, work_bytes, s);
     default: return mw::refine_batched_impl<4>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, work_bytes, s);
+  }
+}
+
+// ---- blocked batched LU and refinement ---------------------------------------
+extern "C" int mw_batch_blocked_workspace_size(int op, int prec, int update, int count, const int* n_host,
+                                               size_t* bytes) {
+  if (op != MW_OP_LUDECOMP && op != MW_OP_REFINE) return -1;
+  if (!bprec_ok(prec)) return -2;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -3;
+  if (count < 0) return -4;
+  if (count > 0 && !n_host) return -5;
+  if (!bytes) return -6;
+  if (update == MW_UPDATE_SPLIT && prec != MW_DD) return MW_EUNSUPPORTED;
+  mw::BatchPlanHost p;
+  if (!mw::make_plan(count, n_host, p)) return -5;
+  mw::BlockedPlanHost bp;
+  mw::make_blocked_plan(p, prec, update, bp);
+  const size_t head = (op == MW_OP_REFINE) ? mw::batch_refine_map(prec, count, p.sum_n, p.sum_n2).total
+                                           : mw::plan_bytes(count);
+  *bytes = mw::align256(head) + mw::blocked_extra_bytes(bp);
+  return MW_OK;
+}
+
+extern "C" int mw_ludecomp_batched_blocked(int prec, int update, int count, const int* n_host, double* A,
+                                           int64_t* piv, int64_t* info, void* work, size_t work_bytes,
+                                           void* stream) {
+  if (!bprec_ok(prec)) return -1;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
+  if (count < 0) return -3;
+  if (count == 0) return MW_OK;
+  if (!n_host) return -4;
+  if (!A) return -5;
+  if (!piv) return -6;
+  if (!info) return -7;
+  if (!work) return -8;
+  if (update == MW_UPDATE_SPLIT && prec != MW_DD) return MW_EUNSUPPORTED;
+  mw::BatchPlanHost p;
+  if (!mw::make_plan(count, n_host, p)) return -4;
+  mw::BlockedPlanHost bp;
+  mw::make_blocked_plan(p, prec, update, bp);
+  const size_t head = mw::align256(mw::plan_bytes(count));
+  if (work_bytes < head + mw::blocked_extra_bytes(bp)) return -9;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(work);
+  mw::BatchPlanDev d;
+  int rc = mw::upload_plan(p, count, ws, d, s);
+  if (rc) return rc;
+  mw::BlockedDev bd;
+  rc = mw::upload_blocked(bp, ws + head, bd, s);
+  if (rc) return rc;
+  switch (prec) {
+    case 2: return mw::lu_blocked_batched_run<2>(p, d, bp, bd, A, piv, info, s);
+    case 3: return mw::lu_blocked_batched_run<3>(p, d, bp, bd, A, piv, info, s);
+    default: return mw::lu_blocked_batched_run<4>(p, d, bp, bd, A, piv, info, s);
+  }
+}
+
+extern "C" int mw_refine_batched_blocked(int count, const int* n_host, const double* A, int a_words,
+                                         const double* b, int b_words, int inner, int update, int target_bits,
+                                         int max_iter, double* x, int x_words, int64_t* stats, void* work,
+                                         size_t work_bytes, void* stream) {
+  if (count < 0) return -1;
+  if (count == 0) return MW_OK;
+  if (!n_host) return -2;
+  if (!A) return -3;
+  if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
+  if (!b) return -5;
+  if (b_words < 1 || b_words > MW_LONG_WORDS) return -6;
+  if (!bprec_ok(inner)) return -7;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -8;
+  if (target_bits < 1 || target_bits > 1000) return -9;
+  if (max_iter < 0) return -10;
+  if (!x) return -11;
+  if (x_words < inner || x_words > MW_LONG_WORDS) return -12;
+  if (!stats) return -13;
+  if (!work) return -14;
+  if (update == MW_UPDATE_SPLIT && inner != MW_DD) return MW_EUNSUPPORTED;
+  mw::BatchPlanHost p;
+  if (!mw::make_plan(count, n_host, p)) return -2;
+  mw::BlockedPlanHost bp;
+  mw::make_blocked_plan(p, inner, update, bp);
+  const size_t head = mw::align256(mw::batch_refine_map(inner, count, p.sum_n, p.sum_n2).total);
+  if (work_bytes < head + mw::blocked_extra_bytes(bp)) return -15;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(work);
+  mw::BatchPlanDev d;
+  int rc = mw::upload_plan(p, count, ws, d, s);
+  if (rc) return rc;
+  mw::BlockedDev bd;
+  rc = mw::upload_blocked(bp, ws + head, bd, s);
+  if (rc) return rc;
+  switch (inner) {
+    case 2: return mw::refine_batched_impl<2>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
+    case 3: return mw::refine_batched_impl<3>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
+    default: return mw::refine_batched_impl<4>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
   }
 }

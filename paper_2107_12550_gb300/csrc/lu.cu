@@ -261,14 +261,13 @@ __global__ void k_laswp(double* __restrict__ A, int64_t lda, int64_t plane, int6
 // memory; every thread then updates its rows r > t.
 // ---------------------------------------------------------------------------
 template <int W, int NB>
-__global__ void __launch_bounds__(256)
-k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0,
-       const int64_t* __restrict__ piv) {
+__device__ __forceinline__ void trsm_cols(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n,
+                                          int64_t k0, const int64_t* __restrict__ piv, int64_t cblock) {
   constexpr int TC = 8;
   constexpr int NG = 256 / TC;
   constexpr int RPT = (NB + NG - 1) / NG;
   const int c = threadIdx.x % TC, g = threadIdx.x / TC;
-  const int64_t j = k0 + NB + (int64_t)blockIdx.x * TC + c;
+  const int64_t j = k0 + NB + cblock * TC + c;
   const bool active = j < n;
   __shared__ double su[2][W][TC];
   if (active && g < W) {
@@ -328,22 +327,29 @@ k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0
   }
 }
 
+template <int W, int NB>
+__global__ void __launch_bounds__(256)
+k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0,
+       const int64_t* __restrict__ piv) {
+  trsm_cols<W, NB>(A, lda, plane, n, k0, piv, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // plain trailing update: C -= L21 * U12 with per-element sequential t.
 // 16 x 16 threads, micro-tile TM x TN per thread, K chunks of KT staged in
 // shared memory with coalesced loads of each word plane.
 // ---------------------------------------------------------------------------
 template <int W, int TM, int TN>
-__global__ void __launch_bounds__(256)
-k_gemm_plain(double* __restrict__ C, int64_t ldc, int64_t planeC, const double* __restrict__ L,
-             int64_t ldl, int64_t planeL, const double* __restrict__ U, int64_t ldu, int64_t planeU,
-             int64_t m, int64_t N, int K) {
+__device__ __forceinline__ void gemm_plain_tile(double* __restrict__ C, int64_t ldc, int64_t planeC,
+                                                const double* __restrict__ L, int64_t ldl, int64_t planeL,
+                                                const double* __restrict__ U, int64_t ldu, int64_t planeU,
+                                                int64_t m, int64_t N, int K, int64_t tile_i, int64_t tile_j) {
   constexpr int KT = 16;
   constexpr int BM = 16 * TM, BN = 16 * TN;
   __shared__ double sL[W][KT][BM];
   __shared__ double sU[W][KT][BN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t bi = (int64_t)blockIdx.x * BM, bj = (int64_t)blockIdx.y * BN;
+  const int64_t bi = tile_i * BM, bj = tile_j * BN;
 
   val<W> acc[TM][TN];
 #pragma unroll
@@ -403,6 +409,14 @@ k_gemm_plain(double* __restrict__ C, int64_t ldc, int64_t planeC, const double* 
     }
 }
 
+template <int W, int TM, int TN>
+__global__ void __launch_bounds__(256)
+k_gemm_plain(double* __restrict__ C, int64_t ldc, int64_t planeC, const double* __restrict__ L,
+             int64_t ldl, int64_t planeL, const double* __restrict__ U, int64_t ldu, int64_t planeU,
+             int64_t m, int64_t N, int K) {
+  gemm_plain_tile<W, TM, TN>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K, blockIdx.x, blockIdx.y);
+}
+
 template <int W> struct GemmTile;
 template <> struct GemmTile<2> { static constexpr int TM = 4, TN = 4; };
 template <> struct GemmTile<3> { static constexpr int TM = 2, TN = 4; };
@@ -428,6 +442,164 @@ int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64
                       int64_t col0, int64_t N, int64_t k0, int nb, cudaStream_t s) {
   return launch_gemm_plain_ptr<W>(m, N, nb, A + col0 * lda + row0, lda, plane, A + k0 * lda + row0, lda,
                                   plane, A + col0 * lda + k0, lda, plane, s);
+}
+
+// ---------------------------------------------------------------------------
+// batched blocked LU: the same panel / laswp / TRSM / trailing-update steps,
+// for every system of a batch that is still active at panel step k0
+// ---------------------------------------------------------------------------
+
+// one CTA per active system: columns [k0, k0+kb) of rows [k0, n), column by
+// column (argmax, swap inside the panel, multipliers, in-panel update)
+// dynamic shared memory: pivot row [W][kBatchNb] and multipliers [W][nmax]
+template <int W>
+__global__ void __launch_bounds__(kPanelThreads)
+k_bpanel(BatchView bv, int nmax, int k0, double* __restrict__ A, int64_t* __restrict__ piv,
+         int64_t* __restrict__ info) {
+  extern __shared__ double bsm[];
+  double* su = bsm;                  // [W][kBatchNb]
+  double* sl = bsm + W * kBatchNb;   // [W][nmax], rows relative to k0
+  __shared__ Cand<W> wred[kPanelThreads / 32];
+  __shared__ long long s_p;
+  __shared__ int s_zero;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sys = bv.order[blockIdx.x];
+  const int n = bv.n[sys];
+  const int kb = min(kBatchNb, n - k0);
+  double* a = A + (int64_t)W * bv.moff[sys];
+  const int64_t plane = (int64_t)n * n;
+  int64_t* pv = piv + bv.voff[sys];
+  int64_t inf = (k0 == 0) ? 0 : info[sys];
+  for (int kk = 0; kk < kb; ++kk) {
+    const int k = k0 + kk;
+    const int64_t colk = (int64_t)k * n;
+    val<W> bvv;
+#pragma unroll
+    for (int c = 0; c < W; ++c) bvv.v[c] = 0.0;
+    long long bi = -1;
+    for (int i = k + tid; i < n; i += kPanelThreads) {
+      const val<W> v = load<W>(a, plane, colk + i);
+      if (better<W>(v, i, bvv, bi)) {
+        bvv = v;
+        bi = i;
+      }
+    }
+    warp_argmax<W>(bvv, bi);
+    if (lane == 0) {
+      wred[warp].v = bvv;
+      wred[warp].idx = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      Cand<W> b = wred[0];
+      for (int w = 1; w < kPanelThreads / 32; ++w)
+        if (better<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
+      s_p = b.idx;
+      s_zero = is_zero<W>(b.v) ? 1 : 0;
+      pv[k] = b.idx;
+    }
+    __syncthreads();
+    const int p = (int)s_p;
+    if (s_zero && inf == 0) inf = k + 1;
+    // swap rows k and p inside the panel; cache the new row k
+    for (int e = tid; e < W * kb; e += kPanelThreads) {
+      const int c = e / kb, j = e % kb;
+      double* col = a + c * plane + (int64_t)(k0 + j) * n;
+      const double x = col[k];
+      const double y = col[p];
+      if (p != k) {
+        col[k] = y;
+        col[p] = x;
+      }
+      su[c * kBatchNb + j] = (p != k) ? y : x;
+    }
+    __syncthreads();
+    val<W> akk;
+#pragma unroll
+    for (int c = 0; c < W; ++c) akk.v[c] = su[c * kBatchNb + kk];
+    const bool zero = is_zero<W>(akk);
+    for (int i = k + 1 + tid; i < n; i += kPanelThreads) {
+      val<W> l = load<W>(a, plane, colk + i);
+      if (!zero) {
+        l = div<W>(l, akk);
+        store<W>(a, plane, colk + i, l);
+      }
+#pragma unroll
+      for (int c = 0; c < W; ++c) sl[c * nmax + (i - k0)] = l.v[c];
+    }
+    __syncthreads();
+    const int rows = n - k - 1;
+    const int cols = kb - kk - 1;
+    if (rows > 0 && cols > 0) {
+      const int items = rows * cols;
+      for (int q = tid; q < items; q += kPanelThreads) {
+        const int i = k + 1 + q % rows;
+        const int j = kk + 1 + q / rows;
+        const int64_t idx = (int64_t)(k0 + j) * n + i;
+        val<W> l, u;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          l.v[c] = sl[c * nmax + (i - k0)];
+          u.v[c] = su[c * kBatchNb + j];
+        }
+        val<W> x = load<W>(a, plane, idx);
+        x = msub<W>(x, l, u);
+        store<W>(a, plane, idx, x);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) info[sys] = inf;
+}
+
+// the panel's row swaps on the columns left of it: CTA (pos, word)
+template <int W>
+__global__ void __launch_bounds__(128)
+k_blaswp(BatchView bv, int k0, double* __restrict__ A, const int64_t* __restrict__ piv) {
+  const int sys = bv.order[blockIdx.x];
+  const int n = bv.n[sys];
+  const int kb = min(kBatchNb, n - k0);
+  const int64_t plane = (int64_t)n * n;
+  const int64_t* pv = piv + bv.voff[sys];
+  double* a = A + (int64_t)W * bv.moff[sys] + blockIdx.y * plane;
+  for (int j = threadIdx.x; j < k0; j += blockDim.x) {
+    double* col = a + (int64_t)j * n;
+    for (int kk = 0; kk < kb; ++kk) {
+      const int k = k0 + kk;
+      const int p = (int)pv[k];
+      if (p != k) {
+        const double t = col[k];
+        col[k] = col[p];
+        col[p] = t;
+      }
+    }
+  }
+}
+
+// swaps + U12 = L11^-1 A12 on 8 columns: CTA (pos, column block)
+template <int W>
+__global__ void __launch_bounds__(256)
+k_btrsm(BatchView bv, int k0, double* __restrict__ A, const int64_t* __restrict__ piv) {
+  const int sys = bv.order[blockIdx.x];
+  const int n = bv.n[sys];
+  if ((int64_t)blockIdx.y * 8 >= (int64_t)n - k0 - kBatchNb) return;   // uniform per CTA
+  trsm_cols<W, kBatchNb>(A + (int64_t)W * bv.moff[sys], n, (int64_t)n * n, n, k0, piv + bv.voff[sys],
+                         blockIdx.y);
+}
+
+// plain trailing update over a tile list
+template <int W, int TM, int TN>
+__global__ void __launch_bounds__(256)
+k_bgemm_plain(BatchView bv, const TileEntry* __restrict__ tiles, int k0, double* __restrict__ A) {
+  const TileEntry t = tiles[blockIdx.x];
+  const int sys = bv.order[t.pos];
+  const int n = bv.n[sys];
+  const int r0 = k0 + kBatchNb;
+  const int64_t m = n - r0;
+  const int64_t plane = (int64_t)n * n;
+  double* a = A + (int64_t)W * bv.moff[sys];
+  gemm_plain_tile<W, TM, TN>(a + (int64_t)r0 * n + r0, n, plane, a + (int64_t)k0 * n + r0, n, plane,
+                             a + (int64_t)r0 * n + k0, n, plane, m, m, kBatchNb, t.ti, t.tj);
 }
 
 // ---------------------------------------------------------------------------
@@ -530,5 +702,67 @@ int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int6
 template int lu_blocked<2>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
 template int lu_blocked<3>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
 template int lu_blocked<4>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
+
+// ---- batched launchers ------------------------------------------------------
+void gemm_plain_tile_shape(int W, int* bm, int* bn) {
+  switch (W) {
+    case 2: *bm = 16 * GemmTile<2>::TM; *bn = 16 * GemmTile<2>::TN; break;
+    case 3: *bm = 16 * GemmTile<3>::TM; *bn = 16 * GemmTile<3>::TN; break;
+    default: *bm = 16 * GemmTile<4>::TM; *bn = 16 * GemmTile<4>::TN; break;
+  }
+}
+
+template <int W>
+int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, double* A, int64_t* piv, int64_t* info,
+                  cudaStream_t s) {
+  if (act <= 0) return MW_OK;
+  const size_t shmem = sizeof(double) * (size_t)W * ((size_t)kBatchNb + (size_t)nmax);
+  if (shmem > 48 * 1024)
+    MW_CUDA_CHECK(cudaFuncSetAttribute(k_bpanel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+  ProfScope ps(kPhPanel, s);
+  k_bpanel<W><<<act, kPanelThreads, shmem, s>>>(bv, nmax, k0, A, piv, info);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+int launch_blaswp(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s) {
+  if (act <= 0 || k0 <= 0) return MW_OK;
+  ProfScope ps(kPhLaswp, s);
+  k_blaswp<W><<<dim3((unsigned)act, W), 128, 0, s>>>(bv, k0, A, piv);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+int launch_btrsm(const BatchView& bv, int act, int max_cblocks, int k0, double* A, const int64_t* piv,
+                 cudaStream_t s) {
+  if (act <= 0 || max_cblocks <= 0) return MW_OK;
+  ProfScope ps(kPhTrsm, s);
+  k_btrsm<W><<<dim3((unsigned)act, (unsigned)max_cblocks), 256, 0, s>>>(bv, k0, A, piv);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+int launch_bgemm_plain(const BatchView& bv, const TileEntry* tiles, int64_t ntiles, int k0, double* A,
+                       cudaStream_t s) {
+  if (ntiles <= 0) return MW_OK;
+  constexpr int TM = GemmTile<W>::TM, TN = GemmTile<W>::TN;
+  ProfScope ps(kPhGemmPlain, s);
+  k_bgemm_plain<W, TM, TN><<<(unsigned)ntiles, 256, 0, s>>>(bv, tiles, k0, A);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+#define MW_BATCHED_INST(W)                                                                                   \
+  template int launch_bpanel<W>(const BatchView&, int, int, int, double*, int64_t*, int64_t*, cudaStream_t); \
+  template int launch_blaswp<W>(const BatchView&, int, int, double*, const int64_t*, cudaStream_t);          \
+  template int launch_btrsm<W>(const BatchView&, int, int, int, double*, const int64_t*, cudaStream_t);      \
+  template int launch_bgemm_plain<W>(const BatchView&, const TileEntry*, int64_t, int, double*, cudaStream_t);
+MW_BATCHED_INST(2)
+MW_BATCHED_INST(3)
+MW_BATCHED_INST(4)
+#undef MW_BATCHED_INST
 
 }  // namespace mw

@@ -46,6 +46,51 @@ int launch_gemm_plain_ptr(int64_t m, int64_t N, int K, double* C, int64_t ldc, i
                           const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
                           int64_t planeU, cudaStream_t s);
 
+// ---- batched blocked LU (batched.cu drives these per panel step) --------
+// A batch in the packed layout: system s has order n[s], its matrix of w
+// words at A + w*moff[s] with lda = n[s] and plane n[s]^2, its pivots at
+// piv + voff[s].  `order` lists the systems largest first, so the systems
+// still active at panel step k0 (n > k0) are order[0 .. act).
+struct BatchView {
+  const int* order;
+  const int* n;
+  const int64_t* moff;
+  const int64_t* voff;
+};
+
+// one work item of a trailing update: system order[pos], tile (ti, tj)
+struct TileEntry {
+  int pos, ti, tj, pad;
+};
+
+constexpr int kBatchNb = 64;   // panel width of the batched blocked LU
+
+template <int W>
+int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, double* A, int64_t* piv, int64_t* info,
+                  cudaStream_t s);
+template <int W>
+int launch_blaswp(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s);
+template <int W>
+int launch_btrsm(const BatchView& bv, int act, int max_cblocks, int k0, double* A, const int64_t* piv,
+                 cudaStream_t s);
+template <int W>
+int launch_bgemm_plain(const BatchView& bv, const TileEntry* tiles, int64_t ntiles, int k0, double* A,
+                       cudaStream_t s);
+// rows x columns of one plain-GEMM tile for W words
+void gemm_plain_tile_shape(int W, int* bm, int* bn);
+
+// split update of the batch (ozaki.cu): per active system with trailing
+// order m = n - k0 - 64 > 0, C -= L21 U12 on the 128 x 32 tiles listed in
+// `tiles`; `bases[pos]` = {first A-slice tile, first B-slice tile} of that
+// system in the slice area; the slicing grids are act x max_mt (128-row
+// tiles) and act x max_cb (128-column blocks).
+constexpr int kSplitTileM = 128;
+constexpr int kSplitTileN = 32;
+size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles);
+int split_bupdate_dd(const BatchView& bv, int act, int max_mt, int max_cb, const TileEntry* tiles,
+                     int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
+                     char* ws, size_t ws_bytes, cudaStream_t s);
+
 // substitution (solve.cu); y is a w-plane vector work area of n
 template <int W>
 int solve_launch(int64_t n, const double* LU, int64_t lda, const int64_t* piv, const double* b,

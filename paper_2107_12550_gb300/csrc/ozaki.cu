@@ -53,6 +53,7 @@ constexpr int kTileN = 32;             // columns per MMA tile
 constexpr int kASliceBytes = kTileM * kK * 2;   // 16 KB
 constexpr int kBSliceBytes = kTileN * kK * 2;   // 4 KB
 constexpr uint32_t kTmemCols = 512;
+static_assert(kTileM == kSplitTileM && kTileN == kSplitTileN && kK == kBatchNb, "batched split tile shape");
 
 // byte offset of element (row r, k) inside a K-major 128B-swizzled tile
 __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
@@ -124,10 +125,9 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
 // slicing: L21 rows -> A slices [tile][p][128 x 64], row exponents e_i
 // one thread per row; 8 consecutive k at a time -> one 16-byte store per slice
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
-k_slice_rows(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t m,
-             unsigned char* __restrict__ aslices, int* __restrict__ ea) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // padded row index
+__device__ __forceinline__ void slice_row(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t m,
+                                          unsigned char* __restrict__ aslices, int* __restrict__ ea,
+                                          int64_t r) {  // padded row index
   const int64_t tile = r / kTileM;
   const int rr = (int)(r % kTileM);
   const bool ok = r < m;
@@ -168,11 +168,16 @@ k_slice_rows(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t 
   }
 }
 
-// U12 columns -> B slices [tile][q][32 x 64] (column j is a K-major row), f_j
 __global__ void __launch_bounds__(128)
-k_slice_cols(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t N, int64_t npad,
-             unsigned char* __restrict__ bslices, int* __restrict__ fb) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // padded column index
+k_slice_rows(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t m,
+             unsigned char* __restrict__ aslices, int* __restrict__ ea) {
+  slice_row(L, ldl, planeL, m, aslices, ea, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// U12 columns -> B slices [tile][q][32 x 64] (column j is a K-major row), f_j
+__device__ __forceinline__ void slice_col(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t N,
+                                          int64_t npad, unsigned char* __restrict__ bslices,
+                                          int* __restrict__ fb, int64_t j) {  // padded column index
   if (j >= npad) return;
   const int64_t tile = j / kTileN;
   const int jj = (int)(j % kTileN);
@@ -212,6 +217,12 @@ k_slice_cols(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t 
       *reinterpret_cast<uint4*>(base + (int64_t)p * kBSliceBytes + sw128_offset(jj, kc * 8)) = v;
     }
   }
+}
+
+__global__ void __launch_bounds__(128)
+k_slice_cols(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t N, int64_t npad,
+             unsigned char* __restrict__ bslices, int* __restrict__ fb) {
+  slice_col(U, ldu, planeU, N, npad, bslices, fb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -359,17 +370,16 @@ struct SplitSmem {
 constexpr int kEpiWarps = 8;                       // two warpgroups over the 4 TMEM lane quarters
 constexpr int kSplitThreads = 64 + 32 * kEpiWarps;  // producer + MMA warps + epilogue
 
-__global__ void __launch_bounds__(kSplitThreads, 1)
-k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int64_t N,
-             const unsigned char* __restrict__ aslices,
-             const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
-             const int* __restrict__ fb, DeviceStatus* status) {
+__device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m,
+                                           int64_t N, const unsigned char* __restrict__ aslices,
+                                           const unsigned char* __restrict__ bslices,
+                                           const int* __restrict__ ea, const int* __restrict__ fb,
+                                           DeviceStatus* status, int64_t tm, int64_t tn) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzle atoms
   SplitSmem& sm = *reinterpret_cast<SplitSmem*>(
       (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tm = blockIdx.x, tn = blockIdx.y;
 
   if (threadIdx.x == 0) {
     tc::mbar_init(&sm.full_b, 1);
@@ -491,6 +501,72 @@ k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int
   }
 }
 
+__global__ void __launch_bounds__(kSplitThreads, 1)
+k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int64_t N,
+             const unsigned char* __restrict__ aslices,
+             const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
+             const int* __restrict__ fb, DeviceStatus* status) {
+  split_tile(C, ldc, planeC, m, N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y);
+}
+
+// ---- batched forms: per active system of a batch at panel step k0 ----------
+// L21 = rows [k0+64, n) of columns [k0, k0+64); U12 = rows [k0, k0+64) of
+// columns [k0+64, n); C = A22; all with lda = n.
+
+// grid (act, max_mt): 128-row tile blockIdx.y of system order[blockIdx.x]
+__global__ void __launch_bounds__(128)
+k_bslice_rows(BatchView bv, const int2* __restrict__ bases, int k0, const double* __restrict__ A,
+              unsigned char* __restrict__ aslices, int* __restrict__ ea) {
+  const int pos = blockIdx.x;
+  const int sys = bv.order[pos];
+  const int n = bv.n[sys];
+  const int64_t m = n - k0 - kK;
+  if ((int64_t)blockIdx.y * kTileM >= m) return;
+  const int64_t plane = (int64_t)n * n;
+  const double* L = A + 2 * bv.moff[sys] + (int64_t)k0 * n + (k0 + kK);
+  const int abase = bases[pos].x;
+  slice_row(L, n, plane, m, aslices + (int64_t)abase * kS * kASliceBytes, ea + (int64_t)abase * kTileM,
+            (int64_t)blockIdx.y * kTileM + threadIdx.x);
+}
+
+// grid (act, max_cb): 128-column block blockIdx.y of system order[blockIdx.x]
+__global__ void __launch_bounds__(128)
+k_bslice_cols(BatchView bv, const int2* __restrict__ bases, int k0, const double* __restrict__ A,
+              unsigned char* __restrict__ bslices, int* __restrict__ fb) {
+  const int pos = blockIdx.x;
+  const int sys = bv.order[pos];
+  const int n = bv.n[sys];
+  const int64_t N = n - k0 - kK;
+  const int64_t npad = (N + kTileN - 1) / kTileN * kTileN;
+  if ((int64_t)blockIdx.y * 128 >= npad) return;
+  const int64_t plane = (int64_t)n * n;
+  const double* U = A + 2 * bv.moff[sys] + (int64_t)(k0 + kK) * n + k0;
+  const int bbase = bases[pos].y;
+  slice_col(U, n, plane, N, npad, bslices + (int64_t)bbase * kS * kBSliceBytes, fb + (int64_t)bbase * kTileN,
+            (int64_t)blockIdx.y * 128 + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(kSplitThreads, 1)
+k_bsplit_gemm(BatchView bv, const TileEntry* __restrict__ tiles, const int2* __restrict__ bases, int k0,
+              double* __restrict__ A, const unsigned char* __restrict__ aslices,
+              const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
+              const int* __restrict__ fb, DeviceStatus* status) {
+  const TileEntry t = tiles[blockIdx.x];
+  const int sys = bv.order[t.pos];
+  const int n = bv.n[sys];
+  const int64_t m = n - k0 - kK;
+  const int64_t plane = (int64_t)n * n;
+  double* C = A + 2 * bv.moff[sys] + (int64_t)(k0 + kK) * n + (k0 + kK);
+  const int2 b = bases[t.pos];
+  split_tile(C, n, plane, m, m, aslices + (int64_t)b.x * kS * kASliceBytes,
+             bslices + (int64_t)b.y * kS * kBSliceBytes, ea + (int64_t)b.x * kTileM, fb + (int64_t)b.y * kTileN,
+             status, t.ti, t.tj);
+}
+
+size_t split_smem_bytes() {
+  return (sizeof(SplitSmem) + 1024 > 120 * 1024) ? sizeof(SplitSmem) + 1024 : 120 * 1024;
+}
+
 }  // namespace
 
 __device__ double scale2_exact(double x, int e) {
@@ -542,7 +618,7 @@ int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t plan
     ProfScope ps(kPhGemmSplit, s);
     // more than half of the SM's shared memory: one CTA per SM, which owns
     // all 512 TMEM columns
-    const size_t shmem = (sizeof(SplitSmem) + 1024 > 120 * 1024) ? sizeof(SplitSmem) + 1024 : 120 * 1024;
+    const size_t shmem = split_smem_bytes();
     static bool attr_set = false;
     if (!attr_set) {
       MW_CUDA_CHECK(cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
@@ -550,6 +626,48 @@ int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t plan
     }
     dim3 grid((unsigned)mt, (unsigned)nt);
     k_split_gemm<<<grid, kSplitThreads, shmem, s>>>(C, ldc, planeC, m, N, aslices, bslices, ea, fb, status);
+    MW_LAUNCH_CHECK();
+  }
+  return MW_OK;
+}
+
+// batched: [status 256 | A slices | B slices | ea | fb]
+size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles) {
+  return 256 + align256((size_t)a_tiles * kS * kASliceBytes) + align256((size_t)b_tiles * kS * kBSliceBytes) +
+         align256(sizeof(int) * (size_t)a_tiles * kTileM) + align256(sizeof(int) * (size_t)b_tiles * kTileN);
+}
+
+int split_bupdate_dd(const BatchView& bv, int act, int max_mt, int max_cb, const TileEntry* tiles,
+                     int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
+                     char* ws, size_t ws_bytes, cudaStream_t s) {
+  if (act <= 0 || ntiles <= 0) return MW_OK;
+  if (split_batched_workspace_bytes(a_tiles, b_tiles) > ws_bytes) return MW_EUNSUPPORTED;
+  size_t off = 256;
+  unsigned char* aslices = reinterpret_cast<unsigned char*>(ws + off);
+  off += align256((size_t)a_tiles * kS * kASliceBytes);
+  unsigned char* bslices = reinterpret_cast<unsigned char*>(ws + off);
+  off += align256((size_t)b_tiles * kS * kBSliceBytes);
+  int* ea = reinterpret_cast<int*>(ws + off);
+  off += align256(sizeof(int) * (size_t)a_tiles * kTileM);
+  int* fb = reinterpret_cast<int*>(ws + off);
+  DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
+  {
+    ProfScope ps(kPhSplitAux, s);
+    k_bslice_rows<<<dim3((unsigned)act, (unsigned)max_mt), 128, 0, s>>>(bv, bases, k0, A, aslices, ea);
+    MW_LAUNCH_CHECK();
+    k_bslice_cols<<<dim3((unsigned)act, (unsigned)max_cb), 128, 0, s>>>(bv, bases, k0, A, bslices, fb);
+    MW_LAUNCH_CHECK();
+  }
+  {
+    ProfScope ps(kPhGemmSplit, s);
+    const size_t shmem = split_smem_bytes();
+    static bool attr_set = false;
+    if (!attr_set) {
+      MW_CUDA_CHECK(cudaFuncSetAttribute(k_bsplit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+      attr_set = true;
+    }
+    k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, tiles, bases, k0, A, aslices, bslices, ea, fb,
+                                                                status);
     MW_LAUNCH_CHECK();
   }
   return MW_OK;

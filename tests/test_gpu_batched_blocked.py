@@ -1,0 +1,180 @@
+"""Blocked batched LU (all systems advance one 64-column panel per step; one
+trailing-update launch over the tiles of every active system) and the
+batched refinement on top of it, through the C ABI.
+
+Plain update: every system's factors, pivots, info, solutions and refined
+solutions are bitwise identical to the CPU oracle's single-system results.
+Split update (DD): per-system normwise backward error <= 1e-28 and pivots
+that agree with the oracle's except at rare near-ties; refinement to
+2^-200 checked exactly against x* = ones."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_12550_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2107_12550_gb300 import build as B
+    B.build()
+
+
+def api():
+    from paper_2107_12550_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _uniform_batch(w, n_list, seed):
+    mats = [W.uniform_matrix(int(n), w, seed=W.system_seed(seed, s), lda=int(n)) for s, n in enumerate(n_list)]
+    vecs = []
+    for s, n in enumerate(n_list):
+        v = np.zeros((w, int(n)))
+        v[0] = W.uniform_matrix(int(n), 1, seed=W.system_seed(seed + 1, s), lda=int(n))[0, 0, :]
+        vecs.append(v)
+    return mats, vecs
+
+
+# orders around the panel width and the tile edges, plus a ragged random mix
+EDGE_N = [1, 2, 63, 64, 65, 127, 128, 129, 192, 257]
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_blocked_plain_bitwise(w):
+    n_list = EDGE_N + [int(v) for v in W.batch_sizes(14, 1, 300, seed=40 + w)]
+    mats, vecs = _uniform_batch(w, n_list, seed=20 * w)
+    A = dev(api().pack_matrices(mats, w))
+    b = dev(api().pack_vectors(vecs, w))
+    LU, piv, info = api().ludecomp_batched_blocked(A, n_list, w, "plain")
+    x = api().solve_batched(LU, piv, b, n_list, w)
+    LUs = api().unpack_matrices(host(LU), n_list, w)
+    xs = api().unpack_vectors(host(x), n_list, w)
+    _, voff = api().batch_offsets(n_list)
+    pv = host(piv)
+    inf = host(info)
+    for s, n in enumerate(n_list):
+        LUo, pivo, infoo = oracle.lu(w, mats[s])
+        assert np.array_equal(LUs[s], LUo[:, :, :n]), (s, n)
+        assert np.array_equal(pv[voff[s]: voff[s] + n], pivo), (s, n)
+        assert inf[s] == infoo
+        assert np.array_equal(xs[s], oracle.solve(w, LUo, pivo, vecs[s])), (s, n)
+
+
+def test_blocked_plain_equals_persistent():
+    """Both batched LUs apply every element's updates in the same order."""
+    w = 2
+    n_list = [int(v) for v in W.batch_sizes(60, 1, 400, seed=5)]
+    mats, _ = _uniform_batch(w, n_list, seed=77)
+    A = dev(api().pack_matrices(mats, w))
+    LUb, pivb, infob = api().ludecomp_batched_blocked(A, n_list, w, "plain")
+    LUp, pivp, infop = api().ludecomp_batched(A, n_list, w)
+    assert torch.equal(LUb, LUp) and torch.equal(pivb, pivp) and torch.equal(infob, infop)
+
+
+def test_blocked_singular_member():
+    w = 3
+    n_list = [70, 130, 9, 200]
+    mats, _ = _uniform_batch(w, n_list, seed=8)
+    mats[1][:, 100, :] = 0.0          # zero column in the second panel
+    mats[2][:, :, 3] = 0.0            # zero row
+    A = dev(api().pack_matrices(mats, w))
+    LU, piv, info = api().ludecomp_batched_blocked(A, n_list, w, "plain")
+    inf = host(info)
+    LUs = api().unpack_matrices(host(LU), n_list, w)
+    for s in range(len(n_list)):
+        LUo, _, infoo = oracle.lu(w, mats[s])
+        assert inf[s] == infoo
+        assert np.array_equal(LUs[s], LUo[:, :, :n_list[s]])
+    assert inf[1] > 0 and inf[2] > 0 and inf[0] == 0 and inf[3] == 0
+
+
+def _eta(A, b, x):
+    n = x.shape[1]
+    r = oracle.residual(A, b, x, 8)
+    Ainf = np.max(np.sum(np.abs(A[0, :, :n]), axis=0))
+    return np.max(np.abs(r[0])) / (Ainf * np.max(np.abs(x[0])) + np.max(np.abs(b[0])))
+
+
+def test_blocked_split_dd_backward_error_and_pivots():
+    n_list = [65, 200, 300, 129, 64, 1, 513, 128, 257]
+    mats, vecs = _uniform_batch(2, n_list, seed=31)
+    A = dev(api().pack_matrices(mats, 2))
+    b = dev(api().pack_vectors(vecs, 2))
+    LU, piv, info = api().ludecomp_batched_blocked(A, n_list, 2, "split")
+    x = api().solve_batched(LU, piv, b, n_list, 2)
+    xs = api().unpack_vectors(host(x), n_list, 2)
+    _, voff = api().batch_offsets(n_list)
+    pv = host(piv)
+    assert int(host(info).max()) == 0
+    for s, n in enumerate(n_list):
+        eta = _eta(mats[s], vecs[s], xs[s])
+        assert eta <= 1e-28, (s, n, eta)
+        _, pivo, _ = oracle.lu(2, mats[s])
+        diff = int((pv[voff[s]: voff[s] + n] != pivo).sum())
+        assert diff <= max(1, n // 50), (s, n, diff)
+
+
+def test_blocked_split_matches_single_system_split():
+    """The batched split LU runs the same slicing, tile products and
+    recombination as the single-system split LU: identical factors."""
+    n_list = [300, 129, 200]
+    mats, _ = _uniform_batch(2, n_list, seed=55)
+    A = dev(api().pack_matrices(mats, 2))
+    LU, piv, _ = api().ludecomp_batched_blocked(A, n_list, 2, "split")
+    LUs = api().unpack_matrices(host(LU), n_list, 2)
+    _, voff = api().batch_offsets(n_list)
+    pv = host(piv)
+    for s, n in enumerate(n_list):
+        LU1, piv1, _ = api().ludecomp(dev(mats[s]), 2, "split")
+        assert np.array_equal(host(LU1)[:, :, :n], LUs[s])
+        assert np.array_equal(host(piv1), pv[voff[s]: voff[s] + n])
+
+
+@pytest.mark.parametrize("inner", [2, 3])
+def test_refine_blocked_plain_bitwise(inner):
+    n_list = [24, 5, 130, 70, 1, 47]
+    systems = [W.svd_system(n, [4.0, 8.0, 12.0][s % 3], seed=300 + s) if n > 1 else
+               W.System(np.array([[[3.0]]]), np.array([[1.0]] + [[0.0]] * 7), None) for s, n in enumerate(n_list)]
+    A = dev(api().pack_matrices([s.A for s in systems], 4))
+    b = dev(api().pack_vectors([s.b for s in systems], 8))
+    x, stats = api().refine_batched_blocked(A, 4, b, 8, n_list, inner, "plain", 200)
+    xs = api().unpack_vectors(host(x), n_list, 8)
+    st = host(stats)
+    for s, sysm in enumerate(systems):
+        status, xo, corr, nres, info = oracle.refine(sysm.A, sysm.b, inner)
+        assert (st[s, 0], st[s, 1], st[s, 2], st[s, 3]) == (corr, nres, info, status), s
+        assert np.array_equal(xs[s], xo), s
+
+
+def test_refine_blocked_split_reaches_target():
+    """DD inner LU with the split update on kappa up to 1e20 (the mixed
+    batched-refinement workload's range): every system converges and every
+    sampled x_i equals x* = 1 to 2^-200 (exact check)."""
+    n_list = [64, 150, 300, 97, 257]
+    kap = [4.0, 20.0, 12.0, 16.0, 8.0]
+    systems = [W.svd_system(n, kap[s], seed=500 + s) for s, n in enumerate(n_list)]
+    A = dev(api().pack_matrices([s.A for s in systems], 4))
+    b = dev(api().pack_vectors([s.b for s in systems], 8))
+    x, stats = api().refine_batched_blocked(A, 4, b, 8, n_list, 2, "split", 200)
+    xs = api().unpack_vectors(host(x), n_list, 8)
+    st = host(stats)
+    for s, n in enumerate(n_list):
+        assert st[s, 3] == 0, (s, st[s])
+        for i in range(0, n, 7):
+            v = sum(Fraction(float(c)) for c in xs[s][:, i])
+            assert abs(v - 1) <= Fraction(1, 2 ** 200), (s, i)
