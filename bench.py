@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the split / large-LU / batched comparison measurements")
+    p.add_argument("--no-mixed-batch", action="store_true",
+                   help="skip the 512-system mixed-precision batched refinement (about a minute of input generation)")
     return p.parse_args()
 
 
@@ -315,11 +317,153 @@ def extras(A, b, n, steps, peak_fp64):
 
     batch_step()
     tb, _ = _time(batch_step, 2, stream)
+    wkb = api.batch_blocked_workspace(L.MW_OP_LUDECOMP, 2, "plain", n_list)
+
+    def batch_step_blocked():
+        LUb.copy_(Ab)
+        LU_, piv_, info_ = api.ludecomp_batched_blocked(LUb, n_list, 2, "plain", work=wkb, inplace=True)
+        return api.solve_batched(LU_, piv_, bb, n_list, 2, work=wk)
+
+    batch_step_blocked()
+    tbb, _ = _time(batch_step_blocked, 2, stream)
     ops = sum((2.0 / 3.0) * m ** 3 for m in n_list)
-    out["batched_config4_dd"] = {"systems": 4096, "n_range": [16, 256], "ms_per_batch": tb,
-                                 "systems_per_s": 4096 / (tb * 1e-3),
-                                 "lu_dd_gops": ops / (tb * 1e-3) / 1e9,
-                                 "workload": "uniform DD systems, one launch each for LU and solve"}
+    out["batch_4096_dd_n16_256"] = {
+        "systems": 4096, "n_range": [16, 256], "ms_per_batch": tb, "systems_per_s": 4096 / (tb * 1e-3),
+        "lu_dd_gops": ops / (tb * 1e-3) / 1e9, "blocked_plain_ms_per_batch": tbb,
+        "workload": "uniform DD systems, LU + solve; persistent one-CTA-per-system LU, and the blocked batched LU"}
+    del Ab, LUb, bb
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_target_met(x_flat, n_list, words=X_WORDS):
+    """Per system: |x_i - 1| <= 2^-200 for every i (math.fsum of the words,
+    exact Fraction check near the threshold)."""
+    import numpy as np
+    lim = 2.0 ** -TARGET_BITS
+    met = []
+    off = 0
+    for n in n_list:
+        X = np.asarray(x_flat[off: off + words * n]).reshape(words, n)
+        off += words * n
+        ok = True
+        for i in range(n):
+            d = math.fsum([X[0, i] - 1.0] + [X[c, i] for c in range(1, words)])
+            if abs(d) > 2.0 * lim:
+                ok = False
+                break
+            if abs(d) >= 0.5 * lim:
+                v = sum((Fraction(float(X[c, i])) for c in range(words)), Fraction(0))
+                if abs(v - 1) > Fraction(1, 2 ** TARGET_BITS):
+                    ok = False
+                    break
+        met.append(ok)
+    return met
+
+
+def blocked_batch_msubs(n_list, nb=64):
+    """Multiword multiply-subtract steps of the blocked batched LU outside the
+    trailing update: (panel, TRSM) summed over systems and panel steps."""
+    panel = trsm = 0
+    for n in n_list:
+        for k0 in range(0, n, nb):
+            kb = min(nb, n - k0)
+            for kk in range(kb):
+                panel += (n - k0 - kk - 1) * (kb - kk - 1)
+            trsm += max(0, n - k0 - kb) * kb * (kb - 1) // 2
+    return panel, trsm
+
+
+def mixed_batch_refine(peak_fp64, count=512):
+    """Batched mixed-precision refinement: `count` SVD systems, n uniform in
+    [64, 1024], log10 kappa uniform in [4, 20], A stored in QD, b = A * ones
+    exact in 8 words.  Split-update DD inner LU (blocked batched) + exact
+    residual + refinement to 2^-200, against the plain FP64-core DD inner LU
+    with the same refinement and the plain QD direct LU (a stratified sample
+    of the systems, no refinement)."""
+    import numpy as np
+    import torch
+    from paper_2107_12550_gb300 import _lib as L
+    from paper_2107_12550_gb300 import api
+    from paper_2107_12550_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    n_list, kap = W.mixed_batch_spec(count, 64, 1024, 4.0, 20.0, seed=0)
+    t0 = time.time()
+    A_np, b_np = W.svd_batch(n_list, kap, seed=0, a_words=4, b_words=X_WORDS,
+                             processes=len(os.sched_getaffinity(0)))
+    gen_s = time.time() - t0
+    A = torch.from_numpy(A_np).cuda()
+    b = torch.from_numpy(b_np).cuda()
+    total_n = int(sum(n_list))
+    ops = sum((2.0 / 3.0) * m ** 3 for m in n_list)
+    out = {"systems": count, "n_range": [64, 1024], "log10_kappa_range": [4, 20],
+           "generation_s": gen_s, "a_words": 4, "b_words": X_WORDS, "target_bits": TARGET_BITS}
+    x = torch.empty(X_WORDS * total_n, dtype=torch.float64, device="cuda")
+    for name, upd, reps in (("split_dd_refine", "split", 2), ("plain_dd_refine", "plain", 1)):
+        work = api.batch_blocked_workspace(L.MW_OP_REFINE, 2, upd, n_list)
+        f = lambda: api.refine_batched_blocked(A, 4, b, X_WORDS, n_list, 2, upd, TARGET_BITS, work=work, out=x)
+        f()
+        L.profile_read(reset=True)
+        L.profile_enable(True)
+        ms, (_, stats) = _time(f, reps, stream)
+        L.profile_enable(False)
+        prof = L.profile_read(reset=True)
+        st = stats.cpu().numpy()
+        met = batch_target_met(x.cpu().numpy(), n_list)
+        lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain", "gemm_split", "split_aux")) / reps
+        out[name] = {"ms_per_batch": ms, "systems_met": int(sum(met)),
+                     "solves_per_s": int(sum(met)) / (ms * 1e-3),
+                     "converged": int((st[:, 3] == 0).sum()),
+                     "corrections_max": int(st[:, 0].max()), "corrections_mean": float(st[:, 0].mean()),
+                     "lu_ms": lu_ms, "lu_dd_gops": ops / (lu_ms * 1e-3) / 1e9 if lu_ms else None,
+                     "phase_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
+                     "gpu_launches": int(sum(c for _, c in prof.values()) / reps)}
+        del work
+    # FP64-pipe fractions of the panel and TRSM kernels (multiply-subtract
+    # instructions only: divisions and compares are not counted)
+    pm, tm = blocked_batch_msubs(n_list)
+    ph = out["split_dd_refine"]["phase_ms"]
+    for key, cnt in (("panel", pm), ("trsm", tm)):
+        t = ph.get(key, 0.0)
+        out["split_dd_refine"][key + "_fp64_frac_msub_only"] = (
+            cnt * FP64_PER_MSUB[2] / (t * 1e-3) / peak_fp64 if t else None)
+    # plain QD direct LU + solve (no refinement) on every 16th system by order
+    order = sorted(range(count), key=lambda s: n_list[s])
+    sample = order[::16]
+    sn = [n_list[s] for s in sample]
+    moff, voff = api.batch_offsets(n_list)
+    As = np.concatenate([A_np[4 * moff[s]: 4 * moff[s + 1]] for s in sample])
+    bs = np.concatenate([b_np[X_WORDS * voff[s]: X_WORDS * voff[s] + 4 * n_list[s]] for s in sample])
+    Asd = torch.from_numpy(As).cuda()
+    bsd = torch.from_numpy(bs).cuda()
+    wk = api.batch_blocked_workspace(L.MW_OP_LUDECOMP, 4, "plain", sn)
+    wks = api.batch_workspace(L.MW_OP_SOLVE, 4, sn)
+    LUq = torch.empty_like(Asd)
+
+    def qd_direct():
+        LUq.copy_(Asd)
+        LU_, piv_, _ = api.ludecomp_batched_blocked(LUq, sn, 4, "plain", work=wk, inplace=True)
+        return api.solve_batched(LU_, piv_, bsd, sn, 4, work=wks)
+
+    qd_direct()
+    tq, xq = _time(qd_direct, 1, stream)
+    xq = xq.cpu().numpy()
+    worst = []
+    off = 0
+    for m in sn:
+        X = xq[off: off + 4 * m].reshape(4, m)
+        off += 4 * m
+        worst.append(max(abs(math.fsum([X[0, i] - 1.0] + [X[c, i] for c in range(1, 4)])) for i in range(m)))
+    sample_ops = sum((2.0 / 3.0) * m ** 3 for m in sn)
+    out["qd_direct_sample"] = {
+        "systems": len(sample), "sample": "every 16th system in order of n", "ms": tq,
+        "ms_scaled_to_batch": tq * ops / sample_ops,
+        "systems_met": int(sum(1 for e in worst if e <= 2.0 ** -TARGET_BITS)),
+        "median_log2_max_error": float(np.median([math.log2(e) if e > 0 else -1100 for e in worst]))}
+    out["workload"] = ("SVD systems (A = U diag(sigma) V^T exact, QD stored), per-system seeds; "
+                       "one call of the blocked batched refinement per batch")
+    del A, b, Asd, bsd, LUq, x
+    torch.cuda.empty_cache()
     return out
 
 
@@ -462,6 +606,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_extras:
         line["extras"] = extras(A, b, n, args.steps, peak_fp64)
+        if not args.no_mixed_batch:
+            line["extras"]["mixed_batch_refine_512"] = mixed_batch_refine(peak_fp64)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(n, s.A, s.b, corrections, residuals)
     if rank == 0:

@@ -196,12 +196,32 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 }
 
 // ---------------------------------------------------------------------------
-// substitution of one system per CTA (column-oriented; x may alias b):
-// y = P b, y_i -= l_ij y_j (j ascending), d_j = 1 / u_jj for all j, then
-// x_j = y_j d_j and y_i -= u_ij x_j (j descending).
+// substitution of one system per CTA (x may alias b): y = P b, then
+// y_i -= l_ij y_j (j ascending), d_j = 1 / u_jj for all j, then
+// x_j = y_j d_j and y_i -= u_ij x_j (j descending) -- blocked by 32 columns:
+// warp 0 solves the 32 x 32 triangle of a block with the rows in its lanes,
+// then all threads apply the block to the remaining rows, four rows per
+// thread, with each row's updates still in the order above.
 // Systems whose state is not "running" are skipped when st is given.
 // dynamic shared memory: 2 * W * nmax doubles
 // ---------------------------------------------------------------------------
+constexpr int kSolveBs = 32;
+constexpr int kSolveRpt = kBatchMaxN / kBatchThreads;   // rows per thread in a block update
+
+template <int W>
+__device__ __forceinline__ val<W> smem_val(const double* v, int nmax, int i) {
+  val<W> r;
+#pragma unroll
+  for (int c = 0; c < W; ++c) r.v[c] = v[c * nmax + i];
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ void smem_put(double* v, int nmax, int i, const val<W>& r) {
+#pragma unroll
+  for (int c = 0; c < W; ++c) v[c * nmax + i] = r.v[c];
+}
+
 template <int W>
 __global__ void __launch_bounds__(kBatchThreads)
 k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
@@ -209,7 +229,9 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
                 const double* __restrict__ LU, const int64_t* __restrict__ piv, const double* b,
                 double* x, const BatchState* __restrict__ st, BatchCursor* cur) {
   extern __shared__ double bsm[];
-  const int tid = threadIdx.x;
+  double* ysm = bsm;
+  double* dsm = bsm + W * nmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
     const int pos = next_system(cur, count);
     if (pos < 0) break;
@@ -223,7 +245,15 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
     double* xs = x + (int64_t)W * voff[s];
     for (int i = tid; i < n; i += kBatchThreads)
 #pragma unroll
-      for (int c = 0; c < W; ++c) bsm[c * nmax + i] = bs[c * n + i];
+      for (int c = 0; c < W; ++c) ysm[c * nmax + i] = bs[c * n + i];
+    // reciprocals of the diagonal, all j in parallel
+    for (int j = tid; j < n; j += kBatchThreads) {
+      val<W> one;
+#pragma unroll
+      for (int c = 0; c < W; ++c) one.v[c] = 0.0;
+      one.v[0] = 1.0;
+      smem_put<W>(dsm, nmax, j, div<W>(one, load_ro<W>(a, plane, (int64_t)j * n + j)));
+    }
     __syncthreads();
     if (tid == 0) {
       for (int k = 0; k < n; ++k) {
@@ -231,68 +261,111 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         if (p != k)
 #pragma unroll
           for (int c = 0; c < W; ++c) {
-            const double t = bsm[c * nmax + k];
-            bsm[c * nmax + k] = bsm[c * nmax + p];
-            bsm[c * nmax + p] = t;
+            const double t = ysm[c * nmax + k];
+            ysm[c * nmax + k] = ysm[c * nmax + p];
+            ysm[c * nmax + p] = t;
           }
       }
     }
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
-      val<W> yj;
-#pragma unroll
-      for (int c = 0; c < W; ++c) yj.v[c] = bsm[c * nmax + j];
-      for (int i = j + 1 + tid; i < n; i += kBatchThreads) {
+    // ---- forward: unit lower L ----
+    for (int j0 = 0; j0 < n; j0 += kSolveBs) {
+      const int bsz = min(kSolveBs, n - j0);
+      if (warp == 0) {
+        const int i = j0 + lane;
         val<W> yi;
+        if (lane < bsz) yi = smem_val<W>(ysm, nmax, i);
+        else {
 #pragma unroll
-        for (int c = 0; c < W; ++c) yi.v[c] = bsm[c * nmax + i];
-        yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)j * n + i), yj);
-#pragma unroll
-        for (int c = 0; c < W; ++c) bsm[c * nmax + i] = yi.v[c];
-      }
-      __syncthreads();
-    }
-    // reciprocals of the diagonal, all j in parallel
-    double* dsm = bsm + W * nmax;
-    for (int j = tid; j < n; j += kBatchThreads) {
-      val<W> one;
-#pragma unroll
-      for (int c = 0; c < W; ++c) one.v[c] = 0.0;
-      one.v[0] = 1.0;
-      const val<W> dj = div<W>(one, load_ro<W>(a, plane, (int64_t)j * n + j));
-#pragma unroll
-      for (int c = 0; c < W; ++c) dsm[c * nmax + j] = dj.v[c];
-    }
-    __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-      if (tid == 0) {
-        val<W> yj, dj;
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-          yj.v[c] = bsm[c * nmax + j];
-          dj.v[c] = dsm[c * nmax + j];
+          for (int c = 0; c < W; ++c) yi.v[c] = 0.0;
         }
-        yj = mul<W>(yj, dj);
+        for (int jj = 0; jj < bsz - 1; ++jj) {
+          val<W> yj;
 #pragma unroll
-        for (int c = 0; c < W; ++c) bsm[c * nmax + j] = yj.v[c];
+          for (int c = 0; c < W; ++c) yj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
+          if (lane > jj && lane < bsz) yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), yj);
+        }
+        if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
       }
       __syncthreads();
-      val<W> xj;
+      const int r0 = j0 + bsz;
+      if (r0 < n) {
+        val<W> yr[kSolveRpt];
 #pragma unroll
-      for (int c = 0; c < W; ++c) xj.v[c] = bsm[c * nmax + j];
-      for (int i = tid; i < j; i += kBatchThreads) {
-        val<W> yi;
+        for (int q = 0; q < kSolveRpt; ++q) {
+          const int i = r0 + tid + q * kBatchThreads;
+          if (i < n) yr[q] = smem_val<W>(ysm, nmax, i);
+        }
+#pragma unroll 4
+        for (int jj = 0; jj < bsz; ++jj) {
+          const val<W> yj = smem_val<W>(ysm, nmax, j0 + jj);
+          const int64_t col = (int64_t)(j0 + jj) * n;
 #pragma unroll
-        for (int c = 0; c < W; ++c) yi.v[c] = bsm[c * nmax + i];
-        yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)j * n + i), xj);
+          for (int q = 0; q < kSolveRpt; ++q) {
+            const int i = r0 + tid + q * kBatchThreads;
+            if (i < n) yr[q] = msub<W>(yr[q], load_ro<W>(a, plane, col + i), yj);
+          }
+        }
 #pragma unroll
-        for (int c = 0; c < W; ++c) bsm[c * nmax + i] = yi.v[c];
+        for (int q = 0; q < kSolveRpt; ++q) {
+          const int i = r0 + tid + q * kBatchThreads;
+          if (i < n) smem_put<W>(ysm, nmax, i, yr[q]);
+        }
+      }
+      __syncthreads();
+    }
+    // ---- backward: upper U with the reciprocals ----
+    for (int j1 = n; j1 > 0; j1 -= kSolveBs) {
+      const int bsz = min(kSolveBs, j1);
+      const int jb = j1 - bsz;              // block rows/columns [jb, j1)
+      if (warp == 0) {
+        const int i = jb + lane;
+        val<W> yi, di;
+        if (lane < bsz) {
+          yi = smem_val<W>(ysm, nmax, i);
+          di = smem_val<W>(dsm, nmax, i);
+        } else {
+#pragma unroll
+          for (int c = 0; c < W; ++c) yi.v[c] = di.v[c] = 0.0;
+        }
+        for (int jj = bsz - 1; jj >= 0; --jj) {
+          if (lane == jj) yi = mul<W>(yi, di);          // x_j = y_j d_j
+          val<W> xj;
+#pragma unroll
+          for (int c = 0; c < W; ++c) xj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
+          if (lane < jj) yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(jb + jj) * n + i), xj);
+        }
+        if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
+      }
+      __syncthreads();
+      if (jb > 0) {
+        val<W> yr[kSolveRpt];
+#pragma unroll
+        for (int q = 0; q < kSolveRpt; ++q) {
+          const int i = tid + q * kBatchThreads;
+          if (i < jb) yr[q] = smem_val<W>(ysm, nmax, i);
+        }
+#pragma unroll 4
+        for (int jj = bsz - 1; jj >= 0; --jj) {
+          const val<W> xj = smem_val<W>(ysm, nmax, jb + jj);
+          const int64_t col = (int64_t)(jb + jj) * n;
+#pragma unroll
+          for (int q = 0; q < kSolveRpt; ++q) {
+            const int i = tid + q * kBatchThreads;
+            if (i < jb) yr[q] = msub<W>(yr[q], load_ro<W>(a, plane, col + i), xj);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kSolveRpt; ++q) {
+          const int i = tid + q * kBatchThreads;
+          if (i < jb) smem_put<W>(ysm, nmax, i, yr[q]);
+        }
       }
       __syncthreads();
     }
     for (int i = tid; i < n; i += kBatchThreads)
 #pragma unroll
-      for (int c = 0; c < W; ++c) xs[c * n + i] = bsm[c * nmax + i];
+      for (int c = 0; c < W; ++c) xs[c * n + i] = ysm[c * nmax + i];
     __syncthreads();
   }
 }

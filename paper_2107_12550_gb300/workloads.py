@@ -29,6 +29,7 @@ d_i = 10^(-26(i-1)/n) and x = [0 1 ... n-1]^T):
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass
 from typing import Optional
 
@@ -161,7 +162,7 @@ def _rn_take(L: np.ndarray):
         v = (chunk << r0).astype(np.int64)                    # < 2^40
         idx = j0 + part
         ok = anynz & (idx < K)
-        np.subtract.at(R, (np.clip(idx, 0, K - 1)[ok], cols[ok]), v[ok])
+        R[idx[ok], cols[ok]] -= v[ok]      # one (limb, column) pair per column: no repeats
     R = _limb_norm(R)
     R = np.where(neg[None, :], -R, R)
     R = _limb_norm(R)
@@ -285,3 +286,97 @@ def batch_sizes(count: int, n_lo: int, n_hi: int, seed: int = 0) -> np.ndarray:
 
 def system_seed(seed: int, index: int) -> int:
     return seed * (1 << 32) + index
+
+
+# ---------------------------------------------------------------------------
+# mixed-precision batched refinement workload: many SVD systems of uneven
+# order with log-uniform condition numbers
+# ---------------------------------------------------------------------------
+
+def mixed_batch_spec(count: int = 512, n_lo: int = 64, n_hi: int = 1024, log10_kappa_lo: float = 4.0,
+                     log10_kappa_hi: float = 20.0, seed: int = 0):
+    """(n_list, log10_kappa_list): n_i uniform in [n_lo, n_hi], log10 kappa_i
+    uniform in [log10_kappa_lo, log10_kappa_hi]."""
+    n_list = [int(v) for v in batch_sizes(count, n_lo, n_hi, seed=seed)]
+    kap = rng(system_seed(seed, 1 << 31)).uniform(log10_kappa_lo, log10_kappa_hi, count)
+    return n_list, [float(k) for k in kap]
+
+
+def _svd_batch_worker(job):
+    from multiprocessing import shared_memory
+    (shm_a, shm_b, total_a, total_b, a_words, b_words, seed, items) = job
+    sa = shared_memory.SharedMemory(name=shm_a)
+    sb = shared_memory.SharedMemory(name=shm_b)
+    try:
+        Aflat = np.ndarray((total_a,), dtype=np.float64, buffer=sa.buf)
+        bflat = np.ndarray((total_b,), dtype=np.float64, buffer=sb.buf)
+        for (s, n, lk, moff, voff) in items:
+            sysm = svd_system(n, lk, seed=system_seed(seed, s), words=a_words, b_words=b_words, lda=n)
+            base = a_words * moff
+            Aflat[base: base + a_words * n * n] = sysm.A.reshape(-1)
+            vb = b_words * voff
+            bflat[vb: vb + b_words * n] = sysm.b.reshape(-1)
+        return len(items)
+    finally:
+        del Aflat, bflat
+        sa.close()
+        sb.close()
+
+
+def svd_batch(n_list, log10_kappa, seed: int = 0, a_words: int = 4, b_words: int = 8,
+              processes: Optional[int] = None):
+    """Packed batch of ``svd_system`` s (system s uses seed system_seed(seed, s),
+    lda = n): returns (A, b) flat float64 arrays in the batch layout (system s:
+    A at a_words * sum_{s'<s} n^2, b at b_words * sum_{s'<s} n), with
+    x* = ones for every system.  Systems are built in a pool of worker
+    processes (spawn start method) writing into shared memory."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    n = np.asarray(n_list, dtype=np.int64)
+    moff = np.concatenate([[0], np.cumsum(n * n)])
+    voff = np.concatenate([[0], np.cumsum(n)])
+    total_a, total_b = a_words * int(moff[-1]), b_words * int(voff[-1])
+    sa = shared_memory.SharedMemory(create=True, size=max(8, 8 * total_a))
+    sb = shared_memory.SharedMemory(create=True, size=max(8, 8 * total_b))
+    try:
+        np.ndarray((total_a,), dtype=np.float64, buffer=sa.buf)[:] = 0.0
+        np.ndarray((total_b,), dtype=np.float64, buffer=sb.buf)[:] = 0.0
+        procs = processes or os.cpu_count() or 1
+        order = sorted(range(len(n_list)), key=lambda s: -int(n_list[s]))
+        buckets = [[] for _ in range(procs)]
+        load = [0.0] * procs
+        for s in order:                              # longest-processing-time first
+            k = int(np.argmin(load))
+            buckets[k].append((s, int(n_list[s]), float(log10_kappa[s]), int(moff[s]), int(voff[s])))
+            load[k] += float(n_list[s]) ** 2.5
+        jobs = [(sa.name, sb.name, total_a, total_b, a_words, b_words, seed, it) for it in buckets if it]
+        if procs == 1:
+            for j in jobs:
+                _svd_batch_worker(j)
+        else:
+            # one BLAS thread per worker (the workers import numpy afresh and
+            # read these); a worker that dies raises BrokenProcessPool here
+            # instead of leaving the parent waiting
+            from concurrent.futures import ProcessPoolExecutor
+            keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+            saved = {k: os.environ.get(k) for k in keys}
+            try:
+                for k in keys:
+                    os.environ[k] = "1"
+                with ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+                    list(ex.map(_svd_batch_worker, jobs))
+            finally:
+                for k, v in saved.items():
+                    if v is None:
+                        os.environ.pop(k, None)
+                    else:
+                        os.environ[k] = v
+        A = np.array(np.ndarray((total_a,), dtype=np.float64, buffer=sa.buf))
+        b = np.array(np.ndarray((total_b,), dtype=np.float64, buffer=sb.buf))
+    finally:
+        sa.close()
+        sa.unlink()
+        sb.close()
+        sb.unlink()
+    return A, b
+

@@ -5,6 +5,7 @@ import math
 from fractions import Fraction
 
 import numpy as np
+import pytest
 
 from oracle import exact as X
 from paper_2107_12550_gb300 import workloads as W
@@ -55,3 +56,33 @@ def test_batch_sizes_range():
     n = W.batch_sizes(1000, 16, 256, seed=0)
     assert n.min() >= 16 and n.max() <= 256
     assert np.array_equal(n, W.batch_sizes(1000, 16, 256, seed=0))
+
+
+def test_mixed_batch_spec_ranges():
+    n_list, kap = W.mixed_batch_spec(512, 64, 1024, 4.0, 20.0, seed=0)
+    assert len(n_list) == len(kap) == 512
+    assert min(n_list) >= 64 and max(n_list) <= 1024
+    assert min(kap) >= 4.0 and max(kap) <= 20.0
+    assert (n_list, kap) == W.mixed_batch_spec(512, 64, 1024, 4.0, 20.0, seed=0)
+
+
+@pytest.mark.timeout(300)
+def test_svd_batch_pool_matches_single_systems():
+    """The packed batch built by worker processes equals the one built in
+    this process and, system by system, svd_system with its per-system seed;
+    b = A * ones exactly for a sampled small member."""
+    n_list, kap = W.mixed_batch_spec(10, 5, 40, 4.0, 20.0, seed=9)
+    A, b = W.svd_batch(n_list, kap, seed=9, processes=2)
+    A1, b1 = W.svd_batch(n_list, kap, seed=9, processes=1)
+    assert np.array_equal(A, A1) and np.array_equal(b, b1)
+    n = np.asarray(n_list)
+    moff = np.concatenate([[0], np.cumsum(n * n)])
+    voff = np.concatenate([[0], np.cumsum(n)])
+    for s, ns in enumerate(n_list):
+        ref = W.svd_system(ns, kap[s], seed=W.system_seed(9, s), lda=ns)
+        assert np.array_equal(A[4 * moff[s]: 4 * moff[s + 1]].reshape(4, ns, ns), ref.A)
+        assert np.array_equal(b[8 * voff[s]: 8 * voff[s + 1]].reshape(8, ns), ref.b)
+    s = int(np.argmin(n))
+    Af = X.mat_to_frac(A[4 * moff[s]: 4 * moff[s + 1]].reshape(4, n[s], n[s]), int(n[s]))
+    bf = X.vec_to_frac(b[8 * voff[s]: 8 * voff[s + 1]].reshape(8, n[s]))
+    assert all(sum(row) == bi for row, bi in zip(Af, bf))
