@@ -712,15 +712,65 @@ static int upload_plan(const BatchPlanHost& p, int count, char* ws, BatchPlanDev
 // and the tile lists; it is computed on the host from n and uploaded with
 // the batch plan.
 // ---------------------------------------------------------------------------
-struct BlockedPlanHost {
-  int update = MW_UPDATE_PLAIN;
-  int nsteps = 0;
-  std::vector<int> act, max_cb_trsm, max_mt, max_cb_slice;
+// one kind of trailing-update work per step: tiles over all active systems
+struct GeomPlanHost {
+  std::vector<int> max_mt, max_cb;   // per step: slicing grid extents (split)
   std::vector<int64_t> toff, boff;   // per step: first tile, first base (nsteps + 1 entries)
   std::vector<TileEntry> tiles;
   std::vector<int2> bases;           // split: {first A-slice tile, first B-slice tile} per (step, pos)
   int64_t a_tiles = 0, b_tiles = 0;  // split: slice tiles of the largest step
 };
+
+struct BlockedPlanHost {
+  int update = MW_UPDATE_PLAIN;
+  int nsteps = 0;
+  std::vector<int> act, max_cb_trsm, max_cols;
+  GeomPlanHost trail;   // plain: BM x BN tiles; split: 128 x 32 tiles of A22
+  GeomPlanHost tinv;    // split: 128 x 32 tiles of U12^T (the TRSM as a product with L11^-1)
+  GeomPlanHost pinner;  // split: 128 x 32 tiles of the panel's right half below its top rows
+};
+
+// tiles of an m x N product for every active system of one step
+static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool split, int bm, int bn,
+                          int (*dims)(int n, int k0, int* N), int k0) {
+  int64_t at = 0, btl = 0;
+  int max_m = 0, max_n = 0;
+  for (int pos = 0; pos < act; ++pos) {
+    int N = 0;
+    const int m = dims(p.n[p.order[pos]], k0, &N);
+    if (split) g.bases.push_back(make_int2((int)at, (int)btl));
+    if (m <= 0 || N <= 0) continue;
+    max_m = std::max(max_m, m);
+    max_n = std::max(max_n, N);
+    const int mt = (m + bm - 1) / bm, nt = (N + bn - 1) / bn;
+    for (int tj = 0; tj < nt; ++tj)
+      for (int ti = 0; ti < mt; ++ti) g.tiles.push_back(TileEntry{pos, ti, tj, 0});
+    at += mt;
+    btl += nt;
+  }
+  g.max_mt.push_back((max_m + kSplitTileM - 1) / kSplitTileM);
+  g.max_cb.push_back(((max_n + kSplitTileN - 1) / kSplitTileN * kSplitTileN + 127) / 128);
+  if (split) {
+    g.a_tiles = std::max(g.a_tiles, at);
+    g.b_tiles = std::max(g.b_tiles, btl);
+  }
+  g.toff.push_back((int64_t)g.tiles.size());
+  g.boff.push_back((int64_t)g.bases.size());
+}
+
+static int dims_trail(int n, int k0, int* N) {
+  *N = n - k0 - kBatchNb;
+  return n - k0 - kBatchNb;
+}
+static int dims_tinv(int n, int k0, int* N) {
+  *N = kBatchNb;
+  return n - k0 - kBatchNb;
+}
+static int dims_pinner(int n, int k0, int* N) {
+  constexpr int H = kBatchNb / 2;
+  *N = std::min(H, n - k0 - H);
+  return n - k0 - H;
+}
 
 static void make_blocked_plan(const BatchPlanHost& p, int W, int update, BlockedPlanHost& bp) {
   bp = BlockedPlanHost();
@@ -733,8 +783,10 @@ static void make_blocked_plan(const BatchPlanHost& p, int W, int update, Blocked
     bn = kSplitTileN;
   }
   const int count = (int)p.n.size();
-  bp.toff.push_back(0);
-  bp.boff.push_back(0);
+  for (GeomPlanHost* g : {&bp.trail, &bp.tinv, &bp.pinner}) {
+    g->toff.push_back(0);
+    g->boff.push_back(0);
+  }
   if (count == 0) return;
   int act = count;
   for (int k0 = 0; k0 < p.nmax; k0 += kBatchNb) {
@@ -742,82 +794,146 @@ static void make_blocked_plan(const BatchPlanHost& p, int W, int update, Blocked
     bp.act.push_back(act);
     const int m0 = p.n[p.order[0]] - k0 - kBatchNb;          // largest trailing order
     bp.max_cb_trsm.push_back(m0 > 0 ? (m0 + 7) / 8 : 0);
-    bp.max_mt.push_back(m0 > 0 ? (m0 + kSplitTileM - 1) / kSplitTileM : 0);
-    bp.max_cb_slice.push_back(m0 > 0 ? ((m0 + kSplitTileN - 1) / kSplitTileN * kSplitTileN + 127) / 128 : 0);
-    int64_t at = 0, btl = 0;
-    for (int pos = 0; pos < act; ++pos) {
-      const int m = p.n[p.order[pos]] - k0 - kBatchNb;
-      if (split) bp.bases.push_back(make_int2((int)at, (int)btl));
-      if (m <= 0) continue;
-      const int mt = (m + bm - 1) / bm, nt = (m + bn - 1) / bn;
-      for (int tj = 0; tj < nt; ++tj)
-        for (int ti = 0; ti < mt; ++ti) bp.tiles.push_back(TileEntry{pos, ti, tj, 0});
-      at += mt;
-      btl += nt;
-    }
+    bp.max_cols.push_back(std::max(m0, 0));
+    add_geom_step(bp.trail, p, act, split, bm, bn, dims_trail, k0);
     if (split) {
-      bp.a_tiles = std::max(bp.a_tiles, at);
-      bp.b_tiles = std::max(bp.b_tiles, btl);
+      add_geom_step(bp.tinv, p, act, true, kSplitTileM, kSplitTileN, dims_tinv, k0);
+      add_geom_step(bp.pinner, p, act, true, kSplitTileM, kSplitTileN, dims_pinner, k0);
     }
-    bp.toff.push_back((int64_t)bp.tiles.size());
-    bp.boff.push_back((int64_t)bp.bases.size());
     ++bp.nsteps;
   }
 }
 
-// [tiles | bases | split scratch]
+static size_t geom_bytes(const GeomPlanHost& g) {
+  return align256(sizeof(TileEntry) * std::max<size_t>(1, g.tiles.size())) +
+         align256(sizeof(int2) * std::max<size_t>(1, g.bases.size()));
+}
+
+static int64_t blocked_count(const BlockedPlanHost& bp) { return bp.act.empty() ? 0 : bp.act[0]; }
+
+static int64_t max_a_tiles(const BlockedPlanHost& bp) {
+  return std::max(bp.trail.a_tiles, std::max(bp.tinv.a_tiles, bp.pinner.a_tiles));
+}
+static int64_t max_b_tiles(const BlockedPlanHost& bp) {
+  return std::max(bp.trail.b_tiles, std::max(bp.tinv.b_tiles, bp.pinner.b_tiles));
+}
+
+// [trail | tinv | pinner tiles and bases | aux | split scratch]
 static size_t blocked_extra_bytes(const BlockedPlanHost& bp) {
-  size_t b = align256(sizeof(TileEntry) * std::max<size_t>(1, bp.tiles.size())) +
-             align256(sizeof(int2) * std::max<size_t>(1, bp.bases.size()));
-  if (bp.update == MW_UPDATE_SPLIT) b += split_batched_workspace_bytes(bp.a_tiles, bp.b_tiles);
+  size_t b = geom_bytes(bp.trail) + geom_bytes(bp.tinv) + geom_bytes(bp.pinner);
+  if (bp.update == MW_UPDATE_SPLIT) {
+    b += align256(sizeof(double) * 2 * kBatchNb * kBatchNb * (size_t)std::max<int64_t>(1, blocked_count(bp)));
+    b += split_batched_workspace_bytes(max_a_tiles(bp), max_b_tiles(bp));
+  }
   return b;
 }
 
-struct BlockedDev {
+struct GeomDev {
   TileEntry* tiles;
   int2* bases;
-  char* split_ws;
-  size_t split_bytes;
 };
 
-static int upload_blocked(const BlockedPlanHost& bp, char* base, BlockedDev& d, cudaStream_t s) {
-  size_t off = 0;
+struct BlockedDev {
+  GeomDev trail, tinv, pinner;
+  double* aux;
+  char* split_ws;
+  size_t split_bytes;
+  int64_t a_tiles, b_tiles;
+};
+
+static int upload_geom(const GeomPlanHost& g, char* base, size_t& off, GeomDev& d, cudaStream_t s) {
   d.tiles = reinterpret_cast<TileEntry*>(base + off);
-  off += align256(sizeof(TileEntry) * std::max<size_t>(1, bp.tiles.size()));
+  off += align256(sizeof(TileEntry) * std::max<size_t>(1, g.tiles.size()));
   d.bases = reinterpret_cast<int2*>(base + off);
-  off += align256(sizeof(int2) * std::max<size_t>(1, bp.bases.size()));
-  d.split_ws = base + off;
-  d.split_bytes = bp.update == MW_UPDATE_SPLIT ? split_batched_workspace_bytes(bp.a_tiles, bp.b_tiles) : 0;
-  if (!bp.tiles.empty())
-    MW_CUDA_CHECK(cudaMemcpyAsync(d.tiles, bp.tiles.data(), sizeof(TileEntry) * bp.tiles.size(),
+  off += align256(sizeof(int2) * std::max<size_t>(1, g.bases.size()));
+  if (!g.tiles.empty())
+    MW_CUDA_CHECK(cudaMemcpyAsync(d.tiles, g.tiles.data(), sizeof(TileEntry) * g.tiles.size(),
                                   cudaMemcpyHostToDevice, s));
-  if (!bp.bases.empty())
-    MW_CUDA_CHECK(cudaMemcpyAsync(d.bases, bp.bases.data(), sizeof(int2) * bp.bases.size(),
+  if (!g.bases.empty())
+    MW_CUDA_CHECK(cudaMemcpyAsync(d.bases, g.bases.data(), sizeof(int2) * g.bases.size(),
                                   cudaMemcpyHostToDevice, s));
-  if (d.split_bytes) MW_CUDA_CHECK(cudaMemsetAsync(d.split_ws, 0, 256, s));
   return MW_OK;
 }
 
+static int upload_blocked(const BlockedPlanHost& bp, char* base, BlockedDev& d, cudaStream_t s) {
+  size_t off = 0;
+  int rc = upload_geom(bp.trail, base, off, d.trail, s);
+  if (rc) return rc;
+  rc = upload_geom(bp.tinv, base, off, d.tinv, s);
+  if (rc) return rc;
+  rc = upload_geom(bp.pinner, base, off, d.pinner, s);
+  if (rc) return rc;
+  d.aux = nullptr;
+  d.split_ws = nullptr;
+  d.split_bytes = 0;
+  d.a_tiles = max_a_tiles(bp);
+  d.b_tiles = max_b_tiles(bp);
+  if (bp.update == MW_UPDATE_SPLIT) {
+    d.aux = reinterpret_cast<double*>(base + off);
+    off += align256(sizeof(double) * 2 * kBatchNb * kBatchNb * (size_t)std::max<int64_t>(1, blocked_count(bp)));
+    d.split_ws = base + off;
+    d.split_bytes = split_batched_workspace_bytes(d.a_tiles, d.b_tiles);
+    MW_CUDA_CHECK(cudaMemsetAsync(d.split_ws, 0, 256, s));
+  }
+  return MW_OK;
+}
+
+// Plain update: panel, swaps left, TRSM (with the swaps right), plain GEMM;
+// every element sees the unblocked order.  Split update (DD): the panel in
+// two halves of 32 columns (left half factored; the right half's top rows
+// solved and the rows below updated by a split product; right half
+// factored), the swaps left and right, M = -(L11^-1) strictly lower, then
+// U12 -= M U12 and A22 -= L21 U12 as split tensor-core products.
 template <int W>
 static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d, const BlockedPlanHost& bp,
                                   const BlockedDev& bd, double* A, int64_t* piv, int64_t* info, cudaStream_t s) {
   const BatchView bv{d.order, d.n, d.moff, d.voff};
+  const bool split = bp.update == MW_UPDATE_SPLIT;
+  if (split && W != 2) return MW_EUNSUPPORTED;
+  constexpr int H = kBatchNb / 2;
+  constexpr int kFar = 1 << 29;
   for (int st = 0; st < bp.nsteps; ++st) {
     const int k0 = st * kBatchNb;
     const int act = bp.act[st];
-    int rc = launch_bpanel<W>(bv, act, p.nmax, k0, A, piv, info, s);
-    if (rc) return rc;
-    rc = launch_blaswp<W>(bv, act, k0, A, piv, s);
-    if (rc) return rc;
-    rc = launch_btrsm<W>(bv, act, bp.max_cb_trsm[st], k0, A, piv, s);
-    if (rc) return rc;
-    const int64_t ntiles = bp.toff[st + 1] - bp.toff[st];
-    if (bp.update == MW_UPDATE_SPLIT) {
-      if (W != 2) return MW_EUNSUPPORTED;
-      rc = split_bupdate_dd(bv, act, bp.max_mt[st], bp.max_cb_slice[st], bd.tiles + bp.toff[st], ntiles,
-                            bd.bases + bp.boff[st], bp.a_tiles, bp.b_tiles, k0, A, bd.split_ws, bd.split_bytes, s);
+    const int64_t nt = bp.trail.toff[st + 1] - bp.trail.toff[st];
+    int rc;
+    if (split) {
+      rc = launch_bpanel<W>(bv, act, p.nmax, k0, 0, H, A, piv, info, s);
+      if (rc) return rc;
+      rc = launch_btrsm_half<W>(bv, act, k0, A, piv, s);
+      if (rc) return rc;
+      rc = split_bupdate_dd(bv, kGeomPanelInner, act, bp.pinner.max_mt[st], bp.pinner.max_cb[st],
+                            bd.pinner.tiles + bp.pinner.toff[st], bp.pinner.toff[st + 1] - bp.pinner.toff[st],
+                            bd.pinner.bases + bp.pinner.boff[st], bd.a_tiles, bd.b_tiles, k0, A, bd.aux,
+                            bd.split_ws, bd.split_bytes, s);
+      if (rc) return rc;
+      rc = launch_bpanel<W>(bv, act, p.nmax, k0, H, H, A, piv, info, s);
+      if (rc) return rc;
+      rc = launch_bswap<W>(bv, act, k0, 0, kBatchNb, -k0, 0, k0, A, piv, s);   // left of the panel
+      if (rc) return rc;
+      rc = launch_bswap<W>(bv, act, k0, H, kBatchNb, 0, H, H, A, piv, s);     // the panel's left half
+      if (rc) return rc;
+      if (bp.max_cols[st] <= 0) continue;
+      rc = launch_bswap<W>(bv, act, k0, 0, kBatchNb, kBatchNb, kFar, bp.max_cols[st], A, piv, s);   // right
+      if (rc) return rc;
+      rc = split_binv_l11(bv, act, k0, A, bd.aux, s);
+      if (rc) return rc;
+      rc = split_bupdate_dd(bv, kGeomTrsmInv, act, bp.tinv.max_mt[st], bp.tinv.max_cb[st],
+                            bd.tinv.tiles + bp.tinv.toff[st], bp.tinv.toff[st + 1] - bp.tinv.toff[st],
+                            bd.tinv.bases + bp.tinv.boff[st], bd.a_tiles, bd.b_tiles, k0, A, bd.aux, bd.split_ws,
+                            bd.split_bytes, s);
+      if (rc) return rc;
+      rc = split_bupdate_dd(bv, kGeomTrail, act, bp.trail.max_mt[st], bp.trail.max_cb[st],
+                            bd.trail.tiles + bp.trail.toff[st], nt, bd.trail.bases + bp.trail.boff[st], bd.a_tiles,
+                            bd.b_tiles, k0, A, bd.aux, bd.split_ws, bd.split_bytes, s);
     } else {
-      rc = launch_bgemm_plain<W>(bv, bd.tiles + bp.toff[st], ntiles, k0, A, s);
+      rc = launch_bpanel<W>(bv, act, p.nmax, k0, 0, kBatchNb, A, piv, info, s);
+      if (rc) return rc;
+      rc = launch_blaswp<W>(bv, act, k0, A, piv, s);
+      if (rc) return rc;
+      rc = launch_btrsm<W>(bv, act, bp.max_cb_trsm[st], k0, A, piv, s);
+      if (rc) return rc;
+      rc = launch_bgemm_plain<W>(bv, bd.trail.tiles + bp.trail.toff[st], nt, k0, A, s);
     }
     if (rc) return rc;
   }

@@ -454,7 +454,7 @@ int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64
 // dynamic shared memory: pivot row [W][kBatchNb] and multipliers [W][nmax]
 template <int W>
 __global__ void __launch_bounds__(kPanelThreads)
-k_bpanel(BatchView bv, int nmax, int k0, double* __restrict__ A, int64_t* __restrict__ piv,
+k_bpanel(BatchView bv, int nmax, int kp, int width, double* __restrict__ A, int64_t* __restrict__ piv,
          int64_t* __restrict__ info) {
   extern __shared__ double bsm[];
   double* su = bsm;                  // [W][kBatchNb]
@@ -465,7 +465,9 @@ k_bpanel(BatchView bv, int nmax, int k0, double* __restrict__ A, int64_t* __rest
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sys = bv.order[blockIdx.x];
   const int n = bv.n[sys];
-  const int kb = min(kBatchNb, n - k0);
+  const int k0 = kp;                  // first column (and row) of this panel
+  const int kb = min(width, n - k0);
+  if (kb <= 0) return;                // uniform per CTA
   double* a = A + (int64_t)W * bv.moff[sys];
   const int64_t plane = (int64_t)n * n;
   int64_t* pv = piv + bv.voff[sys];
@@ -574,6 +576,48 @@ k_blaswp(BatchView bv, int k0, double* __restrict__ A, const int64_t* __restrict
       }
     }
   }
+}
+
+// row swaps k0 + [sw_lo, min(sw_hi, kb)) on the columns
+// [max(0, k0 + c_lo), min(n, k0 + c_hi)): CTA (pos, word, block of 128 columns)
+template <int W>
+__global__ void __launch_bounds__(128)
+k_bswap(BatchView bv, int k0, int sw_lo, int sw_hi, int c_lo, int c_hi, double* __restrict__ A,
+        const int64_t* __restrict__ piv) {
+  const int sys = bv.order[blockIdx.x];
+  const int n = bv.n[sys];
+  const int kb = min(kBatchNb, n - k0);
+  const int j0 = max(0, k0 + c_lo);
+  const int j1 = min(n, k0 + c_hi);
+  const int64_t j = (int64_t)j0 + (int64_t)blockIdx.z * blockDim.x + threadIdx.x;
+  if (j >= j1) return;
+  const int64_t plane = (int64_t)n * n;
+  const int64_t* pv = piv + bv.voff[sys];
+  double* col = A + (int64_t)W * bv.moff[sys] + blockIdx.y * plane + j * n;
+  const int hi = min(sw_hi, kb);
+  for (int kk = sw_lo; kk < hi; ++kk) {
+    const int k = k0 + kk;
+    const int p = (int)pv[k];
+    if (p != k) {
+      const double t = col[k];
+      col[k] = col[p];
+      col[p] = t;
+    }
+  }
+}
+
+// the top 32 rows of the right half of the panel: swaps of the left half,
+// then the unit lower 32 x 32 solve; CTA (pos, block of 8 columns)
+template <int W>
+__global__ void __launch_bounds__(256)
+k_btrsm_half(BatchView bv, int k0, double* __restrict__ A, const int64_t* __restrict__ piv) {
+  constexpr int H = kBatchNb / 2;
+  const int sys = bv.order[blockIdx.x];
+  const int n = bv.n[sys];
+  if (n - k0 - H <= 0) return;        // no right half: uniform per CTA
+  // columns k0 + H + blockIdx.y * 8 + c < min(n, k0 + 2H) (trsm_cols checks < n)
+  trsm_cols<W, H>(A + (int64_t)W * bv.moff[sys], n, (int64_t)n * n, min(n, k0 + 2 * H), k0, piv + bv.voff[sys],
+                  blockIdx.y);
 }
 
 // swaps + U12 = L11^-1 A12 on 8 columns: CTA (pos, column block)
@@ -713,14 +757,35 @@ void gemm_plain_tile_shape(int W, int* bm, int* bn) {
 }
 
 template <int W>
-int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, double* A, int64_t* piv, int64_t* info,
-                  cudaStream_t s) {
+int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, int c_off, int width, double* A, int64_t* piv,
+                  int64_t* info, cudaStream_t s) {
   if (act <= 0) return MW_OK;
+  if (width < 1 || width > kBatchNb) return MW_EUNSUPPORTED;
   const size_t shmem = sizeof(double) * (size_t)W * ((size_t)kBatchNb + (size_t)nmax);
   if (shmem > 48 * 1024)
     MW_CUDA_CHECK(cudaFuncSetAttribute(k_bpanel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
   ProfScope ps(kPhPanel, s);
-  k_bpanel<W><<<act, kPanelThreads, shmem, s>>>(bv, nmax, k0, A, piv, info);
+  k_bpanel<W><<<act, kPanelThreads, shmem, s>>>(bv, nmax, k0 + c_off, width, A, piv, info);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+int launch_bswap(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, int c_lo, int c_hi, int max_cols,
+                 double* A, const int64_t* piv, cudaStream_t s) {
+  if (act <= 0 || max_cols <= 0 || sw_hi <= sw_lo) return MW_OK;
+  ProfScope ps(kPhLaswp, s);
+  k_bswap<W><<<dim3((unsigned)act, W, (unsigned)((max_cols + 127) / 128)), 128, 0, s>>>(bv, k0, sw_lo, sw_hi, c_lo,
+                                                                                       c_hi, A, piv);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+int launch_btrsm_half(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s) {
+  if (act <= 0) return MW_OK;
+  ProfScope ps(kPhPanel, s);
+  k_btrsm_half<W><<<dim3((unsigned)act, kBatchNb / 2 / 8), 256, 0, s>>>(bv, k0, A, piv);
   MW_LAUNCH_CHECK();
   return MW_OK;
 }
@@ -756,7 +821,11 @@ int launch_bgemm_plain(const BatchView& bv, const TileEntry* tiles, int64_t ntil
 }
 
 #define MW_BATCHED_INST(W)                                                                                   \
-  template int launch_bpanel<W>(const BatchView&, int, int, int, double*, int64_t*, int64_t*, cudaStream_t); \
+  template int launch_bpanel<W>(const BatchView&, int, int, int, int, int, double*, int64_t*, int64_t*,        \
+                                cudaStream_t);                                                                \
+  template int launch_bswap<W>(const BatchView&, int, int, int, int, int, int, int, double*, const int64_t*,    \
+                               cudaStream_t);                                                                 \
+  template int launch_btrsm_half<W>(const BatchView&, int, int, double*, const int64_t*, cudaStream_t);       \
   template int launch_blaswp<W>(const BatchView&, int, int, double*, const int64_t*, cudaStream_t);          \
   template int launch_btrsm<W>(const BatchView&, int, int, int, double*, const int64_t*, cudaStream_t);      \
   template int launch_bgemm_plain<W>(const BatchView&, const TileEntry*, int64_t, int, double*, cudaStream_t);

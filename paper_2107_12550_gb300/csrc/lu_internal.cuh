@@ -65,9 +65,20 @@ struct TileEntry {
 
 constexpr int kBatchNb = 64;   // panel width of the batched blocked LU
 
+// panel columns [k0 + c_off, k0 + c_off + width) of rows [k0 + c_off, n); the
+// row swaps are applied inside those columns only
 template <int W>
-int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, double* A, int64_t* piv, int64_t* info,
-                  cudaStream_t s);
+int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, int c_off, int width, double* A, int64_t* piv,
+                  int64_t* info, cudaStream_t s);
+// row swaps k0 + [sw_lo, min(sw_hi, kb)) on the columns
+// [max(0, k0 + c_lo), min(n, k0 + c_hi)); max_cols bounds the column count
+template <int W>
+int launch_bswap(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, int c_lo, int c_hi, int max_cols,
+                 double* A, const int64_t* piv, cudaStream_t s);
+// the top 32 rows of the panel's right half: its swaps from the left half,
+// then L11(left half)^-1
+template <int W>
+int launch_btrsm_half(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s);
 template <int W>
 int launch_blaswp(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s);
 template <int W>
@@ -86,10 +97,17 @@ void gemm_plain_tile_shape(int W, int* bm, int* bn);
 // tiles) and act x max_cb (128-column blocks).
 constexpr int kSplitTileM = 128;
 constexpr int kSplitTileN = 32;
+// Operand geometries (ozaki.cu): the trailing update, and the TRSM as a
+// product with the explicit inverse of L11 (aux: per active position, the
+// strictly lower part of -(L11^-1), 2 words x 64 x 64, column-major).
+constexpr int kGeomTrail = 0;
+constexpr int kGeomTrsmInv = 1;
+constexpr int kGeomPanelInner = 2;   // inside the panel: right half -= left half x solved top rows
 size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles);
-int split_bupdate_dd(const BatchView& bv, int act, int max_mt, int max_cb, const TileEntry* tiles,
+int split_bupdate_dd(const BatchView& bv, int geom, int act, int max_mt, int max_cb, const TileEntry* tiles,
                      int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
-                     char* ws, size_t ws_bytes, cudaStream_t s);
+                     const double* aux, char* ws, size_t ws_bytes, cudaStream_t s);
+int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s);
 
 // substitution (solve.cu); y is a w-plane vector work area of n
 template <int W>

@@ -125,15 +125,17 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
 // slicing: L21 rows -> A slices [tile][p][128 x 64], row exponents e_i
 // one thread per row; 8 consecutive k at a time -> one 16-byte store per slice
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void slice_row(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t m,
-                                          unsigned char* __restrict__ aslices, int* __restrict__ ea,
-                                          int64_t r) {  // padded row index
+// element (r, k) of the row operand at L[r * lrs + k * lks]
+// (k >= kvalid: zero digits)
+__device__ __forceinline__ void slice_row(const double* __restrict__ L, int64_t lrs, int64_t lks, int64_t planeL,
+                                          int64_t m, int kvalid, unsigned char* __restrict__ aslices,
+                                          int* __restrict__ ea, int64_t r) {  // padded row index
   const int64_t tile = r / kTileM;
   const int rr = (int)(r % kTileM);
   const bool ok = r < m;
   double mx = 0.0;
   if (ok) {
-    for (int k = 0; k < kK; ++k) mx = fmax(mx, fabs(L[k * ldl + r]));
+    for (int k = 0; k < kvalid; ++k) mx = fmax(mx, fabs(L[r * lrs + k * lks]));
   }
   const int e = (mx > 0.0) ? exp_of_max(mx) : 0;
   ea[r] = e;
@@ -148,8 +150,8 @@ __device__ __forceinline__ void slice_row(const double* __restrict__ L, int64_t 
     for (int k8 = 0; k8 < 8; ++k8) {
       const int k = kc * 8 + k8;
       int a[kS];
-      if (ok && mx > 0.0) {
-        const int64_t idx = k * ldl + r;
+      if (ok && mx > 0.0 && k < kvalid) {
+        const int64_t idx = r * lrs + k * lks;
         const __int128 X = scaled_floor(L[idx], 120 - e) + scaled_floor(L[planeL + idx], 120 - e);
         digits15(X, a);
       } else {
@@ -171,21 +173,22 @@ __device__ __forceinline__ void slice_row(const double* __restrict__ L, int64_t 
 __global__ void __launch_bounds__(128)
 k_slice_rows(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t m,
              unsigned char* __restrict__ aslices, int* __restrict__ ea) {
-  slice_row(L, ldl, planeL, m, aslices, ea, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  slice_row(L, 1, ldl, planeL, m, kK, aslices, ea, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// U12 columns -> B slices [tile][q][32 x 64] (column j is a K-major row), f_j
-__device__ __forceinline__ void slice_col(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t N,
-                                          int64_t npad, unsigned char* __restrict__ bslices,
+// U12 columns -> B slices [tile][q][32 x 64] (column j is a K-major row), f_j;
+// element (k, j) of the column operand at U[k * uks + j * ujs]
+__device__ __forceinline__ void slice_col(const double* __restrict__ U, int64_t uks, int64_t ujs, int64_t planeU,
+                                          int64_t N, int64_t npad, int kvalid, unsigned char* __restrict__ bslices,
                                           int* __restrict__ fb, int64_t j) {  // padded column index
   if (j >= npad) return;
   const int64_t tile = j / kTileN;
   const int jj = (int)(j % kTileN);
   const bool ok = j < N;
-  const double* col = U + (ok ? j : 0) * ldu;
+  const double* col = U + (ok ? j : 0) * ujs;
   double mx = 0.0;
   if (ok) {
-    for (int k = 0; k < kK; ++k) mx = fmax(mx, fabs(col[k]));
+    for (int k = 0; k < kvalid; ++k) mx = fmax(mx, fabs(col[k * uks]));
   }
   const int f = (mx > 0.0) ? exp_of_max(mx) : 0;
   fb[j] = f;
@@ -200,8 +203,8 @@ __device__ __forceinline__ void slice_col(const double* __restrict__ U, int64_t 
     for (int k8 = 0; k8 < 8; ++k8) {
       const int k = kc * 8 + k8;
       int a[kS];
-      if (ok && mx > 0.0) {
-        const __int128 X = scaled_floor(col[k], 120 - f) + scaled_floor(col[planeU + k], 120 - f);
+      if (ok && mx > 0.0 && k < kvalid) {
+        const __int128 X = scaled_floor(col[k * uks], 120 - f) + scaled_floor(col[planeU + k * uks], 120 - f);
         digits15(X, a);
       } else {
 #pragma unroll
@@ -222,7 +225,7 @@ __device__ __forceinline__ void slice_col(const double* __restrict__ U, int64_t 
 __global__ void __launch_bounds__(128)
 k_slice_cols(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t N, int64_t npad,
              unsigned char* __restrict__ bslices, int* __restrict__ fb) {
-  slice_col(U, ldu, planeU, N, npad, bslices, fb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  slice_col(U, 1, ldu, planeU, N, npad, kK, bslices, fb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,7 +373,8 @@ struct SplitSmem {
 constexpr int kEpiWarps = 8;                       // two warpgroups over the 4 TMEM lane quarters
 constexpr int kSplitThreads = 64 + 32 * kEpiWarps;  // producer + MMA warps + epilogue
 
-__device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m,
+// entry (i, j) of C at C[i * crs + j * cjs]
+__device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, int64_t cjs, int64_t planeC, int64_t m,
                                            int64_t N, const unsigned char* __restrict__ aslices,
                                            const unsigned char* __restrict__ bslices,
                                            const int* __restrict__ ea, const int* __restrict__ fb,
@@ -479,7 +483,7 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t ldc, 
           val<2> pr;
           pr.v[0] = i192_take_rn(R, scale);
           pr.v[1] = i192_take_rn(R, scale);
-          const int64_t idx = j * ldc + i;
+          const int64_t idx = i * crs + j * cjs;
           val<2> cv = load<2>(C, planeC, idx);
           cv = sub<2>(cv, pr);
           store<2>(C, planeC, idx, cv);
@@ -506,61 +510,181 @@ k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int
              const unsigned char* __restrict__ aslices,
              const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
              const int* __restrict__ fb, DeviceStatus* status) {
-  split_tile(C, ldc, planeC, m, N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y);
+  split_tile(C, 1, ldc, planeC, m, N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y);
 }
 
 // ---- batched forms: per active system of a batch at panel step k0 ----------
-// L21 = rows [k0+64, n) of columns [k0, k0+64); U12 = rows [k0, k0+64) of
-// columns [k0+64, n); C = A22; all with lda = n.
+// Operand geometry of one split product C -= L U inside system `a` (lda = n):
+//  kGeomTrail: the trailing update, L = L21 (rows [r0, n) of columns
+//    [k0, r0)), U = U12, C = A22, r0 = k0 + 64;
+//  kGeomTrsmInv: U12 := U12 - M U12 with M the strictly lower part of
+//    -(L11^-1) (64 x 64, column-major in `aux`), which is U12 := L11^-1 U12,
+//    in transposed form C^T -= U12^T M^T: the rows of the product are the
+//    columns of U12;
+//  kGeomPanelInner: inside a 64-column panel, after its left 32 columns are
+//    factored and the top 32 rows of its right half are solved: the right
+//    half's rows below them -= L (left half, same rows) U (the solved rows),
+//    K = 32 (zero digits beyond).
+struct SplitOperands {
+  const double* L;
+  int64_t lrs, lks, planeL;
+  const double* U;
+  int64_t uks, ujs, planeU;
+  double* C;
+  int64_t crs, cjs, planeC;
+  int64_t m, N;
+  int K;
+};
+
+__device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int n, int k0, const double* aux) {
+  SplitOperands o;
+  const int64_t plane = (int64_t)n * n;
+  const int r0 = k0 + kK;
+  o.K = kK;
+  if (geom == kGeomPanelInner) {
+    constexpr int H = kK / 2;
+    const int q0 = k0 + H;
+    o.L = a + (int64_t)k0 * n + q0;
+    o.lrs = 1;
+    o.lks = n;
+    o.planeL = plane;
+    o.U = a + (int64_t)q0 * n + k0;
+    o.uks = 1;
+    o.ujs = n;
+    o.planeU = plane;
+    o.C = a + (int64_t)q0 * n + q0;
+    o.crs = 1;
+    o.cjs = n;
+    o.planeC = plane;
+    o.m = n - q0;
+    o.N = min(H, n - q0);
+    o.K = H;
+  } else if (geom == kGeomTrsmInv) {
+    o.L = a + (int64_t)r0 * n + k0;   // (j, t) -> U12(t, j)
+    o.lrs = n;
+    o.lks = 1;
+    o.planeL = plane;
+    o.U = aux;                        // (t, i) -> M(i, t)
+    o.uks = kK;
+    o.ujs = 1;
+    o.planeU = (int64_t)kK * kK;
+    o.C = a + (int64_t)r0 * n + k0;   // (j, i) -> U12(i, j)
+    o.crs = n;
+    o.cjs = 1;
+    o.planeC = plane;
+    o.m = n - r0;
+    o.N = kK;
+  } else {
+    o.L = a + (int64_t)k0 * n + r0;
+    o.lrs = 1;
+    o.lks = n;
+    o.planeL = plane;
+    o.U = a + (int64_t)r0 * n + k0;
+    o.uks = 1;
+    o.ujs = n;
+    o.planeU = plane;
+    o.C = a + (int64_t)r0 * n + r0;
+    o.crs = 1;
+    o.cjs = n;
+    o.planeC = plane;
+    o.m = n - r0;
+    o.N = n - r0;
+  }
+  return o;
+}
 
 // grid (act, max_mt): 128-row tile blockIdx.y of system order[blockIdx.x]
 __global__ void __launch_bounds__(128)
-k_bslice_rows(BatchView bv, const int2* __restrict__ bases, int k0, const double* __restrict__ A,
-              unsigned char* __restrict__ aslices, int* __restrict__ ea) {
+k_bslice_rows(BatchView bv, int geom, const int2* __restrict__ bases, int k0, double* __restrict__ A,
+              const double* __restrict__ aux, unsigned char* __restrict__ aslices, int* __restrict__ ea) {
   const int pos = blockIdx.x;
   const int sys = bv.order[pos];
   const int n = bv.n[sys];
-  const int64_t m = n - k0 - kK;
-  if ((int64_t)blockIdx.y * kTileM >= m) return;
-  const int64_t plane = (int64_t)n * n;
-  const double* L = A + 2 * bv.moff[sys] + (int64_t)k0 * n + (k0 + kK);
+  const SplitOperands o = batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK);
+  if (o.m <= 0 || o.N <= 0 || (int64_t)blockIdx.y * kTileM >= o.m) return;
   const int abase = bases[pos].x;
-  slice_row(L, n, plane, m, aslices + (int64_t)abase * kS * kASliceBytes, ea + (int64_t)abase * kTileM,
-            (int64_t)blockIdx.y * kTileM + threadIdx.x);
+  slice_row(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices + (int64_t)abase * kS * kASliceBytes,
+            ea + (int64_t)abase * kTileM, (int64_t)blockIdx.y * kTileM + threadIdx.x);
 }
 
 // grid (act, max_cb): 128-column block blockIdx.y of system order[blockIdx.x]
 __global__ void __launch_bounds__(128)
-k_bslice_cols(BatchView bv, const int2* __restrict__ bases, int k0, const double* __restrict__ A,
-              unsigned char* __restrict__ bslices, int* __restrict__ fb) {
+k_bslice_cols(BatchView bv, int geom, const int2* __restrict__ bases, int k0, double* __restrict__ A,
+              const double* __restrict__ aux, unsigned char* __restrict__ bslices, int* __restrict__ fb) {
   const int pos = blockIdx.x;
   const int sys = bv.order[pos];
   const int n = bv.n[sys];
-  const int64_t N = n - k0 - kK;
-  const int64_t npad = (N + kTileN - 1) / kTileN * kTileN;
+  const SplitOperands o = batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK);
+  if (o.m <= 0 || o.N <= 0) return;
+  const int64_t npad = (o.N + kTileN - 1) / kTileN * kTileN;
   if ((int64_t)blockIdx.y * 128 >= npad) return;
-  const int64_t plane = (int64_t)n * n;
-  const double* U = A + 2 * bv.moff[sys] + (int64_t)(k0 + kK) * n + k0;
   const int bbase = bases[pos].y;
-  slice_col(U, n, plane, N, npad, bslices + (int64_t)bbase * kS * kBSliceBytes, fb + (int64_t)bbase * kTileN,
-            (int64_t)blockIdx.y * 128 + threadIdx.x);
+  slice_col(o.U, o.uks, o.ujs, o.planeU, o.N, npad, o.K, bslices + (int64_t)bbase * kS * kBSliceBytes,
+            fb + (int64_t)bbase * kTileN, (int64_t)blockIdx.y * 128 + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 1)
-k_bsplit_gemm(BatchView bv, const TileEntry* __restrict__ tiles, const int2* __restrict__ bases, int k0,
-              double* __restrict__ A, const unsigned char* __restrict__ aslices,
+k_bsplit_gemm(BatchView bv, int geom, const TileEntry* __restrict__ tiles, const int2* __restrict__ bases, int k0,
+              double* __restrict__ A, const double* __restrict__ aux, const unsigned char* __restrict__ aslices,
               const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
               const int* __restrict__ fb, DeviceStatus* status) {
   const TileEntry t = tiles[blockIdx.x];
   const int sys = bv.order[t.pos];
   const int n = bv.n[sys];
-  const int64_t m = n - k0 - kK;
-  const int64_t plane = (int64_t)n * n;
-  double* C = A + 2 * bv.moff[sys] + (int64_t)(k0 + kK) * n + (k0 + kK);
+  const SplitOperands o = batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)t.pos * 2 * kK * kK);
   const int2 b = bases[t.pos];
-  split_tile(C, n, plane, m, m, aslices + (int64_t)b.x * kS * kASliceBytes,
+  split_tile(o.C, o.crs, o.cjs, o.planeC, o.m, o.N, aslices + (int64_t)b.x * kS * kASliceBytes,
              bslices + (int64_t)b.y * kS * kBSliceBytes, ea + (int64_t)b.x * kTileM, fb + (int64_t)b.y * kTileN,
              status, t.ti, t.tj);
+}
+
+// M = strictly lower part of -(L11^-1) for every active system with columns
+// right of the panel; L11 = the unit lower 64 x 64 block at (k0, k0).
+// X = L11^-1 by column-oriented substitution on all 64 columns of the
+// identity at once: for t ascending, x_it -= l_it x_tc for i > t, c <= t.
+// dynamic shared memory: X, 2 words x 64 x 64 doubles
+__global__ void __launch_bounds__(256)
+k_binv_l11(BatchView bv, int k0, const double* __restrict__ A, double* __restrict__ aux) {
+  extern __shared__ double xs[];     // [2][64 cols][64 rows]
+  const int pos = blockIdx.x;
+  const int sys = bv.order[pos];
+  const int n = bv.n[sys];
+  if (n - k0 - kK <= 0) return;
+  const double* a = A + 2 * bv.moff[sys];
+  const int64_t plane = (int64_t)n * n;
+  constexpr int P = kK * kK;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) {
+    const int c = e / kK, i = e % kK;
+    xs[e] = (i == c) ? 1.0 : 0.0;
+    xs[P + e] = 0.0;
+  }
+  for (int t = 0; t < kK - 1; ++t) {
+    __syncthreads();
+    const int rows = kK - 1 - t;          // i in (t, 64)
+    const int items = rows * (t + 1);     // c in [0, t]
+    const int64_t lcol = (int64_t)(k0 + t) * n + k0;
+    for (int q = threadIdx.x; q < items; q += blockDim.x) {
+      const int i = t + 1 + q % rows, c = q / rows;
+      val<2> x, l, u;
+      x.v[0] = xs[c * kK + i];
+      x.v[1] = xs[P + c * kK + i];
+      l.v[0] = __ldg(a + lcol + i);
+      l.v[1] = __ldg(a + plane + lcol + i);
+      u.v[0] = xs[c * kK + t];
+      u.v[1] = xs[P + c * kK + t];
+      x = msub<2>(x, l, u);
+      xs[c * kK + i] = x.v[0];
+      xs[P + c * kK + i] = x.v[1];
+    }
+  }
+  __syncthreads();
+  double* m = aux + (int64_t)pos * 2 * P;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) {
+    const int c = e / kK, i = e % kK;
+    const bool below = i > c;
+    m[e] = below ? -xs[e] : 0.0;
+    m[P + e] = below ? -xs[P + e] : 0.0;
+  }
 }
 
 size_t split_smem_bytes() {
@@ -637,9 +761,9 @@ size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles) {
          align256(sizeof(int) * (size_t)a_tiles * kTileM) + align256(sizeof(int) * (size_t)b_tiles * kTileN);
 }
 
-int split_bupdate_dd(const BatchView& bv, int act, int max_mt, int max_cb, const TileEntry* tiles,
+int split_bupdate_dd(const BatchView& bv, int geom, int act, int max_mt, int max_cb, const TileEntry* tiles,
                      int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
-                     char* ws, size_t ws_bytes, cudaStream_t s) {
+                     const double* aux, char* ws, size_t ws_bytes, cudaStream_t s) {
   if (act <= 0 || ntiles <= 0) return MW_OK;
   if (split_batched_workspace_bytes(a_tiles, b_tiles) > ws_bytes) return MW_EUNSUPPORTED;
   size_t off = 256;
@@ -653,23 +777,37 @@ int split_bupdate_dd(const BatchView& bv, int act, int max_mt, int max_cb, const
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
   {
     ProfScope ps(kPhSplitAux, s);
-    k_bslice_rows<<<dim3((unsigned)act, (unsigned)max_mt), 128, 0, s>>>(bv, bases, k0, A, aslices, ea);
+    k_bslice_rows<<<dim3((unsigned)act, (unsigned)max_mt), 128, 0, s>>>(bv, geom, bases, k0, A, aux, aslices, ea);
     MW_LAUNCH_CHECK();
-    k_bslice_cols<<<dim3((unsigned)act, (unsigned)max_cb), 128, 0, s>>>(bv, bases, k0, A, bslices, fb);
+    k_bslice_cols<<<dim3((unsigned)act, (unsigned)max_cb), 128, 0, s>>>(bv, geom, bases, k0, A, aux, bslices, fb);
     MW_LAUNCH_CHECK();
   }
   {
-    ProfScope ps(kPhGemmSplit, s);
+    ProfScope ps(geom == kGeomTrsmInv ? kPhTrsm : (geom == kGeomPanelInner ? kPhPanel : kPhGemmSplit), s);
     const size_t shmem = split_smem_bytes();
     static bool attr_set = false;
     if (!attr_set) {
       MW_CUDA_CHECK(cudaFuncSetAttribute(k_bsplit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
       attr_set = true;
     }
-    k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, tiles, bases, k0, A, aslices, bslices, ea, fb,
-                                                                status);
+    k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, geom, tiles, bases, k0, A, aux, aslices,
+                                                                bslices, ea, fb, status);
     MW_LAUNCH_CHECK();
   }
+  return MW_OK;
+}
+
+int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s) {
+  if (act <= 0) return MW_OK;
+  const size_t shmem = sizeof(double) * 2 * kK * kK;
+  static bool attr_set = false;
+  if (!attr_set) {
+    MW_CUDA_CHECK(cudaFuncSetAttribute(k_binv_l11, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    attr_set = true;
+  }
+  ProfScope ps(kPhTrsm, s);
+  k_binv_l11<<<(unsigned)act, 256, shmem, s>>>(bv, k0, A, aux);
+  MW_LAUNCH_CHECK();
   return MW_OK;
 }
 

@@ -129,9 +129,11 @@ def test_blocked_split_dd_backward_error_and_pivots():
         assert diff <= max(1, n // 50), (s, n, diff)
 
 
-def test_blocked_split_matches_single_system_split():
-    """The batched split LU runs the same slicing, tile products and
-    recombination as the single-system split LU: identical factors."""
+def test_blocked_split_close_to_plain_factors():
+    """The batched split LU (U12 from the explicit inverse of L11 and both
+    products on the tensor cores) stays within a few DD roundings of the
+    plain factors: same pivots, entrywise |LU_split - LU_plain| <= 2^-90
+    max|A| (uniform entries, moderate growth)."""
     n_list = [300, 129, 200]
     mats, _ = _uniform_batch(2, n_list, seed=55)
     A = dev(api().pack_matrices(mats, 2))
@@ -140,9 +142,10 @@ def test_blocked_split_matches_single_system_split():
     _, voff = api().batch_offsets(n_list)
     pv = host(piv)
     for s, n in enumerate(n_list):
-        LU1, piv1, _ = api().ludecomp(dev(mats[s]), 2, "split")
-        assert np.array_equal(host(LU1)[:, :, :n], LUs[s])
-        assert np.array_equal(host(piv1), pv[voff[s]: voff[s] + n])
+        LUo, pivo, _ = oracle.lu(2, mats[s])
+        assert np.array_equal(pivo, pv[voff[s]: voff[s] + n])
+        d = np.abs((LUs[s][0] - LUo[0, :, :n]) + (LUs[s][1] - LUo[1, :, :n]))
+        assert d.max() <= 2.0 ** -90, (s, n, np.log2(d.max()))
 
 
 @pytest.mark.parametrize("inner", [2, 3])
