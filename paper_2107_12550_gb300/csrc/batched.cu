@@ -200,13 +200,15 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 // y_i -= l_ij y_j (j ascending), d_j = 1 / u_jj for all j, then
 // x_j = y_j d_j and y_i -= u_ij x_j (j descending) -- blocked by 32 columns:
 // warp 0 solves the 32 x 32 triangle of a block with the rows in its lanes,
-// then all threads apply the block to the remaining rows, four rows per
-// thread, with each row's updates still in the order above.
+// then all threads apply the block to the remaining rows, two rows per
+// thread, with each row's updates still in the order above.  One CTA of 512
+// threads per SM takes the systems largest first.
 // Systems whose state is not "running" are skipped when st is given.
 // dynamic shared memory: 2 * W * nmax doubles
 // ---------------------------------------------------------------------------
 constexpr int kSolveBs = 32;
-constexpr int kSolveRpt = kBatchMaxN / kBatchThreads;   // rows per thread in a block update
+constexpr int kSolveThreads = 512;                      // one CTA per SM: the largest systems get a whole SM
+constexpr int kSolveRpt = kBatchMaxN / kSolveThreads;   // rows per thread in a block update
 
 template <int W>
 __device__ __forceinline__ val<W> smem_val(const double* v, int nmax, int i) {
@@ -223,7 +225,7 @@ __device__ __forceinline__ void smem_put(double* v, int nmax, int i, const val<W
 }
 
 template <int W>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kSolveThreads, 1)
 k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
                 const int64_t* __restrict__ moff, const int64_t* __restrict__ voff,
                 const double* __restrict__ LU, const int64_t* __restrict__ piv, const double* b,
@@ -243,11 +245,11 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
     const int64_t* pv = piv + voff[s];
     const double* bs = b + (int64_t)W * voff[s];
     double* xs = x + (int64_t)W * voff[s];
-    for (int i = tid; i < n; i += kBatchThreads)
+    for (int i = tid; i < n; i += kSolveThreads)
 #pragma unroll
       for (int c = 0; c < W; ++c) ysm[c * nmax + i] = bs[c * n + i];
     // reciprocals of the diagonal, all j in parallel
-    for (int j = tid; j < n; j += kBatchThreads) {
+    for (int j = tid; j < n; j += kSolveThreads) {
       val<W> one;
 #pragma unroll
       for (int c = 0; c < W; ++c) one.v[c] = 0.0;
@@ -293,7 +295,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         val<W> yr[kSolveRpt];
 #pragma unroll
         for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = r0 + tid + q * kBatchThreads;
+          const int i = r0 + tid + q * kSolveThreads;
           if (i < n) yr[q] = smem_val<W>(ysm, nmax, i);
         }
 #pragma unroll 4
@@ -302,13 +304,13 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const int64_t col = (int64_t)(j0 + jj) * n;
 #pragma unroll
           for (int q = 0; q < kSolveRpt; ++q) {
-            const int i = r0 + tid + q * kBatchThreads;
+            const int i = r0 + tid + q * kSolveThreads;
             if (i < n) yr[q] = msub<W>(yr[q], load_ro<W>(a, plane, col + i), yj);
           }
         }
 #pragma unroll
         for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = r0 + tid + q * kBatchThreads;
+          const int i = r0 + tid + q * kSolveThreads;
           if (i < n) smem_put<W>(ysm, nmax, i, yr[q]);
         }
       }
@@ -342,7 +344,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         val<W> yr[kSolveRpt];
 #pragma unroll
         for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = tid + q * kBatchThreads;
+          const int i = tid + q * kSolveThreads;
           if (i < jb) yr[q] = smem_val<W>(ysm, nmax, i);
         }
 #pragma unroll 4
@@ -351,19 +353,19 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const int64_t col = (int64_t)(jb + jj) * n;
 #pragma unroll
           for (int q = 0; q < kSolveRpt; ++q) {
-            const int i = tid + q * kBatchThreads;
+            const int i = tid + q * kSolveThreads;
             if (i < jb) yr[q] = msub<W>(yr[q], load_ro<W>(a, plane, col + i), xj);
           }
         }
 #pragma unroll
         for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = tid + q * kBatchThreads;
+          const int i = tid + q * kSolveThreads;
           if (i < jb) smem_put<W>(ysm, nmax, i, yr[q]);
         }
       }
       __syncthreads();
     }
-    for (int i = tid; i < n; i += kBatchThreads)
+    for (int i = tid; i < n; i += kSolveThreads)
 #pragma unroll
       for (int c = 0; c < W; ++c) xs[c * n + i] = ysm[c * nmax + i];
     __syncthreads();
@@ -622,8 +624,8 @@ static int solve_batched_launch(int count, int nmax, const int* order, const int
   int rc = set_smem(k_solve_batched<W>, shmem);
   if (rc) return rc;
   ProfScope ps(kPhBatchSolve, s);
-  const int grid = std::min(count, 4 * sm_count_b());
-  k_solve_batched<W><<<grid, kBatchThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x,
+  const int grid = std::min(count, sm_count_b());
+  k_solve_batched<W><<<grid, kSolveThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x,
                                                        static_cast<const BatchState*>(st), cur);
   MW_LAUNCH_CHECK();
   return MW_OK;
@@ -727,17 +729,26 @@ struct BlockedPlanHost {
   std::vector<int> act, max_cb_trsm, max_cols;
   GeomPlanHost trail;   // plain: BM x BN tiles; split: 128 x 32 tiles of A22
   GeomPlanHost tinv;    // split: 128 x 32 tiles of U12^T (the TRSM as a product with L11^-1)
-  GeomPlanHost pinner;  // split: 128 x 32 tiles of the panel's right half below its top rows
+  GeomPlanHost pinner[3];  // split: 128 x 32 tiles of the inner panel updates (kInner order)
 };
+
+// the inner updates of the recursive split panel: (column offset, half width)
+// of the blocks 64 -> 32 + 32 -> 16 + 16
+struct InnerSpec {
+  int c_off, h;
+};
+constexpr InnerSpec kInner[3] = {{0, 16}, {0, 32}, {32, 16}};
+constexpr int kPanelLeaf = 16;
 
 // tiles of an m x N product for every active system of one step
 static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool split, int bm, int bn,
-                          int (*dims)(int n, int k0, int* N), int k0) {
+                          int (*dims)(int n, int k0, int c_off, int h, int* N), int k0, int c_off = 0,
+                          int h = 0) {
   int64_t at = 0, btl = 0;
   int max_m = 0, max_n = 0;
   for (int pos = 0; pos < act; ++pos) {
     int N = 0;
-    const int m = dims(p.n[p.order[pos]], k0, &N);
+    const int m = dims(p.n[p.order[pos]], k0, c_off, h, &N);
     if (split) g.bases.push_back(make_int2((int)at, (int)btl));
     if (m <= 0 || N <= 0) continue;
     max_m = std::max(max_m, m);
@@ -758,18 +769,18 @@ static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool
   g.boff.push_back((int64_t)g.bases.size());
 }
 
-static int dims_trail(int n, int k0, int* N) {
+static int dims_trail(int n, int k0, int, int, int* N) {
   *N = n - k0 - kBatchNb;
   return n - k0 - kBatchNb;
 }
-static int dims_tinv(int n, int k0, int* N) {
+static int dims_tinv(int n, int k0, int, int, int* N) {
   *N = kBatchNb;
   return n - k0 - kBatchNb;
 }
-static int dims_pinner(int n, int k0, int* N) {
-  constexpr int H = kBatchNb / 2;
-  *N = std::min(H, n - k0 - H);
-  return n - k0 - H;
+static int dims_pinner(int n, int k0, int c_off, int h, int* N) {
+  const int m = n - k0 - c_off - h;
+  *N = std::min(h, m);
+  return m;
 }
 
 static void make_blocked_plan(const BatchPlanHost& p, int W, int update, BlockedPlanHost& bp) {
@@ -783,7 +794,7 @@ static void make_blocked_plan(const BatchPlanHost& p, int W, int update, Blocked
     bn = kSplitTileN;
   }
   const int count = (int)p.n.size();
-  for (GeomPlanHost* g : {&bp.trail, &bp.tinv, &bp.pinner}) {
+  for (GeomPlanHost* g : {&bp.trail, &bp.tinv, &bp.pinner[0], &bp.pinner[1], &bp.pinner[2]}) {
     g->toff.push_back(0);
     g->boff.push_back(0);
   }
@@ -798,7 +809,9 @@ static void make_blocked_plan(const BatchPlanHost& p, int W, int update, Blocked
     add_geom_step(bp.trail, p, act, split, bm, bn, dims_trail, k0);
     if (split) {
       add_geom_step(bp.tinv, p, act, true, kSplitTileM, kSplitTileN, dims_tinv, k0);
-      add_geom_step(bp.pinner, p, act, true, kSplitTileM, kSplitTileN, dims_pinner, k0);
+      for (int q = 0; q < 3; ++q)
+        add_geom_step(bp.pinner[q], p, act, true, kSplitTileM, kSplitTileN, dims_pinner, k0, kInner[q].c_off,
+                      kInner[q].h);
     }
     ++bp.nsteps;
   }
@@ -812,15 +825,20 @@ static size_t geom_bytes(const GeomPlanHost& g) {
 static int64_t blocked_count(const BlockedPlanHost& bp) { return bp.act.empty() ? 0 : bp.act[0]; }
 
 static int64_t max_a_tiles(const BlockedPlanHost& bp) {
-  return std::max(bp.trail.a_tiles, std::max(bp.tinv.a_tiles, bp.pinner.a_tiles));
+  int64_t t = std::max(bp.trail.a_tiles, bp.tinv.a_tiles);
+  for (const auto& g : bp.pinner) t = std::max(t, g.a_tiles);
+  return t;
 }
 static int64_t max_b_tiles(const BlockedPlanHost& bp) {
-  return std::max(bp.trail.b_tiles, std::max(bp.tinv.b_tiles, bp.pinner.b_tiles));
+  int64_t t = std::max(bp.trail.b_tiles, bp.tinv.b_tiles);
+  for (const auto& g : bp.pinner) t = std::max(t, g.b_tiles);
+  return t;
 }
 
 // [trail | tinv | pinner tiles and bases | aux | split scratch]
 static size_t blocked_extra_bytes(const BlockedPlanHost& bp) {
-  size_t b = geom_bytes(bp.trail) + geom_bytes(bp.tinv) + geom_bytes(bp.pinner);
+  size_t b = geom_bytes(bp.trail) + geom_bytes(bp.tinv);
+  for (const auto& g : bp.pinner) b += geom_bytes(g);
   if (bp.update == MW_UPDATE_SPLIT) {
     b += align256(sizeof(double) * 2 * kBatchNb * kBatchNb * (size_t)std::max<int64_t>(1, blocked_count(bp)));
     b += split_batched_workspace_bytes(max_a_tiles(bp), max_b_tiles(bp));
@@ -834,7 +852,7 @@ struct GeomDev {
 };
 
 struct BlockedDev {
-  GeomDev trail, tinv, pinner;
+  GeomDev trail, tinv, pinner[3];
   double* aux;
   char* split_ws;
   size_t split_bytes;
@@ -861,8 +879,10 @@ static int upload_blocked(const BlockedPlanHost& bp, char* base, BlockedDev& d, 
   if (rc) return rc;
   rc = upload_geom(bp.tinv, base, off, d.tinv, s);
   if (rc) return rc;
-  rc = upload_geom(bp.pinner, base, off, d.pinner, s);
-  if (rc) return rc;
+  for (int q = 0; q < 3; ++q) {
+    rc = upload_geom(bp.pinner[q], base, off, d.pinner[q], s);
+    if (rc) return rc;
+  }
   d.aux = nullptr;
   d.split_ws = nullptr;
   d.split_bytes = 0;
@@ -878,11 +898,37 @@ static int upload_blocked(const BlockedPlanHost& bp, char* base, BlockedDev& d, 
   return MW_OK;
 }
 
+// the split path's panel: columns [k0 + c_off, k0 + c_off + w) factored
+// recursively -- left half, the right half's top rows solved, the rows below
+// updated by a split product, right half, then the right half's swaps on the
+// left half -- down to leaves of kPanelLeaf columns factored on the FP64 pipe
+template <int W>
+static int split_panel(const BatchPlanHost& p, const BatchView& bv, const BlockedPlanHost& bp, const BlockedDev& bd,
+                       int st, int act, int k0, int c_off, int w, double* A, int64_t* piv, int64_t* info,
+                       cudaStream_t s) {
+  if (w <= kPanelLeaf) return launch_bpanel<W>(bv, act, p.nmax, k0, c_off, w, A, piv, info, s);
+  const int h = w / 2;
+  int q = -1;
+  for (int i = 0; i < 3; ++i)
+    if (kInner[i].c_off == c_off && kInner[i].h == h) q = i;
+  if (q < 0) return MW_EUNSUPPORTED;
+  int rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off, h, A, piv, info, s);
+  if (rc) return rc;
+  rc = launch_btrsm_sub<W>(bv, act, k0, c_off, h, A, piv, s);
+  if (rc) return rc;
+  const GeomPlanHost& g = bp.pinner[q];
+  rc = split_bupdate_dd(bv, kGeomPanelInner, c_off, h, act, g.max_mt[st], g.max_cb[st], bd.pinner[q].tiles + g.toff[st],
+                        g.toff[st + 1] - g.toff[st], bd.pinner[q].bases + g.boff[st], bd.a_tiles, bd.b_tiles, k0, A,
+                        bd.aux, bd.split_ws, bd.split_bytes, s);
+  if (rc) return rc;
+  rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off + h, w - h, A, piv, info, s);
+  if (rc) return rc;
+  return launch_bswap<W>(bv, act, k0, c_off + h, c_off + w, c_off, c_off + h, h, A, piv, s);
+}
+
 // Plain update: panel, swaps left, TRSM (with the swaps right), plain GEMM;
-// every element sees the unblocked order.  Split update (DD): the panel in
-// two halves of 32 columns (left half factored; the right half's top rows
-// solved and the rows below updated by a split product; right half
-// factored), the swaps left and right, M = -(L11^-1) strictly lower, then
+// every element sees the unblocked order.  Split update (DD): the recursive
+// panel above, the swaps left and right, M = -(L11^-1) strictly lower, then
 // U12 -= M U12 and A22 -= L21 U12 as split tensor-core products.
 template <int W>
 static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d, const BlockedPlanHost& bp,
@@ -890,7 +936,6 @@ static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d,
   const BatchView bv{d.order, d.n, d.moff, d.voff};
   const bool split = bp.update == MW_UPDATE_SPLIT;
   if (split && W != 2) return MW_EUNSUPPORTED;
-  constexpr int H = kBatchNb / 2;
   constexpr int kFar = 1 << 29;
   for (int st = 0; st < bp.nsteps; ++st) {
     const int k0 = st * kBatchNb;
@@ -898,32 +943,21 @@ static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d,
     const int64_t nt = bp.trail.toff[st + 1] - bp.trail.toff[st];
     int rc;
     if (split) {
-      rc = launch_bpanel<W>(bv, act, p.nmax, k0, 0, H, A, piv, info, s);
-      if (rc) return rc;
-      rc = launch_btrsm_half<W>(bv, act, k0, A, piv, s);
-      if (rc) return rc;
-      rc = split_bupdate_dd(bv, kGeomPanelInner, act, bp.pinner.max_mt[st], bp.pinner.max_cb[st],
-                            bd.pinner.tiles + bp.pinner.toff[st], bp.pinner.toff[st + 1] - bp.pinner.toff[st],
-                            bd.pinner.bases + bp.pinner.boff[st], bd.a_tiles, bd.b_tiles, k0, A, bd.aux,
-                            bd.split_ws, bd.split_bytes, s);
-      if (rc) return rc;
-      rc = launch_bpanel<W>(bv, act, p.nmax, k0, H, H, A, piv, info, s);
+      rc = split_panel<W>(p, bv, bp, bd, st, act, k0, 0, kBatchNb, A, piv, info, s);
       if (rc) return rc;
       rc = launch_bswap<W>(bv, act, k0, 0, kBatchNb, -k0, 0, k0, A, piv, s);   // left of the panel
-      if (rc) return rc;
-      rc = launch_bswap<W>(bv, act, k0, H, kBatchNb, 0, H, H, A, piv, s);     // the panel's left half
       if (rc) return rc;
       if (bp.max_cols[st] <= 0) continue;
       rc = launch_bswap<W>(bv, act, k0, 0, kBatchNb, kBatchNb, kFar, bp.max_cols[st], A, piv, s);   // right
       if (rc) return rc;
       rc = split_binv_l11(bv, act, k0, A, bd.aux, s);
       if (rc) return rc;
-      rc = split_bupdate_dd(bv, kGeomTrsmInv, act, bp.tinv.max_mt[st], bp.tinv.max_cb[st],
+      rc = split_bupdate_dd(bv, kGeomTrsmInv, 0, 0, act, bp.tinv.max_mt[st], bp.tinv.max_cb[st],
                             bd.tinv.tiles + bp.tinv.toff[st], bp.tinv.toff[st + 1] - bp.tinv.toff[st],
                             bd.tinv.bases + bp.tinv.boff[st], bd.a_tiles, bd.b_tiles, k0, A, bd.aux, bd.split_ws,
                             bd.split_bytes, s);
       if (rc) return rc;
-      rc = split_bupdate_dd(bv, kGeomTrail, act, bp.trail.max_mt[st], bp.trail.max_cb[st],
+      rc = split_bupdate_dd(bv, kGeomTrail, 0, 0, act, bp.trail.max_mt[st], bp.trail.max_cb[st],
                             bd.trail.tiles + bp.trail.toff[st], nt, bd.trail.bases + bp.trail.boff[st], bd.a_tiles,
                             bd.b_tiles, k0, A, bd.aux, bd.split_ws, bd.split_bytes, s);
     } else {

@@ -606,17 +606,17 @@ k_bswap(BatchView bv, int k0, int sw_lo, int sw_hi, int c_lo, int c_hi, double* 
   }
 }
 
-// the top 32 rows of the right half of the panel: swaps of the left half,
-// then the unit lower 32 x 32 solve; CTA (pos, block of 8 columns)
-template <int W>
+// inside the panel, block of 2H columns at column c0 = k0 + c_off: the top H
+// rows of its right half get the swaps of the left half, then the unit
+// lower H x H solve; CTA (pos, block of 8 columns)
+template <int W, int H>
 __global__ void __launch_bounds__(256)
-k_btrsm_half(BatchView bv, int k0, double* __restrict__ A, const int64_t* __restrict__ piv) {
-  constexpr int H = kBatchNb / 2;
+k_btrsm_sub(BatchView bv, int c0, double* __restrict__ A, const int64_t* __restrict__ piv) {
   const int sys = bv.order[blockIdx.x];
   const int n = bv.n[sys];
-  if (n - k0 - H <= 0) return;        // no right half: uniform per CTA
-  // columns k0 + H + blockIdx.y * 8 + c < min(n, k0 + 2H) (trsm_cols checks < n)
-  trsm_cols<W, H>(A + (int64_t)W * bv.moff[sys], n, (int64_t)n * n, min(n, k0 + 2 * H), k0, piv + bv.voff[sys],
+  if (n - c0 - H <= 0) return;        // no right half: uniform per CTA
+  // columns c0 + H + blockIdx.y * 8 + c < min(n, c0 + 2H) (trsm_cols checks the bound)
+  trsm_cols<W, H>(A + (int64_t)W * bv.moff[sys], n, (int64_t)n * n, min(n, c0 + 2 * H), c0, piv + bv.voff[sys],
                   blockIdx.y);
 }
 
@@ -782,10 +782,15 @@ int launch_bswap(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, int
 }
 
 template <int W>
-int launch_btrsm_half(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s) {
+int launch_btrsm_sub(const BatchView& bv, int act, int k0, int c_off, int h, double* A, const int64_t* piv,
+                     cudaStream_t s) {
   if (act <= 0) return MW_OK;
   ProfScope ps(kPhPanel, s);
-  k_btrsm_half<W><<<dim3((unsigned)act, kBatchNb / 2 / 8), 256, 0, s>>>(bv, k0, A, piv);
+  switch (h) {
+    case 16: k_btrsm_sub<W, 16><<<dim3((unsigned)act, 2), 256, 0, s>>>(bv, k0 + c_off, A, piv); break;
+    case 32: k_btrsm_sub<W, 32><<<dim3((unsigned)act, 4), 256, 0, s>>>(bv, k0 + c_off, A, piv); break;
+    default: return MW_EUNSUPPORTED;
+  }
   MW_LAUNCH_CHECK();
   return MW_OK;
 }
@@ -825,7 +830,7 @@ int launch_bgemm_plain(const BatchView& bv, const TileEntry* tiles, int64_t ntil
                                 cudaStream_t);                                                                \
   template int launch_bswap<W>(const BatchView&, int, int, int, int, int, int, int, double*, const int64_t*,    \
                                cudaStream_t);                                                                 \
-  template int launch_btrsm_half<W>(const BatchView&, int, int, double*, const int64_t*, cudaStream_t);       \
+  template int launch_btrsm_sub<W>(const BatchView&, int, int, int, int, double*, const int64_t*, cudaStream_t); \
   template int launch_blaswp<W>(const BatchView&, int, int, double*, const int64_t*, cudaStream_t);          \
   template int launch_btrsm<W>(const BatchView&, int, int, int, double*, const int64_t*, cudaStream_t);      \
   template int launch_bgemm_plain<W>(const BatchView&, const TileEntry*, int64_t, int, double*, cudaStream_t);

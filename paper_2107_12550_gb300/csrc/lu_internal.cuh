@@ -75,10 +75,12 @@ int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, int c_off, int
 template <int W>
 int launch_bswap(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, int c_lo, int c_hi, int max_cols,
                  double* A, const int64_t* piv, cudaStream_t s);
-// the top 32 rows of the panel's right half: its swaps from the left half,
-// then L11(left half)^-1
+// inside the panel, for the block of 2h columns at column offset c_off: the
+// top h rows of its right half get the left half's swaps, then the unit
+// lower h x h solve (h = 16 or 32)
 template <int W>
-int launch_btrsm_half(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s);
+int launch_btrsm_sub(const BatchView& bv, int act, int k0, int c_off, int h, double* A, const int64_t* piv,
+                     cudaStream_t s);
 template <int W>
 int launch_blaswp(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s);
 template <int W>
@@ -103,8 +105,10 @@ constexpr int kSplitTileN = 32;
 constexpr int kGeomTrail = 0;
 constexpr int kGeomTrsmInv = 1;
 constexpr int kGeomPanelInner = 2;   // inside the panel: right half -= left half x solved top rows
+                                     // (block of 2h columns at column offset c_off)
 size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles);
-int split_bupdate_dd(const BatchView& bv, int geom, int act, int max_mt, int max_cb, const TileEntry* tiles,
+int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
+                     const TileEntry* tiles,
                      int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
                      const double* aux, char* ws, size_t ws_bytes, cudaStream_t s);
 int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s);

@@ -521,10 +521,11 @@ k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int
 //    -(L11^-1) (64 x 64, column-major in `aux`), which is U12 := L11^-1 U12,
 //    in transposed form C^T -= U12^T M^T: the rows of the product are the
 //    columns of U12;
-//  kGeomPanelInner: inside a 64-column panel, after its left 32 columns are
-//    factored and the top 32 rows of its right half are solved: the right
-//    half's rows below them -= L (left half, same rows) U (the solved rows),
-//    K = 32 (zero digits beyond).
+//  kGeomPanelInner: inside the panel, for a block of 2h columns starting at
+//    column k0 + c_off whose left h columns are factored and whose right
+//    half's top h rows are solved: the right half's rows below them
+//    -= L (left half, same rows) U (the solved rows), K = h (zero digits
+//    beyond).
 struct SplitOperands {
   const double* L;
   int64_t lrs, lks, planeL;
@@ -536,19 +537,20 @@ struct SplitOperands {
   int K;
 };
 
-__device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int n, int k0, const double* aux) {
+__device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int n, int k0, const double* aux,
+                                                        int c_off, int h) {
   SplitOperands o;
   const int64_t plane = (int64_t)n * n;
   const int r0 = k0 + kK;
   o.K = kK;
   if (geom == kGeomPanelInner) {
-    constexpr int H = kK / 2;
-    const int q0 = k0 + H;
-    o.L = a + (int64_t)k0 * n + q0;
+    const int c0 = k0 + c_off;
+    const int q0 = c0 + h;
+    o.L = a + (int64_t)c0 * n + q0;
     o.lrs = 1;
     o.lks = n;
     o.planeL = plane;
-    o.U = a + (int64_t)q0 * n + k0;
+    o.U = a + (int64_t)q0 * n + c0;
     o.uks = 1;
     o.ujs = n;
     o.planeU = plane;
@@ -557,8 +559,8 @@ __device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int
     o.cjs = n;
     o.planeC = plane;
     o.m = n - q0;
-    o.N = min(H, n - q0);
-    o.K = H;
+    o.N = min(h, n - q0);
+    o.K = h;
   } else if (geom == kGeomTrsmInv) {
     o.L = a + (int64_t)r0 * n + k0;   // (j, t) -> U12(t, j)
     o.lrs = n;
@@ -595,12 +597,14 @@ __device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int
 
 // grid (act, max_mt): 128-row tile blockIdx.y of system order[blockIdx.x]
 __global__ void __launch_bounds__(128)
-k_bslice_rows(BatchView bv, int geom, const int2* __restrict__ bases, int k0, double* __restrict__ A,
-              const double* __restrict__ aux, unsigned char* __restrict__ aslices, int* __restrict__ ea) {
+k_bslice_rows(BatchView bv, int geom, int c_off, int h, const int2* __restrict__ bases, int k0,
+              double* __restrict__ A, const double* __restrict__ aux, unsigned char* __restrict__ aslices,
+              int* __restrict__ ea) {
   const int pos = blockIdx.x;
   const int sys = bv.order[pos];
   const int n = bv.n[sys];
-  const SplitOperands o = batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK);
+  const SplitOperands o =
+      batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK, c_off, h);
   if (o.m <= 0 || o.N <= 0 || (int64_t)blockIdx.y * kTileM >= o.m) return;
   const int abase = bases[pos].x;
   slice_row(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices + (int64_t)abase * kS * kASliceBytes,
@@ -609,12 +613,14 @@ k_bslice_rows(BatchView bv, int geom, const int2* __restrict__ bases, int k0, do
 
 // grid (act, max_cb): 128-column block blockIdx.y of system order[blockIdx.x]
 __global__ void __launch_bounds__(128)
-k_bslice_cols(BatchView bv, int geom, const int2* __restrict__ bases, int k0, double* __restrict__ A,
-              const double* __restrict__ aux, unsigned char* __restrict__ bslices, int* __restrict__ fb) {
+k_bslice_cols(BatchView bv, int geom, int c_off, int h, const int2* __restrict__ bases, int k0,
+              double* __restrict__ A, const double* __restrict__ aux, unsigned char* __restrict__ bslices,
+              int* __restrict__ fb) {
   const int pos = blockIdx.x;
   const int sys = bv.order[pos];
   const int n = bv.n[sys];
-  const SplitOperands o = batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK);
+  const SplitOperands o =
+      batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK, c_off, h);
   if (o.m <= 0 || o.N <= 0) return;
   const int64_t npad = (o.N + kTileN - 1) / kTileN * kTileN;
   if ((int64_t)blockIdx.y * 128 >= npad) return;
@@ -624,14 +630,15 @@ k_bslice_cols(BatchView bv, int geom, const int2* __restrict__ bases, int k0, do
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 1)
-k_bsplit_gemm(BatchView bv, int geom, const TileEntry* __restrict__ tiles, const int2* __restrict__ bases, int k0,
-              double* __restrict__ A, const double* __restrict__ aux, const unsigned char* __restrict__ aslices,
-              const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
-              const int* __restrict__ fb, DeviceStatus* status) {
+k_bsplit_gemm(BatchView bv, int geom, int c_off, int h, const TileEntry* __restrict__ tiles,
+              const int2* __restrict__ bases, int k0, double* __restrict__ A, const double* __restrict__ aux,
+              const unsigned char* __restrict__ aslices, const unsigned char* __restrict__ bslices,
+              const int* __restrict__ ea, const int* __restrict__ fb, DeviceStatus* status) {
   const TileEntry t = tiles[blockIdx.x];
   const int sys = bv.order[t.pos];
   const int n = bv.n[sys];
-  const SplitOperands o = batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)t.pos * 2 * kK * kK);
+  const SplitOperands o =
+      batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)t.pos * 2 * kK * kK, c_off, h);
   const int2 b = bases[t.pos];
   split_tile(o.C, o.crs, o.cjs, o.planeC, o.m, o.N, aslices + (int64_t)b.x * kS * kASliceBytes,
              bslices + (int64_t)b.y * kS * kBSliceBytes, ea + (int64_t)b.x * kTileM, fb + (int64_t)b.y * kTileN,
@@ -761,7 +768,8 @@ size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles) {
          align256(sizeof(int) * (size_t)a_tiles * kTileM) + align256(sizeof(int) * (size_t)b_tiles * kTileN);
 }
 
-int split_bupdate_dd(const BatchView& bv, int geom, int act, int max_mt, int max_cb, const TileEntry* tiles,
+int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
+                     const TileEntry* tiles,
                      int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
                      const double* aux, char* ws, size_t ws_bytes, cudaStream_t s) {
   if (act <= 0 || ntiles <= 0) return MW_OK;
@@ -777,9 +785,11 @@ int split_bupdate_dd(const BatchView& bv, int geom, int act, int max_mt, int max
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
   {
     ProfScope ps(kPhSplitAux, s);
-    k_bslice_rows<<<dim3((unsigned)act, (unsigned)max_mt), 128, 0, s>>>(bv, geom, bases, k0, A, aux, aslices, ea);
+    k_bslice_rows<<<dim3((unsigned)act, (unsigned)max_mt), 128, 0, s>>>(bv, geom, c_off, h, bases, k0, A, aux,
+                                                                         aslices, ea);
     MW_LAUNCH_CHECK();
-    k_bslice_cols<<<dim3((unsigned)act, (unsigned)max_cb), 128, 0, s>>>(bv, geom, bases, k0, A, aux, bslices, fb);
+    k_bslice_cols<<<dim3((unsigned)act, (unsigned)max_cb), 128, 0, s>>>(bv, geom, c_off, h, bases, k0, A, aux,
+                                                                         bslices, fb);
     MW_LAUNCH_CHECK();
   }
   {
@@ -790,8 +800,8 @@ int split_bupdate_dd(const BatchView& bv, int geom, int act, int max_mt, int max
       MW_CUDA_CHECK(cudaFuncSetAttribute(k_bsplit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
       attr_set = true;
     }
-    k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, geom, tiles, bases, k0, A, aux, aslices,
-                                                                bslices, ea, fb, status);
+    k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, geom, c_off, h, tiles, bases, k0, A, aux,
+                                                                aslices, bslices, ea, fb, status);
     MW_LAUNCH_CHECK();
   }
   return MW_OK;
