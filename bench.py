@@ -419,13 +419,15 @@ def mixed_batch_refine(peak_fp64, count=512):
                      "phase_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
                      "gpu_launches": int(sum(c for _, c in prof.values()) / reps)}
         del work
-    # FP64-pipe fractions of the panel and TRSM kernels (multiply-subtract
-    # instructions only: divisions and compares are not counted)
+    # FP64-pipe fractions of the plain path's panel and TRSM kernels
+    # (multiply-subtract instructions only: divisions and compares are not
+    # counted).  The split path moves most of that work onto the tensor cores
+    # (recursive panel, TRSM through L11^-1), so it has no such fraction.
     pm, tm = blocked_batch_msubs(n_list)
-    ph = out["split_dd_refine"]["phase_ms"]
+    ph = out["plain_dd_refine"]["phase_ms"]
     for key, cnt in (("panel", pm), ("trsm", tm)):
         t = ph.get(key, 0.0)
-        out["split_dd_refine"][key + "_fp64_frac_msub_only"] = (
+        out["plain_dd_refine"][key + "_fp64_frac_msub_only"] = (
             cnt * FP64_PER_MSUB[2] / (t * 1e-3) / peak_fp64 if t else None)
     # plain QD direct LU + solve (no refinement) on every 16th system by order
     order = sorted(range(count), key=lambda s: n_list[s])
