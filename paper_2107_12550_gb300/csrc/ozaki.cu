@@ -326,10 +326,60 @@ __device__ __forceinline__ void i192_sub_shifted(I192& R, unsigned long long q, 
   }
 }
 
-// q * 2^e as a double (q <= 2^53 integer, e within the normal range)
+// q * 2^e as a double (q <= 2^53 integer): the IEEE fields assembled from
+// the bits (exact: q has at most 53 significant bits); the FP64 route only
+// for results outside the normal range
 __device__ __forceinline__ double make_double(unsigned long long q, int e) {
   if (q == 0) return 0.0;
-  return scale2_exact(__ull2double_rn(q), e);
+  const int sh = __clzll((long long)q) - 11;   // moves the top bit of q to bit 52
+  const unsigned long long m = (sh >= 0) ? (q << sh) : (q >> (-sh));   // q = 2^53: exact shift
+  const int biased = e - sh + 52 + 1023;
+  if (biased <= 0 || biased >= 2047) return scale2_exact(__ull2double_rn(q), e);
+  return __longlong_as_double((long long)(((unsigned long long)biased << 52) | (m & ((1ull << 52) - 1))));
+}
+
+// R -= sign(x) * |x| * 2^-scale for a finite double x whose value is an
+// integer multiple of 2^scale with |x| 2^-scale < 2^189; false (R unchanged)
+// otherwise
+__device__ __forceinline__ bool i192_sub_double(I192& R, double x, int scale) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex == 0x7ff) return false;
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  if (ex) m |= (1ull << 52);
+  if (m == 0) return true;
+  int e = (ex ? ex : 1) - 1075;                 // x = m 2^e
+  const int tz = __ffsll((long long)m) - 1;
+  m >>= tz;
+  e += tz;
+  const int s = e - scale;
+  if (s < 0 || s > 135) return false;
+  const int w = s >> 6, b = s & 63;
+  const unsigned long long lo = m << b;
+  const unsigned long long hi = b ? (m >> (64 - b)) : 0ull;
+  const unsigned long long v0 = (w == 0) ? lo : 0ull;
+  const unsigned long long v1 = (w == 0) ? hi : (w == 1 ? lo : 0ull);
+  const unsigned long long v2 = (w == 1) ? hi : (w == 2 ? lo : 0ull);
+  if ((long long)bits < 0) {                    // x < 0: R += |x| 2^-scale
+    const unsigned long long s0 = R.w0 + v0;
+    const unsigned long long c0 = s0 < v0;
+    const unsigned long long t1 = R.w1 + v1;
+    const unsigned long long c1a = t1 < v1;
+    const unsigned long long s1 = t1 + c0;
+    const unsigned long long c1b = s1 < t1;
+    R.w0 = s0;
+    R.w1 = s1;
+    R.w2 = R.w2 + v2 + c1a + c1b;
+  } else {                                      // x > 0: R -= x 2^-scale
+    const unsigned long long b0 = R.w0 < v0;
+    R.w0 -= v0;
+    const unsigned long long t = R.w1 - v1;
+    const unsigned long long b1a = R.w1 < v1;
+    const unsigned long long b1b = t < b0;
+    R.w1 = t - b0;
+    R.w2 = R.w2 - v2 - b1a - b1b;
+  }
+  return true;
 }
 
 
@@ -480,12 +530,23 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
             if (D) i192_add_shifted(R, D, 8 * (kDiag - 1 - d));   // diagonal d+2: weight 2^(8(16-(d+2)))
           }
           const int scale = ei + fb[j] - 128;
-          val<2> pr;
-          pr.v[0] = i192_take_rn(R, scale);
-          pr.v[1] = i192_take_rn(R, scale);
           const int64_t idx = i * crs + j * cjs;
           val<2> cv = load<2>(C, planeC, idx);
-          cv = sub<2>(cv, pr);
+          // C - P exactly in the accumulator when C lies on the product's
+          // grid 2^scale within the 192-bit range (the usual case), then
+          // rounded greedily to DD; otherwise P rounded to DD and the DD
+          // subtraction
+          I192 T = R;
+          if (i192_sub_double(T, cv.v[0], scale) && i192_sub_double(T, cv.v[1], scale)) {
+            i192_neg(T);
+            cv.v[0] = i192_take_rn(T, scale);
+            cv.v[1] = i192_take_rn(T, scale);
+          } else {
+            val<2> pr;
+            pr.v[0] = i192_take_rn(R, scale);
+            pr.v[1] = i192_take_rn(R, scale);
+            cv = sub<2>(cv, pr);
+          }
           store<2>(C, planeC, idx, cv);
         }
       }
