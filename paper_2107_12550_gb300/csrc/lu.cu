@@ -703,9 +703,79 @@ static int launch_trsm(double* A, int64_t lda, int64_t plane, int64_t n, int64_t
   return MW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// split-update DD LU of one system: per 64-column panel, the cooperative
+// panel kernel, the swaps left and right of the panel, M = -(L11^-1)
+// strictly lower (column-parallel), then U12 -= M U12 and A22 -= L21 U12 as
+// split tensor-core products.  (The batched split path also factors the
+// panel recursively; for one system the panel is bound by its per-column
+// latency, and the extra launches and small products of the recursion cost
+// more than the FP64 work they move.)
+// ---------------------------------------------------------------------------
+static int lu_split_dd(int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info, char* ws, size_t ws_bytes,
+                       cudaStream_t s) {
+  const int64_t plane = lda * n;
+  char* sws = ws + kWsSplit;
+  const size_t sbytes = ws_bytes > kWsSplit ? ws_bytes - kWsSplit : 0;
+  if (sbytes < split_workspace_bytes(n, kDefaultNb)) return MW_EUNSUPPORTED;
+  double* aux = split_aux(sws, n);
+  MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand, s));
+  MW_CUDA_CHECK(cudaMemsetAsync(sws, 0, 256, s));
+  MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
+  constexpr int NB = kDefaultNb;
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int kb = (int)std::min<int64_t>(NB, n - k0);
+    int rc;
+    {
+      ProfScope ps(kPhPanel, s);
+      rc = launch_panel<2>(A, lda, plane, n, k0, kb, piv, info, ws, s);
+    }
+    if (rc) return rc;
+    {
+      ProfScope ps(kPhLaswp, s);
+      if (k0 > 0) {
+        dim3 grid((unsigned)((k0 + 127) / 128), 2);
+        k_laswp<2><<<grid, 128, 0, s>>>(A, lda, plane, 0, k0, k0, kb, piv);
+        MW_LAUNCH_CHECK();
+      }
+      if (k0 + kb < n) {
+        dim3 grid((unsigned)((n - k0 - kb + 127) / 128), 2);
+        k_laswp<2><<<grid, 128, 0, s>>>(A, lda, plane, k0 + kb, n, k0, kb, piv);
+        MW_LAUNCH_CHECK();
+      }
+    }
+    if (k0 + kb >= n) break;
+    rc = split_inv_l11(A, lda, plane, k0, aux, s);
+    if (rc) return rc;
+    const int64_t r0 = k0 + NB;
+    SplitOperands o;                 // U12 -= M U12, transposed: rows = the columns of U12
+    o.L = A + r0 * lda + k0;
+    o.lrs = lda;
+    o.lks = 1;
+    o.planeL = plane;
+    o.U = aux;
+    o.uks = NB;
+    o.ujs = 1;
+    o.planeU = (int64_t)NB * NB;
+    o.C = A + r0 * lda + k0;
+    o.crs = lda;
+    o.cjs = 1;
+    o.planeC = plane;
+    o.m = n - r0;
+    o.N = NB;
+    o.K = NB;
+    rc = split_product_dd(o, sws, sbytes, kPhTrsm, s);
+    if (rc) return rc;
+    rc = split_update_dd(A, lda, plane, r0, n - r0, r0, n - r0, k0, NB, sws, sbytes, s);
+    if (rc) return rc;
+  }
+  return MW_OK;
+}
+
 template <int W>
 int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info,
                char* ws, size_t ws_bytes, int nb, cudaStream_t s) {
+  if (update == MW_UPDATE_SPLIT && W == 2) return lu_split_dd(n, A, lda, piv, info, ws, ws_bytes, s);
   const int64_t plane = lda * n;
   MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand, s));
   MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
@@ -730,10 +800,7 @@ int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int6
       }
       if (rc) return rc;
       const int64_t r0 = k0 + kb;
-      if (update == MW_UPDATE_SPLIT && W == 2) {
-        rc = split_update_dd(A, lda, plane, r0, n - r0, r0, n - r0, k0, kb, ws + kWsSplit,
-                             ws_bytes > kWsSplit ? ws_bytes - kWsSplit : 0, s);
-      } else {
+      {
         ProfScope ps(kPhGemmPlain, s);
         rc = launch_gemm_plain<W>(A, lda, plane, r0, n - r0, r0, n - r0, k0, kb, s);
       }

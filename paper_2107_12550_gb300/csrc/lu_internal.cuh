@@ -33,6 +33,29 @@ template <int W>
 int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info,
                char* ws, size_t ws_bytes, int nb, cudaStream_t s);
 
+// One split-precision product C -= L U (DD, ozaki.cu): entry (r, k) of L at
+// L[r*lrs + k*lks], (k, j) of U at U[k*uks + j*ujs], (r, j) of C at
+// C[r*crs + j*cjs]; the second word of each operand one plane further;
+// inner dimension K <= 64 (the digits of k >= K are zero).
+struct SplitOperands {
+  const double* L;
+  int64_t lrs, lks, planeL;
+  const double* U;
+  int64_t uks, ujs, planeU;
+  double* C;
+  int64_t crs, cjs, planeC;
+  int64_t m, N;
+  int K;
+};
+// the product on the work buffer's slice area; its tensor-core launch is
+// counted under profile phase `phase`
+int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phase, cudaStream_t s);
+// M = strictly lower part of -(L11^-1) of the unit lower 64 x 64 block at
+// (k0, k0), column-major in aux (2 words x 64 x 64)
+int split_inv_l11(const double* A, int64_t lda, int64_t plane, int64_t k0, double* aux, cudaStream_t s);
+// the L11 inverse area inside a split work buffer sized for order n
+double* split_aux(char* ws, int64_t n);
+
 // split-precision trailing update for DD (ozaki.cu): C -= L21 * U12
 int split_update_dd(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
                     int64_t col0, int64_t N, int64_t k0, int nb, char* ws, size_t ws_bytes,

@@ -171,9 +171,8 @@ __device__ __forceinline__ void slice_row(const double* __restrict__ L, int64_t 
 }
 
 __global__ void __launch_bounds__(128)
-k_slice_rows(const double* __restrict__ L, int64_t ldl, int64_t planeL, int64_t m,
-             unsigned char* __restrict__ aslices, int* __restrict__ ea) {
-  slice_row(L, 1, ldl, planeL, m, kK, aslices, ea, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+k_slice_rows(SplitOperands o, unsigned char* __restrict__ aslices, int* __restrict__ ea) {
+  slice_row(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices, ea, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // U12 columns -> B slices [tile][q][32 x 64] (column j is a K-major row), f_j;
@@ -223,9 +222,8 @@ __device__ __forceinline__ void slice_col(const double* __restrict__ U, int64_t 
 }
 
 __global__ void __launch_bounds__(128)
-k_slice_cols(const double* __restrict__ U, int64_t ldu, int64_t planeU, int64_t N, int64_t npad,
-             unsigned char* __restrict__ bslices, int* __restrict__ fb) {
-  slice_col(U, 1, ldu, planeU, N, npad, kK, bslices, fb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+k_slice_cols(SplitOperands o, int64_t npad, unsigned char* __restrict__ bslices, int* __restrict__ fb) {
+  slice_col(o.U, o.uks, o.ujs, o.planeU, o.N, npad, o.K, bslices, fb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -567,11 +565,9 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 1)
-k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int64_t N,
-             const unsigned char* __restrict__ aslices,
-             const unsigned char* __restrict__ bslices, const int* __restrict__ ea,
-             const int* __restrict__ fb, DeviceStatus* status) {
-  split_tile(C, 1, ldc, planeC, m, N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y);
+k_split_gemm(SplitOperands o, const unsigned char* __restrict__ aslices, const unsigned char* __restrict__ bslices,
+             const int* __restrict__ ea, const int* __restrict__ fb, DeviceStatus* status) {
+  split_tile(o.C, o.crs, o.cjs, o.planeC, o.m, o.N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y);
 }
 
 // ---- batched forms: per active system of a batch at panel step k0 ----------
@@ -587,17 +583,6 @@ k_split_gemm(double* __restrict__ C, int64_t ldc, int64_t planeC, int64_t m, int
 //    half's top h rows are solved: the right half's rows below them
 //    -= L (left half, same rows) U (the solved rows), K = h (zero digits
 //    beyond).
-struct SplitOperands {
-  const double* L;
-  int64_t lrs, lks, planeL;
-  const double* U;
-  int64_t uks, ujs, planeU;
-  double* C;
-  int64_t crs, cjs, planeC;
-  int64_t m, N;
-  int K;
-};
-
 __device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int n, int k0, const double* aux,
                                                         int c_off, int h) {
   SplitOperands o;
@@ -711,15 +696,9 @@ k_bsplit_gemm(BatchView bv, int geom, int c_off, int h, const TileEntry* __restr
 // X = L11^-1 by column-oriented substitution on all 64 columns of the
 // identity at once: for t ascending, x_it -= l_it x_tc for i > t, c <= t.
 // dynamic shared memory: X, 2 words x 64 x 64 doubles
-__global__ void __launch_bounds__(256)
-k_binv_l11(BatchView bv, int k0, const double* __restrict__ A, double* __restrict__ aux) {
+__device__ __forceinline__ void inv_l11_body(const double* __restrict__ a, int64_t lda, int64_t plane, int k0,
+                                             double* __restrict__ m) {
   extern __shared__ double xs[];     // [2][64 cols][64 rows]
-  const int pos = blockIdx.x;
-  const int sys = bv.order[pos];
-  const int n = bv.n[sys];
-  if (n - k0 - kK <= 0) return;
-  const double* a = A + 2 * bv.moff[sys];
-  const int64_t plane = (int64_t)n * n;
   constexpr int P = kK * kK;
   for (int e = threadIdx.x; e < P; e += blockDim.x) {
     const int c = e / kK, i = e % kK;
@@ -730,7 +709,7 @@ k_binv_l11(BatchView bv, int k0, const double* __restrict__ A, double* __restric
     __syncthreads();
     const int rows = kK - 1 - t;          // i in (t, 64)
     const int items = rows * (t + 1);     // c in [0, t]
-    const int64_t lcol = (int64_t)(k0 + t) * n + k0;
+    const int64_t lcol = (int64_t)(k0 + t) * lda + k0;
     for (int q = threadIdx.x; q < items; q += blockDim.x) {
       const int i = t + 1 + q % rows, c = q / rows;
       val<2> x, l, u;
@@ -746,13 +725,61 @@ k_binv_l11(BatchView bv, int k0, const double* __restrict__ A, double* __restric
     }
   }
   __syncthreads();
-  double* m = aux + (int64_t)pos * 2 * P;
   for (int e = threadIdx.x; e < P; e += blockDim.x) {
     const int c = e / kK, i = e % kK;
     const bool below = i > c;
     m[e] = below ? -xs[e] : 0.0;
     m[P + e] = below ? -xs[P + e] : 0.0;
   }
+}
+
+__global__ void __launch_bounds__(256)
+k_binv_l11(BatchView bv, int k0, const double* __restrict__ A, double* __restrict__ aux) {
+  const int pos = blockIdx.x;
+  const int sys = bv.order[pos];
+  const int n = bv.n[sys];
+  if (n - k0 - kK <= 0) return;
+  inv_l11_body(A + 2 * bv.moff[sys], n, (int64_t)n * n, k0, aux + (int64_t)pos * 2 * kK * kK);
+}
+
+// one system with leading dimension lda: one CTA per column c of X = L11^-1
+// (thread i holds X(i, c)), the same operations per entry as inv_l11_body:
+// for t ascending from c, X(i, c) -= l_it X(t, c) for i > t.
+// dynamic shared memory: L11, 2 words x 64 x 64 doubles
+__global__ void __launch_bounds__(kK)
+k_inv_l11_cols(const double* __restrict__ A, int64_t lda, int64_t plane, int k0, double* __restrict__ aux) {
+  extern __shared__ double ls[];     // [2][64 cols t][64 rows i]
+  __shared__ double xt[2];
+  constexpr int P = kK * kK;
+  const int c = blockIdx.x, i = threadIdx.x;
+  for (int e = i; e < P; e += kK) {
+    const int t = e / kK, r = e % kK;
+    const int64_t idx = (int64_t)(k0 + t) * lda + k0 + r;
+    ls[e] = __ldg(A + idx);
+    ls[P + e] = __ldg(A + plane + idx);
+  }
+  val<2> x;
+  x.v[0] = (i == c) ? 1.0 : 0.0;
+  x.v[1] = 0.0;
+  for (int t = c; t < kK - 1; ++t) {
+    __syncthreads();
+    if (i == t) {
+      xt[0] = x.v[0];
+      xt[1] = x.v[1];
+    }
+    __syncthreads();
+    if (i > t) {
+      val<2> l, u;
+      l.v[0] = ls[t * kK + i];
+      l.v[1] = ls[P + t * kK + i];
+      u.v[0] = xt[0];
+      u.v[1] = xt[1];
+      x = msub<2>(x, l, u);
+    }
+  }
+  const bool below = i > c;
+  aux[c * kK + i] = below ? -x.v[0] : 0.0;
+  aux[P + c * kK + i] = below ? -x.v[1] : 0.0;
 }
 
 size_t split_smem_bytes() {
@@ -773,20 +800,25 @@ __device__ double scale2_exact(double x, int e) {
   return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
 }
 
-// workspace: [status 256 | A slices | B slices | ea | fb]
-size_t split_workspace_bytes(int64_t n, int nb) {
-  (void)nb;
+// workspace: [status 256 | A slices | B slices | ea | fb | L11 inverse (2 x 64 x 64)]
+static size_t split_slices_bytes(int64_t n) {
   const int64_t mt = (n + kTileM - 1) / kTileM, nt = (n + kTileN - 1) / kTileN;
   return 256 + align256((size_t)mt * kS * kASliceBytes) + align256((size_t)nt * kS * kBSliceBytes) +
          align256(sizeof(int) * (size_t)mt * kTileM) + align256(sizeof(int) * (size_t)nt * kTileN);
 }
 
-// C (m x N) -= L (m x 64) * U (64 x N), all DD component-planar column-major
-int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
-                      int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
-                      char* ws, size_t ws_bytes, cudaStream_t s) {
-  if (m <= 0 || N <= 0) return MW_OK;
-  const int64_t mt = (m + kTileM - 1) / kTileM, nt = (N + kTileN - 1) / kTileN;
+size_t split_workspace_bytes(int64_t n, int nb) {
+  (void)nb;
+  return split_slices_bytes(n) + align256(sizeof(double) * 2 * kK * kK);
+}
+
+double* split_aux(char* ws, int64_t n) { return reinterpret_cast<double*>(ws + split_slices_bytes(n)); }
+
+// C (m x N) -= L (m x K) * U (K x N) with the strides of `o` (K <= 64)
+int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phase, cudaStream_t s) {
+  if (o.m <= 0 || o.N <= 0 || o.K <= 0) return MW_OK;
+  if (o.K > kK) return MW_EUNSUPPORTED;
+  const int64_t mt = (o.m + kTileM - 1) / kTileM, nt = (o.N + kTileN - 1) / kTileN;
   size_t off = 256;
   unsigned char* aslices = reinterpret_cast<unsigned char*>(ws + off);
   off += align256((size_t)mt * kS * kASliceBytes);
@@ -800,14 +832,13 @@ int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t plan
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
   {
     ProfScope ps(kPhSplitAux, s);
-    k_slice_rows<<<(unsigned)mt, 128, 0, s>>>(L, ldl, planeL, m, aslices, ea);
+    k_slice_rows<<<(unsigned)mt, 128, 0, s>>>(o, aslices, ea);
     MW_LAUNCH_CHECK();
-    k_slice_cols<<<(unsigned)((nt * kTileN + 127) / 128), 128, 0, s>>>(U, ldu, planeU, N, nt * kTileN,
-                                                                          bslices, fb);
+    k_slice_cols<<<(unsigned)((nt * kTileN + 127) / 128), 128, 0, s>>>(o, nt * kTileN, bslices, fb);
     MW_LAUNCH_CHECK();
   }
   {
-    ProfScope ps(kPhGemmSplit, s);
+    ProfScope ps(phase, s);
     // more than half of the SM's shared memory: one CTA per SM, which owns
     // all 512 TMEM columns
     const size_t shmem = split_smem_bytes();
@@ -817,9 +848,45 @@ int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t plan
       attr_set = true;
     }
     dim3 grid((unsigned)mt, (unsigned)nt);
-    k_split_gemm<<<grid, kSplitThreads, shmem, s>>>(C, ldc, planeC, m, N, aslices, bslices, ea, fb, status);
+    k_split_gemm<<<grid, kSplitThreads, shmem, s>>>(o, aslices, bslices, ea, fb, status);
     MW_LAUNCH_CHECK();
   }
+  return MW_OK;
+}
+
+// C (m x N) -= L (m x 64) * U (64 x N), all DD component-planar column-major
+int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
+                      int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
+                      char* ws, size_t ws_bytes, cudaStream_t s) {
+  SplitOperands o;
+  o.L = L;
+  o.lrs = 1;
+  o.lks = ldl;
+  o.planeL = planeL;
+  o.U = U;
+  o.uks = 1;
+  o.ujs = ldu;
+  o.planeU = planeU;
+  o.C = C;
+  o.crs = 1;
+  o.cjs = ldc;
+  o.planeC = planeC;
+  o.m = m;
+  o.N = N;
+  o.K = kK;
+  return split_product_dd(o, ws, ws_bytes, kPhGemmSplit, s);
+}
+
+int split_inv_l11(const double* A, int64_t lda, int64_t plane, int64_t k0, double* aux, cudaStream_t s) {
+  const size_t shmem = sizeof(double) * 2 * kK * kK;
+  static bool attr_set = false;
+  if (!attr_set) {
+    MW_CUDA_CHECK(cudaFuncSetAttribute(k_inv_l11_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    attr_set = true;
+  }
+  ProfScope ps(kPhTrsm, s);
+  k_inv_l11_cols<<<kK, kK, shmem, s>>>(A, lda, plane, (int)k0, aux);
+  MW_LAUNCH_CHECK();
   return MW_OK;
 }
 
