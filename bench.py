@@ -296,8 +296,50 @@ def extras(A, b, n, steps, peak_fp64):
     if pg:
         instr = panel_sum_sq(n3) * FP64_PER_MSUB[2]
         out["lu_dd_n4096"]["plain_gemm_fp64_frac"] = instr / (pg * 1e-3) / peak_fp64
-    # batch of 4096 DD systems, n in [16, 256], one RHS (x_true = ones)
+    del Au
+    # large DD LU, n = 8192, split update (the plain update would take ~11 s)
+    n8 = 8192
+    A8 = torch.from_numpy(W.uniform_matrix(n8, 2, seed=0)).cuda()
+    wk8 = api.workspace(L.MW_OP_LUDECOMP, 2, 1, n8)
+    g8 = lambda: api.ludecomp(A8, 2, "split", work=wk8)
+    g8()
+    L.profile_read(reset=True)
+    L.profile_enable(True)
+    t8, (_, _, info8) = _time(g8, 1, stream)
+    L.profile_enable(False)
+    prof8 = L.profile_read(reset=True)
+    out["lu_dd_n8192_split"] = {"ms": t8, "dd_gops": (2.0 / 3.0) * n8 ** 3 / (t8 * 1e-3) / 1e9,
+                                "info": int(info8.item()),
+                                "phase_ms": {k: v[0] for k, v in prof8.items() if v[1]}}
+    del A8, wk8
+    torch.cuda.empty_cache()
+    # batches of 4096 TD and DD systems, n in [16, 256], one RHS (x_true = ones)
     n_list = [int(v) for v in W.batch_sizes(4096, 16, 256, seed=0)]
+    mats = [W.uniform_matrix(m, 3, seed=W.system_seed(0, s), lda=m) for s, m in enumerate(n_list)]
+    At = torch.from_numpy(api.pack_matrices(mats, 3)).cuda()
+    del mats
+    vt = np.zeros(3 * int(sum(n_list)))
+    _, voff = api.batch_offsets(n_list)
+    for s, m in enumerate(n_list):
+        vt[3 * voff[s]: 3 * voff[s] + m] = 1.0
+    bt = torch.from_numpy(vt).cuda()
+    wkt = api.batch_workspace(L.MW_OP_LUDECOMP, 3, n_list)
+    LUt = torch.empty_like(At)
+
+    def batch_step_td():
+        LUt.copy_(At)
+        LU_, piv_, info_ = api.ludecomp_batched(LUt, n_list, 3, work=wkt, inplace=True)
+        return api.solve_batched(LU_, piv_, bt, n_list, 3, work=wkt)
+
+    batch_step_td()
+    ttd, _ = _time(batch_step_td, 2, stream)
+    ops_td = sum((2.0 / 3.0) * m ** 3 for m in n_list)
+    out["batch_4096_td_n16_256"] = {
+        "systems": 4096, "n_range": [16, 256], "ms_per_batch": ttd, "systems_per_s": 4096 / (ttd * 1e-3),
+        "lu_td_gops": ops_td / (ttd * 1e-3) / 1e9,
+        "workload": "uniform TD systems, LU + solve; persistent one-CTA-per-system LU"}
+    del At, LUt, bt
+    torch.cuda.empty_cache()
     mats = [W.uniform_matrix(m, 2, seed=W.system_seed(0, s), lda=m) for s, m in enumerate(n_list)]
     Ab = torch.from_numpy(api.pack_matrices(mats, 2)).cuda()
     del mats

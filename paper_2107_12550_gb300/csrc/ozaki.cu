@@ -404,8 +404,8 @@ __device__ __forceinline__ double i192_take_rn(I192& R, int scale) {
 // ---------------------------------------------------------------------------
 // the tensor-core kernel: one CTA per 128 x 32 output tile
 // warp 0: bulk-copy producer; warp 1: TMEM owner + MMA issuer;
-// warps 2..9: epilogue (TMEM lane quarter = warp % 4; warps 2..5 take
-// columns 0..15 of the tile, warps 6..9 columns 16..31)
+// warps 2..17: epilogue (TMEM lane quarter = warp % 4; warps 2..5 take
+// columns 0..7 of the tile, warps 6..9 columns 8..15, and so on)
 // ---------------------------------------------------------------------------
 struct SplitSmem {
   unsigned char b[kS][kBSliceBytes];       // all B slices of the tile (60 KB)
@@ -418,7 +418,7 @@ struct SplitSmem {
   int abort;
 };
 
-constexpr int kEpiWarps = 8;                       // two warpgroups over the 4 TMEM lane quarters
+constexpr int kEpiWarps = 16;                      // four warpgroups over the 4 TMEM lane quarters
 constexpr int kSplitThreads = 64 + 32 * kEpiWarps;  // producer + MMA warps + epilogue
 
 // entry (i, j) of C at C[i * crs + j * cjs]
@@ -500,7 +500,8 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
   } else {
     // epilogue: thread <-> row (TMEM lane) of the tile, half of the columns
     const int quarter = warp & 3;
-    const int chalf = (warp - 2) / 4;
+    constexpr int kCols = kTileN / (kEpiWarps / 4);   // columns per epilogue warp
+    const int cpart = (warp - 2) / 4;
     const int rr = quarter * 32 + lane;
     const int64_t i = tm * kTileM + rr;
     bool ok = tc::mbar_wait(&sm.mma_done, 0);
@@ -512,7 +513,7 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
     } else {
       const int ei = (i < m) ? ea[i] : 0;
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-      for (int c4 = chalf * (kTileN / 2); c4 < (chalf + 1) * (kTileN / 2); c4 += 4) {
+      for (int c4 = cpart * kCols; c4 < (cpart + 1) * kCols; c4 += 4) {
         uint32_t v[kDiag][4];
 #pragma unroll
         for (int d = 0; d < kDiag; ++d) tc::tmem_ld_x4(lane_base + (uint32_t)(d * kTileN + c4), v[d]);
