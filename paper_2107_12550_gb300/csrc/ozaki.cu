@@ -324,6 +324,49 @@ __device__ __forceinline__ void i192_sub_shifted(I192& R, unsigned long long q, 
   }
 }
 
+// the tile's product for one entry from the 15 exact diagonal sums (TMEM
+// words, FP32 integers |D_d| < 2^23, diagonal d+2 weighted 2^(8(14-d))):
+// three int64 Horner groups of five diagonals (each |S| < 2^56), then
+// R = S_C + S_B 2^40 + S_A 2^80 in 192 bits
+template <int CW>
+__device__ __forceinline__ I192 recombine15(const uint32_t (&v)[15][CW], int cc) {
+  long long SA = 0, SB = 0, SC = 0;
+#pragma unroll
+  for (int d = 0; d < 5; ++d) SA = SA * 256 + __float2int_rn(__uint_as_float(v[d][cc]));
+#pragma unroll
+  for (int d = 5; d < 10; ++d) SB = SB * 256 + __float2int_rn(__uint_as_float(v[d][cc]));
+#pragma unroll
+  for (int d = 10; d < 15; ++d) SC = SC * 256 + __float2int_rn(__uint_as_float(v[d][cc]));
+  I192 R;
+  const unsigned long long sxc = (SC < 0) ? ~0ull : 0ull;
+  R.w0 = (unsigned long long)SC;
+  R.w1 = sxc;
+  R.w2 = sxc;
+  {  // + S_B 2^40
+    const unsigned long long p0 = (unsigned long long)SB << 40;
+    const unsigned long long p1 = (unsigned long long)(SB >> 24);
+    const unsigned long long p2 = (SB < 0) ? ~0ull : 0ull;
+    const unsigned long long s0 = R.w0 + p0;
+    const unsigned long long c0 = s0 < p0;
+    const unsigned long long t1 = R.w1 + p1;
+    const unsigned long long c1a = t1 < p1;
+    const unsigned long long s1 = t1 + c0;
+    const unsigned long long c1b = s1 < t1;
+    R.w0 = s0;
+    R.w1 = s1;
+    R.w2 = R.w2 + p2 + c1a + c1b;
+  }
+  {  // + S_A 2^80
+    const unsigned long long p1 = (unsigned long long)SA << 16;
+    const unsigned long long p2 = (unsigned long long)(SA >> 48);
+    const unsigned long long s1 = R.w1 + p1;
+    const unsigned long long c1 = s1 < p1;
+    R.w1 = s1;
+    R.w2 = R.w2 + p2 + c1;
+  }
+  return R;
+}
+
 // q * 2^e as a double (q <= 2^53 integer): the IEEE fields assembled from
 // the bits (exact: q has at most 53 significant bits); the FP64 route only
 // for results outside the normal range
@@ -513,24 +556,34 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
     } else {
       const int ei = (i < m) ? ea[i] : 0;
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-      for (int c4 = cpart * kCols; c4 < (cpart + 1) * kCols; c4 += 4) {
-        uint32_t v[kDiag][4];
+      const int64_t jw = tn * kTileN + cpart * kCols;   // first column of this warp
+      int fbv[kCols];
 #pragma unroll
-        for (int d = 0; d < kDiag; ++d) tc::tmem_ld_x4(lane_base + (uint32_t)(d * kTileN + c4), v[d]);
+      for (int k = 0; k < kCols; ++k) fbv[k] = (jw + k < N) ? fb[jw + k] : 0;
+      constexpr int CW = 2;                             // columns per TMEM read
+#pragma unroll
+      for (int ch = 0; ch < kCols / CW; ++ch) {
+        const int c0 = cpart * kCols + ch * CW;
+        // this chunk's C entries, loaded before the TMEM reads so that their
+        // latency overlaps them
+        val<2> cvs[CW];
+#pragma unroll
+        for (int cc = 0; cc < CW; ++cc) {
+          const int64_t j = jw + ch * CW + cc;
+          if (i < m && j < N) cvs[cc] = load<2>(C, planeC, i * crs + j * cjs);
+        }
+        uint32_t v[kDiag][CW];
+#pragma unroll
+        for (int d = 0; d < kDiag; ++d) tc::tmem_ld_x2(lane_base + (uint32_t)(d * kTileN + c0), v[d]);
         tc::tmem_ld_wait();
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const int64_t j = tn * kTileN + c4 + cc;
+        for (int cc = 0; cc < CW; ++cc) {
+          const int64_t j = jw + ch * CW + cc;
           if (i >= m || j >= N) continue;
-          I192 R = {0ull, 0ull, 0ull};
-#pragma unroll
-          for (int d = 0; d < kDiag; ++d) {
-            const int D = __float2int_rn(__uint_as_float(v[d][cc]));
-            if (D) i192_add_shifted(R, D, 8 * (kDiag - 1 - d));   // diagonal d+2: weight 2^(8(16-(d+2)))
-          }
-          const int scale = ei + fb[j] - 128;
+          I192 R = recombine15<CW>(v, cc);
+          const int scale = ei + fbv[ch * CW + cc] - 128;
           const int64_t idx = i * crs + j * cjs;
-          val<2> cv = load<2>(C, planeC, idx);
+          val<2> cv = cvs[cc];
           // C - P exactly in the accumulator when C lies on the product's
           // grid 2^scale within the 192-bit range (the usual case), then
           // rounded greedily to DD; otherwise P rounded to DD and the DD
