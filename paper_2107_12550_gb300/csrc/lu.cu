@@ -66,7 +66,50 @@ __device__ __forceinline__ void warp_argmax(val<W>& v, long long& idx) {
 // owner may be rewriting it.  The owner of row k also publishes row k's old
 // values (after the records) for the owner of the pivot row, which moves
 // them into its row; the owner of row k writes the pivot row into row k.
+//
+// Each CTA owns the rows [r0, r1) of the panel.  With RES the CTA keeps its
+// rows of all nb panel columns in shared memory from the first column to the
+// last (read once, written back once); otherwise it works on them in global
+// memory.  Every entry receives the same operations in the same order either
+// way.
+template <int W, bool RES>
+struct PanelRows {
+  double* A;
+  int64_t lda, plane, k0, r0, chunk;
+  double* sp;   // RES: [W][nb][chunk]
+  int nb;
+  __device__ __forceinline__ val<W> get(int64_t i, int j) const {
+    val<W> v;
+    if (RES) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) v.v[c] = sp[((int64_t)c * nb + j) * chunk + (i - r0)];
+    } else {
+      v = load_cg<W>(A, plane, (k0 + j) * lda + i);
+    }
+    return v;
+  }
+  __device__ __forceinline__ double get1(int64_t i, int j, int c) const {
+    if (RES) return sp[((int64_t)c * nb + j) * chunk + (i - r0)];
+    return __ldcg(A + c * plane + (k0 + j) * lda + i);
+  }
+  __device__ __forceinline__ void put(int64_t i, int j, const val<W>& v) const {
+    if (RES) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) sp[((int64_t)c * nb + j) * chunk + (i - r0)] = v.v[c];
+    } else {
+      store_cg<W>(A, plane, (k0 + j) * lda + i, v);
+    }
+  }
+};
+
 template <int W>
+struct CandC {
+  val<W> v;
+  long long idx;
+  int cta;
+};
+
+template <int W, bool RES>
 __global__ void __launch_bounds__(kPanelThreads)
 k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
         int64_t* __restrict__ piv, int64_t* __restrict__ info, char* __restrict__ ws) {
@@ -81,17 +124,30 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
   const int64_t chunk = (rows + G - 1) / G;
   const int64_t r0 = k0 + (int64_t)cta * chunk;
   const int64_t r1 = (r0 + chunk < n) ? r0 + chunk : n;
+  const int64_t nown = (r1 > r0) ? r1 - r0 : 0;
 
   extern __shared__ double smem[];
   double* su = smem;                 // [W][nb]  pivot row u_kj (all panel columns)
   double* sl = smem + W * nb;        // [W][chunk]  multipliers of owned rows
-  __shared__ Cand<W> wred[kPanelThreads / 32];
+  const PanelRows<W, RES> pr{A, lda, plane, k0, r0, chunk, sl + W * chunk, nb};
+  __shared__ CandC<W> wred[kPanelThreads / 32];
   __shared__ long long s_piv, s_best;
   __shared__ int s_zero, s_wcta;
 
+  if (RES) {
+    const int64_t per = (int64_t)nb * nown;
+    for (int64_t e = tid; e < W * per; e += kPanelThreads) {
+      const int c = (int)(e / per);
+      const int64_t rem = e % per;
+      const int j = (int)(rem / nown);
+      const int64_t il = rem % nown;
+      pr.sp[((int64_t)c * nb + j) * chunk + il] = __ldcg(A + c * plane + (k0 + j) * lda + r0 + il);
+    }
+    __syncthreads();
+  }
+
   for (int kk = 0; kk < nb; ++kk) {
     const int64_t k = k0 + kk;
-    const int64_t colk = (k0 + kk) * lda;
     double* rec_base = reinterpret_cast<double*>(ws + kWsCand + (size_t)(kk & 1) * kCandParity);
     double* rec = rec_base + (size_t)cta * (kCandStride / 8);
     double* oldk = rec_base + (size_t)kMaxPanelCtas * (kCandStride / 8);
@@ -101,7 +157,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
     for (int c = 0; c < W; ++c) bv.v[c] = 0.0;
     long long bi = -1;
     for (int64_t i = (r0 > k ? r0 : k) + tid; i < r1; i += kPanelThreads) {
-      const val<W> v = load_cg<W>(A, plane, colk + i);
+      const val<W> v = pr.get(i, kk);
       if (better<W>(v, i, bv, bi)) {
         bv = v;
         bi = i;
@@ -114,7 +170,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
     }
     __syncthreads();
     if (tid == 0) {
-      Cand<W> b = wred[0];
+      CandC<W> b = wred[0];
       for (int w = 1; w < kPanelThreads / 32; ++w)
         if (better<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
 #pragma unroll
@@ -129,29 +185,24 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       const bool own_k = (k >= r0 && k < r1);
       for (int e = tid; e < W * nb; e += kPanelThreads) {
         const int c = e / nb, j = e % nb;
-        if (brow >= 0) __stcg(rec + W + 1 + e, __ldcg(A + c * plane + (k0 + j) * lda + brow));
-        if (own_k) __stcg(oldk + e, __ldcg(A + c * plane + (k0 + j) * lda + k));
+        if (brow >= 0) __stcg(rec + W + 1 + e, pr.get1(brow, j, c));
+        if (own_k) __stcg(oldk + e, pr.get1(k, j, c));
       }
     }
     if (!grid_sync(bar, status, 1)) return;
-    // (b) global argmax from all candidates (every CTA computes the same)
-    if (warp == 0) {
+    // (b) global argmax: thread q reads CTA q's candidate (every CTA computes the same)
+    {
       val<W> gv;
 #pragma unroll
       for (int c = 0; c < W; ++c) gv.v[c] = 0.0;
       long long gi = -1;
       int gc = -1;
-      for (int q = lane; q < G; q += 32) {
-        const double* rq = rec_base + (size_t)q * (kCandStride / 8);
-        val<W> v;
+      if (tid < G) {
+        const double* rq = rec_base + (size_t)tid * (kCandStride / 8);
 #pragma unroll
-        for (int c = 0; c < W; ++c) v.v[c] = __ldcg(rq + c);
-        const long long iq = __ldcg(reinterpret_cast<const long long*>(rq + W));
-        if (better<W>(v, iq, gv, gi)) {
-          gv = v;
-          gi = iq;
-          gc = q;
-        }
+        for (int c = 0; c < W; ++c) gv.v[c] = __ldcg(rq + c);
+        gi = __ldcg(reinterpret_cast<const long long*>(rq + W));
+        gc = tid;
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -167,12 +218,21 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
         }
       }
       if (lane == 0) {
-        s_piv = gi;
-        s_wcta = gc;
-        s_zero = is_zero<W>(gv) ? 1 : 0;
+        wred[warp].v = gv;
+        wred[warp].idx = gi;
+        wred[warp].cta = gc;
       }
+      __syncthreads();
+      if (tid == 0) {
+        CandC<W> b = wred[0];
+        for (int w = 1; w < kPanelThreads / 32; ++w)
+          if (better<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
+        s_piv = b.idx;
+        s_wcta = b.cta;
+        s_zero = is_zero<W>(b.v) ? 1 : 0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const int64_t p = s_piv;
     if (cta == 0 && tid == 0) {
       piv[k] = p;
@@ -186,10 +246,15 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       if (p != k) {
         const bool own_k = (k >= r0 && k < r1);
         const bool own_p = (p >= r0 && p < r1);
-        for (int e = tid; e < W * nb; e += kPanelThreads) {
-          const int c = e / nb, j = e % nb;
-          if (own_k) __stcg(A + c * plane + (k0 + j) * lda + k, su[e]);
-          if (own_p) __stcg(A + c * plane + (k0 + j) * lda + p, __ldcg(oldk + e));
+        for (int j = tid; j < nb; j += kPanelThreads) {
+          val<W> vk, vp;
+#pragma unroll
+          for (int c = 0; c < W; ++c) {
+            vk.v[c] = su[c * nb + j];
+            vp.v[c] = __ldcg(oldk + c * nb + j);
+          }
+          if (own_k) pr.put(k, j, vk);
+          if (own_p) pr.put(p, j, vp);
         }
       }
       __syncthreads();
@@ -201,10 +266,10 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
     const bool zero = is_zero<W>(akk);
     const int64_t ilo = (r0 > k + 1) ? r0 : k + 1;
     for (int64_t i = ilo + tid; i < r1; i += kPanelThreads) {
-      val<W> a = load_cg<W>(A, plane, colk + i);
+      val<W> a = pr.get(i, kk);
       if (!zero) {
         a = div<W>(a, akk);
-        store_cg<W>(A, plane, colk + i, a);
+        pr.put(i, kk, a);
       }
 #pragma unroll
       for (int c = 0; c < W; ++c) sl[c * chunk + (i - r0)] = a.v[c];
@@ -217,19 +282,28 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       for (int64_t q = tid; q < items; q += kPanelThreads) {
         const int64_t i = ilo + q % nrows;
         const int j = kk + 1 + (int)(q / nrows);
-        const int64_t idx = (k0 + j) * lda + i;
         val<W> l, u;
 #pragma unroll
         for (int c = 0; c < W; ++c) {
           l.v[c] = sl[c * chunk + (i - r0)];
           u.v[c] = su[c * nb + j];
         }
-        val<W> a = load_cg<W>(A, plane, idx);
+        val<W> a = pr.get(i, j);
         a = msub<W>(a, l, u);
-        store_cg<W>(A, plane, idx, a);
+        pr.put(i, j, a);
       }
     }
     __syncthreads();
+  }
+  if (RES) {
+    const int64_t per = (int64_t)nb * nown;
+    for (int64_t e = tid; e < W * per; e += kPanelThreads) {
+      const int c = (int)(e / per);
+      const int64_t rem = e % per;
+      const int j = (int)(rem / nown);
+      const int64_t il = rem % nown;
+      __stcg(A + c * plane + (k0 + j) * lda + r0 + il, pr.sp[((int64_t)c * nb + j) * chunk + il]);
+    }
   }
 }
 
@@ -668,8 +742,11 @@ int launch_panel(double* A, int64_t lda, int64_t plane, int64_t n, int64_t k0, i
   int G = (int)std::min<int64_t>((rows + rpc - 1) / rpc, sm_count());
   G = std::max(1, std::min(G, kMaxPanelCtas));
   const int64_t chunk = (rows + G - 1) / G;
-  const size_t shmem = sizeof(double) * (size_t)W * ((size_t)nb + (size_t)chunk);
-  auto kern = k_panel<W>;
+  // the CTA's rows of the panel stay in shared memory when they fit
+  const size_t shmem_res = sizeof(double) * (size_t)W * ((size_t)nb + (size_t)chunk + (size_t)nb * (size_t)chunk);
+  const bool res = shmem_res <= kPanelResidentMax;
+  const size_t shmem = res ? shmem_res : sizeof(double) * (size_t)W * ((size_t)nb + (size_t)chunk);
+  auto kern = res ? k_panel<W, true> : k_panel<W, false>;
   if (shmem > 48 * 1024) {
     MW_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
   }

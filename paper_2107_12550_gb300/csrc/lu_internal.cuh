@@ -12,6 +12,7 @@ constexpr int kPanelRowsPerCta = 8;    // panel rows per CTA before adding CTAs
 constexpr int kMaxPanelCtas = 256;
 constexpr int kDefaultNb = 64;          // panel width of the blocked LU
 constexpr int kMaxNb = 128;
+constexpr size_t kPanelResidentMax = 200 * 1024;   // shared memory for panel rows kept resident
 
 // LU work buffer: [barrier | status | panel candidates | split-update scratch]
 // The candidate area holds, for two column parities, one record per CTA
