@@ -58,14 +58,21 @@ __device__ __forceinline__ void warp_argmax(val<W>& v, long long& idx) {
 }
 
 // Candidate record (in the work buffer, per column parity and CTA):
-//   [0, W)          candidate value words
-//   [W]             candidate row index (as int64 bits)
-//   [W+1, W+1+W*nb) the candidate's whole panel row, word-major
-// After the single grid barrier of a column every CTA reads the winner's
-// record, so the pivot row never has to be read from the matrix while its
-// owner may be rewriting it.  The owner of row k also publishes row k's old
-// values (after the records) for the owner of the pivot row, which moves
-// them into its row; the owner of row k writes the pivot row into row k.
+//   [0]             ready tag: k + 1 once the record of column k is complete
+//   [1, 1+W)        candidate value words
+//   [1+W]           candidate row index (as int64 bits)
+//   [2+W, 2+W+W*nb) the candidate's whole panel row, word-major
+// A CTA writes its record (and, if it owns row k, row k's old values after
+// the records), then -- after a fence -- the tag with release semantics.
+// Thread q of every CTA waits (bounded) for CTA q's tag with acquire
+// semantics and reads its candidate: the tags are the column's only grid
+// synchronisation.  A CTA writes the records of column k + 2 (same parity)
+// only after reading every record of column k, and it reads them only after
+// every CTA has written its column k + 1 record, so no record is overwritten
+// while it is still being read.  Every CTA takes the pivot row from the
+// winner's record, so it never has to be read from the matrix while its
+// owner may be rewriting it; the owner of row k writes the pivot row into
+// row k and the owner of the pivot row moves the old row k into its row.
 //
 // Each CTA owns the rows [r0, r1) of the panel.  With RES the CTA keeps its
 // rows of all nb panel columns in shared memory from the first column to the
@@ -133,6 +140,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
   __shared__ CandC<W> wred[kPanelThreads / 32];
   __shared__ long long s_piv, s_best;
   __shared__ int s_zero, s_wcta;
+  constexpr int kRecVal = 1, kRecIdx = 1 + W, kRecRow = 2 + W;
 
   if (RES) {
     const int64_t per = (int64_t)nb * nown;
@@ -174,8 +182,8 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       for (int w = 1; w < kPanelThreads / 32; ++w)
         if (better<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
 #pragma unroll
-      for (int c = 0; c < W; ++c) __stcg(rec + c, b.v.v[c]);
-      __stcg(reinterpret_cast<long long*>(rec + W), b.idx);
+      for (int c = 0; c < W; ++c) __stcg(rec + kRecVal + c, b.v.v[c]);
+      __stcg(reinterpret_cast<long long*>(rec + kRecIdx), b.idx);
       s_best = b.idx;
     }
     __syncthreads();
@@ -185,24 +193,49 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       const bool own_k = (k >= r0 && k < r1);
       for (int e = tid; e < W * nb; e += kPanelThreads) {
         const int c = e / nb, j = e % nb;
-        if (brow >= 0) __stcg(rec + W + 1 + e, pr.get1(brow, j, c));
+        if (brow >= 0) __stcg(rec + kRecRow + e, pr.get1(brow, j, c));
         if (own_k) __stcg(oldk + e, pr.get1(k, j, c));
       }
     }
-    if (!grid_sync(bar, status, 1)) return;
-    // (b) global argmax: thread q reads CTA q's candidate (every CTA computes the same)
+    __syncthreads();
+    const unsigned long long tag = (unsigned long long)k + 1ull;
+    if (tid == 0) {
+      __threadfence();
+      st_release_u64(rec, tag);
+    }
+    // (b) global argmax: thread q waits for CTA q's record and reads its
+    // candidate (every CTA computes the same)
     {
       val<W> gv;
 #pragma unroll
       for (int c = 0; c < W; ++c) gv.v[c] = 0.0;
       long long gi = -1;
       int gc = -1;
+      int failed = 0;
       if (tid < G) {
         const double* rq = rec_base + (size_t)tid * (kCandStride / 8);
+        unsigned long long spins = 0;
+        while (ld_acquire_u64(rq) != tag) {
+          if (++spins > kSpinLimit || ld_acquire_u32(&bar->abort)) {
+            failed = 1;
+            break;
+          }
+          if (spins > 64) __nanosleep(32);
+        }
+        if (!failed) {
 #pragma unroll
-        for (int c = 0; c < W; ++c) gv.v[c] = __ldcg(rq + c);
-        gi = __ldcg(reinterpret_cast<const long long*>(rq + W));
-        gc = tid;
+          for (int c = 0; c < W; ++c) gv.v[c] = __ldcg(rq + kRecVal + c);
+          gi = __ldcg(reinterpret_cast<const long long*>(rq + kRecIdx));
+          gc = tid;
+        }
+      }
+      if (__syncthreads_or(failed)) {
+        if (tid == 0) {
+          atomicExch(&bar->abort, 1u);
+          atomicExch(&status->timeout, 1u);
+          atomicExch(&status->where, 1u);
+        }
+        return;
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -240,7 +273,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
     }
     // (c) pivot row from the winner's record; swap rows k and p
     {
-      const double* wrec = rec_base + (size_t)s_wcta * (kCandStride / 8) + W + 1;
+      const double* wrec = rec_base + (size_t)s_wcta * (kCandStride / 8) + kRecRow;
       for (int e = tid; e < W * nb; e += kPanelThreads) su[e] = __ldcg(wrec + e);
       __syncthreads();
       if (p != k) {
@@ -796,7 +829,7 @@ static int lu_split_dd(int64_t n, double* A, int64_t lda, int64_t* piv, int64_t*
   const size_t sbytes = ws_bytes > kWsSplit ? ws_bytes - kWsSplit : 0;
   if (sbytes < split_workspace_bytes(n, kDefaultNb)) return MW_EUNSUPPORTED;
   double* aux = split_aux(sws, n);
-  MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand, s));
+  MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand + 2 * kCandParity, s));
   MW_CUDA_CHECK(cudaMemsetAsync(sws, 0, 256, s));
   MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
   constexpr int NB = kDefaultNb;
@@ -854,7 +887,7 @@ int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int6
                char* ws, size_t ws_bytes, int nb, cudaStream_t s) {
   if (update == MW_UPDATE_SPLIT && W == 2) return lu_split_dd(n, A, lda, piv, info, ws, ws_bytes, s);
   const int64_t plane = lda * n;
-  MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand, s));
+  MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand + 2 * kCandParity, s));
   MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
   for (int64_t k0 = 0; k0 < n; k0 += nb) {
     const int kb = (int)std::min<int64_t>(nb, n - k0);

@@ -16,12 +16,13 @@ constexpr size_t kPanelResidentMax = 200 * 1024;   // shared memory for panel ro
 
 // LU work buffer: [barrier | status | panel candidates | split-update scratch]
 // The candidate area holds, for two column parities, one record per CTA
-// (the candidate value, its row index and a copy of the whole candidate row
-// of the panel) and a copy of the old row k.
+// (a ready tag, the candidate value, its row index and a copy of the whole
+// candidate row of the panel) and a copy of the old row k.  It is cleared at
+// the start of every factorisation.
 constexpr size_t kWsBarrier = 0;
 constexpr size_t kWsStatus = 64;
 constexpr size_t kWsCand = 256;
-constexpr size_t kCandStride = 8 * (4 + 1 + 4 * kMaxNb);             // doubles of one record, in bytes
+constexpr size_t kCandStride = 8 * (1 + 4 + 1 + 4 * kMaxNb);         // one record, in bytes
 constexpr size_t kCandParity = kCandStride * kMaxPanelCtas + 8 * 4 * kMaxNb;  // records + old row k
 constexpr size_t kWsSplit = (kWsCand + 2 * kCandParity + 65535) & ~(size_t)65535;
 
