@@ -252,6 +252,25 @@ int mw_refine_batched_blocked(int count, const int* n_host, const double* A, int
                               size_t work_bytes, void* stream);
 
 /*
+ * Resident batch plans, for CUDA graph capture of the batched calls.
+ * Every batched call uploads its plan (offsets, processing order, tile
+ * lists) into the work buffer with host-to-device copies, which a stream
+ * capture cannot record from pageable memory.  mw_batch_plan_cache(1)
+ * switches on a host-side record of the plans already resident per work
+ * buffer address: a call whose plan (same kind, batch, precision and update)
+ * is already in its work buffer then issues no copy, so after one ordinary
+ * call the same calls on the same buffers can be captured and replayed.
+ * The caller must keep those work buffers alive and unmodified while the
+ * record is on (a freed buffer's address can come back holding other data).
+ *   mw_batch_plan_cache(on)  returns the previous setting; off forgets all.
+ *   mw_batch_plan_reset()    forgets all records.
+ * The batched refinement reads one integer per step back to the host and
+ * cannot be captured; the LU and solve calls can.
+ */
+int mw_batch_plan_cache(int on);
+int mw_batch_plan_reset(void);
+
+/*
  * mw_arith -- element-wise multiword arithmetic on device arrays (the
  * DD/TD/QD building blocks of Section 1, as used inside every kernel):
  *   op 0: z = x + y   1: z = x - y   2: z = x * y   3: z = x / y

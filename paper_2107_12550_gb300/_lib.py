@@ -43,6 +43,8 @@ SIGNATURES = {
     "mw_batch_blocked_workspace_size": (_I, [_I, _I, _I, _I, _P, ctypes.POINTER(_SZ)]),
     "mw_ludecomp_batched_blocked": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _SZ, _P]),
     "mw_refine_batched_blocked": (_I, [_I, _P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _SZ, _P]),
+    "mw_batch_plan_cache": (_I, [_I]),
+    "mw_batch_plan_reset": (_I, []),
     "mw_profile_enable": (_I, [_I]),
     "mw_profile_read": (_I, [ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I, _I]),
     "mw_set_tuning": (_I, [_I, _I, _I]),

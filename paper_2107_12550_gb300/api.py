@@ -327,6 +327,14 @@ def refine_batched_blocked(A: torch.Tensor, a_words: int, b: torch.Tensor, b_wor
     return x, stats
 
 
+def batch_plan_cache(on: bool) -> bool:
+    """Switch the record of resident batch plans on or off (off forgets all);
+    returns the previous setting.  With it on, repeated batched LU / solve
+    calls on the same batch and work buffers upload nothing and can be
+    captured in a CUDA graph; keep those work buffers alive meanwhile."""
+    return bool(L.lib().mw_batch_plan_cache(1 if on else 0))
+
+
 def arith(op: int, prec, x: torch.Tensor, y: torch.Tensor, *, stream=None) -> torch.Tensor:
     """Element-wise multiword op (0 add, 1 sub, 2 mul, 3 div, 4 compare |x|,|y|)."""
     w = _prec(prec)

@@ -19,6 +19,7 @@
 // substitution), so each system's results are bitwise identical to the
 // single-system calls.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -685,6 +686,64 @@ static size_t plan_bytes(int count) {
          align256(sizeof(int) * count) + align256(sizeof(int64_t) * (count + 1));
 }
 
+// Plans already resident in work buffers: (device address, kind, hash of the
+// batch).  Only while the caller has switched this on (mw_batch_plan_cache):
+// then a call whose plan is already in place issues no host-to-device copy,
+// so repeated calls on the same batch and work buffer can be captured in a
+// CUDA graph.  The caller must keep those work buffers (a freed buffer's
+// address can come back holding other data); mw_batch_plan_reset() or
+// switching the cache off forgets every entry.
+struct ResidentPlan {
+  const void* addr;
+  int kind;
+  unsigned long long hash;
+};
+static std::mutex g_plan_mu;
+static std::vector<ResidentPlan> g_plans;
+static bool g_plan_cache_on = false;
+constexpr size_t kMaxResidentPlans = 256;
+
+static unsigned long long batch_hash(const std::vector<int>& n, int a, int b) {
+  unsigned long long h = 1469598103934665603ull;   // FNV-1a
+  auto mix = [&](unsigned long long v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (v >> (8 * i)) & 0xffull;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((unsigned long long)n.size());
+  mix((unsigned long long)(unsigned)a);
+  mix((unsigned long long)(unsigned)b);
+  for (int v : n) mix((unsigned long long)(unsigned)v);
+  return h;
+}
+
+// true if the plan is already resident; otherwise records it (the caller
+// then uploads it)
+static bool plan_resident(const void* addr, int kind, unsigned long long hash) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (!g_plan_cache_on) return false;
+  for (auto& e : g_plans)
+    if (e.addr == addr) {
+      if (e.kind == kind && e.hash == hash) return true;
+      e.kind = kind;
+      e.hash = hash;
+      return false;
+    }
+  if (g_plans.size() >= kMaxResidentPlans) g_plans.erase(g_plans.begin());
+  g_plans.push_back(ResidentPlan{addr, kind, hash});
+  return false;
+}
+
+static void plan_forget(const void* addr) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (size_t i = 0; i < g_plans.size(); ++i)
+    if (g_plans[i].addr == addr) {
+      g_plans.erase(g_plans.begin() + i);
+      return;
+    }
+}
+
 static int upload_plan(const BatchPlanHost& p, int count, char* ws, BatchPlanDev& d, cudaStream_t s) {
   size_t off = 256;
   d.n = reinterpret_cast<int*>(ws + off);
@@ -696,11 +755,20 @@ static int upload_plan(const BatchPlanHost& p, int count, char* ws, BatchPlanDev
   d.order = reinterpret_cast<int*>(ws + off);
   off += align256(sizeof(int) * count);
   d.rb = reinterpret_cast<int64_t*>(ws + off);
-  MW_CUDA_CHECK(cudaMemcpyAsync(d.n, p.n.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
-  MW_CUDA_CHECK(cudaMemcpyAsync(d.moff, p.moff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
-  MW_CUDA_CHECK(cudaMemcpyAsync(d.voff, p.voff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
-  MW_CUDA_CHECK(cudaMemcpyAsync(d.order, p.order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
-  MW_CUDA_CHECK(cudaMemcpyAsync(d.rb, p.rb.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+  if (plan_resident(ws, 0, batch_hash(p.n, 0, 0))) return MW_OK;
+  cudaError_t e = cudaMemcpyAsync(d.n, p.n.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.moff, p.moff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.voff, p.voff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.order, p.order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.rb, p.rb.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    plan_forget(ws);
+    MW_CUDA_CHECK(e);
+  }
   return MW_OK;
 }
 
@@ -859,11 +927,13 @@ struct BlockedDev {
   int64_t a_tiles, b_tiles;
 };
 
-static int upload_geom(const GeomPlanHost& g, char* base, size_t& off, GeomDev& d, cudaStream_t s) {
+static int upload_geom(const GeomPlanHost& g, char* base, size_t& off, GeomDev& d, cudaStream_t s,
+                       bool resident) {
   d.tiles = reinterpret_cast<TileEntry*>(base + off);
   off += align256(sizeof(TileEntry) * std::max<size_t>(1, g.tiles.size()));
   d.bases = reinterpret_cast<int2*>(base + off);
   off += align256(sizeof(int2) * std::max<size_t>(1, g.bases.size()));
+  if (resident) return MW_OK;
   if (!g.tiles.empty())
     MW_CUDA_CHECK(cudaMemcpyAsync(d.tiles, g.tiles.data(), sizeof(TileEntry) * g.tiles.size(),
                                   cudaMemcpyHostToDevice, s));
@@ -873,15 +943,27 @@ static int upload_geom(const GeomPlanHost& g, char* base, size_t& off, GeomDev& 
   return MW_OK;
 }
 
-static int upload_blocked(const BlockedPlanHost& bp, char* base, BlockedDev& d, cudaStream_t s) {
+static int upload_blocked(const BlockedPlanHost& bp, const std::vector<int>& n, int prec, char* base,
+                          BlockedDev& d, cudaStream_t s) {
+  const bool resident = plan_resident(base, 1, batch_hash(n, prec, bp.update));
   size_t off = 0;
-  int rc = upload_geom(bp.trail, base, off, d.trail, s);
+  int rc = upload_geom(bp.trail, base, off, d.trail, s, resident);
   if (rc) return rc;
-  rc = upload_geom(bp.tinv, base, off, d.tinv, s);
-  if (rc) return rc;
+  if (rc) {
+    plan_forget(base);
+    return rc;
+  }
+  rc = upload_geom(bp.tinv, base, off, d.tinv, s, resident);
+  if (rc) {
+    plan_forget(base);
+    return rc;
+  }
   for (int q = 0; q < 3; ++q) {
-    rc = upload_geom(bp.pinner[q], base, off, d.pinner[q], s);
-    if (rc) return rc;
+    rc = upload_geom(bp.pinner[q], base, off, d.pinner[q], s, resident);
+    if (rc) {
+      plan_forget(base);
+      return rc;
+    }
   }
   d.aux = nullptr;
   d.split_ws = nullptr;
@@ -1215,7 +1297,7 @@ extern "C" int mw_ludecomp_batched_blocked(int prec, int update, int count, cons
   int rc = mw::upload_plan(p, count, ws, d, s);
   if (rc) return rc;
   mw::BlockedDev bd;
-  rc = mw::upload_blocked(bp, ws + head, bd, s);
+  rc = mw::upload_blocked(bp, p.n, prec, ws + head, bd, s);
   if (rc) return rc;
   switch (prec) {
     case 2: return mw::lu_blocked_batched_run<2>(p, d, bp, bd, A, piv, info, s);
@@ -1256,11 +1338,25 @@ extern "C" int mw_refine_batched_blocked(int count, const int* n_host, const dou
   int rc = mw::upload_plan(p, count, ws, d, s);
   if (rc) return rc;
   mw::BlockedDev bd;
-  rc = mw::upload_blocked(bp, ws + head, bd, s);
+  rc = mw::upload_blocked(bp, p.n, inner, ws + head, bd, s);
   if (rc) return rc;
   switch (inner) {
     case 2: return mw::refine_batched_impl<2>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
     case 3: return mw::refine_batched_impl<3>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
     default: return mw::refine_batched_impl<4>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
   }
+}
+
+extern "C" int mw_batch_plan_reset(void) {
+  std::lock_guard<std::mutex> lk(mw::g_plan_mu);
+  mw::g_plans.clear();
+  return MW_OK;
+}
+
+extern "C" int mw_batch_plan_cache(int on) {
+  std::lock_guard<std::mutex> lk(mw::g_plan_mu);
+  const int prev = mw::g_plan_cache_on ? 1 : 0;
+  mw::g_plan_cache_on = on != 0;
+  if (!on) mw::g_plans.clear();
+  return prev;
 }

@@ -181,3 +181,50 @@ def test_refine_blocked_split_reaches_target():
         for i in range(0, n, 7):
             v = sum(Fraction(float(c)) for c in xs[s][:, i])
             assert abs(v - 1) <= Fraction(1, 2 ** 200), (s, i)
+
+
+def test_batched_lu_and_solve_in_a_cuda_graph():
+    """With resident plans, the blocked batched LU (split and plain) and the
+    batched solve are captured in a CUDA graph; each replay reproduces the
+    eager results bitwise."""
+    n_list = [int(v) for v in W.batch_sizes(24, 1, 300, seed=71)]
+    mats, vecs = _uniform_batch(2, n_list, seed=72)
+    A = dev(api().pack_matrices(mats, 2))
+    b = dev(api().pack_vectors(vecs, 2))
+    from paper_2107_12550_gb300 import _lib as L
+    prev = api().batch_plan_cache(True)
+    try:
+        for upd in ("plain", "split"):
+            wk = api().batch_blocked_workspace(L.MW_OP_LUDECOMP, 2, upd, n_list)
+            wks = api().batch_workspace(L.MW_OP_SOLVE, 2, n_list)
+            LU = torch.empty_like(A)
+            x = torch.empty_like(b)
+            total_n = int(sum(n_list))
+            piv = torch.empty(total_n, dtype=torch.int64, device="cuda")
+
+            def step():
+                LU.copy_(A)
+                _, pv, _ = api().ludecomp_batched_blocked(LU, n_list, 2, upd, work=wk, inplace=True)
+                piv.copy_(pv)
+                api().solve_batched(LU, piv, b, n_list, 2, work=wks, out=x)
+
+            step()                                   # uploads the plans
+            torch.cuda.synchronize()
+            LU_ref, x_ref = LU.clone(), x.clone()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                step()                               # warm on the capture stream
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step()
+            LU.zero_()
+            x.zero_()
+            for _ in range(2):
+                g.replay()
+                torch.cuda.synchronize()
+                assert torch.equal(LU, LU_ref) and torch.equal(x, x_ref), upd
+    finally:
+        api().batch_plan_cache(prev)
