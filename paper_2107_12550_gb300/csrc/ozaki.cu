@@ -122,108 +122,130 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
 }
 
 // ---------------------------------------------------------------------------
-// slicing: L21 rows -> A slices [tile][p][128 x 64], row exponents e_i
-// one thread per row; 8 consecutive k at a time -> one 16-byte store per slice
+// slicing: row operand -> A slices [tile][p][128 x 64] with row exponents
+// e_i; column operand -> B slices [tile][q][32 x 64] (column j is a K-major
+// row) with column exponents f_j.  One CTA of 128 threads takes 16 rows (or
+// columns) x 8 chunks of 8 k: each thread reads its 8 entries, the 8
+// threads of a row combine their maxima in shared memory, and each thread
+// writes the 16-byte swizzled piece of each of the 15 digit slices that its
+// chunk fills.  Rows whose data are contiguous in i are read with
+// consecutive threads on consecutive rows, rows contiguous in k with
+// consecutive threads on consecutive chunks.  k >= kvalid: zero digits.
 // ---------------------------------------------------------------------------
-// element (r, k) of the row operand at L[r * lrs + k * lks]
-// (k >= kvalid: zero digits)
-__device__ __forceinline__ void slice_row(const double* __restrict__ L, int64_t lrs, int64_t lks, int64_t planeL,
-                                          int64_t m, int kvalid, unsigned char* __restrict__ aslices,
-                                          int* __restrict__ ea, int64_t r) {  // padded row index
+constexpr int kSliceRows = 16;   // rows (or columns) per CTA
+constexpr int kSliceThreads = kSliceRows * (kK / 8);
+
+// 8 entries (both words) of row or column r from k = kc*8; returns max |hi|
+__device__ __forceinline__ double slice_load8(const double* __restrict__ X, int64_t rs, int64_t ks, int64_t planeX,
+                                              bool ok, int kvalid, int64_t r, int kc, double (&hv)[8],
+                                              double (&lv)[8]) {
+  double mx = 0.0;
+#pragma unroll
+  for (int k8 = 0; k8 < 8; ++k8) {
+    const int k = kc * 8 + k8;
+    if (ok && k < kvalid) {
+      const int64_t idx = r * rs + (int64_t)k * ks;
+      hv[k8] = X[idx];
+      lv[k8] = X[planeX + idx];
+      mx = fmax(mx, fabs(hv[k8]));
+    } else {
+      hv[k8] = 0.0;
+      lv[k8] = 0.0;
+    }
+  }
+  return mx;
+}
+
+// the 15 digit pieces of 8 scaled entries (exponent e) -> dst + p * pstride
+__device__ __forceinline__ void slice_store8(const double (&hv)[8], const double (&lv)[8], int e, bool live,
+                                             unsigned char* __restrict__ dst, int pstride) {
+  uint32_t packed[kS][4];
+#pragma unroll
+  for (int p = 0; p < kS; ++p)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) packed[p][h] = 0u;
+#pragma unroll
+  for (int k8 = 0; k8 < 8; ++k8) {
+    int a[kS];
+    if (live) {
+      const __int128 X = scaled_floor(hv[k8], 120 - e) + scaled_floor(lv[k8], 120 - e);
+      digits15(X, a);
+    } else {
+#pragma unroll
+      for (int p = 0; p < kS; ++p) a[p] = 0;
+    }
+#pragma unroll
+    for (int p = 0; p < kS; ++p) packed[p][k8 >> 1] |= (uint32_t)bf16_bits_of_int(a[p]) << (16 * (k8 & 1));
+  }
+#pragma unroll
+  for (int p = 0; p < kS; ++p) {
+    uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
+    *reinterpret_cast<uint4*>(dst + (int64_t)p * pstride) = v;
+  }
+}
+
+// rows [rbase, rbase + 16) of the row operand (element (r, k) at L[r*lrs + k*lks])
+__device__ __forceinline__ void slice_rows16(const double* __restrict__ L, int64_t lrs, int64_t lks,
+                                             int64_t planeL, int64_t m, int kvalid,
+                                             unsigned char* __restrict__ aslices, int* __restrict__ ea,
+                                             int64_t rbase) {
+  __shared__ double smx[kSliceRows][kK / 8];
+  const int tid = threadIdx.x;
+  const bool rows_fast = lrs == 1;
+  const int rl = rows_fast ? (tid & (kSliceRows - 1)) : (tid >> 3);
+  const int kc = rows_fast ? (tid / kSliceRows) : (tid & 7);
+  const int64_t r = rbase + rl;
+  const bool ok = r < m;
+  double hv[8], lv[8];
+  smx[rl][kc] = slice_load8(L, lrs, lks, planeL, ok, kvalid, r, kc, hv, lv);
+  __syncthreads();
+  double mx = 0.0;
+#pragma unroll
+  for (int q = 0; q < kK / 8; ++q) mx = fmax(mx, smx[rl][q]);
+  const int e = (mx > 0.0) ? exp_of_max(mx) : 0;
+  if (kc == 0) ea[r] = e;
   const int64_t tile = r / kTileM;
   const int rr = (int)(r % kTileM);
-  const bool ok = r < m;
+  slice_store8(hv, lv, e, ok && mx > 0.0, aslices + tile * (int64_t)kS * kASliceBytes + sw128_offset(rr, kc * 8),
+               kASliceBytes);
+}
+
+// columns [jbase, jbase + 16) of the column operand (element (k, j) at U[k*uks + j*ujs])
+__device__ __forceinline__ void slice_cols16(const double* __restrict__ U, int64_t uks, int64_t ujs,
+                                             int64_t planeU, int64_t N, int kvalid,
+                                             unsigned char* __restrict__ bslices, int* __restrict__ fb,
+                                             int64_t jbase) {
+  __shared__ double smx[kSliceRows][kK / 8];
+  const int tid = threadIdx.x;
+  const bool cols_fast = ujs == 1;
+  const int jl = cols_fast ? (tid & (kSliceRows - 1)) : (tid >> 3);
+  const int kc = cols_fast ? (tid / kSliceRows) : (tid & 7);
+  const int64_t j = jbase + jl;
+  const bool ok = j < N;
+  double hv[8], lv[8];
+  smx[jl][kc] = slice_load8(U, ujs, uks, planeU, ok, kvalid, j, kc, hv, lv);
+  __syncthreads();
   double mx = 0.0;
-  if (ok) {
-    for (int k = 0; k < kvalid; ++k) mx = fmax(mx, fabs(L[r * lrs + k * lks]));
-  }
-  const int e = (mx > 0.0) ? exp_of_max(mx) : 0;
-  ea[r] = e;
-  unsigned char* base = aslices + tile * (int64_t)kS * kASliceBytes;
-  for (int kc = 0; kc < kK / 8; ++kc) {
-    uint32_t packed[kS][4];
 #pragma unroll
-    for (int p = 0; p < kS; ++p)
-#pragma unroll
-      for (int h = 0; h < 4; ++h) packed[p][h] = 0u;
-#pragma unroll
-    for (int k8 = 0; k8 < 8; ++k8) {
-      const int k = kc * 8 + k8;
-      int a[kS];
-      if (ok && mx > 0.0 && k < kvalid) {
-        const int64_t idx = r * lrs + k * lks;
-        const __int128 X = scaled_floor(L[idx], 120 - e) + scaled_floor(L[planeL + idx], 120 - e);
-        digits15(X, a);
-      } else {
-#pragma unroll
-        for (int p = 0; p < kS; ++p) a[p] = 0;
-      }
-#pragma unroll
-      for (int p = 0; p < kS; ++p)
-        packed[p][k8 >> 1] |= (uint32_t)bf16_bits_of_int(a[p]) << (16 * (k8 & 1));
-    }
-#pragma unroll
-    for (int p = 0; p < kS; ++p) {
-      uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
-      *reinterpret_cast<uint4*>(base + (int64_t)p * kASliceBytes + sw128_offset(rr, kc * 8)) = v;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(128)
-k_slice_rows(SplitOperands o, unsigned char* __restrict__ aslices, int* __restrict__ ea) {
-  slice_row(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices, ea, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-// U12 columns -> B slices [tile][q][32 x 64] (column j is a K-major row), f_j;
-// element (k, j) of the column operand at U[k * uks + j * ujs]
-__device__ __forceinline__ void slice_col(const double* __restrict__ U, int64_t uks, int64_t ujs, int64_t planeU,
-                                          int64_t N, int64_t npad, int kvalid, unsigned char* __restrict__ bslices,
-                                          int* __restrict__ fb, int64_t j) {  // padded column index
-  if (j >= npad) return;
+  for (int q = 0; q < kK / 8; ++q) mx = fmax(mx, smx[jl][q]);
+  const int f = (mx > 0.0) ? exp_of_max(mx) : 0;
+  if (kc == 0) fb[j] = f;
   const int64_t tile = j / kTileN;
   const int jj = (int)(j % kTileN);
-  const bool ok = j < N;
-  const double* col = U + (ok ? j : 0) * ujs;
-  double mx = 0.0;
-  if (ok) {
-    for (int k = 0; k < kvalid; ++k) mx = fmax(mx, fabs(col[k * uks]));
-  }
-  const int f = (mx > 0.0) ? exp_of_max(mx) : 0;
-  fb[j] = f;
-  unsigned char* base = bslices + tile * (int64_t)kS * kBSliceBytes;
-  for (int kc = 0; kc < kK / 8; ++kc) {
-    uint32_t packed[kS][4];
-#pragma unroll
-    for (int p = 0; p < kS; ++p)
-#pragma unroll
-      for (int h = 0; h < 4; ++h) packed[p][h] = 0u;
-#pragma unroll
-    for (int k8 = 0; k8 < 8; ++k8) {
-      const int k = kc * 8 + k8;
-      int a[kS];
-      if (ok && mx > 0.0 && k < kvalid) {
-        const __int128 X = scaled_floor(col[k * uks], 120 - f) + scaled_floor(col[planeU + k * uks], 120 - f);
-        digits15(X, a);
-      } else {
-#pragma unroll
-        for (int p = 0; p < kS; ++p) a[p] = 0;
-      }
-#pragma unroll
-      for (int p = 0; p < kS; ++p)
-        packed[p][k8 >> 1] |= (uint32_t)bf16_bits_of_int(a[p]) << (16 * (k8 & 1));
-    }
-#pragma unroll
-    for (int p = 0; p < kS; ++p) {
-      uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
-      *reinterpret_cast<uint4*>(base + (int64_t)p * kBSliceBytes + sw128_offset(jj, kc * 8)) = v;
-    }
-  }
+  slice_store8(hv, lv, f, ok && mx > 0.0, bslices + tile * (int64_t)kS * kBSliceBytes + sw128_offset(jj, kc * 8),
+               kBSliceBytes);
 }
 
-__global__ void __launch_bounds__(128)
-k_slice_cols(SplitOperands o, int64_t npad, unsigned char* __restrict__ bslices, int* __restrict__ fb) {
-  slice_col(o.U, o.uks, o.ujs, o.planeU, o.N, npad, o.K, bslices, fb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+// grid: (rows padded to 128) / 16
+__global__ void __launch_bounds__(kSliceThreads)
+k_slice_rows(SplitOperands o, unsigned char* __restrict__ aslices, int* __restrict__ ea) {
+  slice_rows16(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices, ea, (int64_t)blockIdx.x * kSliceRows);
+}
+
+// grid: (columns padded to 32) / 16
+__global__ void __launch_bounds__(kSliceThreads)
+k_slice_cols(SplitOperands o, unsigned char* __restrict__ bslices, int* __restrict__ fb) {
+  slice_cols16(o.U, o.uks, o.ujs, o.planeU, o.N, o.K, bslices, fb, (int64_t)blockIdx.x * kSliceRows);
 }
 
 // ---------------------------------------------------------------------------
@@ -695,8 +717,8 @@ __device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int
   return o;
 }
 
-// grid (act, max_mt): 128-row tile blockIdx.y of system order[blockIdx.x]
-__global__ void __launch_bounds__(128)
+// grid (act, 8 * max_mt): 16 rows blockIdx.y of system order[blockIdx.x]
+__global__ void __launch_bounds__(kSliceThreads)
 k_bslice_rows(BatchView bv, int geom, int c_off, int h, const int2* __restrict__ bases, int k0,
               double* __restrict__ A, const double* __restrict__ aux, unsigned char* __restrict__ aslices,
               int* __restrict__ ea) {
@@ -705,14 +727,15 @@ k_bslice_rows(BatchView bv, int geom, int c_off, int h, const int2* __restrict__
   const int n = bv.n[sys];
   const SplitOperands o =
       batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK, c_off, h);
-  if (o.m <= 0 || o.N <= 0 || (int64_t)blockIdx.y * kTileM >= o.m) return;
+  const int64_t rbase = (int64_t)blockIdx.y * kSliceRows;
+  if (o.m <= 0 || o.N <= 0 || rbase >= (o.m + kTileM - 1) / kTileM * kTileM) return;   // uniform per CTA
   const int abase = bases[pos].x;
-  slice_row(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices + (int64_t)abase * kS * kASliceBytes,
-            ea + (int64_t)abase * kTileM, (int64_t)blockIdx.y * kTileM + threadIdx.x);
+  slice_rows16(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices + (int64_t)abase * kS * kASliceBytes,
+               ea + (int64_t)abase * kTileM, rbase);
 }
 
-// grid (act, max_cb): 128-column block blockIdx.y of system order[blockIdx.x]
-__global__ void __launch_bounds__(128)
+// grid (act, 8 * max_cb): 16 columns blockIdx.y of system order[blockIdx.x]
+__global__ void __launch_bounds__(kSliceThreads)
 k_bslice_cols(BatchView bv, int geom, int c_off, int h, const int2* __restrict__ bases, int k0,
               double* __restrict__ A, const double* __restrict__ aux, unsigned char* __restrict__ bslices,
               int* __restrict__ fb) {
@@ -721,12 +744,11 @@ k_bslice_cols(BatchView bv, int geom, int c_off, int h, const int2* __restrict__
   const int n = bv.n[sys];
   const SplitOperands o =
       batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK, c_off, h);
-  if (o.m <= 0 || o.N <= 0) return;
-  const int64_t npad = (o.N + kTileN - 1) / kTileN * kTileN;
-  if ((int64_t)blockIdx.y * 128 >= npad) return;
+  const int64_t jbase = (int64_t)blockIdx.y * kSliceRows;
+  if (o.m <= 0 || o.N <= 0 || jbase >= (o.N + kTileN - 1) / kTileN * kTileN) return;   // uniform per CTA
   const int bbase = bases[pos].y;
-  slice_col(o.U, o.uks, o.ujs, o.planeU, o.N, npad, o.K, bslices + (int64_t)bbase * kS * kBSliceBytes,
-            fb + (int64_t)bbase * kTileN, (int64_t)blockIdx.y * 128 + threadIdx.x);
+  slice_cols16(o.U, o.uks, o.ujs, o.planeU, o.N, o.K, bslices + (int64_t)bbase * kS * kBSliceBytes,
+               fb + (int64_t)bbase * kTileN, jbase);
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 1)
@@ -886,9 +908,9 @@ int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phas
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
   {
     ProfScope ps(kPhSplitAux, s);
-    k_slice_rows<<<(unsigned)mt, 128, 0, s>>>(o, aslices, ea);
+    k_slice_rows<<<(unsigned)(mt * kTileM / kSliceRows), kSliceThreads, 0, s>>>(o, aslices, ea);
     MW_LAUNCH_CHECK();
-    k_slice_cols<<<(unsigned)((nt * kTileN + 127) / 128), 128, 0, s>>>(o, nt * kTileN, bslices, fb);
+    k_slice_cols<<<(unsigned)(nt * kTileN / kSliceRows), kSliceThreads, 0, s>>>(o, bslices, fb);
     MW_LAUNCH_CHECK();
   }
   {
@@ -967,11 +989,11 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
   {
     ProfScope ps(kPhSplitAux, s);
-    k_bslice_rows<<<dim3((unsigned)act, (unsigned)max_mt), 128, 0, s>>>(bv, geom, c_off, h, bases, k0, A, aux,
-                                                                         aslices, ea);
+    k_bslice_rows<<<dim3((unsigned)act, (unsigned)(max_mt * kTileM / kSliceRows)), kSliceThreads, 0, s>>>(
+        bv, geom, c_off, h, bases, k0, A, aux, aslices, ea);
     MW_LAUNCH_CHECK();
-    k_bslice_cols<<<dim3((unsigned)act, (unsigned)max_cb), 128, 0, s>>>(bv, geom, c_off, h, bases, k0, A, aux,
-                                                                         bslices, fb);
+    k_bslice_cols<<<dim3((unsigned)act, (unsigned)(max_cb * 128 / kSliceRows)), kSliceThreads, 0, s>>>(
+        bv, geom, c_off, h, bases, k0, A, aux, bslices, fb);
     MW_LAUNCH_CHECK();
   }
   {
