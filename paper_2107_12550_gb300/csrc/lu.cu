@@ -446,18 +446,55 @@ k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0
 // 16 x 16 threads, micro-tile TM x TN per thread, K chunks of KT staged in
 // shared memory with coalesced loads of each word plane.
 // ---------------------------------------------------------------------------
+// 8-byte asynchronous copy global -> shared; ok == false fills zeros (no read)
+__device__ __forceinline__ void cp_async8(void* smem_dst, const double* gsrc, bool ok) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(gsrc), "r"(ok ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// K chunks of KT staged in shared memory, double-buffered: the copies of
+// chunk t+1 (cp.async, zero-filled outside the matrix) run while chunk t is
+// consumed.  Each entry of C still receives its updates in ascending t.
 template <int W, int TM, int TN>
 __device__ __forceinline__ void gemm_plain_tile(double* __restrict__ C, int64_t ldc, int64_t planeC,
                                                 const double* __restrict__ L, int64_t ldl, int64_t planeL,
                                                 const double* __restrict__ U, int64_t ldu, int64_t planeU,
                                                 int64_t m, int64_t N, int K, int64_t tile_i, int64_t tile_j) {
-  constexpr int KT = 16;
+  constexpr int KT = 8;
   constexpr int BM = 16 * TM, BN = 16 * TN;
-  __shared__ double sL[W][KT][BM];
-  __shared__ double sU[W][KT][BN];
+  __shared__ double sL[2][W][KT][BM];
+  __shared__ double sU[2][W][KT][BN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t bi = tile_i * BM, bj = tile_j * BN;
 
+  auto stage = [&](int buf, int t0) {
+    const int kt_n = (K - t0 < KT) ? K - t0 : KT;
+    // L tile: rows bi..bi+BM, columns t0..: consecutive threads -> rows
+    for (int e = threadIdx.x; e < BM * KT; e += 256) {
+      const int r = e % BM, kt = e / BM;
+      const int64_t i = bi + r;
+      const bool ok = (i < m) && (kt < kt_n);
+#pragma unroll
+      for (int c = 0; c < W; ++c) cp_async8(&sL[buf][c][kt][r], ok ? L + c * planeL + (t0 + kt) * ldl + i : L, ok);
+    }
+    // U tile: rows t0.., columns bj..: consecutive threads -> rows (t)
+    for (int e = threadIdx.x; e < BN * KT; e += 256) {
+      const int kt = e % KT, cidx = e / KT;
+      const int64_t jj = bj + cidx;
+      const bool ok = (jj < N) && (kt < kt_n);
+#pragma unroll
+      for (int c = 0; c < W; ++c) cp_async8(&sU[buf][c][kt][cidx], ok ? U + c * planeU + jj * ldu + t0 + kt : U, ok);
+    }
+    cp_async_commit();
+  };
+
+  stage(0, 0);
   val<W> acc[TM][TN];
 #pragma unroll
   for (int a = 0; a < TM; ++a)
@@ -471,41 +508,32 @@ __device__ __forceinline__ void gemm_plain_tile(double* __restrict__ C, int64_t 
       }
     }
 
-  for (int t0 = 0; t0 < K; t0 += KT) {
-    const int kt_n = (K - t0 < KT) ? K - t0 : KT;
-    // L tile: rows bi..bi+BM, columns t0..: consecutive threads -> rows
-    for (int e = threadIdx.x; e < BM * KT; e += 256) {
-      const int r = e % BM, kt = e / BM;
-      const int64_t i = bi + r;
-      const bool ok = (i < m) && (kt < kt_n);
-#pragma unroll
-      for (int c = 0; c < W; ++c) sL[c][kt][r] = ok ? __ldg(L + c * planeL + (t0 + kt) * ldl + i) : 0.0;
-    }
-    // U tile: rows t0.., columns bj..: consecutive threads -> rows (t)
-    for (int e = threadIdx.x; e < BN * KT; e += 256) {
-      const int kt = e % KT, cidx = e / KT;
-      const int64_t jj = bj + cidx;
-      const bool ok = (jj < N) && (kt < kt_n);
-#pragma unroll
-      for (int c = 0; c < W; ++c) sU[c][kt][cidx] = ok ? __ldg(U + c * planeU + jj * ldu + t0 + kt) : 0.0;
+  int buf = 0;
+  for (int t0 = 0; t0 < K; t0 += KT, buf ^= 1) {
+    if (t0 + KT < K) {
+      stage(buf ^ 1, t0 + KT);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const int kt_n = (K - t0 < KT) ? K - t0 : KT;
     for (int kt = 0; kt < kt_n; ++kt) {
       val<W> l[TM], u[TN];
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int c = 0; c < W; ++c) l[a].v[c] = sL[c][kt][tx + 16 * a];
+        for (int c = 0; c < W; ++c) l[a].v[c] = sL[buf][c][kt][tx + 16 * a];
 #pragma unroll
       for (int b = 0; b < TN; ++b)
 #pragma unroll
-        for (int c = 0; c < W; ++c) u[b].v[c] = sU[c][kt][ty + 16 * b];
+        for (int c = 0; c < W; ++c) u[b].v[c] = sU[buf][c][kt][ty + 16 * b];
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int b = 0; b < TN; ++b) acc[a][b] = msub<W>(acc[a][b], l[a], u[b]);
     }
-    __syncthreads();
+    __syncthreads();   // every thread is done with `buf` before it is refilled
   }
 #pragma unroll
   for (int a = 0; a < TM; ++a)
