@@ -279,8 +279,8 @@ def extras(A, b, n, steps, peak_fp64):
         if r0 >= n3:
             break
         m_t = -(-(n3 - r0) // 128)
-        n_t = -(-(n3 - r0) // 32)
-        mma_flops += m_t * n_t * 120 * 2 * 128 * 32 * 64
+        n_t = -(-(n3 - r0) // 16)
+        mma_flops += m_t * n_t * 120 * 2 * 128 * 16 * 64
     split_gemm_ms = lu["split"]["phase_ms"].get("gemm_split", 0.0)
     out["lu_dd_n4096"] = {
         "plain_dd_gops": lu["plain"]["dd_gops"], "split_dd_gops": lu["split"]["dd_gops"],

@@ -795,9 +795,9 @@ struct BlockedPlanHost {
   int update = MW_UPDATE_PLAIN;
   int nsteps = 0;
   std::vector<int> act, max_cb_trsm, max_cols;
-  GeomPlanHost trail;   // plain: BM x BN tiles; split: 128 x 32 tiles of A22
-  GeomPlanHost tinv;    // split: 128 x 32 tiles of U12^T (the TRSM as a product with L11^-1)
-  GeomPlanHost pinner[3];  // split: 128 x 32 tiles of the inner panel updates (kInner order)
+  GeomPlanHost trail;   // plain: BM x BN tiles; split: 128 x 16 tiles of A22
+  GeomPlanHost tinv;    // split: 128 x 16 tiles of U12^T (the TRSM as a product with L11^-1)
+  GeomPlanHost pinner[3];  // split: 128 x 16 tiles of the inner panel updates (kInner order)
 };
 
 // the inner updates of the recursive split panel: (column offset, half width)

@@ -118,12 +118,12 @@ int launch_bgemm_plain(const BatchView& bv, const TileEntry* tiles, int64_t ntil
 void gemm_plain_tile_shape(int W, int* bm, int* bn);
 
 // split update of the batch (ozaki.cu): per active system with trailing
-// order m = n - k0 - 64 > 0, C -= L21 U12 on the 128 x 32 tiles listed in
+// order m = n - k0 - 64 > 0, C -= L21 U12 on the 128 x 16 tiles listed in
 // `tiles`; `bases[pos]` = {first A-slice tile, first B-slice tile} of that
 // system in the slice area; the slicing grids are act x max_mt (128-row
 // tiles) and act x max_cb (128-column blocks).
 constexpr int kSplitTileM = 128;
-constexpr int kSplitTileN = 32;
+constexpr int kSplitTileN = 16;
 // Operand geometries (ozaki.cu): the trailing update, and the TRSM as a
 // product with the explicit inverse of L11 (aux: per active position, the
 // strictly lower part of -(L11^-1), 2 words x 64 x 64, column-major).

@@ -14,9 +14,9 @@
 //     (exact: 8 significant bits).  Slices are stored per 128-row (L21) or
 //     32-column (U12) tile in the 128-byte-swizzled K-major layout the MMA
 //     reads, K = nb = 64.
-//  3. Products.  For every pair (p, q) with p + q <= 16 one 128 x 32 x 64 MMA
+//  3. Products.  For every pair (p, q) with p + q <= 16 one 128 x 16 x 64 MMA
 //     accumulates A_p B_q^T into the FP32 accumulator of diagonal d = p + q
-//     (15 accumulators x 32 columns = 480 TMEM columns).  A diagonal gathers
+//     (15 accumulators x 16 columns = 240 TMEM columns).  A diagonal gathers
 //     at most 8 pairs x 64 products of magnitude <= 2^14, so every partial
 //     sum is an integer below 2^23 and the FP32 accumulation is exact.
 //  4. Recombination.  Per output entry the 15 exact diagonal sums D_d are
@@ -49,10 +49,10 @@ constexpr int kS = 15;                 // digits per operand
 constexpr int kDiag = 15;              // diagonals d = 2..16
 constexpr int kK = 64;                 // panel width (K of the update)
 constexpr int kTileM = 128;            // rows per MMA tile
-constexpr int kTileN = 32;             // columns per MMA tile
+constexpr int kTileN = 16;             // columns per MMA tile
 constexpr int kASliceBytes = kTileM * kK * 2;   // 16 KB
-constexpr int kBSliceBytes = kTileN * kK * 2;   // 4 KB
-constexpr uint32_t kTmemCols = 512;
+constexpr int kBSliceBytes = kTileN * kK * 2;   // 2 KB
+constexpr uint32_t kTmemCols = 256;            // 15 x 16 = 240 used; two CTAs per SM
 static_assert(kTileM == kSplitTileM && kTileN == kSplitTileN && kK == kBatchNb, "batched split tile shape");
 
 // byte offset of element (row r, k) inside a K-major 128B-swizzled tile
@@ -123,7 +123,7 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
 
 // ---------------------------------------------------------------------------
 // slicing: row operand -> A slices [tile][p][128 x 64] with row exponents
-// e_i; column operand -> B slices [tile][q][32 x 64] (column j is a K-major
+// e_i; column operand -> B slices [tile][q][16 x 64] (column j is a K-major
 // row) with column exponents f_j.  One CTA of 128 threads takes 16 rows (or
 // columns) x 8 chunks of 8 k: each thread reads its 8 entries, the 8
 // threads of a row combine their maxima in shared memory, and each thread
@@ -467,10 +467,10 @@ __device__ __forceinline__ double i192_take_rn(I192& R, int scale) {
 }
 
 // ---------------------------------------------------------------------------
-// the tensor-core kernel: one CTA per 128 x 32 output tile
+// the tensor-core kernel: one CTA per 128 x 16 output tile, two CTAs per SM
 // warp 0: bulk-copy producer; warp 1: TMEM owner + MMA issuer;
-// warps 2..17: epilogue (TMEM lane quarter = warp % 4; warps 2..5 take
-// columns 0..7 of the tile, warps 6..9 columns 8..15, and so on)
+// warps 2..9: epilogue (TMEM lane quarter = warp % 4; warps 2..5 take
+// columns 0..7 of the tile, warps 6..9 columns 8..15)
 // ---------------------------------------------------------------------------
 struct SplitSmem {
   unsigned char b[kS][kBSliceBytes];       // all B slices of the tile (60 KB)
@@ -483,7 +483,7 @@ struct SplitSmem {
   int abort;
 };
 
-constexpr int kEpiWarps = 16;                      // four warpgroups over the 4 TMEM lane quarters
+constexpr int kEpiWarps = 8;                       // two warpgroups over the 4 TMEM lane quarters
 constexpr int kSplitThreads = 64 + 32 * kEpiWarps;  // producer + MMA warps + epilogue
 
 // entry (i, j) of C at C[i * crs + j * cjs]
@@ -640,7 +640,7 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
   }
 }
 
-__global__ void __launch_bounds__(kSplitThreads, 1)
+__global__ void __launch_bounds__(kSplitThreads, 2)
 k_split_gemm(SplitOperands o, const unsigned char* __restrict__ aslices, const unsigned char* __restrict__ bslices,
              const int* __restrict__ ea, const int* __restrict__ fb, DeviceStatus* status) {
   split_tile(o.C, o.crs, o.cjs, o.planeC, o.m, o.N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y);
@@ -751,7 +751,7 @@ k_bslice_cols(BatchView bv, int geom, int c_off, int h, const int2* __restrict__
                fb + (int64_t)bbase * kTileN, jbase);
 }
 
-__global__ void __launch_bounds__(kSplitThreads, 1)
+__global__ void __launch_bounds__(kSplitThreads, 2)
 k_bsplit_gemm(BatchView bv, int geom, int c_off, int h, const TileEntry* __restrict__ tiles,
               const int2* __restrict__ bases, int k0, double* __restrict__ A, const double* __restrict__ aux,
               const unsigned char* __restrict__ aslices, const unsigned char* __restrict__ bslices,
@@ -859,7 +859,8 @@ k_inv_l11_cols(const double* __restrict__ A, int64_t lda, int64_t plane, int k0,
 }
 
 size_t split_smem_bytes() {
-  return (sizeof(SplitSmem) + 1024 > 120 * 1024) ? sizeof(SplitSmem) + 1024 : 120 * 1024;
+  // at least 100 KB: never more than two CTAs (2 x 256 TMEM columns) on one SM
+  return (sizeof(SplitSmem) + 1024 > 100 * 1024) ? sizeof(SplitSmem) + 1024 : 100 * 1024;
 }
 
 }  // namespace
@@ -915,8 +916,6 @@ int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phas
   }
   {
     ProfScope ps(phase, s);
-    // more than half of the SM's shared memory: one CTA per SM, which owns
-    // all 512 TMEM columns
     const size_t shmem = split_smem_bytes();
     static bool attr_set = false;
     if (!attr_set) {
