@@ -199,17 +199,25 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 // ---------------------------------------------------------------------------
 // substitution of one system per CTA (x may alias b): y = P b, then
 // y_i -= l_ij y_j (j ascending), d_j = 1 / u_jj for all j, then
-// x_j = y_j d_j and y_i -= u_ij x_j (j descending) -- blocked by 32 columns:
-// warp 0 solves the 32 x 32 triangle of a block with the rows in its lanes,
-// then all threads apply the block to the remaining rows, two rows per
-// thread, with each row's updates still in the order above.  One CTA of 512
-// threads per SM takes the systems largest first.
+// x_j = y_j d_j and y_i -= u_ij x_j (j descending), blocked by 32 rows, as a
+// pipeline between warps that synchronise through shared-memory flags:
+//  * the leader (warp 0) takes block b: it applies block b-1 (forward; b+1
+//    backward) to block b's rows, with the rows in its lanes, once the
+//    workers have applied every earlier block to them, then solves block
+//    b's 32 x 32 triangle and publishes it;
+//  * the 15 worker warps apply each published block to the rows two or
+//    more blocks further on; each worker thread always owns the same rows.
+// So every y_i still receives its updates in the order above, while the
+// triangles overlap the workers' updates.  Each wait is bounded; a wait that
+// runs out records an error word and makes all warps leave the system.
 // Systems whose state is not "running" are skipped when st is given.
 // dynamic shared memory: 2 * W * nmax doubles
 // ---------------------------------------------------------------------------
 constexpr int kSolveBs = 32;
-constexpr int kSolveThreads = 512;                      // one CTA per SM: the largest systems get a whole SM
-constexpr int kSolveRpt = kBatchMaxN / kSolveThreads;   // rows per thread in a block update
+constexpr int kSolveThreads = 512;                               // one CTA per SM
+constexpr int kSolveWorkers = kSolveThreads / 32 - 1;            // worker warps
+constexpr int kSolveWRows = (kBatchMaxN + 32 * kSolveWorkers - 1) / (32 * kSolveWorkers);  // rows per worker thread
+constexpr unsigned long long kSolveSpin = 1ull << 24;
 
 template <int W>
 __device__ __forceinline__ val<W> smem_val(const double* v, int nmax, int i) {
@@ -225,6 +233,23 @@ __device__ __forceinline__ void smem_put(double* v, int nmax, int i, const val<W
   for (int c = 0; c < W; ++c) v[c * nmax + i] = r.v[c];
 }
 
+// bounded wait until pred() holds or the system is being abandoned
+template <typename P>
+__device__ __forceinline__ bool solve_wait(P pred, volatile int* abort_flag, BatchCursor* cur) {
+  unsigned long long spins = 0;
+  while (!pred()) {
+    if (*abort_flag) return false;
+    if (++spins > kSolveSpin) {
+      *abort_flag = 1;
+      atomicExch(&cur->pad[0], 1u);   // error word: a solve wait ran out
+      return false;
+    }
+    __nanosleep(32);
+  }
+  __threadfence_block();
+  return true;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kSolveThreads, 1)
 k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
@@ -234,13 +259,21 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
   extern __shared__ double bsm[];
   double* ysm = bsm;
   double* dsm = bsm + W * nmax;
+  __shared__ int far_done[kBatchMaxN / kSolveBs + 2];
+  __shared__ int tri_done;
+  __shared__ int s_abort;
+  volatile int* vfar = far_done;
+  volatile int* vtri = &tri_done;
+  volatile int* vab = &s_abort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wt = tid - 32;                     // worker thread index (warp >= 1)
   for (;;) {
     const int pos = next_system(cur, count);
     if (pos < 0) break;
     const int s = order[pos];
     if (st && st[s].done) continue;
     const int n = nn[s];
+    const int nb = (n + kSolveBs - 1) / kSolveBs;
     const double* a = LU + (int64_t)W * moff[s];
     const int64_t plane = (int64_t)n * n;
     const int64_t* pv = piv + voff[s];
@@ -257,6 +290,11 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
       one.v[0] = 1.0;
       smem_put<W>(dsm, nmax, j, div<W>(one, load_ro<W>(a, plane, (int64_t)j * n + j)));
     }
+    for (int q = tid; q < nb + 2; q += kSolveThreads) far_done[q] = 0;
+    if (tid == 0) {
+      tri_done = -1;
+      s_abort = 0;
+    }
     __syncthreads();
     if (tid == 0) {
       for (int k = 0; k < n; ++k) {
@@ -272,15 +310,23 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
     }
     __syncthreads();
     // ---- forward: unit lower L ----
-    for (int j0 = 0; j0 < n; j0 += kSolveBs) {
-      const int bsz = min(kSolveBs, n - j0);
-      if (warp == 0) {
+    if (warp == 0) {
+      for (int bk = 0; bk < nb; ++bk) {
+        const int j0 = bk * kSolveBs;
+        const int bsz = min(kSolveBs, n - j0);
+        if (bk >= 2 && !solve_wait([&] { return vfar[bk - 2] >= kSolveWorkers; }, vab, cur)) break;
         const int i = j0 + lane;
         val<W> yi;
         if (lane < bsz) yi = smem_val<W>(ysm, nmax, i);
         else {
 #pragma unroll
           for (int c = 0; c < W; ++c) yi.v[c] = 0.0;
+        }
+        if (bk >= 1 && lane < bsz) {
+          const int jp = j0 - kSolveBs;
+#pragma unroll 4
+          for (int jj = 0; jj < kSolveBs; ++jj)
+            yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(jp + jj) * n + i), smem_val<W>(ysm, nmax, jp + jj));
         }
         for (int jj = 0; jj < bsz - 1; ++jj) {
           val<W> yj;
@@ -289,83 +335,95 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           if (lane > jj && lane < bsz) yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), yj);
         }
         if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) *vtri = bk;
       }
-      __syncthreads();
-      const int r0 = j0 + bsz;
-      if (r0 < n) {
-        val<W> yr[kSolveRpt];
+    } else {
+      for (int bk = 0; bk < nb; ++bk) {
+        if (!solve_wait([&] { return *vtri >= bk; }, vab, cur)) break;
+        const int j0 = bk * kSolveBs;
+        const int bsz = min(kSolveBs, n - j0);
+        const int r0 = j0 + 2 * kSolveBs;
 #pragma unroll
-        for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = r0 + tid + q * kSolveThreads;
-          if (i < n) yr[q] = smem_val<W>(ysm, nmax, i);
-        }
+        for (int q = 0; q < kSolveWRows; ++q) {
+          const int i = wt + q * 32 * kSolveWorkers;
+          if (i >= r0 && i < n) {
+            val<W> yi = smem_val<W>(ysm, nmax, i);
 #pragma unroll 4
-        for (int jj = 0; jj < bsz; ++jj) {
-          const val<W> yj = smem_val<W>(ysm, nmax, j0 + jj);
-          const int64_t col = (int64_t)(j0 + jj) * n;
-#pragma unroll
-          for (int q = 0; q < kSolveRpt; ++q) {
-            const int i = r0 + tid + q * kSolveThreads;
-            if (i < n) yr[q] = msub<W>(yr[q], load_ro<W>(a, plane, col + i), yj);
+            for (int jj = 0; jj < bsz; ++jj)
+              yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), smem_val<W>(ysm, nmax, j0 + jj));
+            smem_put<W>(ysm, nmax, i, yi);
           }
         }
-#pragma unroll
-        for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = r0 + tid + q * kSolveThreads;
-          if (i < n) smem_put<W>(ysm, nmax, i, yr[q]);
-        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) atomicAdd(&far_done[bk], 1);
       }
-      __syncthreads();
     }
+    __syncthreads();
+    for (int q = tid; q < nb + 2; q += kSolveThreads) far_done[q] = 0;
+    if (tid == 0) tri_done = nb;
+    __syncthreads();
     // ---- backward: upper U with the reciprocals ----
-    for (int j1 = n; j1 > 0; j1 -= kSolveBs) {
-      const int bsz = min(kSolveBs, j1);
-      const int jb = j1 - bsz;              // block rows/columns [jb, j1)
+    if (!*vab) {
       if (warp == 0) {
-        const int i = jb + lane;
-        val<W> yi, di;
-        if (lane < bsz) {
-          yi = smem_val<W>(ysm, nmax, i);
-          di = smem_val<W>(dsm, nmax, i);
-        } else {
+        for (int bk = nb - 1; bk >= 0; --bk) {
+          const int j0 = bk * kSolveBs;
+          const int bsz = min(kSolveBs, n - j0);
+          if (bk <= nb - 3 && !solve_wait([&] { return vfar[bk + 2] >= kSolveWorkers; }, vab, cur)) break;
+          const int i = j0 + lane;
+          val<W> yi, di;
+          if (lane < bsz) {
+            yi = smem_val<W>(ysm, nmax, i);
+            di = smem_val<W>(dsm, nmax, i);
+          } else {
 #pragma unroll
-          for (int c = 0; c < W; ++c) yi.v[c] = di.v[c] = 0.0;
-        }
-        for (int jj = bsz - 1; jj >= 0; --jj) {
-          if (lane == jj) yi = mul<W>(yi, di);          // x_j = y_j d_j
-          val<W> xj;
-#pragma unroll
-          for (int c = 0; c < W; ++c) xj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
-          if (lane < jj) yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(jb + jj) * n + i), xj);
-        }
-        if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
-      }
-      __syncthreads();
-      if (jb > 0) {
-        val<W> yr[kSolveRpt];
-#pragma unroll
-        for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = tid + q * kSolveThreads;
-          if (i < jb) yr[q] = smem_val<W>(ysm, nmax, i);
-        }
-#pragma unroll 4
-        for (int jj = bsz - 1; jj >= 0; --jj) {
-          const val<W> xj = smem_val<W>(ysm, nmax, jb + jj);
-          const int64_t col = (int64_t)(jb + jj) * n;
-#pragma unroll
-          for (int q = 0; q < kSolveRpt; ++q) {
-            const int i = tid + q * kSolveThreads;
-            if (i < jb) yr[q] = msub<W>(yr[q], load_ro<W>(a, plane, col + i), xj);
+            for (int c = 0; c < W; ++c) yi.v[c] = di.v[c] = 0.0;
           }
-        }
+          if (bk <= nb - 2 && lane < bsz) {
+            const int jn = j0 + kSolveBs;
+            const int bszn = min(kSolveBs, n - jn);
+#pragma unroll 4
+            for (int jj = bszn - 1; jj >= 0; --jj)
+              yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(jn + jj) * n + i), smem_val<W>(ysm, nmax, jn + jj));
+          }
+          for (int jj = bsz - 1; jj >= 0; --jj) {
+            if (lane == jj) yi = mul<W>(yi, di);          // x_j = y_j d_j
+            val<W> xj;
 #pragma unroll
-        for (int q = 0; q < kSolveRpt; ++q) {
-          const int i = tid + q * kSolveThreads;
-          if (i < jb) smem_put<W>(ysm, nmax, i, yr[q]);
+            for (int c = 0; c < W; ++c) xj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
+            if (lane < jj) yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), xj);
+          }
+          if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
+          __threadfence_block();
+          __syncwarp();
+          if (lane == 0) *vtri = bk;
+        }
+      } else {
+        for (int bk = nb - 1; bk >= 0; --bk) {
+          if (!solve_wait([&] { return *vtri <= bk; }, vab, cur)) break;
+          const int j0 = bk * kSolveBs;
+          const int bsz = min(kSolveBs, n - j0);
+          const int rend = j0 - kSolveBs;          // rows [0, rend): blocks <= bk - 2
+#pragma unroll
+          for (int q = 0; q < kSolveWRows; ++q) {
+            const int i = wt + q * 32 * kSolveWorkers;
+            if (i < rend) {
+              val<W> yi = smem_val<W>(ysm, nmax, i);
+#pragma unroll 4
+              for (int jj = bsz - 1; jj >= 0; --jj)
+                yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), smem_val<W>(ysm, nmax, j0 + jj));
+              smem_put<W>(ysm, nmax, i, yi);
+            }
+          }
+          __threadfence_block();
+          __syncwarp();
+          if (lane == 0) atomicAdd(&far_done[bk], 1);
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
     for (int i = tid; i < n; i += kSolveThreads)
 #pragma unroll
       for (int c = 0; c < W; ++c) xs[c * n + i] = ysm[c * nmax + i];
