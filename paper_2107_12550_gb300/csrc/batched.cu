@@ -652,7 +652,7 @@ static int sm_count_b() {
 
 template <typename K>
 static int set_smem(K kern, size_t bytes) {
-  if (bytes > 48 * 1024) MW_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  MW_CUDA_CHECK(ensure_smem_limit(kern, bytes));
   return MW_OK;
 }
 

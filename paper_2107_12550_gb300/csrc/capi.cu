@@ -1,6 +1,8 @@
 // capi.cu -- the extern "C" entry points of libmwlu.so (declared and
 // documented in include/mwlu.h): argument checks, work-buffer sizes,
 // dispatch on the precision, status text and the FP64 microbenchmark.
+#include <mutex>
+#include <vector>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -8,6 +10,34 @@
 #include "mw_arith.cuh"
 #include "mw_common.cuh"
 #include "lu_internal.cuh"
+
+namespace mw {
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  struct Entry {
+    const void* k;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& d : done)
+    if (d.k == kernel && d.dev == dev && d.bytes >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  for (auto& d : done)
+    if (d.k == kernel && d.dev == dev) {
+      d.bytes = bytes;
+      return cudaSuccess;
+    }
+  done.push_back(Entry{kernel, dev, bytes});
+  return cudaSuccess;
+}
+}  // namespace mw
 
 namespace mw {
 size_t refine_workspace_bytes(int inner, int update, int64_t n);

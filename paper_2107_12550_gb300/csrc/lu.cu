@@ -809,7 +809,7 @@ int launch_panel(double* A, int64_t lda, int64_t plane, int64_t n, int64_t k0, i
   const size_t shmem = res ? shmem_res : sizeof(double) * (size_t)W * ((size_t)nb + (size_t)chunk);
   auto kern = res ? k_panel<W, true> : k_panel<W, false>;
   if (shmem > 48 * 1024) {
-    MW_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    MW_CUDA_CHECK(ensure_smem_limit(kern, shmem));
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);
@@ -968,7 +968,7 @@ int launch_bpanel(const BatchView& bv, int act, int nmax, int k0, int c_off, int
   if (width < 1 || width > kBatchNb) return MW_EUNSUPPORTED;
   const size_t shmem = sizeof(double) * (size_t)W * ((size_t)kBatchNb + (size_t)nmax);
   if (shmem > 48 * 1024)
-    MW_CUDA_CHECK(cudaFuncSetAttribute(k_bpanel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    MW_CUDA_CHECK(ensure_smem_limit(k_bpanel<W>, shmem));
   ProfScope ps(kPhPanel, s);
   k_bpanel<W><<<act, kPanelThreads, shmem, s>>>(bv, nmax, k0 + c_off, width, A, piv, info);
   MW_LAUNCH_CHECK();

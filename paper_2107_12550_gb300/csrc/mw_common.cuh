@@ -84,6 +84,16 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DeviceStatus* status
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? MW_OK : MW_ECUDA; }
 
+// Raises a kernel's dynamic shared memory limit to at least `bytes` on the
+// current device, once per (kernel, device) and size: the attribute belongs
+// to the device's context, so every GPU a process uses needs its own call.
+// Safe for concurrent callers.  Returns a cudaError_t.
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes);
+template <typename K>
+inline cudaError_t ensure_smem_limit(K* kernel, size_t bytes) {
+  return ensure_smem_limit(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 }  // namespace mw
 
 // record the last CUDA error of the library for mw_last_cuda_error()

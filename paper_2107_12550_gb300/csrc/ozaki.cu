@@ -255,31 +255,6 @@ struct I192 {
   unsigned long long w0, w1, w2;
 };
 
-// R += D * 2^pos, |D| < 2^24, 0 <= pos <= 112
-__device__ __forceinline__ void i192_add_shifted(I192& R, int D, int pos) {
-  const __int128 v = (__int128)D << (pos & 63);          // |v| < 2^87
-  const unsigned __int128 uv = (unsigned __int128)v;
-  const unsigned long long vlo = (unsigned long long)uv;
-  const unsigned long long vhi = (unsigned long long)(uv >> 64);
-  const unsigned long long sext = (v < 0) ? ~0ull : 0ull;
-  if (pos < 64) {
-    const unsigned long long s0 = R.w0 + vlo;
-    const unsigned long long c0 = s0 < R.w0;
-    const unsigned long long t1 = R.w1 + vhi;
-    const unsigned long long c1a = t1 < R.w1;
-    const unsigned long long s1 = t1 + c0;
-    const unsigned long long c1b = s1 < t1;
-    R.w0 = s0;
-    R.w1 = s1;
-    R.w2 = R.w2 + sext + c1a + c1b;
-  } else {
-    const unsigned long long s1 = R.w1 + vlo;
-    const unsigned long long c1 = s1 < R.w1;
-    R.w1 = s1;
-    R.w2 = R.w2 + vhi + c1;
-  }
-}
-
 __device__ __forceinline__ int i192_bit(const I192& R, int b) {
   const unsigned long long w = (b < 64) ? R.w0 : (b < 128 ? R.w1 : R.w2);
   return (int)((w >> (b & 63)) & 1ull);
@@ -917,11 +892,7 @@ int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phas
   {
     ProfScope ps(phase, s);
     const size_t shmem = split_smem_bytes();
-    static bool attr_set = false;
-    if (!attr_set) {
-      MW_CUDA_CHECK(cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
-      attr_set = true;
-    }
+    MW_CUDA_CHECK(ensure_smem_limit(k_split_gemm, shmem));
     dim3 grid((unsigned)mt, (unsigned)nt);
     k_split_gemm<<<grid, kSplitThreads, shmem, s>>>(o, aslices, bslices, ea, fb, status);
     MW_LAUNCH_CHECK();
@@ -954,11 +925,7 @@ int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t plan
 
 int split_inv_l11(const double* A, int64_t lda, int64_t plane, int64_t k0, double* aux, cudaStream_t s) {
   const size_t shmem = sizeof(double) * 2 * kK * kK;
-  static bool attr_set = false;
-  if (!attr_set) {
-    MW_CUDA_CHECK(cudaFuncSetAttribute(k_inv_l11_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
-    attr_set = true;
-  }
+  MW_CUDA_CHECK(ensure_smem_limit(k_inv_l11_cols, shmem));
   ProfScope ps(kPhTrsm, s);
   k_inv_l11_cols<<<kK, kK, shmem, s>>>(A, lda, plane, (int)k0, aux);
   MW_LAUNCH_CHECK();
@@ -998,11 +965,7 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
   {
     ProfScope ps(geom == kGeomTrsmInv ? kPhTrsm : (geom == kGeomPanelInner ? kPhPanel : kPhGemmSplit), s);
     const size_t shmem = split_smem_bytes();
-    static bool attr_set = false;
-    if (!attr_set) {
-      MW_CUDA_CHECK(cudaFuncSetAttribute(k_bsplit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
-      attr_set = true;
-    }
+    MW_CUDA_CHECK(ensure_smem_limit(k_bsplit_gemm, shmem));
     k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, geom, c_off, h, tiles, bases, k0, A, aux,
                                                                 aslices, bslices, ea, fb, status);
     MW_LAUNCH_CHECK();
@@ -1013,11 +976,7 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
 int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s) {
   if (act <= 0) return MW_OK;
   const size_t shmem = sizeof(double) * 2 * kK * kK;
-  static bool attr_set = false;
-  if (!attr_set) {
-    MW_CUDA_CHECK(cudaFuncSetAttribute(k_binv_l11, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
-    attr_set = true;
-  }
+  MW_CUDA_CHECK(ensure_smem_limit(k_binv_l11, shmem));
   ProfScope ps(kPhTrsm, s);
   k_binv_l11<<<(unsigned)act, 256, shmem, s>>>(bv, k0, A, aux);
   MW_LAUNCH_CHECK();

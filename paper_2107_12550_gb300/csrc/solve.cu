@@ -259,7 +259,7 @@ int perm_launch(int64_t n, const int64_t* piv, int* perm, cudaStream_t s) {
   ProfScope ps(kPhPerm, s);
   const size_t shmem = (n <= kPermSmemMax) ? 8 * (size_t)n : 0;
   if (shmem > 48 * 1024) {
-    MW_CUDA_CHECK(cudaFuncSetAttribute(k_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    MW_CUDA_CHECK(ensure_smem_limit(k_perm, shmem));
   }
   k_perm<<<1, 1024, shmem, s>>>(n, piv, perm);
   MW_LAUNCH_CHECK();

@@ -228,3 +228,27 @@ def test_batched_lu_and_solve_in_a_cuda_graph():
                 assert torch.equal(LU, LU_ref) and torch.equal(x, x_ref), upd
     finally:
         api().batch_plan_cache(prev)
+
+
+def test_mixed_batch_refine_full_range_exact():
+    """The mixed-precision batched refinement at the workload's full ranges:
+    the n and kappa of every 11th member of the 512-system workload plus
+    its largest and most ill-conditioned ones (n up to 1024, kappa up to
+    1e20), each system built with its own seed: split DD inner LU, every
+    system converges and every entry of every x equals x* = 1 to 2^-200
+    (exact check)."""
+    n_all, k_all = W.mixed_batch_spec(512, 64, 1024, 4.0, 20.0, seed=0)
+    pick = sorted(set(list(range(0, 512, 11)) + [int(np.argmax(n_all)), int(np.argmax(k_all))]))
+    n_list = [n_all[s] for s in pick]
+    kap = [k_all[s] for s in pick]
+    A_np, b_np = W.svd_batch(n_list, kap, seed=0, processes=4)
+    x, stats = api().refine_batched_blocked(dev(A_np), 4, dev(b_np), 8, n_list, 2, "split", 200)
+    st = host(stats)
+    assert (st[:, 3] == 0).all(), st[st[:, 3] != 0]
+    xs = api().unpack_vectors(host(x), n_list, 8)
+    lim = Fraction(1, 2 ** 200)
+    for s, n in enumerate(n_list):
+        X = xs[s]
+        for i in range(n):
+            v = sum((Fraction(float(c)) for c in X[:, i]), Fraction(0))
+            assert abs(v - 1) <= lim, (s, n, i)
