@@ -255,34 +255,6 @@ struct I192 {
   unsigned long long w0, w1, w2;
 };
 
-__device__ __forceinline__ int i192_bit(const I192& R, int b) {
-  const unsigned long long w = (b < 64) ? R.w0 : (b < 128 ? R.w1 : R.w2);
-  return (int)((w >> (b & 63)) & 1ull);
-}
-
-// bits [lo, lo+53) of a non-negative R (lo >= 0)
-__device__ __forceinline__ unsigned long long i192_bits53(const I192& R, int lo) {
-  unsigned __int128 x;
-  if (lo < 64) {
-    x = ((unsigned __int128)R.w1 << 64) | R.w0;
-    x >>= lo;
-    if (lo > 0) x |= (unsigned __int128)R.w2 << (128 - lo);
-  } else if (lo < 128) {
-    x = ((unsigned __int128)R.w2 << 64) | R.w1;
-    x >>= (lo - 64);
-  } else {
-    x = (unsigned __int128)(R.w2 >> (lo - 128));
-  }
-  return (unsigned long long)x & ((1ull << 53) - 1);
-}
-
-__device__ __forceinline__ bool i192_any_below(const I192& R, int b) {  // any bit < b set
-  if (b <= 0) return false;
-  if (b >= 128) return R.w0 || R.w1 || (b > 128 && (R.w2 & ((1ull << (b - 128)) - 1)));
-  if (b >= 64) return R.w0 || (b > 64 && (R.w1 & ((1ull << (b - 64)) - 1)));
-  return (R.w0 & ((1ull << b) - 1)) != 0;
-}
-
 __device__ __forceinline__ int i192_top(const I192& R) {  // index of highest set bit, -1 if 0
   if (R.w2) return 128 + 63 - __clzll((long long)R.w2);
   if (R.w1) return 64 + 63 - __clzll((long long)R.w1);
@@ -364,16 +336,70 @@ __device__ __forceinline__ I192 recombine15(const uint32_t (&v)[15][CW], int cc)
   return R;
 }
 
-// q * 2^e as a double (q <= 2^53 integer): the IEEE fields assembled from
-// the bits (exact: q has at most 53 significant bits); the FP64 route only
-// for results outside the normal range
-__device__ __forceinline__ double make_double(unsigned long long q, int e) {
-  if (q == 0) return 0.0;
-  const int sh = __clzll((long long)q) - 11;   // moves the top bit of q to bit 52
-  const unsigned long long m = (sh >= 0) ? (q << sh) : (q >> (-sh));   // q = 2^53: exact shift
-  const int biased = e - sh + 52 + 1023;
-  if (biased <= 0 || biased >= 2047) return scale2_exact(__ull2double_rn(q), e);
-  return __longlong_as_double((long long)(((unsigned long long)biased << 52) | (m & ((1ull << 52) - 1))));
+// x * 2^k for an integer-valued double x: the exponent field moved when the
+// result stays normal, the FP64 route otherwise
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  if (x == 0.0) return x;
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex + k >= 1 && ex + k <= 2046) return __longlong_as_double(bits + ((long long)k << 52));
+  return scale2_exact(x, k);
+}
+
+// RN of a non-negative M (top = index of its highest set bit) as double d
+// with M ~ d * 2^shift: the 64 bits below and including the top bit, with
+// the OR of every lower bit folded into bit 0, round to the same 53 bits as
+// M itself (the rounding position is bit 10 of the window), so the
+// hardware's RN conversion of that window is RN(M)
+__device__ __forceinline__ double i192_window_rn(const I192& M, int top, int& shift) {
+  if (top < 64) {
+    shift = 0;
+    return __ull2double_rn(M.w0);
+  }
+  const int sh = top - 63;   // 1 .. 128
+  unsigned long long w, sticky;
+  if (sh < 64) {
+    w = (M.w1 << (64 - sh)) | (M.w0 >> sh);
+    sticky = M.w0 & ((1ull << sh) - 1);
+  } else if (sh == 64) {
+    w = M.w1;
+    sticky = M.w0;
+  } else {
+    const int s2 = sh - 64;   // 1 .. 64
+    w = (s2 < 64) ? ((M.w2 << (64 - s2)) | (M.w1 >> s2)) : M.w2;
+    sticky = M.w0 | ((s2 < 64) ? (M.w1 & ((1ull << s2) - 1)) : M.w1);
+  }
+  shift = sh;
+  return __ull2double_rn(w | (sticky ? 1ull : 0ull));
+}
+
+// greedy rounding of the signed R * 2^scale to two doubles: hi = RN(v),
+// lo = RN(v - hi)
+__device__ __forceinline__ void i192_to_dd(I192 R, int scale, double& hi, double& lo) {
+  const bool neg = (long long)R.w2 < 0;
+  if (neg) i192_neg(R);
+  const int top = i192_top(R);
+  hi = lo = 0.0;
+  if (top < 0) return;
+  int sh;
+  const double hd = i192_window_rn(R, top, sh);
+  // subtract RN(M) = mant * 2^(ex - 52 + sh) exactly
+  const unsigned long long hb = (unsigned long long)__double_as_longlong(hd);
+  const int ex = (int)((hb >> 52) & 0x7ff) - 1023;
+  const unsigned long long mant = (hb & ((1ull << 52) - 1)) | (1ull << 52);
+  const int pos = ex - 52 + sh;
+  double ld = 0.0;
+  int sh2 = 0;
+  bool lneg = false;
+  if (pos >= 0) {   // otherwise M < 2^53 and the conversion was exact
+    i192_sub_shifted(R, mant, pos);
+    lneg = (long long)R.w2 < 0;
+    if (lneg) i192_neg(R);
+    const int top2 = i192_top(R);
+    if (top2 >= 0) ld = i192_window_rn(R, top2, sh2);
+  }
+  hi = scale_pow2(neg ? -hd : hd, sh + scale);
+  lo = scale_pow2((neg != lneg) ? -ld : ld, sh2 + scale);
 }
 
 // R -= sign(x) * |x| * 2^-scale for a finite double x whose value is an
@@ -420,26 +446,6 @@ __device__ __forceinline__ bool i192_sub_double(I192& R, double x, int scale) {
   return true;
 }
 
-
-// RN of R (signed) -> double, R -= it; R * 2^scale is the value
-__device__ __forceinline__ double i192_take_rn(I192& R, int scale) {
-  const bool neg = (long long)R.w2 < 0;
-  if (neg) i192_neg(R);
-  const int top = i192_top(R);
-  double res = 0.0;
-  if (top >= 0) {
-    const int lo = (top >= 52) ? top - 52 : 0;
-    unsigned long long q = (top >= 52) ? i192_bits53(R, lo) : R.w0;
-    if (lo > 0 && i192_bit(R, lo - 1) && (i192_any_below(R, lo - 1) || (q & 1ull))) q += 1;
-    i192_sub_shifted(R, q, lo);
-    res = make_double(q, lo + scale);
-  }
-  if (neg) {
-    i192_neg(R);
-    res = -res;
-  }
-  return res;
-}
 
 // ---------------------------------------------------------------------------
 // the tensor-core kernel: one CTA per 128 x 16 output tile, two CTAs per SM
@@ -588,12 +594,10 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
           I192 T = R;
           if (i192_sub_double(T, cv.v[0], scale) && i192_sub_double(T, cv.v[1], scale)) {
             i192_neg(T);
-            cv.v[0] = i192_take_rn(T, scale);
-            cv.v[1] = i192_take_rn(T, scale);
+            i192_to_dd(T, scale, cv.v[0], cv.v[1]);
           } else {
             val<2> pr;
-            pr.v[0] = i192_take_rn(R, scale);
-            pr.v[1] = i192_take_rn(R, scale);
+            i192_to_dd(R, scale, pr.v[0], pr.v[1]);
             cv = sub<2>(cv, pr);
           }
           store<2>(C, planeC, idx, cv);
