@@ -961,10 +961,11 @@ static int64_t max_b_tiles(const BlockedPlanHost& bp) {
   return t;
 }
 
-// [trail | tinv | pinner tiles and bases | aux | split scratch]
+// [trail | tinv | pinner tiles and bases | swap plans | aux | split scratch]
 static size_t blocked_extra_bytes(const BlockedPlanHost& bp) {
   size_t b = geom_bytes(bp.trail) + geom_bytes(bp.tinv);
   for (const auto& g : bp.pinner) b += geom_bytes(g);
+  b += align256(sizeof(SwapPlan) * (size_t)std::max<int64_t>(1, blocked_count(bp)));
   if (bp.update == MW_UPDATE_SPLIT) {
     b += align256(sizeof(double) * 2 * kBatchNb * kBatchNb * (size_t)std::max<int64_t>(1, blocked_count(bp)));
     b += split_batched_workspace_bytes(max_a_tiles(bp), max_b_tiles(bp));
@@ -979,6 +980,7 @@ struct GeomDev {
 
 struct BlockedDev {
   GeomDev trail, tinv, pinner[3];
+  SwapPlan* plans;   // one per active position
   double* aux;
   char* split_ws;
   size_t split_bytes;
@@ -1023,6 +1025,8 @@ static int upload_blocked(const BlockedPlanHost& bp, const std::vector<int>& n, 
       return rc;
     }
   }
+  d.plans = reinterpret_cast<SwapPlan*>(base + off);
+  off += align256(sizeof(SwapPlan) * (size_t)std::max<int64_t>(1, blocked_count(bp)));
   d.aux = nullptr;
   d.split_ws = nullptr;
   d.split_bytes = 0;
@@ -1085,10 +1089,12 @@ static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d,
     if (split) {
       rc = split_panel<W>(p, bv, bp, bd, st, act, k0, 0, kBatchNb, A, piv, info, s);
       if (rc) return rc;
-      rc = launch_bswap<W>(bv, act, k0, 0, kBatchNb, -k0, 0, k0, A, piv, s);   // left of the panel
+      rc = launch_bswap_plan(bv, act, k0, 0, kBatchNb, piv, bd.plans, s);
+      if (rc) return rc;
+      rc = launch_bswap_apply<W>(bv, act, k0, -k0, 0, k0, A, bd.plans, s);   // left of the panel
       if (rc) return rc;
       if (bp.max_cols[st] <= 0) continue;
-      rc = launch_bswap<W>(bv, act, k0, 0, kBatchNb, kBatchNb, kFar, bp.max_cols[st], A, piv, s);   // right
+      rc = launch_bswap_apply<W>(bv, act, k0, kBatchNb, kFar, bp.max_cols[st], A, bd.plans, s);   // right
       if (rc) return rc;
       rc = split_binv_l11(bv, act, k0, A, bd.aux, s);
       if (rc) return rc;
@@ -1103,8 +1109,12 @@ static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d,
     } else {
       rc = launch_bpanel<W>(bv, act, p.nmax, k0, 0, kBatchNb, A, piv, info, s);
       if (rc) return rc;
-      rc = launch_blaswp<W>(bv, act, k0, A, piv, s);
-      if (rc) return rc;
+      if (k0 > 0) {
+        rc = launch_bswap_plan(bv, act, k0, 0, kBatchNb, piv, bd.plans, s);
+        if (rc) return rc;
+        rc = launch_bswap_apply<W>(bv, act, k0, -k0, 0, k0, A, bd.plans, s);   // left of the panel
+        if (rc) return rc;
+      }
       rc = launch_btrsm<W>(bv, act, bp.max_cb_trsm[st], k0, A, piv, s);
       if (rc) return rc;
       rc = launch_bgemm_plain<W>(bv, bd.trail.tiles + bp.trail.toff[st], nt, k0, A, s);

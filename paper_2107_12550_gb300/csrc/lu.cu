@@ -6,7 +6,8 @@
 //      argmax of |a_ik| over rows i >= k across all CTAs, the row swap inside
 //      the panel, the multipliers l_ik = a_ik / a_kk and the in-panel
 //      updates a_ij -= l_ik u_kj.
-//   2. k_laswp on the columns left of the panel, and k_trsm on the columns
+//   2. the panel's row swaps on the columns left of it (one gather, k_swap_plan
+//      and k_swap_apply), and k_trsm on the columns
 //      right of it: the panel's row swaps, then U12 = L11^-1 A12.
 //   3. the trailing update A22 -= L21 U12, either the plain multiword GEMM
 //      on the FP64 pipe (k_gemm_plain, here) or the split-precision
@@ -341,25 +342,95 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
 }
 
 // ---------------------------------------------------------------------------
-// row interchanges on a range of columns (one thread per column and word)
+// row interchanges as a gather (SwapPlan): one warp composes the swaps
+// (k0 + kk, piv[k0 + kk]), kk in [lo, hi), in order into the contents of the
+// block rows [k0 + lo, k0 + hi) and of the rows below them that the swaps
+// reach; then one warp per column and word loads every source and stores
+// every destination.
 // ---------------------------------------------------------------------------
-template <int W>
-__global__ void k_laswp(double* __restrict__ A, int64_t lda, int64_t plane, int64_t c_begin,
-                        int64_t c_end, int64_t k0, int nb, const int64_t* __restrict__ piv) {
-  const int64_t j = c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int c = blockIdx.y;
-  if (j >= c_end) return;
-  double* col = A + c * plane + j * lda;
-  for (int kk = 0; kk < nb; ++kk) {
-    const int64_t k = k0 + kk;
-    const int64_t p = piv[k];
-    if (p != k) {
-      const double a = col[k];
-      col[k] = col[p];
-      col[p] = a;
+__device__ __forceinline__ void build_swap_plan(const int64_t* __restrict__ pv, int k0, int lo, int hi,
+                                                SwapPlan* __restrict__ plan) {
+  __shared__ int blk[kMaxNb], orow[kMaxNb], ocont[kMaxNb];
+  const int lane = threadIdx.x & 31;
+  const int nbk = hi - lo;
+  const int base = k0 + lo;
+  for (int q = lane; q < nbk; q += 32) blk[q] = base + q;
+  __syncwarp();
+  int m = 0;
+  for (int kk = 0; kk < nbk; ++kk) {
+    const int p = (int)pv[base + kk];
+    if (p < base + nbk) {
+      if (lane == 0 && p != base + kk) {
+        const int t = blk[kk];
+        blk[kk] = blk[p - base];
+        blk[p - base] = t;
+      }
+    } else {
+      int found = -1;
+      for (int e = lane; e < m; e += 32)
+        if (orow[e] == p) found = e;
+      const unsigned hit = __ballot_sync(0xffffffffu, found >= 0);
+      const int idx = hit ? __shfl_sync(0xffffffffu, found, __ffs(hit) - 1) : -1;
+      if (lane == 0) {
+        if (idx >= 0) {
+          const int t = blk[kk];
+          blk[kk] = ocont[idx];
+          ocont[idx] = t;
+        } else {
+          orow[m] = p;
+          ocont[m] = blk[kk];
+          blk[kk] = p;
+        }
+      }
+      if (idx < 0) ++m;
+    }
+    __syncwarp();
+  }
+  for (int q = lane; q < nbk; q += 32) plan->pairs[q] = make_int2(base + q, blk[q]);
+  for (int e = lane; e < m; e += 32) plan->pairs[nbk + e] = make_int2(orow[e], ocont[e]);
+  if (lane == 0) plan->count = nbk + m;
+}
+
+__device__ __forceinline__ void apply_swap_plan(double* __restrict__ col, const SwapPlan* __restrict__ plan) {
+  constexpr int Q = 2 * kMaxNb / 32;
+  const int lane = threadIdx.x & 31;
+  const int cnt = plan->count;
+  double v[Q];
+  int dst[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = lane + 32 * q;
+    if (e < cnt) {
+      const int2 pr = plan->pairs[e];
+      v[q] = col[pr.y];
+      dst[q] = pr.x;
     }
   }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = lane + 32 * q;
+    if (e < cnt) col[dst[q]] = v[q];
+  }
 }
+
+__global__ void __launch_bounds__(32)
+k_swap_plan(const int64_t* __restrict__ piv, int k0, int nb, SwapPlan* __restrict__ plan) {
+  build_swap_plan(piv, k0, 0, nb, plan);
+}
+
+// 8 columns per CTA (one warp each), blockIdx.y = word
+template <int W>
+__global__ void __launch_bounds__(256)
+k_swap_apply(double* __restrict__ A, int64_t lda, int64_t plane, int64_t c_begin, int64_t c_end,
+             const SwapPlan* __restrict__ plan) {
+  const int64_t j = c_begin + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= c_end) return;   // uniform per warp
+  apply_swap_plan(A + blockIdx.y * plane + j * lda, plan);
+}
+
+static int swap_gather(double* A, int64_t lda, int64_t plane, int W, int64_t n, int64_t k0, int kb,
+                       const int64_t* piv, char* ws, bool left, bool right, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // row interchanges + U12 = L11^-1 A12 on 8 columns per CTA.
@@ -689,30 +760,6 @@ k_bpanel(BatchView bv, int nmax, int kp, int width, double* __restrict__ A, int6
   if (tid == 0) info[sys] = inf;
 }
 
-// the panel's row swaps on the columns left of it: CTA (pos, word)
-template <int W>
-__global__ void __launch_bounds__(128)
-k_blaswp(BatchView bv, int k0, double* __restrict__ A, const int64_t* __restrict__ piv) {
-  const int sys = bv.order[blockIdx.x];
-  const int n = bv.n[sys];
-  const int kb = min(kBatchNb, n - k0);
-  const int64_t plane = (int64_t)n * n;
-  const int64_t* pv = piv + bv.voff[sys];
-  double* a = A + (int64_t)W * bv.moff[sys] + blockIdx.y * plane;
-  for (int j = threadIdx.x; j < k0; j += blockDim.x) {
-    double* col = a + (int64_t)j * n;
-    for (int kk = 0; kk < kb; ++kk) {
-      const int k = k0 + kk;
-      const int p = (int)pv[k];
-      if (p != k) {
-        const double t = col[k];
-        col[k] = col[p];
-        col[p] = t;
-      }
-    }
-  }
-}
-
 // row swaps k0 + [sw_lo, min(sw_hi, kb)) on the columns
 // [max(0, k0 + c_lo), min(n, k0 + c_hi)): CTA (pos, word, block of 128 columns)
 template <int W>
@@ -739,6 +786,30 @@ k_bswap(BatchView bv, int k0, int sw_lo, int sw_hi, int c_lo, int c_hi, double* 
       col[p] = t;
     }
   }
+}
+
+// batched swap plans: one warp per active system
+__global__ void __launch_bounds__(32)
+k_bswap_plan(BatchView bv, int k0, int sw_lo, int sw_hi, const int64_t* __restrict__ piv,
+             SwapPlan* __restrict__ plans) {
+  const int sys = bv.order[blockIdx.x];
+  const int n = bv.n[sys];
+  const int kb = min(kBatchNb, n - k0);
+  build_swap_plan(piv + bv.voff[sys], k0, sw_lo, max(sw_lo, min(sw_hi, kb)), plans + blockIdx.x);
+}
+
+// CTA (pos, word, block of 8 columns), one warp per column
+template <int W>
+__global__ void __launch_bounds__(256)
+k_bswap_apply(BatchView bv, int k0, int c_lo, int c_hi, double* __restrict__ A, const SwapPlan* __restrict__ plans) {
+  const int sys = bv.order[blockIdx.x];
+  const int n = bv.n[sys];
+  const int j0 = max(0, k0 + c_lo);
+  const int j1 = min(n, k0 + c_hi);
+  const int64_t j = (int64_t)j0 + (int64_t)blockIdx.z * 8 + (threadIdx.x >> 5);
+  if (j >= j1) return;   // uniform per warp
+  const int64_t plane = (int64_t)n * n;
+  apply_swap_plan(A + (int64_t)W * bv.moff[sys] + blockIdx.y * plane + j * n, plans + blockIdx.x);
 }
 
 // inside the panel, block of 2H columns at column c0 = k0 + c_off: the top H
@@ -869,19 +940,8 @@ static int lu_split_dd(int64_t n, double* A, int64_t lda, int64_t* piv, int64_t*
       rc = launch_panel<2>(A, lda, plane, n, k0, kb, piv, info, ws, s);
     }
     if (rc) return rc;
-    {
-      ProfScope ps(kPhLaswp, s);
-      if (k0 > 0) {
-        dim3 grid((unsigned)((k0 + 127) / 128), 2);
-        k_laswp<2><<<grid, 128, 0, s>>>(A, lda, plane, 0, k0, k0, kb, piv);
-        MW_LAUNCH_CHECK();
-      }
-      if (k0 + kb < n) {
-        dim3 grid((unsigned)((n - k0 - kb + 127) / 128), 2);
-        k_laswp<2><<<grid, 128, 0, s>>>(A, lda, plane, k0 + kb, n, k0, kb, piv);
-        MW_LAUNCH_CHECK();
-      }
-    }
+    rc = swap_gather(A, lda, plane, 2, n, k0, kb, piv, ws, k0 > 0, k0 + kb < n, s);
+    if (rc) return rc;
     if (k0 + kb >= n) break;
     rc = split_inv_l11(A, lda, plane, k0, aux, s);
     if (rc) return rc;
@@ -926,10 +986,8 @@ int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int6
     }
     if (rc) return rc;
     if (k0 > 0) {
-      ProfScope ps(kPhLaswp, s);
-      dim3 grid((unsigned)((k0 + 127) / 128), W);
-      k_laswp<W><<<grid, 128, 0, s>>>(A, lda, plane, 0, k0, k0, kb, piv);
-      MW_LAUNCH_CHECK();
+      rc = swap_gather(A, lda, plane, W, n, k0, kb, piv, ws, true, false, s);
+      if (rc) return rc;
     }
     if (k0 + kb < n) {
       {
@@ -952,7 +1010,51 @@ template int lu_blocked<2>(int, int64_t, double*, int64_t, int64_t*, int64_t*, c
 template int lu_blocked<3>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
 template int lu_blocked<4>(int, int64_t, double*, int64_t, int64_t*, int64_t*, char*, size_t, int, cudaStream_t);
 
+// the panel's swaps on the columns left of it (left) and right of it (right)
+static int swap_gather(double* A, int64_t lda, int64_t plane, int W, int64_t n, int64_t k0, int kb,
+                       const int64_t* piv, char* ws, bool left, bool right, cudaStream_t s) {
+  if (!left && !right) return MW_OK;
+  ProfScope ps(kPhLaswp, s);
+  SwapPlan* plan = reinterpret_cast<SwapPlan*>(ws + kWsSwapPlan);
+  k_swap_plan<<<1, 32, 0, s>>>(piv, (int)k0, kb, plan);
+  MW_LAUNCH_CHECK();
+  auto apply = [&](int64_t c0, int64_t c1) -> int {
+    const int64_t nc = c1 - c0;
+    if (nc <= 0) return MW_OK;
+    dim3 grid((unsigned)((nc + 7) / 8), W);
+    switch (W) {
+      case 2: k_swap_apply<2><<<grid, 256, 0, s>>>(A, lda, plane, c0, c1, plan); break;
+      case 3: k_swap_apply<3><<<grid, 256, 0, s>>>(A, lda, plane, c0, c1, plan); break;
+      default: k_swap_apply<4><<<grid, 256, 0, s>>>(A, lda, plane, c0, c1, plan); break;
+    }
+    MW_LAUNCH_CHECK();
+    return MW_OK;
+  };
+  int rc = left ? apply(0, k0) : MW_OK;
+  if (rc) return rc;
+  return right ? apply(k0 + kb, n) : MW_OK;
+}
+
 // ---- batched launchers ------------------------------------------------------
+int launch_bswap_plan(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, const int64_t* piv,
+                      SwapPlan* plans, cudaStream_t s) {
+  if (act <= 0) return MW_OK;
+  ProfScope ps(kPhLaswp, s);
+  k_bswap_plan<<<act, 32, 0, s>>>(bv, k0, sw_lo, sw_hi, piv, plans);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+template <int W>
+int launch_bswap_apply(const BatchView& bv, int act, int k0, int c_lo, int c_hi, int max_cols, double* A,
+                       const SwapPlan* plans, cudaStream_t s) {
+  if (act <= 0 || max_cols <= 0) return MW_OK;
+  ProfScope ps(kPhLaswp, s);
+  k_bswap_apply<W><<<dim3((unsigned)act, W, (unsigned)((max_cols + 7) / 8)), 256, 0, s>>>(bv, k0, c_lo, c_hi, A,
+                                                                                         plans);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
 void gemm_plain_tile_shape(int W, int* bm, int* bn) {
   switch (W) {
     case 2: *bm = 16 * GemmTile<2>::TM; *bn = 16 * GemmTile<2>::TN; break;
@@ -1001,15 +1103,6 @@ int launch_btrsm_sub(const BatchView& bv, int act, int k0, int c_off, int h, dou
 }
 
 template <int W>
-int launch_blaswp(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s) {
-  if (act <= 0 || k0 <= 0) return MW_OK;
-  ProfScope ps(kPhLaswp, s);
-  k_blaswp<W><<<dim3((unsigned)act, W), 128, 0, s>>>(bv, k0, A, piv);
-  MW_LAUNCH_CHECK();
-  return MW_OK;
-}
-
-template <int W>
 int launch_btrsm(const BatchView& bv, int act, int max_cblocks, int k0, double* A, const int64_t* piv,
                  cudaStream_t s) {
   if (act <= 0 || max_cblocks <= 0) return MW_OK;
@@ -1036,7 +1129,8 @@ int launch_bgemm_plain(const BatchView& bv, const TileEntry* tiles, int64_t ntil
   template int launch_bswap<W>(const BatchView&, int, int, int, int, int, int, int, double*, const int64_t*,    \
                                cudaStream_t);                                                                 \
   template int launch_btrsm_sub<W>(const BatchView&, int, int, int, int, double*, const int64_t*, cudaStream_t); \
-  template int launch_blaswp<W>(const BatchView&, int, int, double*, const int64_t*, cudaStream_t);          \
+  template int launch_bswap_apply<W>(const BatchView&, int, int, int, int, int, double*, const SwapPlan*,          \
+                                     cudaStream_t);                                                                 \
   template int launch_btrsm<W>(const BatchView&, int, int, int, double*, const int64_t*, cudaStream_t);      \
   template int launch_bgemm_plain<W>(const BatchView&, const TileEntry*, int64_t, int, double*, cudaStream_t);
 MW_BATCHED_INST(2)

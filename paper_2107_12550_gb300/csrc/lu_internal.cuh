@@ -26,6 +26,18 @@ constexpr size_t kCandStride = 8 * (1 + 4 + 1 + 4 * kMaxNb);         // one reco
 constexpr size_t kCandParity = kCandStride * kMaxPanelCtas + 8 * 4 * kMaxNb;  // records + old row k
 constexpr size_t kWsSplit = (kWsCand + 2 * kCandParity + 65535) & ~(size_t)65535;
 
+// The row interchanges of one panel as a single gather: the swaps
+// (k, piv[k]) for k in [k0, k0 + nb) compose to a permutation of at most 2 nb
+// rows, listed as (destination, source) pairs; every column then loads all
+// sources before storing all destinations.
+struct SwapPlan {
+  int count;
+  int pad;
+  int2 pairs[2 * kMaxNb];
+};
+constexpr size_t kWsSwapPlan = (kWsCand + 2 * kCandParity + 255) & ~(size_t)255;
+static_assert(kWsSwapPlan + sizeof(SwapPlan) <= kWsSplit, "swap plan inside the LU work buffer header");
+
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // tuning knobs (capi.cu): value of `param` (MW_TUNE_*) for precision prec
@@ -103,11 +115,17 @@ int launch_bswap(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, int
 // inside the panel, for the block of 2h columns at column offset c_off: the
 // top h rows of its right half get the left half's swaps, then the unit
 // lower h x h solve (h = 16 or 32)
+// batched: the plans of the panel swaps k0 + [sw_lo, min(sw_hi, kb)) of every
+// active system (one warp each, plans[pos]), and their gather on the columns
+// [max(0, k0 + c_lo), min(n, k0 + c_hi))
+int launch_bswap_plan(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, const int64_t* piv,
+                      SwapPlan* plans, cudaStream_t s);
+template <int W>
+int launch_bswap_apply(const BatchView& bv, int act, int k0, int c_lo, int c_hi, int max_cols, double* A,
+                       const SwapPlan* plans, cudaStream_t s);
 template <int W>
 int launch_btrsm_sub(const BatchView& bv, int act, int k0, int c_off, int h, double* A, const int64_t* piv,
                      cudaStream_t s);
-template <int W>
-int launch_blaswp(const BatchView& bv, int act, int k0, double* A, const int64_t* piv, cudaStream_t s);
 template <int W>
 int launch_btrsm(const BatchView& bv, int act, int max_cblocks, int k0, double* A, const int64_t* piv,
                  cudaStream_t s);
