@@ -855,7 +855,7 @@ struct BlockedPlanHost {
   std::vector<int> act, max_cb_trsm, max_cols;
   GeomPlanHost trail;   // plain: BM x BN tiles; split: 128 x 16 tiles of A22
   GeomPlanHost tinv;    // split: 128 x 16 tiles of U12^T (the TRSM as a product with L11^-1)
-  GeomPlanHost pinner[3];  // split: 128 x 16 tiles of the inner panel updates (kInner order)
+  GeomPlanHost pinner[7];  // split: 128 x 16 tiles of the inner panel updates (kInner order)
 };
 
 // the inner updates of the recursive split panel: (column offset, half width)
@@ -863,8 +863,9 @@ struct BlockedPlanHost {
 struct InnerSpec {
   int c_off, h;
 };
-constexpr InnerSpec kInner[3] = {{0, 16}, {0, 32}, {32, 16}};
-constexpr int kPanelLeaf = 16;
+constexpr int kNumInner = 7;
+constexpr InnerSpec kInner[kNumInner] = {{0, 8}, {16, 8}, {0, 16}, {32, 8}, {48, 8}, {32, 16}, {0, 32}};
+constexpr int kPanelLeaf = 8;
 
 // tiles of an m x N product for every active system of one step
 static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool split, int bm, int bn,
@@ -920,9 +921,13 @@ static void make_blocked_plan(const BatchPlanHost& p, int W, int update, Blocked
     bn = kSplitTileN;
   }
   const int count = (int)p.n.size();
-  for (GeomPlanHost* g : {&bp.trail, &bp.tinv, &bp.pinner[0], &bp.pinner[1], &bp.pinner[2]}) {
+  for (GeomPlanHost* g : {&bp.trail, &bp.tinv}) {
     g->toff.push_back(0);
     g->boff.push_back(0);
+  }
+  for (auto& g : bp.pinner) {
+    g.toff.push_back(0);
+    g.boff.push_back(0);
   }
   if (count == 0) return;
   int act = count;
@@ -935,7 +940,7 @@ static void make_blocked_plan(const BatchPlanHost& p, int W, int update, Blocked
     add_geom_step(bp.trail, p, act, split, bm, bn, dims_trail, k0);
     if (split) {
       add_geom_step(bp.tinv, p, act, true, kSplitTileM, kSplitTileN, dims_tinv, k0);
-      for (int q = 0; q < 3; ++q)
+      for (int q = 0; q < kNumInner; ++q)
         add_geom_step(bp.pinner[q], p, act, true, kSplitTileM, kSplitTileN, dims_pinner, k0, kInner[q].c_off,
                       kInner[q].h);
     }
@@ -979,7 +984,7 @@ struct GeomDev {
 };
 
 struct BlockedDev {
-  GeomDev trail, tinv, pinner[3];
+  GeomDev trail, tinv, pinner[kNumInner];
   SwapPlan* plans;   // one per active position
   double* aux;
   char* split_ws;
@@ -1018,7 +1023,7 @@ static int upload_blocked(const BlockedPlanHost& bp, const std::vector<int>& n, 
     plan_forget(base);
     return rc;
   }
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < kNumInner; ++q) {
     rc = upload_geom(bp.pinner[q], base, off, d.pinner[q], s, resident);
     if (rc) {
       plan_forget(base);
@@ -1053,7 +1058,7 @@ static int split_panel(const BatchPlanHost& p, const BatchView& bv, const Blocke
   if (w <= kPanelLeaf) return launch_bpanel<W>(bv, act, p.nmax, k0, c_off, w, A, piv, info, s);
   const int h = w / 2;
   int q = -1;
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < kNumInner; ++i)
     if (kInner[i].c_off == c_off && kInner[i].h == h) q = i;
   if (q < 0) return MW_EUNSUPPORTED;
   int rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off, h, A, piv, info, s);

@@ -1094,6 +1094,7 @@ int launch_btrsm_sub(const BatchView& bv, int act, int k0, int c_off, int h, dou
   if (act <= 0) return MW_OK;
   ProfScope ps(kPhPanel, s);
   switch (h) {
+    case 8: k_btrsm_sub<W, 8><<<dim3((unsigned)act, 1), 256, 0, s>>>(bv, k0 + c_off, A, piv); break;
     case 16: k_btrsm_sub<W, 16><<<dim3((unsigned)act, 2), 256, 0, s>>>(bv, k0 + c_off, A, piv); break;
     case 32: k_btrsm_sub<W, 32><<<dim3((unsigned)act, 4), 256, 0, s>>>(bv, k0 + c_off, A, piv); break;
     default: return MW_EUNSUPPORTED;

@@ -114,7 +114,7 @@ int launch_bswap(const BatchView& bv, int act, int k0, int sw_lo, int sw_hi, int
                  double* A, const int64_t* piv, cudaStream_t s);
 // inside the panel, for the block of 2h columns at column offset c_off: the
 // top h rows of its right half get the left half's swaps, then the unit
-// lower h x h solve (h = 16 or 32)
+// lower h x h solve (h = 8, 16 or 32)
 // batched: the plans of the panel swaps k0 + [sw_lo, min(sw_hi, kb)) of every
 // active system (one warp each, plans[pos]), and their gather on the columns
 // [max(0, k0 + c_lo), min(n, k0 + c_hi))

@@ -206,8 +206,8 @@ __device__ __forceinline__ void slice_rows16(const double* __restrict__ L, int64
   if (kc == 0) ea[r] = e;
   const int64_t tile = r / kTileM;
   const int rr = (int)(r % kTileM);
-  slice_store8(hv, lv, e, ok && mx > 0.0, aslices + tile * (int64_t)kS * kASliceBytes + sw128_offset(rr, kc * 8),
-               kASliceBytes);
+  slice_store8(hv, lv, e, ok && mx > 0.0 && kc * 8 < kvalid,
+               aslices + tile * (int64_t)kS * kASliceBytes + sw128_offset(rr, kc * 8), kASliceBytes);
 }
 
 // columns [jbase, jbase + 16) of the column operand (element (k, j) at U[k*uks + j*ujs])
@@ -232,8 +232,8 @@ __device__ __forceinline__ void slice_cols16(const double* __restrict__ U, int64
   if (kc == 0) fb[j] = f;
   const int64_t tile = j / kTileN;
   const int jj = (int)(j % kTileN);
-  slice_store8(hv, lv, f, ok && mx > 0.0, bslices + tile * (int64_t)kS * kBSliceBytes + sw128_offset(jj, kc * 8),
-               kBSliceBytes);
+  slice_store8(hv, lv, f, ok && mx > 0.0 && kc * 8 < kvalid,
+               bslices + tile * (int64_t)kS * kBSliceBytes + sw128_offset(jj, kc * 8), kBSliceBytes);
 }
 
 // grid: (rows padded to 128) / 16
