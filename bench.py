@@ -129,6 +129,21 @@ def dist_setup(args):
     return world, rank, local
 
 
+def combine_ranks(ms: float, solved: int, device) -> tuple:
+    """(max time over the ranks, systems solved by all ranks) across the
+    process group; the rank's own values without one (replicas: no data
+    leaves a rank, only these two numbers)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, solved
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    c = torch.tensor([float(solved)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), int(c[0])
+
+
 def exact_ok(x_host, n) -> bool:
     """|x_i - 1| <= 2^-200 for every i, evaluated exactly on the words."""
     lim = Fraction(1, 2 ** TARGET_BITS)
@@ -571,15 +586,7 @@ def main():
     prof = L.profile_read(reset=True)
     ms = e0.elapsed_time(e1)
     ok = ok and exact_ok(x.cpu().numpy(), n)
-    t_max = ms
-    solved = args.steps * (1 if ok else 0)
-    if world > 1:
-        tt = torch.tensor([ms, float(solved)], device="cuda", dtype=torch.float64)
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.SUM)
-        t_max = float(mx[0])
-        solved = int(tt[1])
+    t_max, solved = combine_ranks(ms, args.steps * (1 if ok else 0), "cuda")
     value = solved / (t_max * 1e-3)
 
     # roofline of the dominant kernel: the plain TD trailing update
