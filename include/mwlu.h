@@ -334,6 +334,12 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
  *                                always uses 64)
  *   MW_TUNE_PANEL_ROWS_PER_CTA   panel rows per CTA before the panel kernel
  *                                adds CTAs: 1..4096 (default 8)
+ *   MW_TUNE_SPLIT_PANEL_LEAF     the split (DD) LU of one system factors each
+ *                                64-column panel recursively down to leaves of
+ *                                this width (8, 16 or 32), the inner updates
+ *                                as split products; 0: no recursion below 64
+ *                                (the default, chosen by measurement; the
+ *                                results differ by roundings only).
  *   MW_TUNE_BATCH_CTAS_PER_SM    persistent CTAs per SM of the batched LU:
  *                                1..8 (default 2)
  * mw_set_tuning returns the previous value, or -1 (param), -2 (prec) or
@@ -342,6 +348,7 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
 #define MW_TUNE_PANEL_WIDTH 0
 #define MW_TUNE_PANEL_ROWS_PER_CTA 1
 #define MW_TUNE_BATCH_CTAS_PER_SM 2
+#define MW_TUNE_SPLIT_PANEL_LEAF 3
 int mw_set_tuning(int param, int prec, int value);
 int mw_get_tuning(int param, int prec);
 

@@ -921,6 +921,70 @@ static int launch_trsm(double* A, int64_t lda, int64_t plane, int64_t n, int64_t
 // latency, and the extra launches and small products of the recursion cost
 // more than the FP64 work they move.)
 // ---------------------------------------------------------------------------
+// the swaps piv[sk0 .. sk0 + ns) on the columns [c0, c1), as one gather
+static int swap_gather_range(double* A, int64_t lda, int64_t plane, int64_t sk0, int ns, int64_t c0, int64_t c1,
+                             const int64_t* piv, char* ws, cudaStream_t s) {
+  if (ns <= 0 || c1 <= c0) return MW_OK;
+  ProfScope ps(kPhLaswp, s);
+  SwapPlan* plan = reinterpret_cast<SwapPlan*>(ws + kWsSwapPlan);
+  k_swap_plan<<<1, 32, 0, s>>>(piv, (int)sk0, ns, plan);
+  MW_LAUNCH_CHECK();
+  dim3 grid((unsigned)((c1 - c0 + 7) / 8), 2);
+  k_swap_apply<2><<<grid, 256, 0, s>>>(A, lda, plane, c0, c1, plan);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+// the panel [kp, kp + w) of the split LU, recursively: left half, the right
+// half's top rows solved with the left half's unit lower triangle (and its
+// swaps), its rows below updated by a split product (K = half width), right
+// half, then the right half's swaps on the left half; leaves of `leaf`
+// columns on the cooperative panel kernel
+static int split_panel_rec(double* A, int64_t lda, int64_t plane, int64_t n, int64_t kp, int w, int leaf,
+                           int64_t* piv, int64_t* info, char* ws, char* sws, size_t sbytes, cudaStream_t s) {
+  w = (int)std::min<int64_t>(w, n - kp);
+  if (w <= 0) return MW_OK;
+  if (w <= leaf) {
+    ProfScope ps(kPhPanel, s);
+    return launch_panel<2>(A, lda, plane, n, kp, w, piv, info, ws, s);
+  }
+  const int h = (w > 32) ? 32 : (w > 16 ? 16 : 8);   // halves of 64 -> 32 -> 16 -> 8
+  int rc = split_panel_rec(A, lda, plane, n, kp, h, leaf, piv, info, ws, sws, sbytes, s);
+  if (rc) return rc;
+  const int64_t lim = kp + w;   // right half: columns [kp + h, lim)
+  {
+    ProfScope ps(kPhPanel, s);
+    dim3 grid((unsigned)((lim - kp - h + 7) / 8));
+    switch (h) {
+      case 32: k_trsm<2, 32><<<grid, 256, 0, s>>>(A, lda, plane, lim, kp, piv); break;
+      case 16: k_trsm<2, 16><<<grid, 256, 0, s>>>(A, lda, plane, lim, kp, piv); break;
+      default: k_trsm<2, 8><<<grid, 256, 0, s>>>(A, lda, plane, lim, kp, piv); break;
+    }
+    MW_LAUNCH_CHECK();
+  }
+  SplitOperands o;
+  o.L = A + kp * lda + kp + h;
+  o.lrs = 1;
+  o.lks = lda;
+  o.planeL = plane;
+  o.U = A + (kp + h) * lda + kp;
+  o.uks = 1;
+  o.ujs = lda;
+  o.planeU = plane;
+  o.C = A + (kp + h) * lda + kp + h;
+  o.crs = 1;
+  o.cjs = lda;
+  o.planeC = plane;
+  o.m = n - kp - h;
+  o.N = lim - kp - h;
+  o.K = h;
+  rc = split_product_dd(o, sws, sbytes, kPhPanel, s);
+  if (rc) return rc;
+  rc = split_panel_rec(A, lda, plane, n, kp + h, w - h, leaf, piv, info, ws, sws, sbytes, s);
+  if (rc) return rc;
+  return swap_gather_range(A, lda, plane, kp + h, (int)(lim - kp - h), kp, kp + h, piv, ws, s);
+}
+
 static int lu_split_dd(int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info, char* ws, size_t ws_bytes,
                        cudaStream_t s) {
   const int64_t plane = lda * n;
@@ -932,10 +996,13 @@ static int lu_split_dd(int64_t n, double* A, int64_t lda, int64_t* piv, int64_t*
   MW_CUDA_CHECK(cudaMemsetAsync(sws, 0, 256, s));
   MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
   constexpr int NB = kDefaultNb;
+  const int leaf = tune_get(MW_TUNE_SPLIT_PANEL_LEAF, 2);
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int kb = (int)std::min<int64_t>(NB, n - k0);
     int rc;
-    {
+    if (leaf > 0) {
+      rc = split_panel_rec(A, lda, plane, n, k0, kb, leaf, piv, info, ws, sws, sbytes, s);
+    } else {
       ProfScope ps(kPhPanel, s);
       rc = launch_panel<2>(A, lda, plane, n, k0, kb, piv, info, ws, s);
     }

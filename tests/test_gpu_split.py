@@ -148,3 +148,25 @@ def test_refine_split_dd_inner():
     x = host(res.x)
     for i in range(0, 300, 5):
         assert abs(X.words_to_frac(x[:, i]) - 1) <= Fraction(1, 2 ** 200)
+
+
+@pytest.mark.parametrize("leaf", [8, 16, 32])
+def test_lu_split_recursive_panel(leaf):
+    """The split LU of one system with its panels factored recursively down
+    to `leaf` columns (MW_TUNE_SPLIT_PANEL_LEAF): backward error <= 1e-28 and
+    pivots as the oracle's up to near-ties."""
+    from paper_2107_12550_gb300 import _lib as L
+    lib = L.lib()
+    prev = lib.mw_set_tuning(L.MW_TUNE_SPLIT_PANEL_LEAF, 2, leaf)
+    try:
+        for n in (200, 513):
+            s = W.uniform_system(n, words=2, seed=60 + n, b_words=2)
+            LUs, pivs, info = api().ludecomp(dev(s.A), 2, "split")
+            assert int(info.item()) == 0
+            xs = host(api().solve(LUs, pivs, dev(s.b), 2))
+            eta = _eta(s.A, s.b, xs)
+            assert eta <= 1e-28, (n, eta)
+            _, pivo, _ = oracle.lu(2, s.A)
+            assert int((host(pivs) != pivo).sum()) <= n // 50
+    finally:
+        lib.mw_set_tuning(L.MW_TUNE_SPLIT_PANEL_LEAF, 2, prev)
