@@ -342,6 +342,15 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
  *                                results differ by roundings only).
  *   MW_TUNE_BATCH_CTAS_PER_SM    persistent CTAs per SM of the batched LU:
  *                                1..8 (default 2)
+ *   MW_TUNE_GEMM_TILE            tile of the plain trailing update of one
+ *                                system (and of mw_gemm_sub): 0 (default)
+ *                                picks per launch the tile with the least
+ *                                per-SM work, ceil(tiles / SMs) x tile size,
+ *                                the smaller on a tie (all three run a full
+ *                                wave at the same rate); 1, 2, 3 force the
+ *                                large, middle or small tile (DD 64x64,
+ *                                32x64, 32x32; TD 32x64, 32x32, 16x32; QD
+ *                                32x32, 16x32, 16x16, rows x columns)
  * mw_set_tuning returns the previous value, or -1 (param), -2 (prec) or
  * -3 (value) when invalid; mw_get_tuning returns the value or -1/-2.
  */
@@ -349,6 +358,7 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
 #define MW_TUNE_PANEL_ROWS_PER_CTA 1
 #define MW_TUNE_BATCH_CTAS_PER_SM 2
 #define MW_TUNE_SPLIT_PANEL_LEAF 3
+#define MW_TUNE_GEMM_TILE 4
 int mw_set_tuning(int param, int prec, int value);
 int mw_get_tuning(int param, int prec);
 

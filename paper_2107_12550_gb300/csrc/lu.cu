@@ -17,6 +17,7 @@
 // rounded multiply and subtraction, so the plain form is bitwise identical
 // to unblocked elimination.
 #include <algorithm>
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include "mw_arith.cuh"
@@ -623,19 +624,89 @@ k_gemm_plain(double* __restrict__ C, int64_t ldc, int64_t planeC, const double* 
   gemm_plain_tile<W, TM, TN>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K, blockIdx.x, blockIdx.y);
 }
 
+// micro-tile of the batched trailing update (tile lists; many systems keep
+// the waves full)
 template <int W> struct GemmTile;
 template <> struct GemmTile<2> { static constexpr int TM = 4, TN = 4; };
 template <> struct GemmTile<3> { static constexpr int TM = 2, TN = 4; };
 template <> struct GemmTile<4> { static constexpr int TM = 2, TN = 2; };
 
+// Tile variants of the trailing update, largest first.  A launch is a few
+// waves of equal tiles over (SMs x resident CTAs) slots; when its last wave
+// is partly empty, a smaller tile can finish in fewer slot-units.  Every
+// entry of C still receives its updates in ascending k, so all variants give
+// bitwise the same result.
+template <int W, int V> struct GemmVariant;
+template <> struct GemmVariant<2, 0> { static constexpr int TM = 4, TN = 4; };
+template <> struct GemmVariant<2, 1> { static constexpr int TM = 2, TN = 4; };
+template <> struct GemmVariant<2, 2> { static constexpr int TM = 2, TN = 2; };
+template <> struct GemmVariant<3, 0> { static constexpr int TM = 2, TN = 4; };
+template <> struct GemmVariant<3, 1> { static constexpr int TM = 2, TN = 2; };
+template <> struct GemmVariant<3, 2> { static constexpr int TM = 1, TN = 2; };
+template <> struct GemmVariant<4, 0> { static constexpr int TM = 2, TN = 2; };
+template <> struct GemmVariant<4, 1> { static constexpr int TM = 1, TN = 2; };
+template <> struct GemmVariant<4, 2> { static constexpr int TM = 1, TN = 1; };
+constexpr int kGemmVariants = 3;
+
+static int gemm_sm_count() {
+  static std::atomic<int> cached{0};
+  int v = cached.load(std::memory_order_relaxed);
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+    cached.store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+template <int W, int V>
+static int64_t gemm_variant_cost(int64_t m, int64_t N) {
+  constexpr int BM = 16 * GemmVariant<W, V>::TM, BN = 16 * GemmVariant<W, V>::TN;
+  const int64_t tiles = ((m + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t sms = gemm_sm_count();
+  // the CTAs resident on an SM share its FP64 pipe, so an SM's time is the
+  // number of its tiles times the tile size, however many run at once
+  return ((tiles + sms - 1) / sms) * BM * BN;
+}
+
+// the variant a launch of m x N uses: MW_TUNE_GEMM_TILE 1..3 forces one,
+// 0 picks the least per-SM pipe time (the smaller tile on a tie; a full
+// wave runs at the same rate with any of the three)
+template <int W>
+int gemm_plain_variant(int64_t m, int64_t N) {
+  const int forced = tune_get(MW_TUNE_GEMM_TILE, W);
+  if (forced >= 1 && forced <= kGemmVariants) return forced - 1;
+  const int64_t c0 = gemm_variant_cost<W, 0>(m, N);
+  const int64_t c1 = gemm_variant_cost<W, 1>(m, N);
+  const int64_t c2 = gemm_variant_cost<W, 2>(m, N);
+  int v = 2;
+  int64_t best = c2;
+  if (c1 < best) v = 1, best = c1;
+  if (c0 < best) v = 0;
+  return v;
+}
+
+template <int W, int V>
+static void launch_gemm_variant(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
+                                const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
+                                int64_t planeU, cudaStream_t s) {
+  constexpr int TM = GemmVariant<W, V>::TM, TN = GemmVariant<W, V>::TN;
+  dim3 grid((unsigned)((m + 16 * TM - 1) / (16 * TM)), (unsigned)((N + 16 * TN - 1) / (16 * TN)));
+  k_gemm_plain<W, TM, TN><<<grid, 256, 0, s>>>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K);
+}
+
 template <int W>
 int launch_gemm_plain_ptr(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
                           const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
                           int64_t planeU, cudaStream_t s) {
-  constexpr int TM = GemmTile<W>::TM, TN = GemmTile<W>::TN;
   if (m <= 0 || N <= 0 || K <= 0) return MW_OK;
-  dim3 grid((unsigned)((m + 16 * TM - 1) / (16 * TM)), (unsigned)((N + 16 * TN - 1) / (16 * TN)));
-  k_gemm_plain<W, TM, TN><<<grid, 256, 0, s>>>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K);
+  switch (gemm_plain_variant<W>(m, N)) {
+    case 0: launch_gemm_variant<W, 0>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, s); break;
+    case 1: launch_gemm_variant<W, 1>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, s); break;
+    default: launch_gemm_variant<W, 2>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, s); break;
+  }
   MW_LAUNCH_CHECK();
   return MW_OK;
 }

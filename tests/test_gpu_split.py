@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from oracle import exact as X
+from paper_2107_12550_gb300 import _lib as L
 from paper_2107_12550_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -56,13 +57,23 @@ def _mat(w, rows, cols, seed, ld=None, scale_rows=False):
     return M
 
 
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 @pytest.mark.parametrize("w", [2, 3, 4])
-def test_gemm_sub_plain_bitwise(w):
+def test_gemm_sub_plain_bitwise(w, tile):
+    """Every tile variant of the plain update (MW_TUNE_GEMM_TILE: 0 automatic,
+    1-3 forced) gives the oracle's operation sequence bitwise; 70 x 45 leaves
+    a ragged tail for every tile size and K = 21 a ragged K chunk."""
     m, N, K = 70, 45, 21
     C = _mat(w, m, N, 1)
     A = _mat(w, m, K, 2)
     B = _mat(w, K, N, 3)
-    got = host(api().gemm_sub(dev(C), dev(A), dev(B), m, w, "plain"))
+    lib = L.lib()
+    prev = lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, w, tile)
+    assert prev >= 0
+    try:
+        got = host(api().gemm_sub(dev(C), dev(A), dev(B), m, w, "plain"))
+    finally:
+        lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, w, prev)
     ref = C[:, :, :m].copy()
     for t in range(K):
         a = np.repeat(A[:, t, :m][:, None, :], N, axis=1).reshape(w, -1)      # (w, N*m)

@@ -34,6 +34,12 @@ def test_knob_validation():
     assert lib.mw_get_tuning(L.MW_TUNE_PANEL_WIDTH, 2) == 32
     lib.mw_set_tuning(L.MW_TUNE_PANEL_WIDTH, 2, prev)
     assert lib.mw_set_tuning(L.MW_TUNE_BATCH_CTAS_PER_SM, 3, 0) == -3
+    assert lib.mw_get_tuning(L.MW_TUNE_GEMM_TILE, 3) == 0
+    assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, 4) == -3
+    assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, -1) == -3
+    assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, 2) == 0
+    assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, 0) == 2
+    assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE + 1, 3, 0) == -1
 
 
 def test_apply_from_cache(tmp_path):
@@ -72,6 +78,15 @@ def test_tuned_lu_is_bitwise_unchanged(tmp_path):
                 torch.cuda.synchronize()
                 assert np.array_equal(LU.cpu().numpy()[:, :, :260], LUo[:, :, :260]), (nb, rpc)
                 assert np.array_equal(piv.cpu().numpy(), pivo)
+        T.set_knob(0, 3, 64)
+        T.set_knob(1, 3, 8)
+        for tile in (1, 2, 3, 0):
+            T.set_knob(L.MW_TUNE_GEMM_TILE, 3, tile)
+            LU, piv, info = api.ludecomp(torch.from_numpy(A).cuda(), 3)
+            torch.cuda.synchronize()
+            assert np.array_equal(LU.cpu().numpy()[:, :, :260], LUo[:, :, :260]), tile
+            assert np.array_equal(piv.cpu().numpy(), pivo)
     finally:
         lib.mw_set_tuning(0, 3, old[0])
         lib.mw_set_tuning(1, 3, old[1])
+        lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, 0)
