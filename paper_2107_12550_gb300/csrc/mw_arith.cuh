@@ -272,15 +272,33 @@ __device__ __forceinline__ val<W> msub(const val<W>& c, const val<W>& a, const v
   return sub<W>(c, mul<W>(a, b));
 }
 
-// |x| vs |y| on the sign-adjusted words (|x0|, s x1, s x2, ...): -1, 0, +1
+// |x| vs |y| on the sign-adjusted words (|x0|, s x1, s x2, ...): -1, 0, +1,
+// with s = -1 where x0 < 0.  Decided on the bit patterns with integer
+// operations (the FP64 pipe is slow here and this sits on the pivot search's
+// critical path), with the floating-point comparison's outcome in every case:
+// a key that orders non-NaN doubles by value (+0 and -0 equal), negated for
+// the sign adjustment; a word pair with a NaN is unordered and skipped.
+__device__ __forceinline__ bool bits_nan(unsigned long long u) {
+  return (u & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ long long order_key(unsigned long long u) {
+  const long long mag = (long long)(u & 0x7fffffffffffffffull);
+  return (u >> 63) ? -mag : mag;
+}
 template <int W>
 __device__ __forceinline__ int cmp_abs(const val<W>& x, const val<W>& y) {
-  const double sx = (x.v[0] < 0.0) ? -1.0 : 1.0;
-  const double sy = (y.v[0] < 0.0) ? -1.0 : 1.0;
+  const unsigned long long x0 = (unsigned long long)__double_as_longlong(x.v[0]);
+  const unsigned long long y0 = (unsigned long long)__double_as_longlong(y.v[0]);
+  // x0 < 0: sign set, not a zero, not a NaN
+  const bool nx = (x0 >> 63) && (x0 << 1) != 0ull && !bits_nan(x0);
+  const bool ny = (y0 >> 63) && (y0 << 1) != 0ull && !bits_nan(y0);
 #pragma unroll
   for (int c = 0; c < W; ++c) {
-    const double a = fmul(sx, x.v[c]);
-    const double b = fmul(sy, y.v[c]);
+    const unsigned long long ux = (unsigned long long)__double_as_longlong(x.v[c]);
+    const unsigned long long uy = (unsigned long long)__double_as_longlong(y.v[c]);
+    if (bits_nan(ux) || bits_nan(uy)) continue;
+    const long long a = nx ? -order_key(ux) : order_key(ux);
+    const long long b = ny ? -order_key(uy) : order_key(uy);
     if (a > b) return 1;
     if (a < b) return -1;
   }
@@ -291,7 +309,7 @@ template <int W>
 __device__ __forceinline__ bool is_zero(const val<W>& x) {
   bool z = true;
 #pragma unroll
-  for (int c = 0; c < W; ++c) z = z && (x.v[c] == 0.0);
+  for (int c = 0; c < W; ++c) z = z && !nonzero(x.v[c]);
   return z;
 }
 

@@ -73,6 +73,25 @@ def test_arith_bitwise(w):
             assert np.array_equal(got, ref, equal_nan=True), (op, np.argwhere(got != ref)[:5])
 
 
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_cmpabs_special_values(w):
+    """The magnitude comparison of the pivot search on signed zeros,
+    infinities, NaNs, subnormals and ties in every word, against the
+    oracle's floating-point comparison (a NaN word pair is unordered)."""
+    special = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, -np.nan, 5e-324, -5e-324,
+                        2.2250738585072014e-308, -1.5, 1.5, 3.0, -3.0, 1e300, -1e-300])
+    rng = np.random.default_rng(71 + w)
+    cnt = 6000
+    x = special[rng.integers(0, len(special), (w, cnt))]
+    y = special[rng.integers(0, len(special), (w, cnt))]
+    y[:, :500] = x[:, :500]
+    y[0, 500:1500] = x[0, 500:1500]                  # equal leading words, later words decide
+    y[0, 1500:2000] = -x[0, 1500:2000]               # opposite signs of the same magnitude
+    got = host(api().arith(4, w, dev(x), dev(y)))
+    ref = oracle.arith(oracle.OP_CMPABS, w, x, y)
+    assert np.array_equal(got[0].astype(np.int64), ref), np.argwhere(got[0].astype(np.int64) != ref)[:5]
+
+
 def _lu_compare(A, w, update="plain"):
     LUg, pivg, infog = api().ludecomp(dev(A), w, update)
     LUo, pivo, infoo = oracle.lu(w, A)
