@@ -140,7 +140,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
   double* sl = smem + W * nb;        // [W][chunk]  multipliers of owned rows
   const PanelRows<W, RES> pr{A, lda, plane, k0, r0, chunk, sl + W * chunk, nb};
   __shared__ CandC<W> wred[kPanelThreads / 32];
-  __shared__ long long s_piv, s_best;
+  __shared__ long long s_piv;
   __shared__ int s_zero, s_wcta;
   constexpr int kRecVal = 1, kRecIdx = 1 + W, kRecRow = 2 + W;
 
@@ -179,19 +179,22 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       wred[warp].idx = bi;
     }
     __syncthreads();
-    if (tid == 0) {
+    // every thread combines the warps' candidates (integer comparisons), so
+    // the row copy needs no second barrier
+    long long brow;
+    {
       CandC<W> b = wred[0];
       for (int w = 1; w < kPanelThreads / 32; ++w)
         if (better<W>(wred[w].v, wred[w].idx, b.v, b.idx)) b = wred[w];
+      if (tid == 0) {
 #pragma unroll
-      for (int c = 0; c < W; ++c) __stcg(rec + kRecVal + c, b.v.v[c]);
-      __stcg(reinterpret_cast<long long*>(rec + kRecIdx), b.idx);
-      s_best = b.idx;
+        for (int c = 0; c < W; ++c) __stcg(rec + kRecVal + c, b.v.v[c]);
+        __stcg(reinterpret_cast<long long*>(rec + kRecIdx), b.idx);
+      }
+      brow = b.idx;
     }
-    __syncthreads();
     // publish the candidate's whole panel row, and old row k if this CTA owns it
     {
-      const long long brow = s_best;
       const bool own_k = (k >= r0 && k < r1);
       for (int e = tid; e < W * nb; e += kPanelThreads) {
         const int c = e / nb, j = e % nb;
@@ -200,11 +203,10 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
       }
     }
     __syncthreads();
+    // the barrier orders the CTA's record stores before tid 0's release
+    // store, which is cumulative over them (gpu scope)
     const unsigned long long tag = (unsigned long long)k + 1ull;
-    if (tid == 0) {
-      __threadfence();
-      st_release_u64(rec, tag);
-    }
+    if (tid == 0) st_release_u64(rec, tag);
     // (b) global argmax: thread q waits for CTA q's record and reads its
     // candidate (every CTA computes the same)
     {
