@@ -152,6 +152,57 @@ def test_lu_split_full_size_backward_error():
     assert eta <= 1e-28
 
 
+def _first_columns_bitwise(A, w, LUg, pivg, ks=8):
+    """The first ks columns of a full-size GPU factorisation against the
+    oracle's first ks elimination steps: pivots 0..ks-1 equal, and columns
+    0..ks-1 equal bitwise once the GPU's later row swaps are applied to the
+    oracle's (those columns are final after step ks-1 up to the swaps)."""
+    n = A.shape[1]
+    LUo, pivo, _ = oracle.lu_steps(w, A, ks)
+    assert np.array_equal(pivg[:ks], pivo[:ks])
+    cols = LUo[:w, :ks, :n].copy()
+    for k in range(ks, n):
+        p = int(pivg[k])
+        if p != k:
+            cols[:, :, [k, p]] = cols[:, :, [p, k]]
+    assert np.array_equal(LUg[:w, :ks, :n], cols)
+
+
+@pytest.mark.parametrize("n", [4096, 8192])
+def test_config3_full_size_plain_and_split(n):
+    """The large-LU configuration at full size, n = 4096 and 8192 DD (uniform
+    entries): the plain LU's pivots and first 8 columns bitwise equal to the
+    oracle's first 8 steps (sampled), the split LU's normwise backward error
+    <= 1e-28 (exact residual) with pivots equal to the plain LU's up to
+    near-ties."""
+    s = W.uniform_system(n, words=2, seed=0, b_words=2)
+    A = dev(s.A)
+    LUp, pivp, infop = api().ludecomp(A, 2, "plain")
+    assert int(infop.item()) == 0
+    pivp = host(pivp)
+    _first_columns_bitwise(s.A, 2, host(LUp), pivp)
+    del LUp
+    LUs, pivs, infos = api().ludecomp(A, 2, "split")
+    assert int(infos.item()) == 0
+    x = host(api().solve(LUs, pivs, dev(s.b), 2))
+    eta = _eta(s.A, s.b, x)
+    diff = int((host(pivs) != pivp).sum())
+    print(f"n={n} split: eta {eta:.2e}, pivots differing from plain {diff}")
+    assert eta <= 1e-28
+    assert diff <= n // 50
+
+
+def test_config2_n2048_td_lu_first_columns_bitwise():
+    """The bench's TD LU at n = 2048 (SVD-built, kappa 2^33), full size:
+    pivots and the first 8 columns bitwise equal to the oracle's first 8
+    elimination steps, with the GPU's later row swaps applied."""
+    s = W.svd_system(2048, 10.0, seed=0)
+    A3 = np.ascontiguousarray(s.A[:3])
+    LU, piv, info = api().ludecomp(dev(A3), 3)
+    assert int(info.item()) == 0
+    _first_columns_bitwise(A3, 3, host(LU), host(piv))
+
+
 def test_refine_split_dd_inner():
     s = W.svd_system(300, 10.0, seed=7)
     res = api().refine(dev(s.A), dev(s.b), 2, 200, update="split")
