@@ -339,8 +339,8 @@ __device__ __forceinline__ I192 recombine15(const uint32_t (&v)[15][CW], int cc)
 // x * 2^k for an integer-valued double x: the exponent field moved when the
 // result stays normal, the FP64 route otherwise
 __device__ __forceinline__ double scale_pow2(double x, int k) {
-  if (x == 0.0) return x;
   const long long bits = __double_as_longlong(x);
+  if (((unsigned long long)bits << 1) == 0ull) return x;   // +-0, tested off the FP64 pipe
   const int ex = (int)((bits >> 52) & 0x7ff);
   if (ex + k >= 1 && ex + k <= 2046) return __longlong_as_double(bits + ((long long)k << 52));
   return scale2_exact(x, k);
@@ -547,9 +547,27 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
     // epilogue: thread <-> row (TMEM lane) of the tile, half of the columns
     const int quarter = warp & 3;
     constexpr int kCols = kTileN / (kEpiWarps / 4);   // columns per epilogue warp
+    constexpr int CW = 2;                             // columns per TMEM read
     const int cpart = (warp - 2) / 4;
     const int rr = quarter * 32 + lane;
     const int64_t i = tm * kTileM + rr;
+    const int64_t jw = tn * kTileN + cpart * kCols;   // first column of this warp
+    // C entries of a chunk, loaded one chunk ahead so that their latency
+    // overlaps the MMAs (first chunk) or the previous chunk's work
+    auto load_chunk = [&](int ch, val<2> (&cv)[CW]) {
+#pragma unroll
+      for (int cc = 0; cc < CW; ++cc) {
+        const int64_t j = jw + ch * CW + cc;
+        if (i < m && j < N) cv[cc] = load<2>(C, planeC, i * crs + j * cjs);
+      }
+    };
+    val<2> cnext[CW];
+    load_chunk(0, cnext);
+    // the row and column scale exponents, also before the wait
+    const int ei = (i < m) ? ea[i] : 0;
+    int fbv[kCols];
+#pragma unroll
+    for (int k = 0; k < kCols; ++k) fbv[k] = (jw + k < N) ? fb[jw + k] : 0;
     bool ok = tc::mbar_wait(&sm.mma_done, 0);
     tc::tc_fence_after();
     // one decision per warp: the TMEM loads below are warp-collective
@@ -557,24 +575,14 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
     if (!ok) {
       if (threadIdx.x == 64) atomicExch(&status->timeout, 1u);
     } else {
-      const int ei = (i < m) ? ea[i] : 0;
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-      const int64_t jw = tn * kTileN + cpart * kCols;   // first column of this warp
-      int fbv[kCols];
-#pragma unroll
-      for (int k = 0; k < kCols; ++k) fbv[k] = (jw + k < N) ? fb[jw + k] : 0;
-      constexpr int CW = 2;                             // columns per TMEM read
 #pragma unroll
       for (int ch = 0; ch < kCols / CW; ++ch) {
         const int c0 = cpart * kCols + ch * CW;
-        // this chunk's C entries, loaded before the TMEM reads so that their
-        // latency overlaps them
         val<2> cvs[CW];
 #pragma unroll
-        for (int cc = 0; cc < CW; ++cc) {
-          const int64_t j = jw + ch * CW + cc;
-          if (i < m && j < N) cvs[cc] = load<2>(C, planeC, i * crs + j * cjs);
-        }
+        for (int cc = 0; cc < CW; ++cc) cvs[cc] = cnext[cc];
+        if (ch + 1 < kCols / CW) load_chunk(ch + 1, cnext);
         uint32_t v[kDiag][CW];
 #pragma unroll
         for (int d = 0; d < kDiag; ++d) tc::tmem_ld_x2(lane_base + (uint32_t)(d * kTileN + c0), v[d]);
