@@ -60,8 +60,14 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
 }
 
-__device__ __forceinline__ int exp_of_max(double mx) {  // ilogb(mx) + 2, mx > 0
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(mx);
+// magnitude bits of a double for a running maximum: |x| ordered as an
+// unsigned integer; a NaN counts as zero (as fmax skips it)
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  return (u > 0x7ff0000000000000ull) ? 0ull : u;
+}
+
+__device__ __forceinline__ int exp_of_max(unsigned long long bits) {  // ilogb(mx) + 2 of mx's bits, mx > 0
   const int ex = (int)((bits >> 52) & 0x7ff);
   int lg;
   if (ex) lg = ex - 1023;
@@ -71,8 +77,8 @@ __device__ __forceinline__ int exp_of_max(double mx) {  // ilogb(mx) + 2, mx > 0
 
 // floor(v * 2^sh) as a signed 128-bit integer (|result| < 2^126)
 __device__ __forceinline__ __int128 scaled_floor(double v, int sh) {
-  if (v == 0.0) return 0;
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  if ((bits << 1) == 0ull) return 0;
   const bool neg = (bits >> 63) != 0;
   const int ex = (int)((bits >> 52) & 0x7ff);
   unsigned long long m = bits & ((1ull << 52) - 1);
@@ -135,11 +141,12 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
 constexpr int kSliceRows = 16;   // rows (or columns) per CTA
 constexpr int kSliceThreads = kSliceRows * (kK / 8);
 
-// 8 entries (both words) of row or column r from k = kc*8; returns max |hi|
-__device__ __forceinline__ double slice_load8(const double* __restrict__ X, int64_t rs, int64_t ks, int64_t planeX,
+// 8 entries (both words) of row or column r from k = kc*8; returns the
+// magnitude bits of max |hi| (integer operations, off the FP64 pipe)
+__device__ __forceinline__ unsigned long long slice_load8(const double* __restrict__ X, int64_t rs, int64_t ks, int64_t planeX,
                                               bool ok, int kvalid, int64_t r, int kc, double (&hv)[8],
                                               double (&lv)[8]) {
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
 #pragma unroll
   for (int k8 = 0; k8 < 8; ++k8) {
     const int k = kc * 8 + k8;
@@ -147,7 +154,8 @@ __device__ __forceinline__ double slice_load8(const double* __restrict__ X, int6
       const int64_t idx = r * rs + (int64_t)k * ks;
       hv[k8] = X[idx];
       lv[k8] = X[planeX + idx];
-      mx = fmax(mx, fabs(hv[k8]));
+      const unsigned long long mb = mag_bits(hv[k8]);
+      mx = (mb > mx) ? mb : mx;
     } else {
       hv[k8] = 0.0;
       lv[k8] = 0.0;
@@ -189,7 +197,7 @@ __device__ __forceinline__ void slice_rows16(const double* __restrict__ L, int64
                                              int64_t planeL, int64_t m, int kvalid,
                                              unsigned char* __restrict__ aslices, int* __restrict__ ea,
                                              int64_t rbase) {
-  __shared__ double smx[kSliceRows][kK / 8];
+  __shared__ unsigned long long smx[kSliceRows][kK / 8];
   const int tid = threadIdx.x;
   const bool rows_fast = lrs == 1;
   const int rl = rows_fast ? (tid & (kSliceRows - 1)) : (tid >> 3);
@@ -199,14 +207,14 @@ __device__ __forceinline__ void slice_rows16(const double* __restrict__ L, int64
   double hv[8], lv[8];
   smx[rl][kc] = slice_load8(L, lrs, lks, planeL, ok, kvalid, r, kc, hv, lv);
   __syncthreads();
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
 #pragma unroll
-  for (int q = 0; q < kK / 8; ++q) mx = fmax(mx, smx[rl][q]);
-  const int e = (mx > 0.0) ? exp_of_max(mx) : 0;
+  for (int q = 0; q < kK / 8; ++q) mx = (smx[rl][q] > mx) ? smx[rl][q] : mx;
+  const int e = mx ? exp_of_max(mx) : 0;
   if (kc == 0) ea[r] = e;
   const int64_t tile = r / kTileM;
   const int rr = (int)(r % kTileM);
-  slice_store8(hv, lv, e, ok && mx > 0.0 && kc * 8 < kvalid,
+  slice_store8(hv, lv, e, ok && mx != 0ull && kc * 8 < kvalid,
                aslices + tile * (int64_t)kS * kASliceBytes + sw128_offset(rr, kc * 8), kASliceBytes);
 }
 
@@ -215,7 +223,7 @@ __device__ __forceinline__ void slice_cols16(const double* __restrict__ U, int64
                                              int64_t planeU, int64_t N, int kvalid,
                                              unsigned char* __restrict__ bslices, int* __restrict__ fb,
                                              int64_t jbase) {
-  __shared__ double smx[kSliceRows][kK / 8];
+  __shared__ unsigned long long smx[kSliceRows][kK / 8];
   const int tid = threadIdx.x;
   const bool cols_fast = ujs == 1;
   const int jl = cols_fast ? (tid & (kSliceRows - 1)) : (tid >> 3);
@@ -225,14 +233,14 @@ __device__ __forceinline__ void slice_cols16(const double* __restrict__ U, int64
   double hv[8], lv[8];
   smx[jl][kc] = slice_load8(U, ujs, uks, planeU, ok, kvalid, j, kc, hv, lv);
   __syncthreads();
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
 #pragma unroll
-  for (int q = 0; q < kK / 8; ++q) mx = fmax(mx, smx[jl][q]);
-  const int f = (mx > 0.0) ? exp_of_max(mx) : 0;
+  for (int q = 0; q < kK / 8; ++q) mx = (smx[jl][q] > mx) ? smx[jl][q] : mx;
+  const int f = mx ? exp_of_max(mx) : 0;
   if (kc == 0) fb[j] = f;
   const int64_t tile = j / kTileN;
   const int jj = (int)(j % kTileN);
-  slice_store8(hv, lv, f, ok && mx > 0.0 && kc * 8 < kvalid,
+  slice_store8(hv, lv, f, ok && mx != 0ull && kc * 8 < kvalid,
                bslices + tile * (int64_t)kS * kBSliceBytes + sw128_offset(jj, kc * 8), kBSliceBytes);
 }
 
