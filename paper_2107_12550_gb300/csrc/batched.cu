@@ -639,17 +639,6 @@ __global__ void k_bt_stats(int count, const BatchState* __restrict__ st, const i
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static int sm_count_b() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached <= 0) cached = 1;
-  }
-  return cached;
-}
-
 template <typename K>
 static int set_smem(K kern, size_t bytes) {
   MW_CUDA_CHECK(ensure_smem_limit(kern, bytes));
@@ -666,7 +655,7 @@ static int lu_batched_launch(int count, int nmax, const int* order, const int* n
   int rc = set_smem(k_lu_batched<W>, shmem);
   if (rc) return rc;
   ProfScope ps(kPhBatchLu, s);
-  const int grid = std::min(count, std::max(1, tune_get(MW_TUNE_BATCH_CTAS_PER_SM, W)) * sm_count_b());
+  const int grid = std::min(count, std::max(1, tune_get(MW_TUNE_BATCH_CTAS_PER_SM, W)) * device_sm_count());
   k_lu_batched<W><<<grid, kBatchThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, A, piv, info, cur);
   MW_LAUNCH_CHECK();
   return MW_OK;
@@ -683,7 +672,7 @@ static int solve_batched_launch(int count, int nmax, const int* order, const int
   int rc = set_smem(k_solve_batched<W>, shmem);
   if (rc) return rc;
   ProfScope ps(kPhBatchSolve, s);
-  const int grid = std::min(count, sm_count_b());
+  const int grid = std::min(count, device_sm_count());
   k_solve_batched<W><<<grid, kSolveThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x,
                                                        static_cast<const BatchState*>(st), cur);
   MW_LAUNCH_CHECK();

@@ -1,6 +1,7 @@
 // capi.cu -- the extern "C" entry points of libmwlu.so (declared and
 // documented in include/mwlu.h): argument checks, work-buffer sizes,
 // dispatch on the precision, status text and the FP64 microbenchmark.
+#include <atomic>
 #include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
@@ -36,6 +37,18 @@ cudaError_t ensure_smem_limit(const void* kernel, size_t bytes) {
     }
   done.push_back(Entry{kernel, dev, bytes});
   return cudaSuccess;
+}
+
+int device_sm_count() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cached[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  int v = (dev >= 0 && dev < kMaxDevices) ? cached[dev].load(std::memory_order_relaxed) : 0;
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  if (dev >= 0 && dev < kMaxDevices) cached[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 }  // namespace mw
 

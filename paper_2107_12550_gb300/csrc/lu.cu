@@ -17,7 +17,6 @@
 // rounded multiply and subtraction, so the plain form is bitwise identical
 // to unblocked elimination.
 #include <algorithm>
-#include <atomic>
 #include <cuda_runtime.h>
 
 #include "mw_arith.cuh"
@@ -650,24 +649,11 @@ template <> struct GemmVariant<4, 1> { static constexpr int TM = 1, TN = 2; };
 template <> struct GemmVariant<4, 2> { static constexpr int TM = 1, TN = 1; };
 constexpr int kGemmVariants = 3;
 
-static int gemm_sm_count() {
-  static std::atomic<int> cached{0};
-  int v = cached.load(std::memory_order_relaxed);
-  if (!v) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    if (v <= 0) v = 1;
-    cached.store(v, std::memory_order_relaxed);
-  }
-  return v;
-}
-
 template <int W, int V>
 static int64_t gemm_variant_cost(int64_t m, int64_t N) {
   constexpr int BM = 16 * GemmVariant<W, V>::TM, BN = 16 * GemmVariant<W, V>::TN;
   const int64_t tiles = ((m + BM - 1) / BM) * ((N + BN - 1) / BN);
-  const int64_t sms = gemm_sm_count();
+  const int64_t sms = device_sm_count();
   // the CTAs resident on an SM share its FP64 pipe, so an SM's time is the
   // number of its tiles times the tile size, however many run at once
   return ((tiles + sms - 1) / sms) * BM * BN;
@@ -928,23 +914,12 @@ k_bgemm_plain(BatchView bv, const TileEntry* __restrict__ tiles, int k0, double*
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
-static int sm_count() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached <= 0) cached = 1;
-  }
-  return cached;
-}
-
 template <int W>
 int launch_panel(double* A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
                  int64_t* piv, int64_t* info, char* ws, cudaStream_t s) {
   const int64_t rows = n - k0;
   const int rpc = std::max(1, tune_get(MW_TUNE_PANEL_ROWS_PER_CTA, W));
-  int G = (int)std::min<int64_t>((rows + rpc - 1) / rpc, sm_count());
+  int G = (int)std::min<int64_t>((rows + rpc - 1) / rpc, device_sm_count());
   G = std::max(1, std::min(G, kMaxPanelCtas));
   const int64_t chunk = (rows + G - 1) / G;
   // the CTA's rows of the panel stay in shared memory when they fit

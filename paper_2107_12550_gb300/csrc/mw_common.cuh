@@ -94,6 +94,9 @@ inline cudaError_t ensure_smem_limit(K* kernel, size_t bytes) {
   return ensure_smem_limit(reinterpret_cast<const void*>(kernel), bytes);
 }
 
+// the current device's SM count (cached per device; 1 if it cannot be read)
+int device_sm_count();
+
 }  // namespace mw
 
 // record the last CUDA error of the library for mw_last_cuda_error()

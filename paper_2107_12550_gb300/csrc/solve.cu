@@ -244,17 +244,6 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
   }
 }
 
-static int sm_count_solve() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached <= 0) cached = 1;
-  }
-  return cached;
-}
-
 int perm_launch(int64_t n, const int64_t* piv, int* perm, cudaStream_t s) {
   ProfScope ps(kPhPerm, s);
   const size_t shmem = (n <= kPermSmemMax) ? 8 * (size_t)n : 0;
@@ -273,12 +262,12 @@ int solve_with_perm(int64_t n, const double* LU, int64_t lda, const double* b, d
   const int64_t plane = lda * n;
   ProfScope ps(kPhSolve, s);
   const int64_t nblk = solve_nblk(n);
-  int64_t G = std::min<int64_t>(nblk, 4 * (int64_t)sm_count_solve());
+  int64_t G = std::min<int64_t>(nblk, 4 * (int64_t)device_sm_count());
   if (nblk > G * kSolveMaxOwned) return MW_EUNSUPPORTED;
   G = std::max<int64_t>(G, (nblk + kSolveMaxOwned - 1) / kSolveMaxOwned);
   MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kSolveWsPerm, s));
   {
-    const int pg = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)sm_count_solve());
+    const int pg = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)device_sm_count());
     k_solve_prep<W><<<std::max(pg, 1), 256, 0, s>>>(LU, lda, plane, n, ws);
     MW_LAUNCH_CHECK();
   }
