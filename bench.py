@@ -328,6 +328,41 @@ def extras(A, b, n, steps, peak_fp64):
                                 "phase_ms": {k: v[0] for k, v in prof8.items() if v[1]}}
     del A8, wk8
     torch.cuda.empty_cache()
+    # the standalone block matrix product C = A B, DD, 4096 x 4096 x 1024,
+    # plain vs split (DD-Gop/s = 2 m N K / t: a multiword multiply and an
+    # addition per term)
+    mg, kg = 4096, 1024
+    rg = np.random.default_rng(5)
+    ga = np.zeros((2, kg, mg))
+    ga[0] = rg.uniform(-1, 1, (kg, mg))
+    ga[1] = ga[0] * np.ldexp(rg.uniform(-1, 1, (kg, mg)), -53)
+    gb = np.zeros((2, mg, kg))
+    gb[0] = rg.uniform(-1, 1, (mg, kg))
+    gb[1] = gb[0] * np.ldexp(rg.uniform(-1, 1, (mg, kg)), -53)
+    gA = torch.from_numpy(ga).cuda()
+    gB = torch.from_numpy(gb).cuda()
+    gC = torch.empty((2, mg, mg), dtype=torch.float64, device="cuda")
+    del ga, gb
+    gm = {}
+    for upd, reps in (("plain", 1), ("split", 3)):
+        wkg = api.workspace(L.MW_OP_GEMM, 2, 1 if upd == "split" else 0, mg)
+
+        def gstep():
+            gC.zero_()
+            return api.gemm_add(gC, gA, gB, mg, 2, upd, work=wkg)
+        gstep()
+        t, _ = _time(gstep, reps, stream)
+        gm[upd] = t
+    tiles = -(-mg // 128) * -(-mg // 16)
+    mma = tiles * (kg // 64) * 120 * 2 * 128 * 16 * 64
+    out["gemm_dd_4096x4096x1024"] = {
+        "plain_ms": gm["plain"], "split_ms": gm["split"],
+        "plain_dd_gops": 2.0 * mg * mg * kg / (gm["plain"] * 1e-3) / 1e9,
+        "split_dd_gops": 2.0 * mg * mg * kg / (gm["split"] * 1e-3) / 1e9,
+        "split_mma_tflops": mma / (gm["split"] * 1e-3) / 1e12,
+        "workload": "C = A B from a zero C (mw_gemm_add), DD entries uniform in [-1, 1]"}
+    del gA, gB, gC
+    torch.cuda.empty_cache()
     # batches of 4096 TD and DD systems, n in [16, 256], one RHS (x_true = ones)
     n_list = [int(v) for v in W.batch_sizes(4096, 16, 256, seed=0)]
     mats = [W.uniform_matrix(m, 3, seed=W.system_seed(0, s), lda=m) for s, m in enumerate(n_list)]

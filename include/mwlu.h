@@ -195,6 +195,22 @@ int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K, double* C
                 size_t work_bytes, void* stream);
 
 /*
+ * mw_gemm_add -- C += A * B: the paper's multiword block matrix product
+ * (BNCmatmul, Section 2) as a standalone call; with C zero on entry it is
+ * C = A * B.  Arguments, layouts, work buffer and return codes as
+ * mw_gemm_sub.
+ *   MW_UPDATE_PLAIN: each entry applies c = c + a_t * b_t for t = 0..K-1 in
+ *           order (a rounded multiword multiply, then a rounded addition).
+ *   MW_UPDATE_SPLIT: per 64-wide slab of K, C + (slab product) formed
+ *           exactly and rounded once to DD (the slab product as for
+ *           mw_gemm_sub, error at most 2^-107 max_t|a_it| max_t|b_tj| per
+ *           entry and slab).
+ */
+int mw_gemm_add(int prec, int update, int64_t m, int64_t N, int64_t K, double* C, int64_t ldc,
+                const double* A, int64_t lda, const double* B, int64_t ldb, void* work,
+                size_t work_bytes, void* stream);
+
+/*
  * Batches of independent systems of uneven order (one launch per step for
  * the whole batch: the batched persistent form of the method).
  *   count    number of systems; n_host: HOST int32[count], 1 <= n[s] <= 1024.

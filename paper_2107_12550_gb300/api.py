@@ -144,11 +144,7 @@ def refine(A: torch.Tensor, b: torch.Tensor, inner_prec="td", target_bits: int =
     return RefineResult(x, rc, int(stats[0]), int(stats[1]), int(stats[2]))
 
 
-def gemm_sub(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, prec=None, update="plain", *,
-             work: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-    """C -= A B in multiword arithmetic on the leading m rows (in place;
-    returns C).  C: (w, N, ldc), A: (w, K, lda), B: (w, N, ldb), component
-    planes, column-major."""
+def _gemm(name: str, C, A, B, m, prec, update, work, stream):
     for t, nm in ((C, "C"), (A, "A"), (B, "B")):
         _check_mat(t, nm)
     w = _prec(prec) if prec is not None else C.shape[0]
@@ -158,9 +154,34 @@ def gemm_sub(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, prec=Non
     ldb = B.shape[2]
     if work is None:
         work = workspace(L.MW_OP_GEMM, w, u, max(m, N), C.device)
-    L.check("mw_gemm_sub", L.lib().mw_gemm_sub(w, u, m, N, K, _ptr(C), ldc, _ptr(A), lda, _ptr(B), ldb,
-                                               _ptr(work), work.numel(), _stream(stream)))
+    L.check(name, getattr(L.lib(), name)(w, u, m, N, K, _ptr(C), ldc, _ptr(A), lda, _ptr(B), ldb,
+                                         _ptr(work), work.numel(), _stream(stream)))
     return C
+
+
+def gemm_sub(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, prec=None, update="plain", *,
+             work: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """C -= A B in multiword arithmetic on the leading m rows (in place;
+    returns C).  C: (w, N, ldc), A: (w, K, lda), B: (w, N, ldb), component
+    planes, column-major."""
+    return _gemm("mw_gemm_sub", C, A, B, m, prec, update, work, stream)
+
+
+def gemm_add(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, prec=None, update="plain", *,
+             work: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """C += A B (the block matrix product; C = A B from a zero C), in place
+    on the leading m rows; returns C.  Shapes as gemm_sub."""
+    return _gemm("mw_gemm_add", C, A, B, m, prec, update, work, stream)
+
+
+def gemm(A: torch.Tensor, B: torch.Tensor, m: int, prec=None, update="plain", *,
+         work: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """C = A B in multiword arithmetic: a new (w, N, m) tensor."""
+    _check_mat(A, "A")
+    _check_mat(B, "B")
+    w = _prec(prec) if prec is not None else A.shape[0]
+    C = torch.zeros((w, B.shape[1], max(m, 1)), dtype=torch.float64, device=A.device)
+    return gemm_add(C, A, B, m, w, update, work=work, stream=stream)
 
 
 # ---------------------------------------------------------------------------

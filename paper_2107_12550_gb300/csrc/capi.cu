@@ -206,9 +206,9 @@ extern "C" int mw_refine(int64_t n, const double* A, int64_t lda, int a_words, c
                              work_bytes, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K, double* C, int64_t ldc,
-                           const double* A, int64_t lda, const double* B, int64_t ldb, void* work,
-                           size_t work_bytes, void* stream) {
+static int gemm_impl(int prec, int update, int64_t m, int64_t N, int64_t K, double* C, int64_t ldc,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, void* work, size_t work_bytes,
+                     void* stream, bool plus) {
   if (!prec_ok(prec)) return -1;
   if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
   if (m < 0) return -3;
@@ -230,17 +230,29 @@ extern "C" int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K
   const int64_t pc = ldc * N, pa = lda * K, pb = ldb * N;
   if (update == MW_UPDATE_PLAIN) {
     switch (prec) {
-      case 2: return mw::launch_gemm_plain_ptr<2>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s);
-      case 3: return mw::launch_gemm_plain_ptr<3>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s);
-      default: return mw::launch_gemm_plain_ptr<4>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s);
+      case 2: return mw::launch_gemm_plain_ptr<2>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s, plus);
+      case 3: return mw::launch_gemm_plain_ptr<3>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s, plus);
+      default: return mw::launch_gemm_plain_ptr<4>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s, plus);
     }
   }
   for (int64_t k0 = 0; k0 < K; k0 += 64) {
     const int rc = mw::split_gemm_sub_dd(m, N, C, ldc, pc, A + k0 * lda, lda, pa, B + k0, ldb, pb,
-                                         static_cast<char*>(work), work_bytes, s);
+                                         static_cast<char*>(work), work_bytes, s, plus);
     if (rc) return rc;
   }
   return MW_OK;
+}
+
+extern "C" int mw_gemm_sub(int prec, int update, int64_t m, int64_t N, int64_t K, double* C, int64_t ldc,
+                           const double* A, int64_t lda, const double* B, int64_t ldb, void* work,
+                           size_t work_bytes, void* stream) {
+  return gemm_impl(prec, update, m, N, K, C, ldc, A, lda, B, ldb, work, work_bytes, stream, false);
+}
+
+extern "C" int mw_gemm_add(int prec, int update, int64_t m, int64_t N, int64_t K, double* C, int64_t ldc,
+                           const double* A, int64_t lda, const double* B, int64_t ldb, void* work,
+                           size_t work_bytes, void* stream) {
+  return gemm_impl(prec, update, m, N, K, C, ldc, A, lda, B, ldb, work, work_bytes, stream, true);
 }
 
 // ---------------------------------------------------------------------------

@@ -533,8 +533,10 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // K chunks of KT staged in shared memory, double-buffered: the copies of
 // chunk t+1 (cp.async, zero-filled outside the matrix) run while chunk t is
-// consumed.  Each entry of C still receives its updates in ascending t.
-template <int W, int TM, int TN>
+// consumed.  Each entry of C still receives its updates in ascending t:
+// c -= l_t u_t, or with ADD c += l_t u_t (a rounded multiword multiply, then
+// a rounded addition or subtraction).
+template <int W, int TM, int TN, bool ADD = false>
 __device__ __forceinline__ void gemm_plain_tile(double* __restrict__ C, int64_t ldc, int64_t planeC,
                                                 const double* __restrict__ L, int64_t ldl, int64_t planeL,
                                                 const double* __restrict__ U, int64_t ldu, int64_t planeU,
@@ -604,7 +606,8 @@ __device__ __forceinline__ void gemm_plain_tile(double* __restrict__ C, int64_t 
 #pragma unroll
       for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < TN; ++b) acc[a][b] = msub<W>(acc[a][b], l[a], u[b]);
+        for (int b = 0; b < TN; ++b)
+          acc[a][b] = ADD ? add<W>(acc[a][b], mul<W>(l[a], u[b])) : msub<W>(acc[a][b], l[a], u[b]);
     }
     __syncthreads();   // every thread is done with `buf` before it is refilled
   }
@@ -617,12 +620,13 @@ __device__ __forceinline__ void gemm_plain_tile(double* __restrict__ C, int64_t 
     }
 }
 
-template <int W, int TM, int TN>
+template <int W, int TM, int TN, bool ADD>
 __global__ void __launch_bounds__(256)
 k_gemm_plain(double* __restrict__ C, int64_t ldc, int64_t planeC, const double* __restrict__ L,
              int64_t ldl, int64_t planeL, const double* __restrict__ U, int64_t ldu, int64_t planeU,
              int64_t m, int64_t N, int K) {
-  gemm_plain_tile<W, TM, TN>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K, blockIdx.x, blockIdx.y);
+  gemm_plain_tile<W, TM, TN, ADD>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K, blockIdx.x,
+                                  blockIdx.y);
 }
 
 // micro-tile of the batched trailing update (tile lists; many systems keep
@@ -679,28 +683,31 @@ int gemm_plain_variant(int64_t m, int64_t N) {
 template <int W, int V>
 static void launch_gemm_variant(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
                                 const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
-                                int64_t planeU, cudaStream_t s) {
+                                int64_t planeU, bool add, cudaStream_t s) {
   constexpr int TM = GemmVariant<W, V>::TM, TN = GemmVariant<W, V>::TN;
   dim3 grid((unsigned)((m + 16 * TM - 1) / (16 * TM)), (unsigned)((N + 16 * TN - 1) / (16 * TN)));
-  k_gemm_plain<W, TM, TN><<<grid, 256, 0, s>>>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K);
+  if (add)
+    k_gemm_plain<W, TM, TN, true><<<grid, 256, 0, s>>>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K);
+  else
+    k_gemm_plain<W, TM, TN, false><<<grid, 256, 0, s>>>(C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, m, N, K);
 }
 
 template <int W>
 int launch_gemm_plain_ptr(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
                           const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
-                          int64_t planeU, cudaStream_t s) {
+                          int64_t planeU, cudaStream_t s, bool add) {
   if (m <= 0 || N <= 0 || K <= 0) return MW_OK;
   switch (gemm_plain_variant<W>(m, N)) {
-    case 0: launch_gemm_variant<W, 0>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, s); break;
-    case 1: launch_gemm_variant<W, 1>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, s); break;
-    default: launch_gemm_variant<W, 2>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, s); break;
+    case 0: launch_gemm_variant<W, 0>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, add, s); break;
+    case 1: launch_gemm_variant<W, 1>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, add, s); break;
+    default: launch_gemm_variant<W, 2>(m, N, K, C, ldc, planeC, L, ldl, planeL, U, ldu, planeU, add, s); break;
   }
   MW_LAUNCH_CHECK();
   return MW_OK;
 }
-template int launch_gemm_plain_ptr<2>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t);
-template int launch_gemm_plain_ptr<3>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t);
-template int launch_gemm_plain_ptr<4>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t);
+template int launch_gemm_plain_ptr<2>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t, bool);
+template int launch_gemm_plain_ptr<3>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t, bool);
+template int launch_gemm_plain_ptr<4>(int64_t, int64_t, int, double*, int64_t, int64_t, const double*, int64_t, int64_t, const double*, int64_t, int64_t, cudaStream_t, bool);
 
 template <int W>
 int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m,

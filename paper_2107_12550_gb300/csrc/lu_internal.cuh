@@ -60,6 +60,7 @@ struct SplitOperands {
   int64_t crs, cjs, planeC;
   int64_t m, N;
   int K;
+  int plus = 0;   // 1: C += L U instead of C -= L U
 };
 // the product on the work buffer's slice area; its tensor-core launch is
 // counted under profile phase `phase`
@@ -75,13 +76,15 @@ int split_update_dd(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t
                     int64_t col0, int64_t N, int64_t k0, int nb, char* ws, size_t ws_bytes,
                     cudaStream_t s);
 size_t split_workspace_bytes(int64_t n, int nb);
+// C -= L U (plus: C += L U) for one 64-wide slab of the inner dimension
 int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
                       int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
-                      char* ws, size_t ws_bytes, cudaStream_t s);
+                      char* ws, size_t ws_bytes, cudaStream_t s, bool plus = false);
+// C -= L U (add: C += L U) in plain multiword arithmetic, any K
 template <int W>
 int launch_gemm_plain_ptr(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
                           const double* L, int64_t ldl, int64_t planeL, const double* U, int64_t ldu,
-                          int64_t planeU, cudaStream_t s);
+                          int64_t planeU, cudaStream_t s, bool add = false);
 
 // ---- batched blocked LU (batched.cu drives these per panel step) --------
 // A batch in the packed layout: system s has order n[s], its matrix of w

@@ -480,7 +480,7 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
                                            int64_t N, const unsigned char* __restrict__ aslices,
                                            const unsigned char* __restrict__ bslices,
                                            const int* __restrict__ ea, const int* __restrict__ fb,
-                                           DeviceStatus* status, int64_t tm, int64_t tn) {
+                                           DeviceStatus* status, int64_t tm, int64_t tn, bool plus = false) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzle atoms
   SplitSmem& sm = *reinterpret_cast<SplitSmem*>(
@@ -603,18 +603,20 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
           const int scale = ei + fbv[ch * CW + cc] - 128;
           const int64_t idx = i * crs + j * cjs;
           val<2> cv = cvs[cc];
-          // C - P exactly in the accumulator when C lies on the product's
-          // grid 2^scale within the 192-bit range (the usual case), then
-          // rounded greedily to DD; otherwise P rounded to DD and the DD
-          // subtraction
+          // C - P (plus: C + P) exactly in the accumulator when C lies on
+          // the product's grid 2^scale within the 192-bit range (the usual
+          // case), then rounded greedily to DD; otherwise P rounded to DD and
+          // the DD subtraction (addition)
           I192 T = R;
-          if (i192_sub_double(T, cv.v[0], scale) && i192_sub_double(T, cv.v[1], scale)) {
-            i192_neg(T);
+          const double c0 = plus ? -cv.v[0] : cv.v[0];
+          const double c1 = plus ? -cv.v[1] : cv.v[1];
+          if (i192_sub_double(T, c0, scale) && i192_sub_double(T, c1, scale)) {
+            if (!plus) i192_neg(T);
             i192_to_dd(T, scale, cv.v[0], cv.v[1]);
           } else {
             val<2> pr;
             i192_to_dd(R, scale, pr.v[0], pr.v[1]);
-            cv = sub<2>(cv, pr);
+            cv = plus ? add<2>(cv, pr) : sub<2>(cv, pr);
           }
           store<2>(C, planeC, idx, cv);
         }
@@ -638,7 +640,8 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
 __global__ void __launch_bounds__(kSplitThreads, 2)
 k_split_gemm(SplitOperands o, const unsigned char* __restrict__ aslices, const unsigned char* __restrict__ bslices,
              const int* __restrict__ ea, const int* __restrict__ fb, DeviceStatus* status) {
-  split_tile(o.C, o.crs, o.cjs, o.planeC, o.m, o.N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y);
+  split_tile(o.C, o.crs, o.cjs, o.planeC, o.m, o.N, aslices, bslices, ea, fb, status, blockIdx.x, blockIdx.y,
+             o.plus != 0);
 }
 
 // ---- batched forms: per active system of a batch at panel step k0 ----------
@@ -923,8 +926,9 @@ int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phas
 // C (m x N) -= L (m x 64) * U (64 x N), all DD component-planar column-major
 int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
                       int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
-                      char* ws, size_t ws_bytes, cudaStream_t s) {
+                      char* ws, size_t ws_bytes, cudaStream_t s, bool plus) {
   SplitOperands o;
+  o.plus = plus ? 1 : 0;
   o.L = L;
   o.lrs = 1;
   o.lks = ldl;

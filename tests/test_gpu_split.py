@@ -83,6 +83,70 @@ def test_gemm_sub_plain_bitwise(w, tile):
     assert np.array_equal(got[:, :, :m], ref)
 
 
+@pytest.mark.parametrize("tile", [0, 1, 3])
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_gemm_add_plain_bitwise(w, tile):
+    """C += A B (the standalone block matrix product) on every tile variant:
+    each entry applies c = c + a_t b_t in ascending t with the oracle's
+    multiword multiply and add, bitwise; gemm() from a zero C likewise."""
+    m, N, K = 70, 45, 21
+    C = _mat(w, m, N, 31)
+    A = _mat(w, m, K, 32)
+    B = _mat(w, K, N, 33)
+    lib = L.lib()
+    prev = lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, w, tile)
+    try:
+        got = host(api().gemm_add(dev(C), dev(A), dev(B), m, w, "plain"))
+        got0 = host(api().gemm(dev(A), dev(B), m, w, "plain"))
+    finally:
+        lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, w, prev)
+    for start, res in ((C[:, :, :m].copy(), got), (np.zeros((w, N, m)), got0)):
+        ref = start
+        for t in range(K):
+            a = np.repeat(A[:, t, :m][:, None, :], N, axis=1).reshape(w, -1)
+            b = np.repeat(B[:, :, t][:, :, None], m, axis=2).reshape(w, -1)
+            prod = oracle.arith(oracle.OP_MUL, w, a, b)
+            ref = oracle.arith(oracle.OP_ADD, w, ref.reshape(w, -1), prod).reshape(w, N, m)
+        assert np.array_equal(res[:, :, :m], ref)
+
+
+@pytest.mark.parametrize("update", ["plain", "split"])
+def test_gemm_add_is_negated_sub(update):
+    """Multiword addition and the greedy rounding are odd functions, so
+    C + A B = -((-C) - A B) bitwise, for both update forms."""
+    m, N, K = 150, 40, 128
+    C = _mat(2, m, N, 41)
+    A = _mat(2, m, K, 42)
+    B = _mat(2, K, N, 43)
+    ga = host(api().gemm_add(dev(C), dev(A), dev(B), m, 2, update))
+    gs = host(api().gemm_sub(dev(-C), dev(A), dev(B), m, 2, update))
+    assert np.array_equal(ga[:, :, :m], -gs[:, :, :m])
+
+
+def test_gemm_add_split_error_per_result():
+    """Split C += A B: per result, |C_out - (C + A B)| minus the final DD
+    rounding is at most 2^-104 max|a| max|b| (exact products from the oracle)."""
+    m, N, K = 130, 70, 64
+    C = _mat(2, m, N, 51)
+    A = _mat(2, m, K, 52, scale_rows=True)
+    B = _mat(2, K, N, 53)
+    got = host(api().gemm_add(dev(C), dev(A), dev(B), m, 2, "split"))
+    worst = 0.0
+    for i in range(0, m, 3):
+        amax = np.max(np.abs(A[0, :, i]))
+        for j in range(0, N, 2):
+            bmax = np.max(np.abs(B[0, j, :K]))
+            xs = np.concatenate([A[0, :, i], A[0, :, i], A[1, :, i], A[1, :, i]])
+            ys = np.concatenate([B[0, j, :K], B[1, j, :K], B[0, j, :K], B[1, j, :K]])
+            P = oracle.exact_dot(xs, ys, 4)
+            exact = X.words_to_frac(C[:, j, i]) + X.words_to_frac(P)
+            err = abs(X.words_to_frac(got[:, j, i]) - exact)
+            allowed_rounding = Fraction(3, 2 ** 106) * abs(exact)
+            ratio = max(err - allowed_rounding, Fraction(0)) / (Fraction(amax) * Fraction(bmax))
+            worst = max(worst, float(ratio))
+    assert worst <= 2.0 ** -104
+
+
 @pytest.mark.parametrize("m,N,scaled", [(130, 70, False), (257, 33, True), (64, 32, False)])
 def test_gemm_sub_split_error_per_result(m, N, scaled):
     K = 64
