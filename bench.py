@@ -363,6 +363,27 @@ def extras(A, b, n, steps, peak_fp64):
         "workload": "C = A B from a zero C (mw_gemm_add), DD entries uniform in [-1, 1]"}
     del gA, gB, gC
     torch.cuda.empty_cache()
+    # Strassen's recursion over the block product, DD: plain at n = 2048
+    # (levels 0-2), split at n = 4096 (levels 0-1); DD-Gop/s counts the
+    # classical 2 n^3 operations
+    st = {}
+    for upd, ns, lv_list, reps in (("plain", 2048, (0, 1, 2), 1), ("split", 4096, (0, 1), 3)):
+        rs = np.random.default_rng(9)
+        sa = np.zeros((2, ns, ns))
+        sa[0] = rs.uniform(-1, 1, (ns, ns))
+        sa[1] = sa[0] * np.ldexp(rs.uniform(-1, 1, (ns, ns)), -53)
+        sA = torch.from_numpy(sa).cuda()
+        sB = torch.from_numpy(sa[:, ::-1, :].copy()).cuda()
+        del sa
+        sC = torch.empty_like(sA)
+        for lv in lv_list:
+            g = lambda: api.gemm_strassen(sA, sB, 2, upd, lv, out=sC)
+            g()
+            t, _ = _time(g, reps, stream)
+            st[f"{upd}_n{ns}_levels{lv}"] = {"ms": t, "dd_gops": 2.0 * ns ** 3 / (t * 1e-3) / 1e9}
+        del sA, sB, sC
+        torch.cuda.empty_cache()
+    out["gemm_strassen_dd"] = st
     # batches of 4096 TD and DD systems, n in [16, 256], one RHS (x_true = ones)
     n_list = [int(v) for v in W.batch_sizes(4096, 16, 256, seed=0)]
     mats = [W.uniform_matrix(m, 3, seed=W.system_seed(0, s), lda=m) for s, m in enumerate(n_list)]

@@ -211,6 +211,31 @@ int mw_gemm_add(int prec, int update, int64_t m, int64_t N, int64_t K, double* C
                 size_t work_bytes, void* stream);
 
 /*
+ * mw_gemm_strassen -- C = A * B for n x n multiword matrices by Strassen's
+ * recursion over the block matrix product (the paper's Strassen form of
+ * BNCmatmul, Section 2): `levels` levels of seven half-size products and 18
+ * rounded multiword additions (Strassen 1969; the order of the additions is
+ * listed in strassen.cu), then the block product from a zero C
+ * (mw_gemm_add's plain or split form) on blocks of n / 2^levels.
+ *   prec, update  as mw_gemm_add (split: MW_DD and (n >> levels) % 64 == 0).
+ *   levels  0..8; n must be divisible by 2^levels (else MW_EUNSUPPORTED).
+ *           levels = 0 is mw_gemm_add from a zero C.
+ *   A, B    device, prec planes (lda, n) / (ldb, n): n x n, not overwritten.
+ *   C       device, prec planes (ldc, n): overwritten with A * B; must not
+ *           overlap A or B.
+ *   work    mw_gemm_strassen_workspace_size(...) bytes (the temporaries:
+ *           9 (n/2^l)^2 prec doubles per level l, and the split scratch).
+ * The result differs from the classical product by roundings: the error
+ * bound grows by about a factor 12 per level instead of 2 (Higham, Accuracy
+ * and Stability of Numerical Algorithms, Section 23.2.2).
+ * Returns MW_OK, -i, MW_EUNSUPPORTED or MW_ECUDA.
+ */
+int mw_gemm_strassen_workspace_size(int prec, int update, int levels, int64_t n, size_t* bytes);
+int mw_gemm_strassen(int prec, int update, int levels, int64_t n, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, double* C, int64_t ldc, void* work, size_t work_bytes,
+                     void* stream);
+
+/*
  * Batches of independent systems of uneven order (one launch per step for
  * the whole batch: the batched persistent form of the method).
  *   count    number of systems; n_host: HOST int32[count], 1 <= n[s] <= 1024.

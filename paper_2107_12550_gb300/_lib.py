@@ -37,6 +37,8 @@ SIGNATURES = {
     "mw_arith": (_I, [_I, _I, _I64, _P, _P, _P, _P]),
     "mw_gemm_sub": (_I, [_I, _I, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ, _P]),
     "mw_gemm_add": (_I, [_I, _I, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ, _P]),
+    "mw_gemm_strassen_workspace_size": (_I, [_I, _I, _I, _I64, _P]),
+    "mw_gemm_strassen": (_I, [_I, _I, _I, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _SZ, _P]),
     "mw_peak_fp64": (_I, [ctypes.POINTER(_D), _P]),
     "mw_solve_noalloc": (_I, [_I, _I64, _P, _I64, _P, _P, _P, _P]),
     "mw_batch_workspace_size": (_I, [_I, _I, _I, _P, ctypes.POINTER(_SZ)]),

@@ -174,6 +174,31 @@ def gemm_add(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, prec=Non
     return _gemm("mw_gemm_add", C, A, B, m, prec, update, work, stream)
 
 
+def gemm_strassen(A: torch.Tensor, B: torch.Tensor, prec=None, update="plain", levels: int = 1, *,
+                  work: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    """C = A B for n x n multiword matrices by Strassen's recursion over the
+    block matrix product (`levels` levels).  A, B: (w, n, ld); returns C
+    (w, n, n) (or `out`)."""
+    _check_mat(A, "A")
+    _check_mat(B, "B")
+    w = _prec(prec) if prec is not None else A.shape[0]
+    u = UPDATE[update]
+    n = A.shape[1]
+    if out is None:
+        out = torch.empty((w, n, max(n, 1)), dtype=torch.float64, device=A.device)
+    _check_mat(out, "out")
+    if work is None:
+        nbytes = ctypes.c_size_t(0)
+        L.check("mw_gemm_strassen_workspace_size",
+                L.lib().mw_gemm_strassen_workspace_size(w, u, levels, n, ctypes.byref(nbytes)))
+        work = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=A.device)
+    L.check("mw_gemm_strassen", L.lib().mw_gemm_strassen(w, u, levels, n, _ptr(A), A.shape[2], _ptr(B), B.shape[2],
+                                                         _ptr(out), out.shape[2], _ptr(work), work.numel(),
+                                                         _stream(stream)))
+    return out
+
+
 def gemm(A: torch.Tensor, B: torch.Tensor, m: int, prec=None, update="plain", *,
          work: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """C = A B in multiword arithmetic: a new (w, N, m) tensor."""

@@ -255,6 +255,42 @@ extern "C" int mw_gemm_add(int prec, int update, int64_t m, int64_t N, int64_t K
   return gemm_impl(prec, update, m, N, K, C, ldc, A, lda, B, ldb, work, work_bytes, stream, true);
 }
 
+static int strassen_check(int prec, int update, int levels, int64_t n) {
+  if (!prec_ok(prec)) return -1;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
+  if (levels < 0 || levels > 8) return -3;
+  if (n < 0) return -4;
+  if (n % ((int64_t)1 << levels) != 0) return MW_EUNSUPPORTED;
+  if (update == MW_UPDATE_SPLIT && (prec != MW_DD || (n >> levels) % 64 != 0)) return MW_EUNSUPPORTED;
+  return MW_OK;
+}
+
+extern "C" int mw_gemm_strassen_workspace_size(int prec, int update, int levels, int64_t n, size_t* bytes) {
+  const int rc = strassen_check(prec, update, levels, n);
+  if (rc) return rc;
+  if (!bytes) return -5;
+  *bytes = mw::strassen_workspace_bytes(prec, update, levels, n);
+  return MW_OK;
+}
+
+extern "C" int mw_gemm_strassen(int prec, int update, int levels, int64_t n, const double* A, int64_t lda,
+                                const double* B, int64_t ldb, double* C, int64_t ldc, void* work,
+                                size_t work_bytes, void* stream) {
+  int rc = strassen_check(prec, update, levels, n);
+  if (rc) return rc;
+  if (n > 0 && !A) return -5;
+  if (lda < (n > 1 ? n : 1)) return -6;
+  if (n > 0 && !B) return -7;
+  if (ldb < (n > 1 ? n : 1)) return -8;
+  if (n > 0 && !C) return -9;
+  if (ldc < (n > 1 ? n : 1)) return -10;
+  if (n > 0 && !work) return -11;
+  if (work_bytes < mw::strassen_workspace_bytes(prec, update, levels, n)) return -12;
+  if (n == 0) return MW_OK;
+  return mw::strassen_run(prec, update, levels, n, A, lda, B, ldb, C, ldc, static_cast<char*>(work), work_bytes,
+                          static_cast<cudaStream_t>(stream));
+}
+
 // ---------------------------------------------------------------------------
 // element-wise arithmetic
 // ---------------------------------------------------------------------------

@@ -159,6 +159,12 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
                      const double* aux, char* ws, size_t ws_bytes, cudaStream_t s);
 int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s);
 
+// Strassen's recursion over the block matrix product (strassen.cu): C = A B,
+// n x n, n divisible by 2^levels (split: DD and (n >> levels) % 64 == 0)
+size_t strassen_workspace_bytes(int w, int update, int levels, int64_t n);
+int strassen_run(int w, int update, int levels, int64_t n, const double* A, int64_t lda, const double* B,
+                 int64_t ldb, double* C, int64_t ldc, char* ws, size_t ws_bytes, cudaStream_t s);
+
 // substitution (solve.cu); y is a w-plane vector work area of n
 template <int W>
 int solve_launch(int64_t n, const double* LU, int64_t lda, const int64_t* piv, const double* b,

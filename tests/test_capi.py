@@ -58,3 +58,25 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.mw_arith(9, 2, 4, 8, 8, 8, None) == -1
     assert lib.mw_strerror(L.MW_ESINGULAR).startswith(b"exactly zero pivot")
     assert lib.mw_version().startswith(b"mwlu")
+
+
+def test_strassen_workspace_argument_checks():
+    """mw_gemm_strassen_workspace_size (host only): sizes that the recursion
+    cannot split, the split form's DD-only and 64-multiple block rules, and
+    invalid arguments."""
+    import ctypes
+    from paper_2107_12550_gb300 import build as B
+    B.build()
+    from paper_2107_12550_gb300 import _lib as L
+    lib = L.lib()
+    nb = ctypes.c_size_t(0)
+    assert lib.mw_gemm_strassen_workspace_size(2, 0, 2, 102, ctypes.byref(nb)) == L.MW_EUNSUPPORTED   # 102 % 4
+    assert lib.mw_gemm_strassen_workspace_size(2, 1, 1, 192, ctypes.byref(nb)) == L.MW_EUNSUPPORTED   # 96 % 64
+    assert lib.mw_gemm_strassen_workspace_size(3, 1, 1, 256, ctypes.byref(nb)) == L.MW_EUNSUPPORTED   # split: DD only
+    assert lib.mw_gemm_strassen_workspace_size(5, 0, 1, 64, ctypes.byref(nb)) == -1
+    assert lib.mw_gemm_strassen_workspace_size(2, 2, 1, 64, ctypes.byref(nb)) == -2
+    assert lib.mw_gemm_strassen_workspace_size(2, 0, 9, 512, ctypes.byref(nb)) == -3
+    assert lib.mw_gemm_strassen_workspace_size(2, 0, 1, 64, None) == -5
+    # levels 2 at n = 256, plain DD: 9 x 2 x (128^2 + 64^2) doubles after a 256-byte header
+    assert lib.mw_gemm_strassen_workspace_size(2, 0, 2, 256, ctypes.byref(nb)) == 0
+    assert nb.value == 256 + 8 * 9 * 2 * (128 * 128 + 64 * 64)
