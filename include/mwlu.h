@@ -8,7 +8,10 @@
  * A x = b (Section 3, Eq. (1)) and the calls of its refinement listing
  * (Section 2, Listing 1): TDLUdecompPM(af, af_ch) -> mw_ludecomp,
  * SolveTDLSPM(xf, af, bf, af_ch) -> mw_solve, the long-precision residual
- * b - a*x -> mw_residual, and the whole loop -> mw_refine.
+ * b - a*x -> mw_residual, and the whole loop -> mw_refine.  The paper's
+ * multiword block matrix product (BNCmatmul, Section 2) -> mw_gemm_add
+ * (C += A B) and mw_gemm_sub (C -= A B), its Strassen form ->
+ * mw_gemm_strassen; batches of independent systems -> the *_batched calls.
  *
  * Numbers.  A multiword value of precision w is w binary64 words whose sum
  * is the value: w = 2 double-double (DD), 3 triple-double (TD), 4
