@@ -47,7 +47,7 @@ FP64_PER_MSUB = {2: 29, 3: 117, 4: 196}
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum over the 124
 # launches of one bench run (warm-up, one step, the end-to-end steps),
 # averaged per launch.  Must be re-measured whenever k_gemm_plain changes.
-GEMM_TD_TRAFFIC_PER_LAUNCH = 40.41e6
+GEMM_TD_TRAFFIC_PER_LAUNCH = 40.40e6
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

@@ -393,7 +393,7 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
  *                                the smaller on a tie (all three run a full
  *                                wave at the same rate); 1, 2, 3 force the
  *                                large, middle or small tile (DD 64x64,
- *                                32x64, 32x32; TD 32x64, 32x32, 16x32; QD
+ *                                32x64, 32x32; TD 32x64, 16x32, 16x16; QD
  *                                32x32, 16x32, 16x16, rows x columns)
  * mw_set_tuning returns the previous value, or -1 (param), -2 (prec) or
  * -3 (value) when invalid; mw_get_tuning returns the value or -1/-2.

@@ -646,8 +646,8 @@ template <> struct GemmVariant<2, 0> { static constexpr int TM = 4, TN = 4; };
 template <> struct GemmVariant<2, 1> { static constexpr int TM = 2, TN = 4; };
 template <> struct GemmVariant<2, 2> { static constexpr int TM = 2, TN = 2; };
 template <> struct GemmVariant<3, 0> { static constexpr int TM = 2, TN = 4; };
-template <> struct GemmVariant<3, 1> { static constexpr int TM = 2, TN = 2; };
-template <> struct GemmVariant<3, 2> { static constexpr int TM = 1, TN = 2; };
+template <> struct GemmVariant<3, 1> { static constexpr int TM = 1, TN = 2; };
+template <> struct GemmVariant<3, 2> { static constexpr int TM = 1, TN = 1; };
 template <> struct GemmVariant<4, 0> { static constexpr int TM = 2, TN = 2; };
 template <> struct GemmVariant<4, 1> { static constexpr int TM = 1, TN = 2; };
 template <> struct GemmVariant<4, 2> { static constexpr int TM = 1, TN = 1; };
