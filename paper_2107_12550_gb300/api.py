@@ -185,9 +185,13 @@ def gemm_strassen(A: torch.Tensor, B: torch.Tensor, prec=None, update="plain", l
     w = _prec(prec) if prec is not None else A.shape[0]
     u = UPDATE[update]
     n = A.shape[1]
+    if B.shape[1] != n or A.shape[0] < w or B.shape[0] < w:
+        raise ValueError("A and B must be n x n with at least `prec` planes each")
     if out is None:
         out = torch.empty((w, n, max(n, 1)), dtype=torch.float64, device=A.device)
     _check_mat(out, "out")
+    if out.shape[0] < w or out.shape[1] != n or out.shape[2] < n:
+        raise ValueError("out must hold `prec` planes of n x n")
     if work is None:
         nbytes = ctypes.c_size_t(0)
         L.check("mw_gemm_strassen_workspace_size",

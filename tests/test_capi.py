@@ -80,3 +80,18 @@ def test_strassen_workspace_argument_checks():
     # levels 2 at n = 256, plain DD: 9 x 2 x (128^2 + 64^2) doubles after a 256-byte header
     assert lib.mw_gemm_strassen_workspace_size(2, 0, 2, 256, ctypes.byref(nb)) == 0
     assert nb.value == 256 + 8 * 9 * 2 * (128 * 128 + 64 * 64)
+
+
+def test_python_binding_rejects_host_and_mismatched_operands():
+    """The binding checks device, dtype and shapes before any library call
+    (no GPU needed to see the errors)."""
+    import torch
+    import pytest as _pt
+    from paper_2107_12550_gb300 import api
+    A = torch.zeros((2, 8, 8), dtype=torch.float64)          # host tensor
+    with _pt.raises(ValueError):
+        api.gemm_strassen(A, A, 2, "plain", 1)
+    with _pt.raises(ValueError):
+        api.ludecomp(A, 2)
+    with _pt.raises(ValueError):
+        api.gemm_sub(A, A, A, 8, 2)
