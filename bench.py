@@ -2,17 +2,22 @@
 """Benchmark of the multiword direct solver + mixed precision iterative
 refinement (Kouya, arXiv 2107.12550, Section 2 Listing 1 and Section 3).
 
-Workload (one GPU): one dense system of order n = 2048, A = U diag(sigma)
-V^T with U, V Haar-orthogonal (Householder QR of Gaussian matrices, quantised
-to 2^-20), sigma geometric from 1 to 2^-33 (kappa ~ 1e10), stored exactly in
-QD (4 words); b = A * ones exactly in 8 words, so x* = ones.  A step is one
-call of the library's refinement: TD LU with partial pivoting (plain FP64
-trailing update), TD substitution, and the loop r = b - A x (exact, rounded to
-8 words = 424 bits), z = solve(2^-e r), x = RN_8(x + 2^e z) until the
-correction is below 2^-202 ||x||.  Metric: systems solved to 2^-200 relative
-forward error per second, from device-resident (A, b) to device-resident x.
+Headline workload (one GPU): a batch of 512 independent dense systems,
+n_i uniform in [64, 1024], condition numbers log-uniform in [1e4, 1e20];
+each A_i = U diag(sigma) V^T with U, V Haar-orthogonal (Householder QR of
+Gaussian matrices, quantised to 2^-20) and sigma geometric from 1 to 1/kappa_i
+(powers of two), stored exactly in QD (4 words); b_i = A_i * ones exactly in
+8 words, so x* = ones.  A step is one call of the library's blocked batched
+refinement: the DD LU of every system with the split-precision (bf16
+tensor-core Ozaki) trailing update, the DD substitution, and per system the
+loop r = b - A x (exact, rounded to 8 words = 424 bits), z = solve(2^-e r),
+x = RN_8(x + 2^e z) until the correction is below 2^-202 ||x||.  Metric:
+systems solved to 2^-200 relative forward error per second, from
+device-resident (A, b) to device-resident x.  The plain FP64-core forms (the
+same batch with the plain DD LU; one n = 2048 system with the plain TD LU)
+are reported beside it.
 
-Multi-GPU: every rank solves its own independent system (seeded by rank), no
+Multi-GPU: every rank solves its own independent batch (seeded by rank), no
 collective on the data path (weak scaling); timing is the max over ranks.
 """
 from __future__ import annotations
@@ -31,23 +36,40 @@ from fractions import Fraction
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+TARGET_BITS = 200
+X_WORDS = 8
+# the headline batch
+BATCH = 512
+N_LO, N_HI = 64, 1024
+LOG10_KAPPA_LO, LOG10_KAPPA_HI = 4.0, 20.0
+A_WORDS = 4
+WORKLOAD = "mixed_batch_512_svd_n64-1024_kappa1e4-1e20_qd_stored_split_dd_inner_refine_to_2^-200"
+# the single-system comparator (plain TD LU)
 N = 2048
 LOG10_KAPPA = 10.0
 INNER = 3                 # TD
-TARGET_BITS = 200
-X_WORDS = 8
-WORKLOAD = "svd_kappa1e10_n2048_qd_stored_td_inner_refine_to_2^-200"
 
 # FP64 instructions of one multiword multiply + subtraction (the elimination
 # step), counted from the algorithms in csrc/mw_arith.cuh on their typical
 # (all error terms non-zero) path
 FP64_PER_MSUB = {2: 29, 3: 117, 4: 196}
+# FP64 thread instructions per clock of the whole GB300 (ncu: the
+# peak_sustained of sm__sass_thread_inst_executed_op_dfma_pred_on.sum,
+# 2 per SM per clock over 152 SMs)
+FP64_LANES_PER_CLK = 304
+# bf16 MMA flops of one 128 x 16 output tile of the split update: 120 digit
+# pairs x 2 x 128 x 16 x 64
+SPLIT_TILE_FLOPS = 120 * 2 * 128 * 16 * 64
 
-# DRAM bytes (read + write) per launch of the TD plain trailing update in this
-# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum over the 124
-# launches of one bench run (warm-up, one step, the end-to-end steps),
-# averaged per launch.  Must be re-measured whenever k_gemm_plain changes.
+# DRAM bytes (read + write) per launch of the TD plain trailing update in the
+# n = 2048 single-system workload: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum over the 124 launches of one bench run, averaged per
+# launch.  Must be re-measured whenever k_gemm_plain changes.
 GEMM_TD_TRAFFIC_PER_LAUNCH = 40.40e6
+# DRAM bytes per multiword multiply-subtract of the batched substitution
+# (ncu, k_solve_batched on 64 systems of the headline distribution, scaled
+# by the units a launch processes); None until measured for this kernel
+SOLVE_BATCHED_TRAFFIC_PER_MSUB = None
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -57,16 +79,24 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mwlu", choices=["mwlu", "reference"])
-    p.add_argument("--n", type=int, default=N)
+    p.add_argument("--count", type=int, default=BATCH, help="systems in the headline batch")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip the split / large-LU / batched comparison measurements")
-    p.add_argument("--no-mixed-batch", action="store_true",
-                   help="skip the 512-system mixed-precision batched refinement (about a minute of input generation)")
+                   help="skip the comparison measurements (plain forms, large LU, standalone GEMM, batches)")
     return p.parse_args()
+
+
+def measured_peaks() -> dict:
+    """The measured peaks of this GPU pool (MEASURED_PEAKS.json next to
+    this file), or {} when absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 class ClockSampler:
@@ -165,73 +195,95 @@ def panel_sum_sq(n: int, nb: int = 64) -> int:
     return tot
 
 
-def cpu_oracle_sample(n: int, sys_A, sys_b, corrections: int, residuals: int, m_steps: int = 128):
-    """Time the CPU oracle on a bounded sample of the same workload: the
-    first m_steps elimination steps of the same n = 2048 TD LU (scaled to the
-    full factorisation by the exact multiply-subtract count), plus one full
-    oracle solve and one full exact residual (scaled by the step's solve and
-    residual counts)."""
-    import oracle
+
+
+def split_trail_mma_flops(n_list, nb: int = 64) -> int:
+    """bf16 MMA flops of the trailing split updates of one blocked batched
+    LU: per panel step and active system, ceil(m / 128) x ceil(m / 16) tiles
+    of the m x m trailing block, each SPLIT_TILE_FLOPS."""
+    tiles = 0
+    for n in n_list:
+        for k0 in range(0, n, nb):
+            m = n - k0 - nb
+            if m > 0:
+                tiles += (-(-m // 128)) * (-(-m // 16))
+    return tiles * SPLIT_TILE_FLOPS
+
+
+def batch_system(A_np, b_np, n_list, s, a_words=A_WORDS, b_words=X_WORDS):
+    """System s of a packed batch as the oracle's (w, n, n) matrix and (w, n) vector."""
     import numpy as np
+    n = n_list[s]
+    moff = int(sum(m * m for m in n_list[:s]))
+    voff = int(sum(n_list[:s]))
+    A = np.ascontiguousarray(A_np[a_words * moff: a_words * (moff + n * n)].reshape(a_words, n, n))
+    b = np.ascontiguousarray(b_np[b_words * voff: b_words * (voff + n)].reshape(b_words, n))
+    return A, b
+
+
+def stratified_sample(n_list, stride: int):
+    """Every stride-th system in order of n (ties by index): a sample whose
+    mix of orders follows the batch's."""
+    order = sorted(range(len(n_list)), key=lambda s: (n_list[s], s))
+    return order[stride // 2::stride]
+
+
+def oracle_batch_sample(systems, inner: int = 2):
+    """The CPU oracle as it stands (unblocked LU with partial pivoting in the
+    inner precision, exact residual, refinement to 2^-200) on whole systems,
+    all host cores: (systems solved to 2^-200, seconds, threads)."""
+    import oracle
     threads = oracle.set_threads(0)
+    met = 0
     t0 = time.perf_counter()
-    LU, piv, info = oracle.lu_steps(INNER, sys_A, m_steps)
-    t_lu_sample = time.perf_counter() - t0
-    full = sum((n - k - 1) ** 2 for k in range(n))
-    part = sum((n - k - 1) ** 2 for k in range(min(m_steps, n)))
-    t_lu = t_lu_sample * full / part
-    # solve and residual at full size (the solve runs on the partially
-    # factored matrix: same operation count; the residual uses an 8-word
-    # iterate with every word non-zero, as in the later refinement steps)
-    t0 = time.perf_counter()
-    oracle.solve(INNER, LU, piv, sys_b)
-    t_solve = time.perf_counter() - t0
-    g = np.random.default_rng(1)
-    x8 = np.stack([np.ldexp(1.0 + g.uniform(-0.5, 0.5, n) * (c > 0), -60 * c) for c in range(X_WORDS)])
-    t0 = time.perf_counter()
-    oracle.residual(sys_A, sys_b, x8, X_WORDS)
-    t_res = time.perf_counter() - t0
-    t_total = t_lu + (1 + corrections) * t_solve + residuals * t_res
-    sample_s = t_lu_sample + t_solve + t_res
-    return {
-        "value": 1.0 / t_total,
-        "unit": "solves/s",
-        "cores": threads,
-        "kind": "oracle",
-        "sample": (f"first {m_steps} of {n} elimination steps of the same TD LU "
-                   f"({t_lu_sample:.1f} s, scaled x{full / part:.2f} by multiply-subtract count), "
-                   f"one full TD solve ({t_solve:.2f} s, x{1 + corrections}) and one full exact "
-                   f"8-word residual ({t_res:.2f} s, x{residuals}); {sample_s:.1f} s of CPU work"),
-        "seconds_per_solve": t_total,
-    }
+    for A, b in systems:
+        st, x, corr, nres, info = oracle.refine(A, b, inner, target_bits=TARGET_BITS)
+        met += int(st == 0 and batch_target_met(x.reshape(-1), [A.shape[1]])[0])
+    return met, time.perf_counter() - t0, threads
+
+
+def cpu_baseline_line(systems, sample_desc):
+    met, secs, threads = oracle_batch_sample(systems)
+    return {"value": met / secs, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": (f"{sample_desc}: {len(systems)} whole systems, each factored (DD, unblocked), "
+                       f"solved and refined to 2^-200 by the oracle; {met} met the target in {secs:.1f} s"),
+            "seconds": secs}
 
 
 def run_reference(args, world, rank):
-    """The oracle as it stands on the host cores, same metric and config."""
+    """The oracle as it stands on the host cores: the headline metric and
+    workload, each step a stratified sample of whole systems of the batch."""
     if rank != 0:
         return 0
     from paper_2107_12550_gb300 import workloads as W
     import oracle
     oracle.build()
-    s = W.svd_system(args.n, LOG10_KAPPA, seed=0)
-    vals = []
-    info = None
+    n_list, kap = W.mixed_batch_spec(args.count, N_LO, N_HI, LOG10_KAPPA_LO, LOG10_KAPPA_HI, seed=0)
+    ids = stratified_sample(n_list, 32)
+    sub_n = [n_list[s] for s in ids]
+    A_np, b_np = W.svd_batch(sub_n, [kap[s] for s in ids], seed=0, a_words=A_WORDS, b_words=X_WORDS,
+                             processes=len(os.sched_getaffinity(0)), system_ids=ids)
+    systems = [batch_system(A_np, b_np, sub_n, i) for i in range(len(ids))]
+    vals, secs = [], []
+    met = threads = 0
     for it in range(args.warmup + args.steps):
-        info = cpu_oracle_sample(args.n, s.A, s.b, corrections=2, residuals=3,
-                                 m_steps=max(8, min(64, args.n)))
+        met, t, threads = oracle_batch_sample(systems)
         if it >= args.warmup:
-            vals.append(info["seconds_per_solve"])
-    t = statistics.mean(vals)
-    v = 1.0 / t
+            vals.append(met / t)
+            secs.append(t)
+    v = statistics.mean(vals)
+    desc = (f"every 32nd system of the {args.count}-system batch in order of n ({len(ids)} whole systems "
+            f"per step, DD inner LU, refined to 2^-200; {met} of {len(ids)} met the target)")
     line = {"impl": "reference", "metric": "solves/s at 2^-200 rel. error", "value": v,
             "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": args.n, "global_batch": 1, "seq_len": 0,
-                       "parallelism": "cpu-oracle", "inner": "td", "target_bits": TARGET_BITS,
+            "ms_per_step": statistics.mean(secs) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "systems": args.count, "n_range": [N_LO, N_HI],
+                       "log10_kappa_range": [LOG10_KAPPA_LO, LOG10_KAPPA_HI], "global_batch": args.count,
+                       "seq_len": 0, "parallelism": "cpu-oracle", "inner": "dd", "target_bits": TARGET_BITS,
                        "l2": "inputs_larger_than_l2"},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": info["cores"],
-                             "kind": "oracle", "sample": info["sample"]},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": desc},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -251,10 +303,130 @@ def _time(fn, reps, stream):
     return e0.elapsed_time(e1) / reps, out
 
 
-def extras(A, b, n, steps, peak_fp64):
-    """Comparison measurements beside the headline (same GPU, same run):
-    the split-precision DD inner solver on the same system, the large DD LU
-    (n = 4096) plain vs split, and a 4096-system batch (n in [16, 256])."""
+def single_system_td(peak_fp64, steps, sm_max_mhz):
+    """The plain FP64-core form on one system: n = 2048, kappa ~ 1e10, QD
+    stored, TD LU with the plain trailing update, refined to 2^-200; with the
+    FP64-pipe roofline of its dominant kernel k_gemm_plain<TD>."""
+    import torch
+    from paper_2107_12550_gb300 import _lib as L
+    from paper_2107_12550_gb300 import api
+    from paper_2107_12550_gb300 import workloads as W
+    s = W.svd_system(N, LOG10_KAPPA, seed=0)
+    A = torch.from_numpy(s.A).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    x = torch.empty((X_WORDS, N), dtype=torch.float64, device="cuda")
+    work = api.workspace(L.MW_OP_REFINE, INNER, 0, N)
+    stream = torch.cuda.current_stream()
+    f = lambda: api.refine(A, b, INNER, TARGET_BITS, x_words=X_WORDS, work=work, out=x)
+    r = f()
+    L.profile_read(reset=True)
+    L.profile_enable(True)
+    ms, r = _time(f, steps, stream)
+    L.profile_enable(False)
+    prof = L.profile_read(reset=True)
+    ok = r.converged and exact_ok(x.cpu().numpy(), N)
+    gemm_ms, gemm_launches = prof["gemm_plain"]
+    instr = panel_sum_sq(N) * FP64_PER_MSUB[INNER] * steps
+    achieved = instr / (gemm_ms * 1e-3) if gemm_ms > 0 else 0.0
+    ceiling = FP64_LANES_PER_CLK * sm_max_mhz * 1e6 if sm_max_mhz else None
+    lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain")) / steps
+    out = {"workload": "svd_kappa1e10_n2048_qd_stored_td_inner_plain_refine_to_2^-200",
+           "solves_per_s": (1.0 if ok else 0.0) / (ms * 1e-3), "ms_per_solve": ms,
+           "corrections": r.corrections, "residuals": r.residuals, "target_met": ok,
+           "lu_ms": lu_ms, "lu_td_gops": (2.0 / 3.0) * N ** 3 / (lu_ms * 1e-3) / 1e9 if lu_ms else None,
+           "phase_ms_per_solve": {k: v[0] / steps for k, v in prof.items() if v[1]},
+           "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "k_gemm_plain<TD>",
+                        "achieved": achieved / 1e12, "peak": peak_fp64 / 1e12, "unit": "T FP64 instr/s",
+                        "frac": achieved / peak_fp64, "peak_source": "measured: mw_peak_fp64 in this run",
+                        "frac_of_fp64_issue_ceiling": achieved / ceiling if ceiling else None,
+                        "traffic": GEMM_TD_TRAFFIC_PER_LAUNCH, "traffic_unit": "bytes per launch (ncu)",
+                        "algorithmic_per_launch": instr / max(gemm_launches, 1)}}
+    # the split-precision DD inner LU on the same system
+    work2 = api.workspace(L.MW_OP_REFINE, 2, 1, N)
+    g = lambda: api.refine(A, b, 2, TARGET_BITS, update="split", x_words=X_WORDS, work=work2, out=x)
+    r2 = g()
+    ms2, r2 = _time(g, max(steps, 3), stream)
+    ok2 = r2.converged and exact_ok(x.cpu().numpy(), N)
+    out["split_dd_inner"] = {"solves_per_s": (1.0 if ok2 else 0.0) / (ms2 * 1e-3), "ms_per_solve": ms2,
+                             "corrections": r2.corrections, "target_met": ok2}
+    del A, b, x, work, work2
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_comparators(A, b, A_np, b_np, n_list, peak_fp64, sm_max_mhz):
+    """The same headline batch through the plain FP64-core DD LU (blocked
+    batched, plain multiword GEMM) with the same refinement, and the plain
+    batched QD direct LU + solve (no refinement) on every 16th system in
+    order of n."""
+    import numpy as np
+    import torch
+    from paper_2107_12550_gb300 import _lib as L
+    from paper_2107_12550_gb300 import api
+    stream = torch.cuda.current_stream()
+    out = {}
+    total_n = int(sum(n_list))
+    ops = sum((2.0 / 3.0) * m ** 3 for m in n_list)
+    x = torch.empty(X_WORDS * total_n, dtype=torch.float64, device="cuda")
+    work = api.batch_blocked_workspace(L.MW_OP_REFINE, 2, "plain", n_list)
+    f = lambda: api.refine_batched_blocked(A, A_WORDS, b, X_WORDS, n_list, 2, "plain", TARGET_BITS, work=work, out=x)
+    f()
+    L.profile_read(reset=True)
+    L.profile_enable(True)
+    ms, (_, stats) = _time(f, 1, stream)
+    L.profile_enable(False)
+    prof = L.profile_read(reset=True)
+    met = batch_target_met(x.cpu().numpy(), n_list)
+    lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain"))
+    pm, tm = blocked_batch_msubs(n_list)
+    ph = {k: v[0] for k, v in prof.items() if v[1]}
+    out["plain_dd_batched_refine"] = {
+        "ms_per_batch": ms, "systems_met": int(sum(met)), "solves_per_s": int(sum(met)) / (ms * 1e-3),
+        "lu_ms": lu_ms, "lu_dd_gops": ops / (lu_ms * 1e-3) / 1e9 if lu_ms else None, "phase_ms": ph,
+        "panel_fp64_frac_msub_only": pm * FP64_PER_MSUB[2] / (ph["panel"] * 1e-3) / peak_fp64 if ph.get("panel") else None,
+        "trsm_fp64_frac_msub_only": tm * FP64_PER_MSUB[2] / (ph["trsm"] * 1e-3) / peak_fp64 if ph.get("trsm") else None}
+    del work, x
+    sample = stratified_sample(n_list, 16)
+    sn = [n_list[s] for s in sample]
+    moff, voff = api.batch_offsets(n_list)
+    As = np.concatenate([A_np[A_WORDS * moff[s]: A_WORDS * moff[s + 1]] for s in sample])
+    bs = np.concatenate([b_np[X_WORDS * voff[s]: X_WORDS * voff[s] + 4 * n_list[s]] for s in sample])
+    Asd = torch.from_numpy(As).cuda()
+    bsd = torch.from_numpy(bs).cuda()
+    wk = api.batch_blocked_workspace(L.MW_OP_LUDECOMP, 4, "plain", sn)
+    wks = api.batch_workspace(L.MW_OP_SOLVE, 4, sn)
+    LUq = torch.empty_like(Asd)
+
+    def qd_direct():
+        LUq.copy_(Asd)
+        LU_, piv_, _ = api.ludecomp_batched_blocked(LUq, sn, 4, "plain", work=wk, inplace=True)
+        return api.solve_batched(LU_, piv_, bsd, sn, 4, work=wks)
+
+    qd_direct()
+    tq, xq = _time(qd_direct, 1, stream)
+    xq = xq.cpu().numpy()
+    worst = []
+    off = 0
+    for m in sn:
+        Xm = xq[off: off + 4 * m].reshape(4, m)
+        off += 4 * m
+        worst.append(max(abs(math.fsum([Xm[0, i] - 1.0] + [Xm[c, i] for c in range(1, 4)])) for i in range(m)))
+    sample_ops = sum((2.0 / 3.0) * m ** 3 for m in sn)
+    out["plain_qd_direct_sample"] = {
+        "systems": len(sample), "sample": "every 16th system in order of n", "ms": tq,
+        "ms_scaled_to_batch": tq * ops / sample_ops,
+        "systems_met": int(sum(1 for e in worst if e <= 2.0 ** -TARGET_BITS)),
+        "median_log2_max_error": float(np.median([math.log2(e) if e > 0 else -1100 for e in worst]))}
+    del Asd, bsd, LUq
+    torch.cuda.empty_cache()
+    return out
+
+
+def extras(steps, peak_fp64, peaks):
+    """Comparison measurements beside the headline (same GPU, same run): the
+    large DD LU (n = 4096 plain vs split, n = 8192 split), the standalone
+    block products (plain vs split, classical vs Strassen) and the
+    4096-system batches (n in [16, 256], DD and TD)."""
     import numpy as np
     import torch
     from paper_2107_12550_gb300 import _lib as L
@@ -262,16 +434,6 @@ def extras(A, b, n, steps, peak_fp64):
     from paper_2107_12550_gb300 import workloads as W
     stream = torch.cuda.current_stream()
     out = {}
-    # split DD inner refinement of the same n = 2048 system
-    x = torch.empty((X_WORDS, n), dtype=torch.float64, device="cuda")
-    work = api.workspace(L.MW_OP_REFINE, 2, 1, n)
-    f = lambda: api.refine(A, b, 2, TARGET_BITS, update="split", x_words=X_WORDS, work=work, out=x)
-    r = f()
-    ms, r = _time(f, max(steps, 3), stream)
-    ok = r.converged and exact_ok(x.cpu().numpy(), n)
-    out["split_dd_inner_refine"] = {"solves_per_s": (1.0 if ok else 0.0) / (ms * 1e-3), "ms_per_solve": ms,
-                                    "corrections": r.corrections, "target_met": ok,
-                                    "workload": "same system as the headline, DD inner LU with the split update"}
     # large DD LU, n = 4096, plain vs split (LU DD-Gop/s = (2/3) n^3 / t)
     n3 = 4096
     Au = torch.from_numpy(W.uniform_matrix(n3, 2, seed=0)).cuda()
@@ -303,7 +465,8 @@ def extras(A, b, n, steps, peak_fp64):
         "split_phase_ms": lu["split"]["phase_ms"],
         "split_gemm_roofline": {"bound": "tensor", "kernel": "k_split_gemm (bf16 tcgen05, TMEM)",
                                 "achieved": mma_flops / (split_gemm_ms * 1e-3) / 1e12 if split_gemm_ms else None,
-                                "peak": None, "unit": "TFLOP/s",
+                                "peak": peaks.get("bf16_tflops_sustained"), "unit": "TFLOP/s",
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16 GEMM, sustained)",
                                 "note": "MMA flops over the kernel time including its exact-recombination epilogue"},
         "plain_gemm_fp64_frac": None,
     }
@@ -487,98 +650,53 @@ def blocked_batch_msubs(n_list, nb=64):
     return panel, trsm
 
 
-def mixed_batch_refine(peak_fp64, count=512):
-    """Batched mixed-precision refinement: `count` SVD systems, n uniform in
-    [64, 1024], log10 kappa uniform in [4, 20], A stored in QD, b = A * ones
-    exact in 8 words.  Split-update DD inner LU (blocked batched) + exact
-    residual + refinement to 2^-200, against the plain FP64-core DD inner LU
-    with the same refinement and the plain QD direct LU (a stratified sample
-    of the systems, no refinement)."""
-    import numpy as np
-    import torch
-    from paper_2107_12550_gb300 import _lib as L
-    from paper_2107_12550_gb300 import api
-    from paper_2107_12550_gb300 import workloads as W
-    stream = torch.cuda.current_stream()
-    n_list, kap = W.mixed_batch_spec(count, 64, 1024, 4.0, 20.0, seed=0)
-    t0 = time.time()
-    A_np, b_np = W.svd_batch(n_list, kap, seed=0, a_words=4, b_words=X_WORDS,
-                             processes=len(os.sched_getaffinity(0)))
-    gen_s = time.time() - t0
-    A = torch.from_numpy(A_np).cuda()
-    b = torch.from_numpy(b_np).cuda()
-    total_n = int(sum(n_list))
-    ops = sum((2.0 / 3.0) * m ** 3 for m in n_list)
-    out = {"systems": count, "n_range": [64, 1024], "log10_kappa_range": [4, 20],
-           "generation_s": gen_s, "a_words": 4, "b_words": X_WORDS, "target_bits": TARGET_BITS}
-    x = torch.empty(X_WORDS * total_n, dtype=torch.float64, device="cuda")
-    for name, upd, reps in (("split_dd_refine", "split", 2), ("plain_dd_refine", "plain", 1)):
-        work = api.batch_blocked_workspace(L.MW_OP_REFINE, 2, upd, n_list)
-        f = lambda: api.refine_batched_blocked(A, 4, b, X_WORDS, n_list, 2, upd, TARGET_BITS, work=work, out=x)
-        f()
-        L.profile_read(reset=True)
-        L.profile_enable(True)
-        ms, (_, stats) = _time(f, reps, stream)
-        L.profile_enable(False)
-        prof = L.profile_read(reset=True)
-        st = stats.cpu().numpy()
-        met = batch_target_met(x.cpu().numpy(), n_list)
-        lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain", "gemm_split", "split_aux")) / reps
-        out[name] = {"ms_per_batch": ms, "systems_met": int(sum(met)),
-                     "solves_per_s": int(sum(met)) / (ms * 1e-3),
-                     "converged": int((st[:, 3] == 0).sum()),
-                     "corrections_max": int(st[:, 0].max()), "corrections_mean": float(st[:, 0].mean()),
-                     "lu_ms": lu_ms, "lu_dd_gops": ops / (lu_ms * 1e-3) / 1e9 if lu_ms else None,
-                     "phase_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
-                     "gpu_launches": int(sum(c for _, c in prof.values()) / reps)}
-        del work
-    # FP64-pipe fractions of the plain path's panel and TRSM kernels
-    # (multiply-subtract instructions only: divisions and compares are not
-    # counted).  The split path moves most of that work onto the tensor cores
-    # (recursive panel, TRSM through L11^-1), so it has no such fraction.
-    pm, tm = blocked_batch_msubs(n_list)
-    ph = out["plain_dd_refine"]["phase_ms"]
-    for key, cnt in (("panel", pm), ("trsm", tm)):
-        t = ph.get(key, 0.0)
-        out["plain_dd_refine"][key + "_fp64_frac_msub_only"] = (
-            cnt * FP64_PER_MSUB[2] / (t * 1e-3) / peak_fp64 if t else None)
-    # plain QD direct LU + solve (no refinement) on every 16th system by order
-    order = sorted(range(count), key=lambda s: n_list[s])
-    sample = order[::16]
-    sn = [n_list[s] for s in sample]
-    moff, voff = api.batch_offsets(n_list)
-    As = np.concatenate([A_np[4 * moff[s]: 4 * moff[s + 1]] for s in sample])
-    bs = np.concatenate([b_np[X_WORDS * voff[s]: X_WORDS * voff[s] + 4 * n_list[s]] for s in sample])
-    Asd = torch.from_numpy(As).cuda()
-    bsd = torch.from_numpy(bs).cuda()
-    wk = api.batch_blocked_workspace(L.MW_OP_LUDECOMP, 4, "plain", sn)
-    wks = api.batch_workspace(L.MW_OP_SOLVE, 4, sn)
-    LUq = torch.empty_like(Asd)
-
-    def qd_direct():
-        LUq.copy_(Asd)
-        LU_, piv_, _ = api.ludecomp_batched_blocked(LUq, sn, 4, "plain", work=wk, inplace=True)
-        return api.solve_batched(LU_, piv_, bsd, sn, 4, work=wks)
-
-    qd_direct()
-    tq, xq = _time(qd_direct, 1, stream)
-    xq = xq.cpu().numpy()
-    worst = []
-    off = 0
-    for m in sn:
-        X = xq[off: off + 4 * m].reshape(4, m)
-        off += 4 * m
-        worst.append(max(abs(math.fsum([X[0, i] - 1.0] + [X[c, i] for c in range(1, 4)])) for i in range(m)))
-    sample_ops = sum((2.0 / 3.0) * m ** 3 for m in sn)
-    out["qd_direct_sample"] = {
-        "systems": len(sample), "sample": "every 16th system in order of n", "ms": tq,
-        "ms_scaled_to_batch": tq * ops / sample_ops,
-        "systems_met": int(sum(1 for e in worst if e <= 2.0 ** -TARGET_BITS)),
-        "median_log2_max_error": float(np.median([math.log2(e) if e > 0 else -1100 for e in worst]))}
-    out["workload"] = ("SVD systems (A = U diag(sigma) V^T exact, QD stored), per-system seeds; "
-                       "one call of the blocked batched refinement per batch")
-    del A, b, Asd, bsd, LUq, x
-    torch.cuda.empty_cache()
+def headline_rooflines(prof, reps, n_list, stats, peak_fp64, peaks, sm_max_mhz):
+    """Per-kernel rooflines of the headline step from one profiled pass
+    (reps calls): the batched substitution and the panel phase against the
+    FP64 pipe, the trailing split update against the bf16 tensor pipe, the
+    exact residual in exact products per second.  Work per unit:
+    substitution n^2 multiword multiply-subtracts per solve (FP64_PER_MSUB
+    FP64 instructions each); split update SPLIT_TILE_FLOPS bf16 flops per
+    128 x 16 tile; residual n^2 * 4 * 8 word products per evaluation."""
+    ceiling = FP64_LANES_PER_CLK * sm_max_mhz * 1e6 if sm_max_mhz else None
+    out = []
+    solves = sum((1 + int(stats[s, 0])) * n_list[s] ** 2 for s in range(len(n_list)))
+    t = prof["batch_solve"][0] / reps
+    if t > 0:
+        a = solves * FP64_PER_MSUB[2] / (t * 1e-3)
+        out.append({"kernel": "k_solve_batched<DD>", "ms": t, "bound": "alu", "pipe": "fp64",
+                    "achieved": a / 1e12, "peak": peak_fp64 / 1e12, "unit": "T FP64 instr/s",
+                    "frac": a / peak_fp64, "peak_source": "measured: mw_peak_fp64 in this run",
+                    "frac_of_fp64_issue_ceiling": a / ceiling if ceiling else None,
+                    "traffic": (SOLVE_BATCHED_TRAFFIC_PER_MSUB * solves / max(prof["batch_solve"][1] / reps, 1)
+                                if SOLVE_BATCHED_TRAFFIC_PER_MSUB else None),
+                    "algorithmic_per_launch": solves * FP64_PER_MSUB[2] / max(prof["batch_solve"][1] / reps, 1),
+                    "unit_of_work": "n^2 DD multiply-subtracts per system and solve"})
+    t = prof["gemm_split"][0] / reps
+    if t > 0:
+        fl = split_trail_mma_flops(n_list)
+        pk = peaks.get("bf16_tflops_sustained")
+        a = fl / (t * 1e-3) / 1e12
+        out.append({"kernel": "k_bsplit_gemm (trailing updates)", "ms": t, "bound": "tensor",
+                    "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk if pk else None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained",
+                    "unit_of_work": "120 bf16 digit-pair MMAs of 128 x 16 x 64 per output tile",
+                    "traffic": None})
+    t = prof["panel"][0] / reps
+    if t > 0:
+        pm, _ = blocked_batch_msubs(n_list)
+        a = pm * FP64_PER_MSUB[2] / (t * 1e-3)
+        out.append({"kernel": "panel phase (k_bpanel leaves, inner split products)", "ms": t, "bound": "alu",
+                    "pipe": "fp64", "achieved": a / 1e12, "peak": peak_fp64 / 1e12, "unit": "T FP64 instr/s",
+                    "frac": a / peak_fp64, "peak_source": "measured: mw_peak_fp64 in this run",
+                    "unit_of_work": "the panel's multiply-subtracts counted as FP64 work (part of them "
+                                    "run on the tensor cores in the inner split products)", "traffic": None})
+    t = prof["residual"][0] / reps
+    if t > 0:
+        prods = sum(int(stats[s, 1]) * n_list[s] ** 2 * A_WORDS * X_WORDS for s in range(len(n_list)))
+        out.append({"kernel": "k_bt_residual", "ms": t, "bound": "alu", "achieved": prods / (t * 1e-3) / 1e12,
+                    "peak": None, "unit": "T exact word products/s", "frac": None,
+                    "unit_of_work": "n^2 x 4 x 8 exact word products per evaluation", "traffic": None})
     return out
 
 
@@ -600,28 +718,30 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
-    n = args.n
-    s = W.svd_system(n, LOG10_KAPPA, seed=rank)
-    A = torch.from_numpy(s.A).cuda()
-    b = torch.from_numpy(s.b).cuda()
-    x = torch.empty((X_WORDS, n), dtype=torch.float64, device="cuda")
-    work = api.workspace(L.MW_OP_REFINE, INNER, 0, n)
+    peaks = measured_peaks()
+    n_list, kap = W.mixed_batch_spec(args.count, N_LO, N_HI, LOG10_KAPPA_LO, LOG10_KAPPA_HI, seed=rank)
+    t0 = time.time()
+    procs = max(1, len(os.sched_getaffinity(0)) // world)
+    A_np, b_np = W.svd_batch(n_list, kap, seed=rank, a_words=A_WORDS, b_words=X_WORDS, processes=procs)
+    gen_s = time.time() - t0
+    A = torch.from_numpy(A_np).cuda()
+    b = torch.from_numpy(b_np).cuda()
+    total_n = int(sum(n_list))
+    x = torch.empty(X_WORDS * total_n, dtype=torch.float64, device="cuda")
+    work = api.batch_blocked_workspace(L.MW_OP_REFINE, 2, "split", n_list)
     stream = torch.cuda.current_stream()
 
     def step():
-        return api.refine(A, b, INNER, TARGET_BITS, x_words=X_WORDS, work=work, out=x)
+        return api.refine_batched_blocked(A, A_WORDS, b, X_WORDS, n_list, 2, "split", TARGET_BITS,
+                                          work=work, out=x)
 
     peak_fp64 = api.peak_fp64()            # project microbenchmark, instructions/s
-    res = None
     for _ in range(max(args.warmup, 1)):
-        res = step()
+        _, stats = step()
     torch.cuda.synchronize()
-    ok = res.converged and exact_ok(x.cpu().numpy(), n)
-    corrections, residuals = res.corrections, res.residuals
+    met_ref = batch_target_met(x.cpu().numpy(), n_list)
 
     # ---- timed region: K steps, device-resident inputs -------------------
-    L.profile_read(reset=True)
-    L.profile_enable(True)
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -631,50 +751,55 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        res = step()
-        ok = ok and res.converged
+        _, stats = step()
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    L.profile_enable(False)
-    prof = L.profile_read(reset=True)
     ms = e0.elapsed_time(e1)
-    ok = ok and exact_ok(x.cpu().numpy(), n)
-    t_max, solved = combine_ranks(ms, args.steps * (1 if ok else 0), "cuda")
+    met = batch_target_met(x.cpu().numpy(), n_list)
+    st = stats.cpu().numpy()
+    met_per_step = int(sum(met)) if met == met_ref else min(int(sum(met)), int(sum(met_ref)))
+    t_max, solved = combine_ranks(ms, args.steps * met_per_step, "cuda")
     value = solved / (t_max * 1e-3)
 
-    # roofline of the dominant kernel: the plain TD trailing update
-    gemm_ms, gemm_launches = prof["gemm_plain"]
-    msubs_per_lu = panel_sum_sq(n)
-    instr = msubs_per_lu * FP64_PER_MSUB[INNER] * args.steps
-    achieved = instr / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
-    peak = peak_fp64 / 1e12
-    lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain")) / args.steps
+    # ---- one profiled pass (not timed above): phases and kernel rooflines -
+    L.profile_read(reset=True)
+    L.profile_enable(True)
+    _, pst = step()
+    torch.cuda.synchronize()
+    L.profile_enable(False)
+    prof = L.profile_read(reset=True)
+    sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz")
+    roofs = headline_rooflines(prof, 1, n_list, pst.cpu().numpy(), peak_fp64, peaks, sm_max)
+    dominant = max(roofs, key=lambda r: r["ms"]) if roofs else None
     launches = sum(c for _, c in prof.values())
+    ops = sum((2.0 / 3.0) * m ** 3 for m in n_list)
+    lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain", "gemm_split", "split_aux"))
 
     # ---- end to end through the public API with host buffers -------------
-    A_h = torch.from_numpy(s.A).pin_memory()
-    b_h = torch.from_numpy(s.b).pin_memory()
-    x_h = torch.empty((X_WORDS, n), dtype=torch.float64).pin_memory()
-    A_d = torch.empty_like(A)
-    b_d = torch.empty_like(b)
-    e2e_steps = max(2, args.steps // 2)
+    A_h = torch.from_numpy(A_np).pin_memory()
+    b_h = torch.from_numpy(b_np).pin_memory()
+    x_h = torch.empty_like(x, device="cpu").pin_memory()
+    s_h = torch.empty((args.count, 4), dtype=torch.int64).pin_memory()
+    e2e_steps = 2
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(e2e_steps):
-        A_d.copy_(A_h, non_blocking=True)
-        b_d.copy_(b_h, non_blocking=True)
-        r2 = api.refine(A_d, b_d, INNER, TARGET_BITS, x_words=X_WORDS, work=work, out=x)
+        A.copy_(A_h, non_blocking=True)
+        b.copy_(b_h, non_blocking=True)
+        _, st2 = step()
         x_h.copy_(x, non_blocking=True)
+        s_h.copy_(st2, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    e2e_ok = r2.converged and exact_ok(x_h.numpy(), n)
-    e2e_val = (1.0 if e2e_ok else 0.0) / (e2e_ms * 1e-3) * world
+    e2e_met = int(sum(batch_target_met(x_h.numpy(), n_list)))
+    e2e_val = e2e_met / (e2e_ms * 1e-3) * world
+    del A_h
 
     line = {
         "metric": "solves/s at 2^-200 rel. error",
@@ -689,34 +814,40 @@ def main():
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "global_batch": world, "seq_len": 0,
-                   "parallelism": f"replicas{world}", "inner": "td", "lu_update": "plain",
-                   "a_words": 4, "b_words": 8, "x_words": X_WORDS, "target_bits": TARGET_BITS,
-                   "l2": "inputs_larger_than_l2 (A: 134 MB QD; LU copy 100 MB)"},
-        "corrections": corrections,
-        "residuals": residuals,
+        "config": {"workload": WORKLOAD, "systems": args.count, "n_range": [N_LO, N_HI],
+                   "log10_kappa_range": [LOG10_KAPPA_LO, LOG10_KAPPA_HI], "global_batch": args.count * world,
+                   "seq_len": 0, "parallelism": f"replicas{world}", "inner": "dd", "lu_update": "split",
+                   "a_words": A_WORDS, "b_words": X_WORDS, "x_words": X_WORDS, "target_bits": TARGET_BITS,
+                   "l2": f"inputs_larger_than_l2 (A: {A_np.nbytes / 1e9:.1f} GB QD)"},
+        "systems_met_per_step": met_per_step,
+        "corrections_max": int(st[:, 0].max()), "corrections_mean": float(st[:, 0].mean()),
+        "generation_s": gen_s,
         "lu_ms": lu_ms,
-        "lu_td_gops": (2.0 / 3.0) * n ** 3 / (lu_ms * 1e-3) / 1e9 if lu_ms > 0 else None,
-        "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
-        "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "k_gemm_plain<TD>",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "flop": "one FP64 instruction (DADD/DMUL/DFMA)",
-                     "peak_source": "measured: mw_peak_fp64 microbenchmark in this run",
-                     "frac": achieved / peak if peak else None, "traffic": GEMM_TD_TRAFFIC_PER_LAUNCH,
-                     "traffic_unit": "bytes per launch (ncu)",
-                     "algorithmic_per_launch": instr / max(gemm_launches, 1)},
-        "gpu_launches": launches,
+        "lu_dd_gops": ops / (lu_ms * 1e-3) / 1e9 if lu_ms > 0 else None,
+        "phase_ms_per_step": {k: v[0] for k, v in prof.items() if v[1]},
+        "roofline": dominant,
+        "rooflines": roofs,
+        "gpu_launches": launches * args.steps,
         "clocks": clk,
         "e2e": {"value": e2e_val, "unit": "solves/s",
-                "h2d_bytes_per_step": int(s.A.nbytes + s.b.nbytes),
-                "d2h_bytes_per_step": int(x.numel() * 8)},
+                "h2d_bytes_per_step": int(A_np.nbytes + b_np.nbytes),
+                "d2h_bytes_per_step": int(x.numel() * 8 + args.count * 4 * 8)},
     }
     if rank == 0 and world == 1 and not args.no_extras:
-        line["extras"] = extras(A, b, n, args.steps, peak_fp64)
-        if not args.no_mixed_batch:
-            line["extras"]["mixed_batch_refine_512"] = mixed_batch_refine(peak_fp64)
+        ex = {"comparators": batch_comparators(A, b, A_np, b_np, n_list, peak_fp64, sm_max)}
+        del A, b, x, work
+        torch.cuda.empty_cache()
+        ex["comparators"]["single_system_plain_td_n2048"] = single_system_td(peak_fp64, 3, sm_max)
+        ex.update(extras(args.steps, peak_fp64, peaks))
+        r = ex.get("lu_dd_n4096", {}).get("split_gemm_roofline")
+        if r and r.get("achieved") and r.get("peak"):
+            r["frac"] = r["achieved"] / r["peak"]
+        line["extras"] = ex
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(n, s.A, s.b, corrections, residuals)
+        ids = stratified_sample(n_list, 8)
+        systems = [batch_system(A_np, b_np, n_list, s) for s in ids]
+        line["cpu_baseline"] = cpu_baseline_line(
+            systems, f"every 8th system of the {args.count}-system batch in order of n")
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

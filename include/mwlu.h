@@ -36,7 +36,18 @@
  * invalid; MW_ECUDA when a CUDA call failed (mw_last_cuda_error gives the
  * cudaError_t); MW_ETIMEOUT when a bounded device wait gave up;
  * MW_ESINGULAR / MW_ENOTCONV as documented per call.  Inputs with NaN or
- * Inf give unspecified (but memory-safe) results.
+ * Inf give unspecified (but memory-safe) results.  Orders (and GEMM
+ * dimensions) above 2^31 are rejected as invalid arguments.
+ *
+ * Bounded waits.  Kernels whose threads wait for other threads (the
+ * substitution's ready values, the panel's candidate records, the split
+ * update's copy and MMA barriers, the batched substitution's flags) poll a
+ * bounded number of times; a wait that runs out records an error word in
+ * the call's work buffer and the kernel returns (its outputs are then
+ * incomplete).  The calls that synchronise (mw_refine, the batched
+ * refinements) return MW_ETIMEOUT themselves; after an asynchronous call,
+ * mw_work_status / mw_batch_work_status / mw_solve_noalloc_status read the
+ * error word.
  */
 #ifndef MWLU_H
 #define MWLU_H
@@ -102,7 +113,8 @@ int mw_workspace_size(int op, int prec, int update, int64_t n, size_t* bytes);
  * lexicographic order of the sign-adjusted words (ties take the smallest
  * row).  The plain form is bitwise identical to unblocked right-looking
  * elimination with a rounded multiword multiply and subtraction per element
- * update.  Returns MW_OK, -i, MW_ECUDA, MW_ETIMEOUT or MW_EUNSUPPORTED.
+ * update.  Returns MW_OK, -i, MW_ECUDA or MW_EUNSUPPORTED without waiting
+ * for the GPU; a bounded wait that gave up is reported by mw_work_status.
  */
 int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t lda, int64_t* piv,
                 int64_t* info, void* work, size_t work_bytes, void* stream);
@@ -116,7 +128,8 @@ int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t lda, int64_t
  * Order of operations per entry: y = P b; y_i -= l_ij y_j for j ascending;
  * d_j = 1 / u_jj (multiword division) for every j, then x_j = y_j * d_j and
  * y_i -= u_ij x_j for j descending.  A zero u_jj gives Inf/NaN entries (check
- * mw_ludecomp's info).  Returns MW_OK, -i, MW_ECUDA or MW_ETIMEOUT.
+ * mw_ludecomp's info).  Returns MW_OK, -i or MW_ECUDA without waiting for
+ * the GPU; a bounded wait that gave up is reported by mw_work_status.
  */
 int mw_solve(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
              const double* b, double* x, void* work, size_t work_bytes, void* stream);
@@ -359,12 +372,19 @@ int mw_profile_read(double* ms, long long* launches, int nphase, int reset);
  *   Nothing is allocated or freed by this call.
  *   Set-up: the first call on each device looks up the scratch address with
  *   cudaGetSymbolAddress (with that device current) and caches it; make that
- *   first call outside any stream capture.
+ *   first call outside any stream capture.  The cache does not survive
+ *   cudaDeviceReset: after a reset the library's device memory is loaded
+ *   again at another address, so do not call this entry point after
+ *   resetting a device it has been used on.
+ *   Orders above 40320 (the largest that fits at any precision) are
+ *   rejected before any size is computed.
+ *   Error word: a bounded wait that gave up is recorded in the scratch;
+ *   mw_solve_noalloc_status reads it.
  *   Sharing: all calls on a device use the same scratch, which keeps the last
  *   call's contents (the parts that must start at zero are cleared by each
  *   call); calls that overlap on the GPU, e.g. on two streams at once, race
  *   on it and must be serialised by the caller.
- * Returns MW_OK, -i or MW_ECUDA, as mw_solve.
+ * Returns MW_OK, -i or MW_ECUDA.
  */
 #define MW_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
 int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
@@ -405,6 +425,35 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
 #define MW_TUNE_GEMM_TILE 4
 int mw_set_tuning(int param, int prec, int value);
 int mw_get_tuning(int param, int prec);
+
+/*
+ * mw_work_status -- synchronises `stream`, then reports whether a bounded
+ * device wait gave up in the last call that used the single-system work
+ * buffer `work` for operation `op` (MW_OP_LUDECOMP, MW_OP_SOLVE or
+ * MW_OP_GEMM) with trailing-update form `update`: MW_OK, MW_ETIMEOUT, -i or
+ * MW_ECUDA.  Every such call clears the error word when it starts.
+ *
+ * mw_batch_work_status -- the same for the work buffer of any batched call
+ * (mw_*_batched, mw_*_batched_blocked): the error word sits in the buffer's
+ * head and is cleared at the start of every batched call.
+ *
+ * mw_solve_noalloc_status -- the same for the fixed scratch of
+ * mw_solve_noalloc on the current device.
+ */
+int mw_work_status(int op, int update, const void* work, void* stream);
+int mw_batch_work_status(const void* work, void* stream);
+int mw_solve_noalloc_status(void* stream);
+
+/*
+ * mw_set_wait_limit -- the number of polls after which the bounded waits of
+ * the substitution, the panel factorisation and the batched substitution
+ * give up, for every later launch in the process (0, the default: each
+ * kernel's own limit, which corresponds to seconds of waiting).  A small
+ * value makes those waits run out on purpose, to exercise the error path
+ * (the kernels return and the status calls report MW_ETIMEOUT; nothing
+ * hangs or faults).  Returns the previous value, or -1 for polls < 0.
+ */
+long long mw_set_wait_limit(long long polls);
 
 /* mw_strerror -- static text for a status code. */
 const char* mw_strerror(int code);

@@ -57,6 +57,10 @@ SIGNATURES = {
     "mw_strerror": (ctypes.c_char_p, [_I]),
     "mw_last_cuda_error": (_I, []),
     "mw_version": (ctypes.c_char_p, []),
+    "mw_work_status": (_I, [_I, _I, _P, _P]),
+    "mw_batch_work_status": (_I, [_P, _P]),
+    "mw_solve_noalloc_status": (_I, [_P]),
+    "mw_set_wait_limit": (ctypes.c_longlong, [ctypes.c_longlong]),
 }
 
 _lock = threading.Lock()
@@ -125,4 +129,4 @@ def declared_symbols() -> list:
     import re
     with open(HEADER) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(mw_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(mw_\w+)\s*\(", text, re.M)))

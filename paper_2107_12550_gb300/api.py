@@ -400,3 +400,26 @@ def peak_fp64() -> float:
     out = ctypes.c_double(0.0)
     L.check("mw_peak_fp64", L.lib().mw_peak_fp64(ctypes.byref(out), _stream()))
     return out.value
+
+
+def work_status(op: int, update, work: torch.Tensor, *, stream=None) -> int:
+    """MW_OK or MW_ETIMEOUT for the last call that used this single-system
+    work buffer (synchronises the stream; mw_work_status)."""
+    return L.check("mw_work_status", L.lib().mw_work_status(op, UPDATE[update], _ptr(work), _stream(stream)),
+                   ok=(L.MW_OK, L.MW_ETIMEOUT))
+
+
+def batch_work_status(work: torch.Tensor, *, stream=None) -> int:
+    """MW_OK or MW_ETIMEOUT for the last batched call that used this work
+    buffer (synchronises the stream; mw_batch_work_status)."""
+    return L.check("mw_batch_work_status", L.lib().mw_batch_work_status(_ptr(work), _stream(stream)),
+                   ok=(L.MW_OK, L.MW_ETIMEOUT))
+
+
+def set_wait_limit(polls: int) -> int:
+    """Poll limit of the bounded device waits for later launches (0: each
+    kernel's default); returns the previous value (mw_set_wait_limit)."""
+    prev = int(L.lib().mw_set_wait_limit(int(polls)))
+    if prev < 0:
+        raise ValueError("polls must be >= 0")
+    return prev

@@ -34,10 +34,16 @@ namespace mw {
 constexpr int kBatchThreads = 256;
 constexpr int kBatchMaxN = 1024;   // largest order in a batch (shared-memory caches)
 
+// Head of a batched work buffer: the systems' counter of the persistent
+// kernels, then the error word of the call (pad[0], pad[1] laid out as a
+// DeviceStatus: non-zero pad[0] when a bounded wait gave up).
 struct BatchCursor {
   unsigned int next;
   unsigned int pad[63];
 };
+__host__ __device__ inline DeviceStatus* cursor_status(BatchCursor* c) {
+  return reinterpret_cast<DeviceStatus*>(&c->pad[0]);
+}
 
 struct BatchState {
   int er;            // exponent of max |r_0|
@@ -235,11 +241,12 @@ __device__ __forceinline__ void smem_put(double* v, int nmax, int i, const val<W
 
 // bounded wait until pred() holds or the system is being abandoned
 template <typename P>
-__device__ __forceinline__ bool solve_wait(P pred, volatile int* abort_flag, BatchCursor* cur) {
+__device__ __forceinline__ bool solve_wait(P pred, volatile int* abort_flag, BatchCursor* cur,
+                                           unsigned long long limit) {
   unsigned long long spins = 0;
   while (!pred()) {
     if (*abort_flag) return false;
-    if (++spins > kSolveSpin) {
+    if (++spins > pick_limit(limit, kSolveSpin)) {
       *abort_flag = 1;
       atomicExch(&cur->pad[0], 1u);   // error word: a solve wait ran out
       return false;
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
 k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
                 const int64_t* __restrict__ moff, const int64_t* __restrict__ voff,
                 const double* __restrict__ LU, const int64_t* __restrict__ piv, const double* b,
-                double* x, const BatchState* __restrict__ st, BatchCursor* cur) {
+                double* x, const BatchState* __restrict__ st, BatchCursor* cur, unsigned long long spin_limit) {
   extern __shared__ double bsm[];
   double* ysm = bsm;
   double* dsm = bsm + W * nmax;
@@ -314,7 +321,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
       for (int bk = 0; bk < nb; ++bk) {
         const int j0 = bk * kSolveBs;
         const int bsz = min(kSolveBs, n - j0);
-        if (bk >= 2 && !solve_wait([&] { return vfar[bk - 2] >= kSolveWorkers; }, vab, cur)) break;
+        if (bk >= 2 && !solve_wait([&] { return vfar[bk - 2] >= kSolveWorkers; }, vab, cur, spin_limit)) break;
         const int i = j0 + lane;
         val<W> yi;
         if (lane < bsz) yi = smem_val<W>(ysm, nmax, i);
@@ -341,7 +348,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
       }
     } else {
       for (int bk = 0; bk < nb; ++bk) {
-        if (!solve_wait([&] { return *vtri >= bk; }, vab, cur)) break;
+        if (!solve_wait([&] { return *vtri >= bk; }, vab, cur, spin_limit)) break;
         const int j0 = bk * kSolveBs;
         const int bsz = min(kSolveBs, n - j0);
         const int r0 = j0 + 2 * kSolveBs;
@@ -371,7 +378,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         for (int bk = nb - 1; bk >= 0; --bk) {
           const int j0 = bk * kSolveBs;
           const int bsz = min(kSolveBs, n - j0);
-          if (bk <= nb - 3 && !solve_wait([&] { return vfar[bk + 2] >= kSolveWorkers; }, vab, cur)) break;
+          if (bk <= nb - 3 && !solve_wait([&] { return vfar[bk + 2] >= kSolveWorkers; }, vab, cur, spin_limit)) break;
           const int i = j0 + lane;
           val<W> yi, di;
           if (lane < bsz) {
@@ -402,7 +409,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         }
       } else {
         for (int bk = nb - 1; bk >= 0; --bk) {
-          if (!solve_wait([&] { return *vtri <= bk; }, vab, cur)) break;
+          if (!solve_wait([&] { return *vtri <= bk; }, vab, cur, spin_limit)) break;
           const int j0 = bk * kSolveBs;
           const int bsz = min(kSolveBs, n - j0);
           const int rend = j0 - kSolveBs;          // rows [0, rend): blocks <= bk - 2
@@ -650,7 +657,7 @@ static int lu_batched_launch(int count, int nmax, const int* order, const int* n
                              const int64_t* voff, double* A, int64_t* piv, int64_t* info, char* ws, cudaStream_t s) {
   if (count <= 0) return MW_OK;
   BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
-  MW_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(BatchCursor), s));
+  MW_CUDA_CHECK(cudaMemsetAsync(&cur->next, 0, sizeof(cur->next), s));   // the error word stays
   const size_t shmem = sizeof(double) * 2 * W * (size_t)nmax;
   int rc = set_smem(k_lu_batched<W>, shmem);
   if (rc) return rc;
@@ -667,14 +674,14 @@ static int solve_batched_launch(int count, int nmax, const int* order, const int
                                 double* x, const void* st, char* ws, cudaStream_t s) {
   if (count <= 0) return MW_OK;
   BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
-  MW_CUDA_CHECK(cudaMemsetAsync(cur, 0, sizeof(BatchCursor), s));
+  MW_CUDA_CHECK(cudaMemsetAsync(&cur->next, 0, sizeof(cur->next), s));   // the error word stays
   const size_t shmem = sizeof(double) * 2 * W * (size_t)nmax;
   int rc = set_smem(k_solve_batched<W>, shmem);
   if (rc) return rc;
   ProfScope ps(kPhBatchSolve, s);
   const int grid = std::min(count, device_sm_count());
   k_solve_batched<W><<<grid, kSolveThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x,
-                                                       static_cast<const BatchState*>(st), cur);
+                                                       static_cast<const BatchState*>(st), cur, wait_limit());
   MW_LAUNCH_CHECK();
   return MW_OK;
 }
@@ -792,6 +799,9 @@ static void plan_forget(const void* addr) {
 }
 
 static int upload_plan(const BatchPlanHost& p, int count, char* ws, BatchPlanDev& d, cudaStream_t s) {
+  // the cursor and its error word (a bounded wait that gave up) start clear
+  // in every call
+  MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, sizeof(BatchCursor), s));
   size_t off = 256;
   d.n = reinterpret_cast<int*>(ws + off);
   off += align256(sizeof(int) * count);
@@ -979,6 +989,7 @@ struct BlockedDev {
   char* split_ws;
   size_t split_bytes;
   int64_t a_tiles, b_tiles;
+  DeviceStatus* status;   // the call's error word (in the batch cursor)
 };
 
 static int upload_geom(const GeomPlanHost& g, char* base, size_t& off, GeomDev& d, cudaStream_t s,
@@ -1057,7 +1068,7 @@ static int split_panel(const BatchPlanHost& p, const BatchView& bv, const Blocke
   const GeomPlanHost& g = bp.pinner[q];
   rc = split_bupdate_dd(bv, kGeomPanelInner, c_off, h, act, g.max_mt[st], g.max_cb[st], bd.pinner[q].tiles + g.toff[st],
                         g.toff[st + 1] - g.toff[st], bd.pinner[q].bases + g.boff[st], bd.a_tiles, bd.b_tiles, k0, A,
-                        bd.aux, bd.split_ws, bd.split_bytes, s);
+                        bd.aux, bd.split_ws, bd.split_bytes, bd.status, s);
   if (rc) return rc;
   rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off + h, w - h, A, piv, info, s);
   if (rc) return rc;
@@ -1095,11 +1106,11 @@ static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d,
       rc = split_bupdate_dd(bv, kGeomTrsmInv, 0, 0, act, bp.tinv.max_mt[st], bp.tinv.max_cb[st],
                             bd.tinv.tiles + bp.tinv.toff[st], bp.tinv.toff[st + 1] - bp.tinv.toff[st],
                             bd.tinv.bases + bp.tinv.boff[st], bd.a_tiles, bd.b_tiles, k0, A, bd.aux, bd.split_ws,
-                            bd.split_bytes, s);
+                            bd.split_bytes, bd.status, s);
       if (rc) return rc;
       rc = split_bupdate_dd(bv, kGeomTrail, 0, 0, act, bp.trail.max_mt[st], bp.trail.max_cb[st],
                             bd.trail.tiles + bp.trail.toff[st], nt, bd.trail.bases + bp.trail.boff[st], bd.a_tiles,
-                            bd.b_tiles, k0, A, bd.aux, bd.split_ws, bd.split_bytes, s);
+                            bd.b_tiles, k0, A, bd.aux, bd.split_ws, bd.split_bytes, bd.status, s);
     } else {
       rc = launch_bpanel<W>(bv, act, p.nmax, k0, 0, kBatchNb, A, piv, info, s);
       if (rc) return rc;
@@ -1163,6 +1174,7 @@ static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPla
   BatchState* st = reinterpret_cast<BatchState*>(ws + mp.st);
   int* running_d = reinterpret_cast<int*>(ws + mp.running);
   char* cur = ws;
+  bool timed_out = false;
   const int64_t nrb = p.rb[count];
   prof_count(kPhRefineAux);
   k_bt_take_mat<<<(unsigned)((p.sum_n2 + 255) / 256), 256, 0, s>>>(count, d.moff, d.n, p.sum_n2, A, a_words, LU, W);
@@ -1193,9 +1205,13 @@ static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPla
     k_bt_count_running<<<1, 256, 0, s>>>(count, st, running_d);
     MW_LAUNCH_CHECK();
     int running = 0;
+    DeviceStatus sv = {};
     MW_CUDA_CHECK(cudaMemcpyAsync(&running, running_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MW_CUDA_CHECK(cudaMemcpyAsync(&sv, cursor_status(reinterpret_cast<BatchCursor*>(cur)), sizeof(sv),
+                                  cudaMemcpyDeviceToHost, s));
     MW_CUDA_CHECK(cudaStreamSynchronize(s));
-    if (running == 0) break;
+    if (sv.timeout) timed_out = true;   // a bounded wait of the LU or a substitution gave up
+    if (running == 0 || timed_out) break;
     rc = solve_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, rhat, z, st, cur, s);
     if (rc) return rc;
     prof_count(kPhRefineAux);
@@ -1208,7 +1224,7 @@ static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPla
   prof_count(kPhRefineAux);
   k_bt_stats<<<(count + 255) / 256, 256, 0, s>>>(count, st, info, stats);
   MW_LAUNCH_CHECK();
-  return MW_OK;
+  return timed_out ? MW_ETIMEOUT : MW_OK;
 }
 
 }  // namespace mw
@@ -1361,6 +1377,7 @@ extern "C" int mw_ludecomp_batched_blocked(int prec, int update, int count, cons
   mw::BlockedDev bd;
   rc = mw::upload_blocked(bp, p.n, prec, ws + head, bd, s);
   if (rc) return rc;
+  bd.status = mw::cursor_status(reinterpret_cast<mw::BatchCursor*>(ws));
   switch (prec) {
     case 2: return mw::lu_blocked_batched_run<2>(p, d, bp, bd, A, piv, info, s);
     case 3: return mw::lu_blocked_batched_run<3>(p, d, bp, bd, A, piv, info, s);
@@ -1402,11 +1419,22 @@ extern "C" int mw_refine_batched_blocked(int count, const int* n_host, const dou
   mw::BlockedDev bd;
   rc = mw::upload_blocked(bp, p.n, inner, ws + head, bd, s);
   if (rc) return rc;
+  bd.status = mw::cursor_status(reinterpret_cast<mw::BatchCursor*>(ws));
   switch (inner) {
     case 2: return mw::refine_batched_impl<2>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
     case 3: return mw::refine_batched_impl<3>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
     default: return mw::refine_batched_impl<4>(count, p, d, A, a_words, b, b_words, target_bits, max_iter, x, x_words, stats, ws, head, s, &bp, &bd);
   }
+}
+
+extern "C" int mw_batch_work_status(const void* work, void* stream) {
+  if (!work) return -1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mw::DeviceStatus sv = {};
+  MW_CUDA_CHECK(cudaMemcpyAsync(&sv, mw::cursor_status(reinterpret_cast<mw::BatchCursor*>(const_cast<void*>(work))),
+                                sizeof(sv), cudaMemcpyDeviceToHost, s));
+  MW_CUDA_CHECK(cudaStreamSynchronize(s));
+  return sv.timeout ? MW_ETIMEOUT : MW_OK;
 }
 
 extern "C" int mw_batch_plan_reset(void) {

@@ -60,6 +60,9 @@ int refine_dispatch(int64_t n, const double* A, int64_t lda, int a_words, const 
                     cudaStream_t s);
 }  // namespace mw
 
+static std::atomic<unsigned long long> g_wait_limit{0};
+unsigned long long mw::wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 static thread_local int g_last_cuda_error = 0;
 extern "C" void mw_internal_set_cuda_error(int e) { g_last_cuda_error = e; }
 
@@ -104,7 +107,7 @@ extern "C" int mw_workspace_size(int op, int prec, int update, int64_t n, size_t
   if (op < MW_OP_LUDECOMP || op > MW_OP_GEMM) return -1;
   if (!prec_ok(prec)) return -2;
   if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -3;
-  if (n < 0) return -4;
+  if (n < 0 || n > mw::kMaxOrder) return -4;
   if (!bytes) return -5;
   switch (op) {
     case MW_OP_LUDECOMP: *bytes = lu_ws_bytes(update, n); break;
@@ -119,7 +122,7 @@ extern "C" int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t l
                            int64_t* info, void* work, size_t work_bytes, void* stream) {
   if (!prec_ok(prec)) return -1;
   if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
-  if (n < 0) return -3;
+  if (n < 0 || n > mw::kMaxOrder) return -3;
   if (n > 0 && !A) return -4;
   if (lda < (n > 1 ? n : 1)) return -5;
   if (n > 0 && !piv) return -6;
@@ -144,7 +147,7 @@ extern "C" int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t l
 extern "C" int mw_solve(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
                         const double* b, double* x, void* work, size_t work_bytes, void* stream) {
   if (!prec_ok(prec)) return -1;
-  if (n < 0) return -2;
+  if (n < 0 || n > mw::kMaxOrder) return -2;
   if (n > 0 && !LU) return -3;
   if (lda < (n > 1 ? n : 1)) return -4;
   if (n > 0 && !piv) return -5;
@@ -164,7 +167,7 @@ extern "C" int mw_solve(int prec, int64_t n, const double* LU, int64_t lda, cons
 extern "C" int mw_residual(int64_t n, const double* A, int64_t lda, int a_words, const double* b,
                            int b_words, const double* x, int x_words, double* r, int r_words,
                            void* stream) {
-  if (n < 0) return -1;
+  if (n < 0 || n > mw::kMaxOrder) return -1;
   if (n > 0 && !A) return -2;
   if (lda < (n > 1 ? n : 1)) return -3;
   if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
@@ -182,7 +185,7 @@ extern "C" int mw_refine(int64_t n, const double* A, int64_t lda, int a_words, c
                          int b_words, int inner, int update, int target_bits, int max_iter,
                          int stop_mode, double rtol, double atol, double* x, int x_words,
                          int64_t* stats, void* work, size_t work_bytes, void* stream) {
-  if (n < 0) return -1;
+  if (n < 0 || n > mw::kMaxOrder) return -1;
   if (n > 0 && !A) return -2;
   if (lda < (n > 1 ? n : 1)) return -3;
   if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
@@ -211,9 +214,9 @@ static int gemm_impl(int prec, int update, int64_t m, int64_t N, int64_t K, doub
                      void* stream, bool plus) {
   if (!prec_ok(prec)) return -1;
   if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
-  if (m < 0) return -3;
-  if (N < 0) return -4;
-  if (K < 0) return -5;
+  if (m < 0 || m > mw::kMaxOrder) return -3;
+  if (N < 0 || N > mw::kMaxOrder) return -4;
+  if (K < 0 || K > mw::kMaxOrder) return -5;
   if (m > 0 && N > 0 && !C) return -6;
   if (ldc < (m > 1 ? m : 1)) return -7;
   if (m > 0 && K > 0 && !A) return -8;
@@ -228,6 +231,7 @@ static int gemm_impl(int prec, int update, int64_t m, int64_t N, int64_t K, doub
   if (m == 0 || N == 0 || K == 0) return MW_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t pc = ldc * N, pa = lda * K, pb = ldb * N;
+  if (update == MW_UPDATE_SPLIT) MW_CUDA_CHECK(cudaMemsetAsync(work, 0, 256, s));   // the status word
   if (update == MW_UPDATE_PLAIN) {
     switch (prec) {
       case 2: return mw::launch_gemm_plain_ptr<2>(m, N, (int)K, C, ldc, pc, A, lda, pa, B, ldb, pb, s, plus);
@@ -380,6 +384,28 @@ extern "C" int mw_peak_fp64(double* instr_per_s, void* stream) {
   MW_LAUNCH_CHECK();
   *instr_per_s = (double)threads * blocks * iters * 8 / (best * 1e-3);
   return MW_OK;
+}
+
+extern "C" long long mw_set_wait_limit(long long polls) {
+  if (polls < 0) return -1;
+  return (long long)g_wait_limit.exchange((unsigned long long)polls);
+}
+
+extern "C" int mw_work_status(int op, int update, const void* work, void* stream) {
+  if (op != MW_OP_LUDECOMP && op != MW_OP_SOLVE && op != MW_OP_GEMM) return -1;
+  if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
+  if (!work) return -3;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mw::DeviceStatus st[2] = {};
+  const char* w = static_cast<const char*>(work);
+  const bool plain_gemm = op == MW_OP_GEMM && update == MW_UPDATE_PLAIN;   // waits on nothing
+  if (!plain_gemm)
+    MW_CUDA_CHECK(cudaMemcpyAsync(&st[0], w + mw::kWsStatus, sizeof(mw::DeviceStatus), cudaMemcpyDeviceToHost, s));
+  if (op == MW_OP_LUDECOMP && update == MW_UPDATE_SPLIT)
+    MW_CUDA_CHECK(cudaMemcpyAsync(&st[1], w + mw::kWsSplit + mw::kWsStatus, sizeof(mw::DeviceStatus),
+                                  cudaMemcpyDeviceToHost, s));
+  MW_CUDA_CHECK(cudaStreamSynchronize(s));
+  return (st[0].timeout || st[1].timeout) ? MW_ETIMEOUT : MW_OK;
 }
 
 extern "C" const char* mw_strerror(int code) {

@@ -120,7 +120,8 @@ struct CandC {
 template <int W, bool RES>
 __global__ void __launch_bounds__(kPanelThreads)
 k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
-        int64_t* __restrict__ piv, int64_t* __restrict__ info, char* __restrict__ ws) {
+        int64_t* __restrict__ piv, int64_t* __restrict__ info, char* __restrict__ ws,
+        unsigned long long spin_limit) {
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + kWsBarrier);
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
 
@@ -219,7 +220,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
         const double* rq = rec_base + (size_t)tid * (kCandStride / 8);
         unsigned long long spins = 0;
         while (ld_acquire_u64(rq) != tag) {
-          if (++spins > kSpinLimit || ld_acquire_u32(&bar->abort)) {
+          if (++spins > pick_limit(spin_limit, kSpinLimit) || ld_acquire_u32(&bar->abort)) {
             failed = 1;
             break;
           }
@@ -947,7 +948,7 @@ int launch_panel(double* A, int64_t lda, int64_t plane, int64_t n, int64_t k0, i
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  MW_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, A, lda, plane, n, k0, nb, piv, info, ws));
+  MW_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, A, lda, plane, n, k0, nb, piv, info, ws, wait_limit()));
   return MW_OK;
 }
 

@@ -7,6 +7,8 @@
 
 namespace mw {
 
+struct DeviceStatus;   // mw_common.cuh
+
 constexpr int kPanelThreads = 256;
 constexpr int kPanelRowsPerCta = 8;    // panel rows per CTA before adding CTAs
 constexpr int kMaxPanelCtas = 256;
@@ -39,6 +41,10 @@ constexpr size_t kWsSwapPlan = (kWsCand + 2 * kCandParity + 255) & ~(size_t)255;
 static_assert(kWsSwapPlan + sizeof(SwapPlan) <= kWsSplit, "swap plan inside the LU work buffer header");
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Largest order any single-system entry point accepts; every size computed
+// from an order up to this bound fits in size_t without overflow.
+constexpr int64_t kMaxOrder = (int64_t)1 << 31;
 
 // tuning knobs (capi.cu): value of `param` (MW_TUNE_*) for precision prec
 int tune_get(int param, int prec);
@@ -156,7 +162,7 @@ size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles);
 int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
                      const TileEntry* tiles,
                      int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
-                     const double* aux, char* ws, size_t ws_bytes, cudaStream_t s);
+                     const double* aux, char* ws, size_t ws_bytes, DeviceStatus* status, cudaStream_t s);
 int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s);
 
 // Strassen's recursion over the block matrix product (strassen.cu): C = A B,

@@ -28,6 +28,15 @@ struct GridBarrier {
 
 constexpr unsigned long long kSpinLimit = 1ull << 26;  // ~seconds at worst
 
+// The poll limit that the host passes to the kernels whose waits it bounds
+// (the substitution's ready-value polls, the panel's record waits, the
+// batched substitution's flag waits): 0 (each kernel's own default) unless
+// mw_set_wait_limit chose another (host function, capi.cu).
+unsigned long long wait_limit();
+__host__ __device__ constexpr unsigned long long pick_limit(unsigned long long given, unsigned long long dflt) {
+  return given ? given : dflt;
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const void* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

@@ -14,7 +14,13 @@
 // GPU that loads the library holds it until the process exits.  Host code
 // cannot use the array's name as a device address, so on the first call on
 // each device (with that device current) the address is fetched with
-// cudaGetSymbolAddress and cached.
+// cudaGetSymbolAddress and cached.  The cache is keyed on the device index
+// only: it does not survive cudaDeviceReset (the library's device memory,
+// the scratch array included, is reloaded at a new address afterwards).
+//
+// Order bound: the largest order whose scratch fits at any precision is
+// DD's 40320; orders above it are rejected before any size is computed, so
+// no size arithmetic can overflow.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <mutex>
@@ -25,6 +31,7 @@
 namespace {
 
 constexpr size_t kNoallocScratchBytes = MW_NOALLOC_SCRATCH_BYTES;
+constexpr int64_t kNoallocMaxOrder = 40320;   // DD; TD and QD fit fewer
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -51,7 +58,7 @@ int scratch_address(void** out) {
 extern "C" int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const int64_t* piv,
                                 const double* b, double* x, void* stream) {
   if (prec != MW_DD && prec != MW_TD && prec != MW_QD) return -1;
-  if (n < 0) return -2;
+  if (n < 0 || n > kNoallocMaxOrder) return -2;                               // before any size arithmetic
   if (mw::solve_workspace_bytes(prec, n) > kNoallocScratchBytes) return -2;  // beyond the fixed scratch
   if (n > 0 && !LU) return -3;
   if (lda < (n > 1 ? n : 1)) return -4;
@@ -69,4 +76,16 @@ extern "C" int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t l
     case MW_TD: return mw::solve_launch<3>(n, LU, lda, piv, b, x, ws, kNoallocScratchBytes, s);
     default: return mw::solve_launch<4>(n, LU, lda, piv, b, x, ws, kNoallocScratchBytes, s);
   }
+}
+
+extern "C" int mw_solve_noalloc_status(void* stream) {
+  void* scratch = nullptr;
+  const int rc = scratch_address(&scratch);
+  if (rc != MW_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mw::DeviceStatus st = {};
+  MW_CUDA_CHECK(cudaMemcpyAsync(&st, static_cast<char*>(scratch) + mw::kWsStatus, sizeof(st),
+                                cudaMemcpyDeviceToHost, s));
+  MW_CUDA_CHECK(cudaStreamSynchronize(s));
+  return st.timeout ? MW_ETIMEOUT : MW_OK;
 }

@@ -16,9 +16,12 @@
 //     reads, K = nb = 64.
 //  3. Products.  For every pair (p, q) with p + q <= 16 one 128 x 16 x 64 MMA
 //     accumulates A_p B_q^T into the FP32 accumulator of diagonal d = p + q
-//     (15 accumulators x 16 columns = 240 TMEM columns).  A diagonal gathers
-//     at most 8 pairs x 64 products of magnitude <= 2^14, so every partial
-//     sum is an integer below 2^23 and the FP32 accumulation is exact.
+//     (15 accumulators x 16 columns = 240 TMEM columns).  Diagonal d holds
+//     the d - 1 pairs (p, q) with p + q = d, so at most 15 pairs (d = 16)
+//     x 64 products of magnitude <= 2^14: every partial sum is an integer
+//     of magnitude <= 15 * 64 * 2^14 = 15728640 < 2^24, and the FP32
+//     accumulation is exact (kExactSumBound below checks this at compile
+//     time; a 16th digit or K = 128 would break it).
 //  4. Recombination.  Per output entry the 15 exact diagonal sums D_d are
 //     combined in a 192-bit integer R = sum_d D_d 2^(8(16-d)); R 2^(e_i+f_j-128)
 //     is the (truncated-digit) product L21 U12 exactly.  R is rounded greedily
@@ -54,6 +57,11 @@ constexpr int kASliceBytes = kTileM * kK * 2;   // 16 KB
 constexpr int kBSliceBytes = kTileN * kK * 2;   // 2 KB
 constexpr uint32_t kTmemCols = 256;            // 15 x 16 = 240 used; two CTAs per SM
 static_assert(kTileM == kSplitTileM && kTileN == kSplitTileN && kK == kBatchNb, "batched split tile shape");
+// FP32 accumulation of a diagonal is exact while every partial sum stays an
+// integer below 2^24: (most pairs on one diagonal) x K x (largest digit
+// product 128 * 128)
+constexpr long long kExactSumBound = (long long)kS * kK * 128 * 128;
+static_assert(kExactSumBound < (1ll << 24), "diagonal sums must stay exact in FP32");
 
 // byte offset of element (row r, k) inside a K-major 128B-swizzled tile
 __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
@@ -302,7 +310,7 @@ __device__ __forceinline__ void i192_sub_shifted(I192& R, unsigned long long q, 
 }
 
 // the tile's product for one entry from the 15 exact diagonal sums (TMEM
-// words, FP32 integers |D_d| < 2^23, diagonal d+2 weighted 2^(8(14-d))):
+// words, FP32 integers |D_d| < 2^24, diagonal d+2 weighted 2^(8(14-d))):
 // three int64 Horner groups of five diagonals (each |S| < 2^56), then
 // R = S_C + S_B 2^40 + S_A 2^80 in 192 bits
 template <int CW>
@@ -904,7 +912,7 @@ int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phas
   int* fb = reinterpret_cast<int*>(ws + off);
   off += align256(sizeof(int) * (size_t)nt * kTileN);
   if (off > ws_bytes) return MW_EUNSUPPORTED;
-  DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
+  DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
   {
     ProfScope ps(kPhSplitAux, s);
     k_slice_rows<<<(unsigned)(mt * kTileM / kSliceRows), kSliceThreads, 0, s>>>(o, aslices, ea);
@@ -965,7 +973,7 @@ size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles) {
 int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
                      const TileEntry* tiles,
                      int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
-                     const double* aux, char* ws, size_t ws_bytes, cudaStream_t s) {
+                     const double* aux, char* ws, size_t ws_bytes, DeviceStatus* status, cudaStream_t s) {
   if (act <= 0 || ntiles <= 0) return MW_OK;
   if (split_batched_workspace_bytes(a_tiles, b_tiles) > ws_bytes) return MW_EUNSUPPORTED;
   size_t off = 256;
@@ -976,7 +984,6 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
   int* ea = reinterpret_cast<int*>(ws + off);
   off += align256(sizeof(int) * (size_t)a_tiles * kTileM);
   int* fb = reinterpret_cast<int*>(ws + off);
-  DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws);
   {
     ProfScope ps(kPhSplitAux, s);
     k_bslice_rows<<<dim3((unsigned)act, (unsigned)(max_mt * kTileM / kSliceRows)), kSliceThreads, 0, s>>>(

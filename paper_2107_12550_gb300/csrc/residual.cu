@@ -338,9 +338,18 @@ static int refine_impl(int64_t n, const double* A, int64_t lda, int a_words, con
   int rc = lu_blocked<W>(update, n, LU, ldl, piv, info_d, ws + m.lu_ws, m.solve_ws - m.lu_ws, nb, s);
   if (rc) return rc;
   int64_t info = 0;
+  DeviceStatus lu_st[2] = {};
   MW_CUDA_CHECK(cudaMemcpyAsync(&info, info_d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  MW_CUDA_CHECK(cudaMemcpyAsync(&lu_st[0], ws + m.lu_ws + kWsStatus, sizeof(DeviceStatus), cudaMemcpyDeviceToHost, s));
+  if (update == MW_UPDATE_SPLIT)
+    MW_CUDA_CHECK(cudaMemcpyAsync(&lu_st[1], ws + m.lu_ws + kWsSplit + kWsStatus, sizeof(DeviceStatus),
+                                  cudaMemcpyDeviceToHost, s));
   MW_CUDA_CHECK(cudaStreamSynchronize(s));
   stats[2] = info;
+  if (lu_st[0].timeout || lu_st[1].timeout) {   // a bounded wait of the LU gave up
+    stats[3] = MW_ETIMEOUT;
+    return MW_ETIMEOUT;
+  }
   if (info != 0) {
     stats[3] = MW_ESINGULAR;
     return MW_ESINGULAR;
@@ -362,6 +371,7 @@ static int refine_impl(int64_t n, const double* A, int64_t lda, int a_words, con
   }
   int corrections = 0, residuals = 0, status = MW_ENOTCONV;
   RefineState h;
+  DeviceStatus sv = {};
   for (;;) {
     rc = residual_launch(n, A, lda, a_words, b, b_words, x, x_words, r, x_words, s);
     if (rc) return rc;
@@ -370,7 +380,12 @@ static int refine_impl(int64_t n, const double* A, int64_t lda, int a_words, con
   k_refine_check<<<1, 1024, 0, s>>>(n, r, x, W, rhat, stop_mode, rtol, atol, st);
     MW_LAUNCH_CHECK();
     MW_CUDA_CHECK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MW_CUDA_CHECK(cudaMemcpyAsync(&sv, solve_ws + kWsStatus, sizeof(sv), cudaMemcpyDeviceToHost, s));
     MW_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (sv.timeout) {   // the last substitution's bounded wait gave up
+      status = MW_ETIMEOUT;
+      break;
+    }
     if (h.rzero || (stop_mode == MW_STOP_EQ2 && h.done == 1)) {
       status = MW_OK;
       break;
@@ -387,7 +402,12 @@ static int refine_impl(int64_t n, const double* A, int64_t lda, int a_words, con
   k_refine_check2<<<1, 1024, 0, s>>>(n, z, x, target_bits, corrections, st);
       MW_LAUNCH_CHECK();
       MW_CUDA_CHECK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+      MW_CUDA_CHECK(cudaMemcpyAsync(&sv, solve_ws + kWsStatus, sizeof(sv), cudaMemcpyDeviceToHost, s));
       MW_CUDA_CHECK(cudaStreamSynchronize(s));
+      if (sv.timeout) {
+        status = MW_ETIMEOUT;
+        break;
+      }
       if (h.done == 1) {
         status = MW_OK;
         break;

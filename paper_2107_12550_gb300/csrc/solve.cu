@@ -37,6 +37,7 @@ __host__ __device__ inline size_t solve_vec_bytes(int w, int64_t n) {
 }
 __host__ __device__ inline int64_t solve_nblk(int64_t n) { return (n + kSolveBlock - 1) / kSolveBlock; }
 
+// n <= kMaxOrder (checked by every entry point before sizes are computed)
 size_t solve_workspace_bytes(int w, int64_t n) { return solve_ws_y(n) + 3 * solve_vec_bytes(w, n); }
 
 // perm[i] = index of b that lands in row i after the swaps piv[0..n-1]
@@ -117,8 +118,9 @@ __device__ __forceinline__ unsigned poll_block(const double* buf, int64_t n, int
   return __ballot_sync(0xffffffffu, ok);
 }
 
-__device__ __forceinline__ bool spin_backoff(unsigned long long& spins, DeviceStatus* status, int tag) {
-  if (++spins > kSpinLimit) {
+__device__ __forceinline__ bool spin_backoff(unsigned long long& spins, unsigned long long limit,
+                                             DeviceStatus* status, int tag) {
+  if (++spins > pick_limit(limit, kSpinLimit)) {
     if ((threadIdx.x & 31) == 0) {
       atomicExch(&status->timeout, 1u);
       atomicExch(&status->where, (unsigned)tag);
@@ -133,7 +135,7 @@ __device__ __forceinline__ bool spin_backoff(unsigned long long& spins, DeviceSt
 template <int W>
 __global__ void __launch_bounds__(32)
 k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
-        const double* b, double* x, char* __restrict__ ws) {
+        const double* b, double* x, char* __restrict__ ws, unsigned long long spin_limit) {
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
   const int* perm = reinterpret_cast<const int*>(ws + kSolveWsPerm);
   double* y = reinterpret_cast<double*>(ws + solve_ws_y(n));
@@ -176,7 +178,7 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
         const unsigned notready = ~(mask >> done);
         const int k = notready ? __ffs(notready) - 1 : kSolveBlock - done;
         if (k == 0) {
-          if (!spin_backoff(spins, status, 31)) return;
+          if (!spin_backoff(spins, spin_limit, status, 31)) return;
           continue;
         }
         for (int jj = done; jj < done + k; ++jj) {
@@ -217,7 +219,7 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
         int k = __clz(~top);
         if (k > done) k = done;
         if (k == 0) {
-          if (!spin_backoff(spins, status, 32)) return;
+          if (!spin_backoff(spins, spin_limit, status, 32)) return;
           continue;
         }
         for (int jj = done - 1; jj >= done - k; --jj) {
@@ -281,7 +283,7 @@ int solve_with_perm(int64_t n, const double* LU, int64_t lda, const double* b, d
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  MW_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_solve<W>, LU, lda, plane, n, b, x, ws));
+  MW_CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_solve<W>, LU, lda, plane, n, b, x, ws, wait_limit()));
   return MW_OK;
 }
 

@@ -310,8 +310,8 @@ def _svd_batch_worker(job):
     try:
         Aflat = np.ndarray((total_a,), dtype=np.float64, buffer=sa.buf)
         bflat = np.ndarray((total_b,), dtype=np.float64, buffer=sb.buf)
-        for (s, n, lk, moff, voff) in items:
-            sysm = svd_system(n, lk, seed=system_seed(seed, s), words=a_words, b_words=b_words, lda=n)
+        for (s, n, lk, moff, voff, sid) in items:
+            sysm = svd_system(n, lk, seed=system_seed(seed, sid), words=a_words, b_words=b_words, lda=n)
             base = a_words * moff
             Aflat[base: base + a_words * n * n] = sysm.A.reshape(-1)
             vb = b_words * voff
@@ -324,12 +324,15 @@ def _svd_batch_worker(job):
 
 
 def svd_batch(n_list, log10_kappa, seed: int = 0, a_words: int = 4, b_words: int = 8,
-              processes: Optional[int] = None):
+              processes: Optional[int] = None, system_ids=None):
     """Packed batch of ``svd_system`` s (system s uses seed system_seed(seed, s),
     lda = n): returns (A, b) flat float64 arrays in the batch layout (system s:
     A at a_words * sum_{s'<s} n^2, b at b_words * sum_{s'<s} n), with
     x* = ones for every system.  Systems are built in a pool of worker
-    processes (spawn start method) writing into shared memory."""
+    processes (spawn start method) writing into shared memory.
+    system_ids: for a subset of a larger batch, the original index of each
+    listed system (its seed is system_seed(seed, id)); default 0..count-1."""
+    ids = list(range(len(n_list))) if system_ids is None else [int(v) for v in system_ids]
     import multiprocessing as mp
     from multiprocessing import shared_memory
     n = np.asarray(n_list, dtype=np.int64)
@@ -347,7 +350,7 @@ def svd_batch(n_list, log10_kappa, seed: int = 0, a_words: int = 4, b_words: int
         load = [0.0] * procs
         for s in order:                              # longest-processing-time first
             k = int(np.argmin(load))
-            buckets[k].append((s, int(n_list[s]), float(log10_kappa[s]), int(moff[s]), int(voff[s])))
+            buckets[k].append((s, int(n_list[s]), float(log10_kappa[s]), int(moff[s]), int(voff[s]), ids[s]))
             load[k] += float(n_list[s]) ** 2.5
         jobs = [(sa.name, sb.name, total_a, total_b, a_words, b_words, seed, it) for it in buckets if it]
         if procs == 1:

@@ -95,3 +95,30 @@ def test_python_binding_rejects_host_and_mismatched_operands():
         api.ludecomp(A, 2)
     with _pt.raises(ValueError):
         api.gemm_sub(A, A, A, 8, 2)
+
+
+def test_huge_orders_rejected_before_any_size_arithmetic(lib):
+    """Orders far beyond any device (here 2^62, whose byte counts would wrap
+    around size_t) are rejected on the host as invalid arguments."""
+    big = 1 << 62
+    out = ctypes.c_size_t(0)
+    assert lib.mw_workspace_size(L.MW_OP_SOLVE, 4, 0, big, ctypes.byref(out)) == -4
+    assert lib.mw_ludecomp(2, 0, big, 8, big, 8, 8, 8, 1 << 30, None) == -3
+    assert lib.mw_solve(4, big, 8, big, 8, 8, 8, 8, 1 << 30, None) == -2
+    assert lib.mw_solve_noalloc(4, big, 8, big, 8, 8, 8, None) == -2
+    assert lib.mw_solve_noalloc(2, 40321, 8, 40321, 8, 8, 8, None) == -2
+    assert lib.mw_residual(big, 8, big, 1, 8, 1, 8, 1, 8, 1, None) == -1
+    stats = (ctypes.c_int64 * 4)()
+    assert lib.mw_refine(big, 8, big, 2, 8, 2, 3, 0, 200, 5, 1, 0.0, 0.0, 8, 8, stats, 8, 1 << 30, None) == -1
+    assert lib.mw_gemm_sub(2, 0, big, 4, 4, 8, big, 8, big, 8, 4, None, 0, None) == -3
+
+
+def test_status_and_wait_limit_arguments(lib):
+    assert lib.mw_work_status(7, 0, 8, None) == -1
+    assert lib.mw_work_status(L.MW_OP_SOLVE, 5, 8, None) == -2
+    assert lib.mw_work_status(L.MW_OP_SOLVE, 0, None, None) == -3
+    assert lib.mw_batch_work_status(None, None) == -1
+    assert lib.mw_set_wait_limit(-1) == -1
+    prev = lib.mw_set_wait_limit(1000)
+    assert prev == 0
+    assert lib.mw_set_wait_limit(prev) == 1000

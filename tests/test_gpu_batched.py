@@ -95,28 +95,30 @@ def test_refine_batched_bitwise(inner):
         assert np.array_equal(xs[s], xo), s
 
 
-def test_config4_batch_4096_sampled():
-    """4096 DD systems, n uniform in [16, 256] (uniform entries, one RHS from
-    x_true = ones): one batched LU + solve; 12 sampled systems (including
-    the largest and smallest) are bitwise equal to the oracle."""
+@pytest.mark.parametrize("w", [2, 3])
+def test_config4_batch_4096_sampled(w):
+    """4096 DD and TD systems, n uniform in [16, 256] (uniform entries, one
+    RHS from x_true = ones), the bench's launch: one batched LU + solve; 12
+    sampled systems (including the largest and smallest) are bitwise equal
+    to the oracle."""
     n_list = [int(v) for v in W.batch_sizes(4096, 16, 256, seed=0)]
     mats, vecs = [], []
     for s, n in enumerate(n_list):
-        mats.append(W.uniform_matrix(n, 2, seed=W.system_seed(0, s), lda=n))
+        mats.append(W.uniform_matrix(n, w, seed=W.system_seed(0, s), lda=n))
     for s, n in enumerate(n_list):
-        v = np.zeros((2, n))
+        v = np.zeros((w, n))
         v[0] = 1.0
         vecs.append(v)
-    A = dev(api().pack_matrices(mats, 2))
-    b = dev(api().pack_vectors(vecs, 2))
-    LU, piv, info = api().ludecomp_batched(A, n_list, 2)
-    x = api().solve_batched(LU, piv, b, n_list, 2)
-    LUs = api().unpack_matrices(host(LU), n_list, 2)
-    xs = api().unpack_vectors(host(x), n_list, 2)
+    A = dev(api().pack_matrices(mats, w))
+    b = dev(api().pack_vectors(vecs, w))
+    LU, piv, info = api().ludecomp_batched(A, n_list, w)
+    x = api().solve_batched(LU, piv, b, n_list, w)
+    LUs = api().unpack_matrices(host(LU), n_list, w)
+    xs = api().unpack_vectors(host(x), n_list, w)
     order = np.argsort(n_list)
     sample = list(order[:4]) + list(order[-4:]) + [0, 1, 2, 3]
     for s in sample:
-        LUo, pivo, infoo = oracle.lu(2, mats[s])
+        LUo, pivo, infoo = oracle.lu(w, mats[s])
         assert np.array_equal(LUs[s], LUo[:, :, :n_list[s]]), s
-        assert np.array_equal(xs[s], oracle.solve(2, LUo, pivo, vecs[s])), s
+        assert np.array_equal(xs[s], oracle.solve(w, LUo, pivo, vecs[s])), s
     assert int(host(info).max()) == 0

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from parity_rules import check_pivots_near_tie
 from paper_2107_12550_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -125,8 +126,7 @@ def test_blocked_split_dd_backward_error_and_pivots():
         eta = _eta(mats[s], vecs[s], xs[s])
         assert eta <= 1e-28, (s, n, eta)
         _, pivo, _ = oracle.lu(2, mats[s])
-        diff = int((pv[voff[s]: voff[s] + n] != pivo).sum())
-        assert diff <= max(1, n // 50), (s, n, diff)
+        check_pivots_near_tie(mats[s], 2, pv[voff[s]: voff[s] + n], pivo)
 
 
 def test_blocked_split_close_to_plain_factors():
@@ -234,14 +234,14 @@ def test_mixed_batch_refine_full_range_exact():
     """The mixed-precision batched refinement at the workload's full ranges:
     the n and kappa of every 11th member of the 512-system workload plus
     its largest and most ill-conditioned ones (n up to 1024, kappa up to
-    1e20), each system built with its own seed: split DD inner LU, every
+    1e20), each system built with its seed in the workload: split DD inner LU, every
     system converges and every entry of every x equals x* = 1 to 2^-200
     (exact check)."""
     n_all, k_all = W.mixed_batch_spec(512, 64, 1024, 4.0, 20.0, seed=0)
     pick = sorted(set(list(range(0, 512, 11)) + [int(np.argmax(n_all)), int(np.argmax(k_all))]))
     n_list = [n_all[s] for s in pick]
     kap = [k_all[s] for s in pick]
-    A_np, b_np = W.svd_batch(n_list, kap, seed=0, processes=4)
+    A_np, b_np = W.svd_batch(n_list, kap, seed=0, processes=4, system_ids=pick)
     x, stats = api().refine_batched_blocked(dev(A_np), 4, dev(b_np), 8, n_list, 2, "split", 200)
     st = host(stats)
     assert (st[:, 3] == 0).all(), st[st[:, 3] != 0]

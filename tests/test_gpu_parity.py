@@ -218,6 +218,33 @@ def test_refine_dd_rhs_and_limits():
     assert res.status == 1 and res.info == 1
 
 
+@pytest.mark.parametrize("w,u,y", [(2, 35, 105), (3, 45, 45), (4, 35, 105)])
+def test_back_substitution_reciprocal_case(w, u, y):
+    """The oracle pin that separates the two readings of the back
+    substitution (y/u is an integer; y * RN(1/u) is not): the GPU solve
+    gives the oracle's value, bitwise."""
+    A = np.zeros((w, 1, 1)); A[0, 0, 0] = float(u)
+    b = np.zeros((w, 1)); b[0, 0] = float(y)
+    LU, piv, info = api().ludecomp(dev(A), w)
+    xg = host(api().solve(LU, piv, dev(b), w))
+    LUo, pivo, _ = oracle.lu(w, A)
+    xo = oracle.solve(w, LUo, pivo, b)
+    assert np.array_equal(xg, xo)
+    assert X.words_to_frac(xg[:, 0]) != Fraction(y, u)
+
+
+def test_refine_stagnation_exit_case():
+    """The oracle's hand-traced stagnation case (A = 1/4 in four words whose
+    DD part is 1, b = 1): the GPU refinement stops after 2 corrections as
+    not converged, with x = 37/16, as the oracle does."""
+    A = np.zeros((4, 1, 1)); A[0, 0, 0] = 1.0; A[2, 0, 0] = -0.75
+    b = np.ones((1, 1))
+    res = api().refine(dev(A), dev(b), 2, 200)
+    st, xo, corr, nres, info = oracle.refine(A, b, 2)
+    assert (res.status, res.corrections, res.residuals) == (st, corr, nres) == (2, 2, 2)
+    assert np.array_equal(host(res.x), xo)
+
+
 def test_config1_dd_n256_bitwise():
     """Single DD LU + substitution at n = 256 (uniform entries, b = A*1
     rounded to DD), plain path: bitwise equal to the oracle."""

@@ -118,6 +118,38 @@ def pin_refine():
     return st == 0 and X.forward_error(X.vec_to_frac(x), [Fraction(1)] * 12) <= Fraction(1, 2 ** 200)
 
 
+def pin_back_substitution_reciprocal():
+    """Reading of the back substitution (Section 2, Listing 1's SolveTDLSPM
+    does not fix the order): d_j = 1/u_jj first, then x_j = y_j d_j.  For
+    u = 35, y = 105 (DD, QD) and u = 45, y = 45 (TD) the quotient y/u is an
+    integer, which a division returns exactly, while y times the rounded
+    reciprocal misses it by a few units in the last place."""
+    for w, u, y in ((2, 35, 105), (3, 45, 45), (4, 35, 105)):
+        A = np.zeros((w, 1, 1)); A[0, 0, 0] = float(u)
+        LU, piv, info = oracle.lu(w, A)
+        b = np.zeros((w, 1)); b[0, 0] = float(y)
+        x = X.words_to_frac(oracle.solve(w, LU, piv, b)[:, 0])
+        k = Fraction(y, u)
+        if x == k or abs(x - k) > 4 * U ** w * k:
+            return False
+    return True
+
+
+def pin_stagnation_exit():
+    """Stop mode 1's stagnation exit, traced by hand on a 1 x 1 system.
+    A = 1 + 0 - 3/4 + 0 = 1/4 in four words, whose leading DD words give the
+    inner factor 1; b = 1, so x* = 4.  x0 = 1.  Each step solves with 1
+    instead of 1/4, so the error shrinks by 3/4 per correction:
+    r0 = 3/4 -> correction 3/4 (x1 = 7/4);  r1 = 9/16 -> correction 9/16
+    (x2 = 37/16).  The second correction exceeds half the first, so the
+    loop stops there as not converged: status 2 after 2 corrections and 2
+    residuals, with x = 37/16 exactly."""
+    A = np.zeros((4, 1, 1)); A[0, 0, 0] = 1.0; A[2, 0, 0] = -0.75
+    b = np.ones((1, 1))
+    st, x, corr, nres, info = oracle.refine(A, b, 2)
+    return (st, corr, nres, info) == (2, 2, 2, 0) and x[0, 0] == 37 / 16 and not np.any(x[1:, 0])
+
+
 MUTATIONS = [
     ("dd_mul drops the cross terms", "    cl3 = cl1 + cl2;\n", "    cl3 = cl1;\n", pin_dd_mul),
     ("dd_add wrong sign", "    c = sl + th;\n", "    c = sl - th;\n", pin_add(2)),
@@ -131,6 +163,15 @@ MUTATIONS = [
     ("rounding ties away from even", "(acc_any_below(a, lsb - 1) || (q & 1u))", "(acc_any_below(a, lsb - 1) || 1)", pin_rn_ties),
     ("solve ignores the pivots", "        int64_t p = piv[k];\n        if (p != k) {", "        int64_t p = piv[k];\n        if (0 && p != k) {", pin_solve_pivots),
     ("refinement forgets to scale back", "acc_add_double(&a, z[c * n + i], er);", "acc_add_double(&a, z[c * n + i], 0);", pin_refine),
+    ("back substitution divides by u_jj", "        mw_mul(w, yj, dj, xj);\n",
+     "        { double uu[4]; ld_m(w, LU, plane, j * lda + j, uu); mw_div(w, yj, uu, xj); }\n",
+     pin_back_substitution_reciprocal),
+    ("stagnation test against twice the previous correction", "corr > 0.5 * prev", "corr > 2.0 * prev",
+     pin_stagnation_exit),
+    ("stagnation test never updates the previous correction", "            prev = corr;\n", "\n",
+     pin_stagnation_exit),
+    ("stagnation test starts a correction late", "if (corrections >= 2 && corr > 0.5 * prev)",
+     "if (corrections >= 3 && corr > 0.5 * prev)", pin_stagnation_exit),
 ]
 
 

@@ -66,7 +66,36 @@ def test_noalloc_solve_matches_solve_twice(lib):
 
 
 def test_noalloc_rejects_orders_beyond_scratch(lib):
-    # checked on the host before any GPU work: -2 (the order n is invalid)
+    # checked on the host before any GPU work: -2 (the order n is invalid);
+    # 2^62 would wrap the byte counts around size_t if it got that far
     assert lib.mw_solve_noalloc(4, 20969, 8, 20969, 8, 8, 8, None) == -2
     assert lib.mw_solve_noalloc(2, 40321, 8, 40321, 8, 8, 8, None) == -2
+    assert lib.mw_solve_noalloc(4, 1 << 62, 8, 1 << 62, 8, 8, 8, None) == -2
+    assert lib.mw_solve_noalloc(2, 1 << 62, 8, 1 << 62, 8, 8, 8, None) == -2
     assert lib.mw_solve_noalloc(4, 10, 8, 5, 8, 8, 8, None) == -4
+
+
+def test_noalloc_largest_qd_order_fills_the_scratch_exactly(lib):
+    """QD n = 20968 needs exactly the whole fixed scratch (2 MiB): the
+    boundary case that is still accepted.  A hand-built factorisation
+    (unit lower L = I, upper U = a random diagonal, no row swaps) keeps it
+    cheap; the result must equal mw_solve's with an exactly sized work
+    buffer, bitwise, on two calls in a row, and report no wait timeout."""
+    from paper_2107_12550_gb300 import _lib as L
+    w, n = 4, 20968
+    assert L.workspace_size(L.MW_OP_SOLVE, w, 0, n) == 2 * 1024 * 1024
+    LU = torch.zeros((w, n, n), dtype=torch.float64, device="cuda")
+    g = np.random.default_rng(11)
+    d = torch.from_numpy(g.uniform(1.0, 2.0, n)).cuda()
+    idx = torch.arange(n, device="cuda")
+    LU[0, idx, idx] = d
+    piv = torch.arange(n, dtype=torch.int64, device="cuda")
+    b = torch.from_numpy(np.ascontiguousarray(g.uniform(-1, 1, (w, n)))).cuda()
+    ref = _solve_with_work(lib, w, LU, piv, b)
+    x1 = _solve_noalloc(lib, w, LU, piv, b)
+    x2 = _solve_noalloc(lib, w, LU, piv, b)
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.mw_solve_noalloc_status(s) == 0
+    assert torch.equal(x1, ref) and torch.equal(x2, ref)
+    del LU
+    torch.cuda.empty_cache()
