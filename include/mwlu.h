@@ -344,7 +344,8 @@ int mw_arith(int op, int prec, int64_t cnt, const double* x, const double* y, do
  * 1 row interchanges, 2 triangular solve of U12, 3 plain trailing update,
  * 4 split trailing update (tensor-core GEMMs), 5 substitution, 6 pivot
  * permutation, 7 exact residual, 8 refinement bookkeeping, 9 split-update
- * slicing and recombination.
+ * slicing, 10 batched persistent LU, 11 batched substitution, 12 the inner
+ * tensor-core products of the split LU's recursive panel.
  * mw_profile_enable(1) brackets every later kernel launch of the library with
  * two CUDA events on its stream (0 turns this off; launches are counted
  * either way).  mw_profile_read synchronises on the recorded events and

@@ -108,7 +108,7 @@ def workspace_size(op: int, prec: int, update: int, n: int) -> int:
 
 
 PHASES = ["panel", "laswp", "trsm", "gemm_plain", "gemm_split", "solve", "perm", "residual",
-          "refine_aux", "split_aux", "batch_lu", "batch_solve"]
+          "refine_aux", "split_aux", "batch_lu", "batch_solve", "panel_inner"]
 
 
 def profile_enable(on: bool = True) -> None:

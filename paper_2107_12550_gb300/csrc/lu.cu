@@ -1034,7 +1034,7 @@ static int split_panel_rec(double* A, int64_t lda, int64_t plane, int64_t n, int
   o.m = n - kp - h;
   o.N = lim - kp - h;
   o.K = h;
-  rc = split_product_dd(o, sws, sbytes, kPhPanel, s);
+  rc = split_product_dd(o, sws, sbytes, kPhPanelInner, s);
   if (rc) return rc;
   rc = split_panel_rec(A, lda, plane, n, kp + h, w - h, leaf, piv, info, ws, sws, sbytes, s);
   if (rc) return rc;

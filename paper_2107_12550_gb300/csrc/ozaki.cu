@@ -14,18 +14,26 @@
 //     (exact: 8 significant bits).  Slices are stored per 128-row (L21) or
 //     32-column (U12) tile in the 128-byte-swizzled K-major layout the MMA
 //     reads, K = nb = 64.
-//  3. Products.  For every pair (p, q) with p + q <= 16 one 128 x 16 x 64 MMA
-//     accumulates A_p B_q^T into the FP32 accumulator of diagonal d = p + q
-//     (15 accumulators x 16 columns = 240 TMEM columns).  Diagonal d holds
+//  3. Products.  Every pair (p, q) with p + q <= 16 accumulates A_p B_q^T
+//     (128 x 16 x 64) into the FP32 accumulator of diagonal d = p + q (15
+//     accumulators x 16 columns = 240 TMEM columns).  The B slices are
+//     stored back to back, so for a fixed p the pairs q = 1 .. 16 - p form
+//     ONE MMA of N = 16 (16 - p) columns whose output columns are exactly
+//     those diagonals: 15 MMA instructions per K step instead of 120 narrow
+//     ones, and each A tile is read from shared memory 15 times, not 120.  Diagonal d holds
 //     the d - 1 pairs (p, q) with p + q = d, so at most 15 pairs (d = 16)
 //     x 64 products of magnitude <= 2^14: every partial sum is an integer
 //     of magnitude <= 15 * 64 * 2^14 = 15728640 < 2^24, and the FP32
 //     accumulation is exact (kExactSumBound below checks this at compile
 //     time; a 16th digit or K = 128 would break it).
 //  4. Recombination.  Per output entry the 15 exact diagonal sums D_d are
-//     combined in a 192-bit integer R = sum_d D_d 2^(8(16-d)); R 2^(e_i+f_j-128)
-//     is the (truncated-digit) product L21 U12 exactly.  R is rounded greedily
-//     to a double-double and subtracted from C with the DD subtraction.
+//     combined in a 160-bit integer R = sum_d D_d 2^(8(16-d)); R 2^(e_i+f_j-128)
+//     is the (truncated-digit) product L21 U12 exactly.  When both words of
+//     C are integer multiples of that grid below 2^158 of it (the usual
+//     case), C - P is formed exactly in the integer and rounded greedily to
+//     DD once (recomb.cuh); otherwise, or when the result would be
+//     subnormal, R is rounded greedily to DD and subtracted from C with the
+//     DD subtraction.  oracle/ozaki.py states the same steps.
 //
 // Error per entry (stated per result in the tests): the dropped pairs
 // p + q > 16 and the digit truncation give
@@ -40,6 +48,7 @@
 #include "lu_internal.cuh"
 #include "profile.cuh"
 #include "tc.cuh"
+#include "recomb.cuh"
 
 namespace mw {
 
@@ -309,46 +318,12 @@ __device__ __forceinline__ void i192_sub_shifted(I192& R, unsigned long long q, 
   }
 }
 
-// the tile's product for one entry from the 15 exact diagonal sums (TMEM
-// words, FP32 integers |D_d| < 2^24, diagonal d+2 weighted 2^(8(14-d))):
-// three int64 Horner groups of five diagonals (each |S| < 2^56), then
-// R = S_C + S_B 2^40 + S_A 2^80 in 192 bits
-template <int CW>
-__device__ __forceinline__ I192 recombine15(const uint32_t (&v)[15][CW], int cc) {
-  long long SA = 0, SB = 0, SC = 0;
-#pragma unroll
-  for (int d = 0; d < 5; ++d) SA = SA * 256 + __float2int_rn(__uint_as_float(v[d][cc]));
-#pragma unroll
-  for (int d = 5; d < 10; ++d) SB = SB * 256 + __float2int_rn(__uint_as_float(v[d][cc]));
-#pragma unroll
-  for (int d = 10; d < 15; ++d) SC = SC * 256 + __float2int_rn(__uint_as_float(v[d][cc]));
+// the 160-bit product integer widened to 192 bits (sign-extended)
+__device__ __forceinline__ I192 to_i192(const rc::I160& r) {
   I192 R;
-  const unsigned long long sxc = (SC < 0) ? ~0ull : 0ull;
-  R.w0 = (unsigned long long)SC;
-  R.w1 = sxc;
-  R.w2 = sxc;
-  {  // + S_B 2^40
-    const unsigned long long p0 = (unsigned long long)SB << 40;
-    const unsigned long long p1 = (unsigned long long)(SB >> 24);
-    const unsigned long long p2 = (SB < 0) ? ~0ull : 0ull;
-    const unsigned long long s0 = R.w0 + p0;
-    const unsigned long long c0 = s0 < p0;
-    const unsigned long long t1 = R.w1 + p1;
-    const unsigned long long c1a = t1 < p1;
-    const unsigned long long s1 = t1 + c0;
-    const unsigned long long c1b = s1 < t1;
-    R.w0 = s0;
-    R.w1 = s1;
-    R.w2 = R.w2 + p2 + c1a + c1b;
-  }
-  {  // + S_A 2^80
-    const unsigned long long p1 = (unsigned long long)SA << 16;
-    const unsigned long long p2 = (unsigned long long)(SA >> 48);
-    const unsigned long long s1 = R.w1 + p1;
-    const unsigned long long c1 = s1 < p1;
-    R.w1 = s1;
-    R.w2 = R.w2 + p2 + c1;
-  }
+  R.w0 = (unsigned long long)r.l0 | ((unsigned long long)r.l1 << 32);
+  R.w1 = (unsigned long long)r.l2 | ((unsigned long long)r.l3 << 32);
+  R.w2 = (unsigned long long)(long long)(int)r.l4;
   return R;
 }
 
@@ -417,51 +392,6 @@ __device__ __forceinline__ void i192_to_dd(I192 R, int scale, double& hi, double
   hi = scale_pow2(neg ? -hd : hd, sh + scale);
   lo = scale_pow2((neg != lneg) ? -ld : ld, sh2 + scale);
 }
-
-// R -= sign(x) * |x| * 2^-scale for a finite double x whose value is an
-// integer multiple of 2^scale with |x| 2^-scale < 2^189; false (R unchanged)
-// otherwise
-__device__ __forceinline__ bool i192_sub_double(I192& R, double x, int scale) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((bits >> 52) & 0x7ff);
-  if (ex == 0x7ff) return false;
-  unsigned long long m = bits & ((1ull << 52) - 1);
-  if (ex) m |= (1ull << 52);
-  if (m == 0) return true;
-  int e = (ex ? ex : 1) - 1075;                 // x = m 2^e
-  const int tz = __ffsll((long long)m) - 1;
-  m >>= tz;
-  e += tz;
-  const int s = e - scale;
-  if (s < 0 || s > 135) return false;
-  const int w = s >> 6, b = s & 63;
-  const unsigned long long lo = m << b;
-  const unsigned long long hi = b ? (m >> (64 - b)) : 0ull;
-  const unsigned long long v0 = (w == 0) ? lo : 0ull;
-  const unsigned long long v1 = (w == 0) ? hi : (w == 1 ? lo : 0ull);
-  const unsigned long long v2 = (w == 1) ? hi : (w == 2 ? lo : 0ull);
-  if ((long long)bits < 0) {                    // x < 0: R += |x| 2^-scale
-    const unsigned long long s0 = R.w0 + v0;
-    const unsigned long long c0 = s0 < v0;
-    const unsigned long long t1 = R.w1 + v1;
-    const unsigned long long c1a = t1 < v1;
-    const unsigned long long s1 = t1 + c0;
-    const unsigned long long c1b = s1 < t1;
-    R.w0 = s0;
-    R.w1 = s1;
-    R.w2 = R.w2 + v2 + c1a + c1b;
-  } else {                                      // x > 0: R -= x 2^-scale
-    const unsigned long long b0 = R.w0 < v0;
-    R.w0 -= v0;
-    const unsigned long long t = R.w1 - v1;
-    const unsigned long long b1a = R.w1 < v1;
-    const unsigned long long b1b = t < b0;
-    R.w1 = t - b0;
-    R.w2 = R.w2 - v2 - b1a - b1b;
-  }
-  return true;
-}
-
 
 // ---------------------------------------------------------------------------
 // the tensor-core kernel: one CTA per 128 x 16 output tile, two CTAs per SM
@@ -533,8 +463,8 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
       bool ok = tc::mbar_wait(&sm.full_b, 0);
+      const uint32_t b_addr = tc::smem_u32(&sm.b[0][0]);
       for (int p = 0; p < kS && ok; ++p) {
         const int buf = p & 1;
         if (!tc::mbar_wait(&sm.full_a[buf], (p >> 1) & 1)) {
@@ -543,16 +473,18 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
         }
         tc::tc_fence_after();
         const uint32_t a_addr = tc::smem_u32(&sm.a[buf][0]);
-        for (int q = 0; q + p + 2 <= 16; ++q) {   // p+1 + q+1 <= 16
-          const int d = (p + 1) + (q + 1);        // 2..16
-          const uint32_t dcol = tmem + (uint32_t)((d - 2) * kTileN);
-          const uint32_t b_addr = tc::smem_u32(&sm.b[q][0]);
+        // digit p of A against digits q = 0 .. 14 - p of B in ONE product:
+        // the B slices lie back to back (16 rows each, 1024-byte atoms), so
+        // they form one operand of 16 (15 - p) rows, and pair (p, q) lands
+        // in the accumulator of diagonal p + q, whose columns start at
+        // (p + q) 16: the product's columns are exactly diagonals p .. 14
+        const uint32_t dcol = tmem + (uint32_t)(p * kTileN);
+        const uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN * (kS - p));
 #pragma unroll
-          for (int kk = 0; kk < kK / 16; ++kk) {
-            const uint64_t adesc = tc::sdesc_sw128_kmajor(a_addr + kk * 32);
-            const uint64_t bdesc = tc::sdesc_sw128_kmajor(b_addr + kk * 32);
-            tc::mma_bf16(dcol, adesc, bdesc, idesc, (p > 0 || kk > 0) ? 1u : 0u);
-          }
+        for (int kk = 0; kk < kK / 16; ++kk) {
+          const uint64_t adesc = tc::sdesc_sw128_kmajor(a_addr + kk * 32);
+          const uint64_t bdesc = tc::sdesc_sw128_kmajor(b_addr + kk * 32);
+          tc::mma_bf16(dcol, adesc, bdesc, idesc, (p > 0 || kk > 0) ? 1u : 0u);
         }
         tc::mma_commit(&sm.empty_a[buf]);   // frees the A buffer when these MMAs finish
       }
@@ -607,23 +539,28 @@ __device__ __forceinline__ void split_tile(double* __restrict__ C, int64_t crs, 
         for (int cc = 0; cc < CW; ++cc) {
           const int64_t j = jw + ch * CW + cc;
           if (i >= m || j >= N) continue;
-          I192 R = recombine15<CW>(v, cc);
+          int D[kDiag];
+#pragma unroll
+          for (int d = 0; d < kDiag; ++d) D[d] = __float2int_rn(__uint_as_float(v[d][cc]));
           const int scale = ei + fbv[ch * CW + cc] - 128;
           const int64_t idx = i * crs + j * cjs;
           val<2> cv = cvs[cc];
-          // C - P (plus: C + P) exactly in the accumulator when C lies on
-          // the product's grid 2^scale within the 192-bit range (the usual
-          // case), then rounded greedily to DD; otherwise P rounded to DD and
-          // the DD subtraction (addition)
-          I192 T = R;
-          const double c0 = plus ? -cv.v[0] : cv.v[0];
-          const double c1 = plus ? -cv.v[1] : cv.v[1];
-          if (i192_sub_double(T, c0, scale) && i192_sub_double(T, c1, scale)) {
-            if (!plus) i192_neg(T);
-            i192_to_dd(T, scale, cv.v[0], cv.v[1]);
+          // exact form: T = P + C (plus) or P - C, both C words added on the
+          // product's grid 2^scale, then the greedy DD rounding of T (plus)
+          // or -T; the other form (C off the grid or out of the 160-bit
+          // range, or a subnormal result) rounds P to DD and uses the DD
+          // addition (subtraction)
+          rc::I160 T = rc::diag_sum(D);
+          const unsigned long long flipc = plus ? 0ull : 0x8000000000000000ull;
+          const double w0 = __longlong_as_double((long long)((unsigned long long)__double_as_longlong(cv.v[0]) ^ flipc));
+          const double w1 = __longlong_as_double((long long)((unsigned long long)__double_as_longlong(cv.v[1]) ^ flipc));
+          double rh, rl;
+          if (rc::add_word(T, w0, scale) && rc::add_word(T, w1, scale) && rc::round_dd(T, scale, !plus, rh, rl)) {
+            cv.v[0] = rh;
+            cv.v[1] = rl;
           } else {
             val<2> pr;
-            i192_to_dd(R, scale, pr.v[0], pr.v[1]);
+            i192_to_dd(to_i192(rc::diag_sum(D)), scale, pr.v[0], pr.v[1]);
             cv = plus ? add<2>(cv, pr) : sub<2>(cv, pr);
           }
           store<2>(C, planeC, idx, cv);
@@ -994,7 +931,7 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
     MW_LAUNCH_CHECK();
   }
   {
-    ProfScope ps(geom == kGeomTrsmInv ? kPhTrsm : (geom == kGeomPanelInner ? kPhPanel : kPhGemmSplit), s);
+    ProfScope ps(geom == kGeomTrsmInv ? kPhTrsm : (geom == kGeomPanelInner ? kPhPanelInner : kPhGemmSplit), s);
     const size_t shmem = split_smem_bytes();
     MW_CUDA_CHECK(ensure_smem_limit(k_bsplit_gemm, shmem));
     k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, geom, c_off, h, tiles, bases, k0, A, aux,

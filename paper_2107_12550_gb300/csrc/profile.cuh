@@ -17,7 +17,8 @@ enum Phase {
   kPhSplitAux = 9,
   kPhBatchLu = 10,
   kPhBatchSolve = 11,
-  kNumPhases = 12
+  kPhPanelInner = 12,   // the split panel's inner tensor-core products
+  kNumPhases = 13
 };
 
 bool prof_enabled();

@@ -180,6 +180,35 @@ def test_gemm_sub_split_error_per_result(m, N, scaled):
     assert worst_el <= 2.0 ** -100
 
 
+@pytest.mark.parametrize("m,N,plus,scaled,off_grid", [(130, 70, False, False, False), (257, 33, True, True, False),
+                                                       (64, 48, False, False, True), (129, 17, True, False, True)])
+def test_split_slab_bitwise_against_model(m, N, plus, scaled, off_grid):
+    """One 64-wide slab of the split product, C -= A B (plus: C += A B),
+    bitwise against the oracle's statement of the method (oracle/ozaki.py:
+    scales, floored integers, 15 balanced digits, pairs p + q <= 16, the
+    exact form C -/+ P rounded once, else the rounded product and the DD
+    subtraction).  Ragged tiles in both directions; rows scaled by 2^+-20;
+    with off_grid, a third of C is far below the product's grid, so those
+    entries take the second form.  Bit patterns are compared, signs of
+    zeros included."""
+    from oracle import ozaki as Z
+    K = 64
+    C = _mat(2, m, N, 61)
+    A = _mat(2, m, K, 62, scale_rows=scaled)
+    B = _mat(2, K, N, 63)
+    if off_grid:
+        g = np.random.default_rng(64)
+        pick = g.random((N, m)) < 1 / 3
+        C[0, :, :m] = np.where(pick, C[0, :, :m] * 2.0 ** -200, C[0, :, :m])
+        C[1, :, :m] = np.where(pick, C[1, :, :m] * 2.0 ** -200, C[1, :, :m])
+    fn = api().gemm_add if plus else api().gemm_sub
+    got = host(fn(dev(C), dev(A), dev(B), m, 2, "split"))
+    ref, nexact = Z.update(C, A, B, m, N, K, plus=plus)
+    print(f"m={m} N={N}: {nexact} of {m * N} entries in the exact form")
+    assert (nexact < m * N) == off_grid
+    assert np.array_equal(got[:, :, :m].view(np.int64), ref.view(np.int64))
+
+
 def test_gemm_sub_split_matches_plain_closely():
     m, N, K = 300, 200, 128
     C = _mat(2, m, N, 21)
