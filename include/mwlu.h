@@ -273,8 +273,10 @@ int mw_ludecomp_batched(int prec, int count, const int* n_host, double* A, int64
 int mw_solve_batched(int prec, int count, const int* n_host, const double* LU, const int64_t* piv,
                      const double* b, double* x, void* work, size_t work_bytes, void* stream);
 /* stats: DEVICE int64[4*count]: corrections, residuals, LU info, status
- * (MW_OK, MW_ENOTCONV or MW_ESINGULAR) per system.  x: x_words planes per
- * system (inner <= x_words <= 8).  Reads one int back per refinement step. */
+ * (MW_OK, MW_ENOTCONV, MW_ESINGULAR, or MW_ETIMEOUT when a bounded wait
+ * gave up) per system.  x: x_words planes per system (inner <= x_words <=
+ * 8).  Reads one int back per refinement step, except inside a stream
+ * capture (see mw_batch_plan_cache). */
 int mw_refine_batched(int count, const int* n_host, const double* A, int a_words, const double* b,
                       int b_words, int inner, int target_bits, int max_iter, double* x, int x_words,
                       int64_t* stats, void* work, size_t work_bytes, void* stream);
@@ -321,8 +323,14 @@ int mw_refine_batched_blocked(int count, const int* n_host, const double* A, int
  * record is on (a freed buffer's address can come back holding other data).
  *   mw_batch_plan_cache(on)  returns the previous setting; off forgets all.
  *   mw_batch_plan_reset()    forgets all records.
- * The batched refinement reads one integer per step back to the host and
- * cannot be captured; the LU and solve calls can.
+ * The batched refinements can be captured too: called while their stream
+ * is being captured, they record the refinement loop as a graph while node
+ * (CUDA conditional node) whose condition a kernel sets at the end of each
+ * step to "systems still running", so a replay reads nothing back; outside
+ * a capture they read one integer per step instead.  The first call on a
+ * device must run outside a capture (it also creates the library's stream
+ * into which the loop body is captured).  Per-system results, including
+ * MW_ETIMEOUT, are in `stats`.
  */
 int mw_batch_plan_cache(int on);
 int mw_batch_plan_reset(void);

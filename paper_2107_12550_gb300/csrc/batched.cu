@@ -632,15 +632,31 @@ __global__ void k_bt_count_running(int count, const BatchState* __restrict__ st,
   if (threadIdx.x == 0) *running = cnt;
 }
 
+// per-system results; a bounded wait that gave up anywhere in the call
+// (the cursor's error word) marks every system MW_ETIMEOUT
 __global__ void k_bt_stats(int count, const BatchState* __restrict__ st, const int64_t* __restrict__ info,
-                           int64_t* __restrict__ stats) {
+                           const DeviceStatus* __restrict__ err, int64_t* __restrict__ stats) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= count) return;
   const BatchState q = st[s];
   stats[4 * s + 0] = q.corrections;
   stats[4 * s + 1] = q.residuals;
   stats[4 * s + 2] = info[s];
-  stats[4 * s + 3] = q.done == 1 ? MW_OK : (q.done == 3 ? MW_ESINGULAR : MW_ENOTCONV);
+  stats[4 * s + 3] = err->timeout ? MW_ETIMEOUT
+                                  : (q.done == 1 ? MW_OK : (q.done == 3 ? MW_ESINGULAR : MW_ENOTCONV));
+}
+
+// the number of systems still running, as the condition of the refinement's
+// graph while node (capture mode)
+__global__ void k_bt_running_cond(int count, const BatchState* __restrict__ st, cudaGraphConditionalHandle h) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int s = threadIdx.x; s < count; s += blockDim.x) c += (st[s].done == 0);
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, cnt > 0 ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -1157,6 +1173,69 @@ static BatchRefineMap batch_refine_map(int W, int count, int64_t sum_n, int64_t 
   return m;
 }
 
+// A stream of the library's own per device, into which the refinement's
+// loop body is captured while the caller's stream is being captured.  It is
+// created by the first call on the device, which must run outside a capture
+// (as the resident plans already require).
+static int body_stream(cudaStream_t* out) {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static cudaStream_t streams[kMaxDev] = {};
+  int dev = 0;
+  MW_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return MW_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev]) MW_CUDA_CHECK(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+  *out = streams[dev];
+  return MW_OK;
+}
+
+// Inside a capture of stream s: appends a while node whose body is one
+// refinement step (captured on the library's own stream) followed by
+// k_bt_running_cond, which sets the node's condition to "systems still
+// running".  The condition starts at 1 on every launch of the graph, so the
+// body runs at least once, as the loop outside a capture does.
+template <typename F1, typename F2>
+static int capture_refine_loop(cudaStream_t s, int count, const BatchState* st, F1& residual_and_check,
+                               F2& correct) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  unsigned long long id = 0;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t nd = 0;
+  MW_CUDA_CHECK(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, &edata, &nd));
+  if (cs != cudaStreamCaptureStatusActive || !g) return MW_EUNSUPPORTED;
+  cudaStream_t q = nullptr;
+  int rc = body_stream(&q);
+  if (rc) return rc;
+  cudaGraphConditionalHandle h;
+  MW_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  MW_CUDA_CHECK(cudaGraphAddNode(&node, g, deps, edata, nd, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  MW_CUDA_CHECK(cudaStreamBeginCaptureToGraph(q, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  rc = residual_and_check(q);
+  if (!rc) rc = correct(q);
+  if (!rc) {
+    prof_count(kPhRefineAux);
+    k_bt_running_cond<<<1, 256, 0, q>>>(count, st, h);
+  }
+  const cudaError_t le = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(q, &captured);
+  if (rc) return rc;
+  MW_CUDA_CHECK(le);
+  MW_CUDA_CHECK(ee);
+  MW_CUDA_CHECK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return MW_OK;
+}
+
 // blk: null for the persistent one-CTA-per-system LU, else the blocked LU
 template <int W>
 static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPlanDev& d, const double* A, int a_words,
@@ -1192,37 +1271,67 @@ static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPla
   prof_count(kPhRefineAux);
   k_bt_take_vec<<<(unsigned)((p.sum_n + 255) / 256), 256, 0, s>>>(count, d.voff, d.n, p.sum_n, z, W, x, x_words);
   MW_LAUNCH_CHECK();
-  for (int it = 0; it <= max_iter; ++it) {
+  // one refinement step, in two halves: the exact residual and the tests,
+  // then the correction solve, the exact update and the correction test
+  // (every kernel skips the systems that are no longer running)
+  auto residual_and_check = [&](cudaStream_t q) -> int {
     {
-      ProfScope ps(kPhResidual, s);
-      k_bt_residual<<<(unsigned)nrb, kResThreads, 0, s>>>(count, d.n, d.moff, d.voff, d.rb, A, a_words, b, b_words,
+      ProfScope ps(kPhResidual, q);
+      k_bt_residual<<<(unsigned)nrb, kResThreads, 0, q>>>(count, d.n, d.moff, d.voff, d.rb, A, a_words, b, b_words,
                                                           x, x_words, r, x_words, st);
       MW_LAUNCH_CHECK();
     }
     prof_count(kPhRefineAux);
-    k_bt_check<<<count, 256, 0, s>>>(count, d.n, d.voff, r, x_words, rhat, W, max_iter, st);
-    prof_count(kPhRefineAux);
-    k_bt_count_running<<<1, 256, 0, s>>>(count, st, running_d);
+    k_bt_check<<<count, 256, 0, q>>>(count, d.n, d.voff, r, x_words, rhat, W, max_iter, st);
     MW_LAUNCH_CHECK();
-    int running = 0;
-    DeviceStatus sv = {};
-    MW_CUDA_CHECK(cudaMemcpyAsync(&running, running_d, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MW_CUDA_CHECK(cudaMemcpyAsync(&sv, cursor_status(reinterpret_cast<BatchCursor*>(cur)), sizeof(sv),
-                                  cudaMemcpyDeviceToHost, s));
-    MW_CUDA_CHECK(cudaStreamSynchronize(s));
-    if (sv.timeout) timed_out = true;   // a bounded wait of the LU or a substitution gave up
-    if (running == 0 || timed_out) break;
-    rc = solve_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, rhat, z, st, cur, s);
-    if (rc) return rc;
+    return MW_OK;
+  };
+  auto correct = [&](cudaStream_t q) -> int {
+    int rc2 = solve_batched_launch<W>(count, p.nmax, d.order, d.n, d.moff, d.voff, LU, piv, rhat, z, st, cur, q);
+    if (rc2) return rc2;
     prof_count(kPhRefineAux);
-    k_bt_update<<<(unsigned)((p.sum_n + kRowsPerCta - 1) / kRowsPerCta), kRowsPerCta, 0, s>>>(
+    k_bt_update<<<(unsigned)((p.sum_n + kRowsPerCta - 1) / kRowsPerCta), kRowsPerCta, 0, q>>>(
         count, d.n, d.voff, p.sum_n, x, x_words, z, W, st);
     prof_count(kPhRefineAux);
-    k_bt_check2<<<count, 256, 0, s>>>(count, d.n, d.voff, z, W, x, x_words, target_bits, st);
+    k_bt_check2<<<count, 256, 0, q>>>(count, d.n, d.voff, z, W, x, x_words, target_bits, st);
     MW_LAUNCH_CHECK();
+    return MW_OK;
+  };
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  MW_CUDA_CHECK(cudaStreamIsCapturing(s, &cap));
+  if (cap == cudaStreamCaptureStatusNone) {
+    cudaStream_t q = nullptr;
+    rc = body_stream(&q);   // created here, outside any capture
+    if (rc) return rc;
+  }
+  if (cap == cudaStreamCaptureStatusActive) {
+    // inside a stream capture: the loop becomes a while node of the graph
+    // whose condition the last kernel of each step sets on the device (the
+    // number of systems still running), so no value comes back to the host
+    rc = capture_refine_loop(s, count, st, residual_and_check, correct);
+    if (rc) return rc;
+  } else {
+    for (int it = 0; it <= max_iter; ++it) {
+      rc = residual_and_check(s);
+      if (rc) return rc;
+      prof_count(kPhRefineAux);
+      k_bt_count_running<<<1, 256, 0, s>>>(count, st, running_d);
+      MW_LAUNCH_CHECK();
+      int running = 0;
+      DeviceStatus sv = {};
+      MW_CUDA_CHECK(cudaMemcpyAsync(&running, running_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+      MW_CUDA_CHECK(cudaMemcpyAsync(&sv, cursor_status(reinterpret_cast<BatchCursor*>(cur)), sizeof(sv),
+                                    cudaMemcpyDeviceToHost, s));
+      MW_CUDA_CHECK(cudaStreamSynchronize(s));
+      if (sv.timeout) timed_out = true;   // a bounded wait of the LU or a substitution gave up
+      if (running == 0 || timed_out) break;
+      rc = correct(s);
+      if (rc) return rc;
+    }
   }
   prof_count(kPhRefineAux);
-  k_bt_stats<<<(count + 255) / 256, 256, 0, s>>>(count, st, info, stats);
+  k_bt_stats<<<(count + 255) / 256, 256, 0, s>>>(count, st, info, cursor_status(reinterpret_cast<BatchCursor*>(cur)),
+                                                 stats);
   MW_LAUNCH_CHECK();
   return timed_out ? MW_ETIMEOUT : MW_OK;
 }

@@ -44,6 +44,10 @@ void prof_count(int phase) {
 ProfScope::ProfScope(int phase, cudaStream_t s) : phase_(phase), s_(s), a_(nullptr) {
   prof_count(phase);
   if (!g_on) return;
+  // inside a stream capture the events would become graph nodes that the
+  // host never sees complete: count the launch only
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   std::lock_guard<std::mutex> lk(g_mu);
   a_ = take_event();
   cudaEventRecord(a_, s_);

@@ -252,3 +252,49 @@ def test_mixed_batch_refine_full_range_exact():
         for i in range(n):
             v = sum((Fraction(float(c)) for c in X[:, i]), Fraction(0))
             assert abs(v - 1) <= lim, (s, n, i)
+
+
+@pytest.mark.parametrize("update", ["split", "plain"])
+def test_batched_refinement_in_one_cuda_graph(update):
+    """The whole batched refinement (blocked batched LU, substitution, and
+    the refinement loop as a while node whose condition a kernel sets) is
+    captured in one CUDA graph; each replay reproduces the eager call's x and
+    per-system statistics bitwise, with no value read back in between."""
+    n_all, k_all = W.mixed_batch_spec(512, 64, 1024, 4.0, 20.0, seed=0)
+    pick = [s for s in range(512) if n_all[s] <= 320][:24]
+    n_list = [n_all[s] for s in pick]
+    kap = [k_all[s] for s in pick]
+    A_np, b_np = W.svd_batch(n_list, kap, seed=0, processes=4, system_ids=pick)
+    A, b = dev(A_np), dev(b_np)
+    from paper_2107_12550_gb300 import _lib as L
+    prev = api().batch_plan_cache(True)
+    try:
+        work = api().batch_blocked_workspace(L.MW_OP_REFINE, 2, update, n_list)
+        x = torch.empty(8 * int(sum(n_list)), dtype=torch.float64, device="cuda")
+        st = torch.empty((len(n_list), 4), dtype=torch.int64, device="cuda")
+
+        def step():
+            _, stats = api().refine_batched_blocked(A, 4, b, 8, n_list, 2, update, 200, work=work, out=x)
+            st.copy_(stats)
+
+        step()                                   # uploads the plans, outside the capture
+        torch.cuda.synchronize()
+        x_ref, st_ref = x.clone(), st.clone()
+        assert (st_ref[:, 3] == 0).all()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(2):
+            x.zero_()
+            st.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(x, x_ref) and torch.equal(st, st_ref), update
+    finally:
+        api().batch_plan_cache(prev)
