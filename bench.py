@@ -7,8 +7,9 @@ n_i uniform in [64, 1024], condition numbers log-uniform in [1e4, 1e20];
 each A_i = U diag(sigma) V^T with U, V Haar-orthogonal (Householder QR of
 Gaussian matrices, quantised to 2^-20) and sigma geometric from 1 to 1/kappa_i
 (powers of two), stored exactly in QD (4 words); b_i = A_i * ones exactly in
-8 words, so x* = ones.  A step is one call of the library's blocked batched
-refinement: the DD LU of every system with the split-precision (bf16
+8 words, so x* = ones.  A step is one replay of a CUDA graph holding one call
+of the library's blocked batched refinement (captured once; its refinement
+loop is a graph while node whose condition the device sets): the DD LU of every system with the split-precision (bf16
 tensor-core Ozaki) trailing update, the DD substitution, and per system the
 loop r = b - A x (exact, rounded to 8 words = 424 bits), z = solve(2^-e r),
 x = RN_8(x + 2^e z) until the correction is below 2^-202 ||x||.  Metric:
@@ -765,6 +766,43 @@ def main():
     torch.cuda.synchronize()
     met_ref = batch_target_met(x.cpu().numpy(), n_list)
 
+    # the whole step captured once as a CUDA graph (the blocked batched LU and
+    # the refinement loop as a while node whose condition the device sets);
+    # the timed region replays it.  Replays must reproduce the eager step.
+    api.batch_plan_cache(True)
+    st_buf = torch.empty((args.count, 4), dtype=torch.int64, device="cuda")
+
+    def step_into():
+        _, s_ = step()
+        st_buf.copy_(s_)
+
+    step_into()
+    torch.cuda.synchronize()
+    x_eager, st_eager = x.clone(), st_buf.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step_into()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_into()
+    x.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    graph_bitwise = bool(torch.equal(x, x_eager) and torch.equal(st_buf, st_eager))
+    # eager steps timed apart, for comparison
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(max(2, args.steps // 2)):
+        step()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = g0.elapsed_time(g1) / max(2, args.steps // 2)
+
     # ---- timed region: K steps, device-resident inputs -------------------
     clocks = ClockSampler(local)
     clocks.start()
@@ -775,7 +813,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        _, stats = step()
+        graph.replay()
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -783,7 +821,7 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     met = batch_target_met(x.cpu().numpy(), n_list)
-    st = stats.cpu().numpy()
+    st = st_buf.cpu().numpy()
     met_per_step = int(sum(met)) if met == met_ref else min(int(sum(met)), int(sum(met_ref)))
     t_max, solved = combine_ranks(ms, args.steps * met_per_step, "cuda")
     value = solved / (t_max * 1e-3)
@@ -815,9 +853,9 @@ def main():
     for _ in range(e2e_steps):
         A.copy_(A_h, non_blocking=True)
         b.copy_(b_h, non_blocking=True)
-        _, st2 = step()
+        graph.replay()
         x_h.copy_(x, non_blocking=True)
-        s_h.copy_(st2, non_blocking=True)
+        s_h.copy_(st_buf, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
@@ -844,6 +882,7 @@ def main():
                    "a_words": A_WORDS, "b_words": X_WORDS, "x_words": X_WORDS, "target_bits": TARGET_BITS,
                    "l2": f"inputs_larger_than_l2 (A: {A_np.nbytes / 1e9:.1f} GB QD)"},
         "systems_met_per_step": met_per_step,
+        "cuda_graph": {"replay_bitwise_equal_to_eager": graph_bitwise, "eager_ms_per_step": eager_ms},
         "corrections_max": int(st[:, 0].max()), "corrections_mean": float(st[:, 0].mean()),
         "generation_s": gen_s,
         "lu_ms": lu_ms,
@@ -859,7 +898,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_extras:
         ex = {"comparators": batch_comparators(A, b, A_np, b_np, n_list, peak_fp64, sm_max)}
-        del A, b, x, work
+        del graph, A, b, x, work
         torch.cuda.empty_cache()
         ex["comparators"]["single_system_plain_td_n2048"] = single_system_td(peak_fp64, 3, sm_max)
         ex.update(extras(args.steps, peak_fp64, peaks))
