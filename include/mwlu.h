@@ -401,7 +401,8 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
 
 /*
  * Tuning knobs (process-wide, per precision; read at each launch).  They
- * change the blocking only: every result is bitwise the same for any value.
+ * change the blocking only: every plain-path result is bitwise the same for
+ * any value (the split path's leaf widths change roundings only).
  *   MW_TUNE_PANEL_WIDTH          panel width nb of the plain blocked LU:
  *                                32, 64 (default) or 128 (the split update
  *                                always uses 64)
@@ -424,6 +425,12 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
  *                                large, middle or small tile (DD 64x64,
  *                                32x64, 32x32; TD 32x64, 16x32, 16x16; QD
  *                                32x32, 16x32, 16x16, rows x columns)
+ *   MW_TUNE_BATCH_SPLIT_LEAF     the blocked batched split (DD) LU factors
+ *                                each 64-column panel recursively down to
+ *                                leaves of this width (8, 16 or 32; default
+ *                                8), the wider inner updates as split
+ *                                products; the results differ by roundings
+ *                                only, within the split path's error bound
  * mw_set_tuning returns the previous value, or -1 (param), -2 (prec) or
  * -3 (value) when invalid; mw_get_tuning returns the value or -1/-2.
  */
@@ -432,6 +439,7 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
 #define MW_TUNE_BATCH_CTAS_PER_SM 2
 #define MW_TUNE_SPLIT_PANEL_LEAF 3
 #define MW_TUNE_GEMM_TILE 4
+#define MW_TUNE_BATCH_SPLIT_LEAF 5
 int mw_set_tuning(int param, int prec, int value);
 int mw_get_tuning(int param, int prec);
 

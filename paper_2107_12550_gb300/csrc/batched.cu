@@ -352,17 +352,29 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         const int j0 = bk * kSolveBs;
         const int bsz = min(kSolveBs, n - j0);
         const int r0 = j0 + 2 * kSolveBs;
+        // the thread's rows advance together, one column at a time, so their
+        // independent multiply-subtract chains interleave (each row still
+        // takes its updates in ascending column order)
+        val<W> yq[kSolveWRows];
+        bool act[kSolveWRows];
 #pragma unroll
         for (int q = 0; q < kSolveWRows; ++q) {
           const int i = wt + q * 32 * kSolveWorkers;
-          if (i >= r0 && i < n) {
-            val<W> yi = smem_val<W>(ysm, nmax, i);
-#pragma unroll 4
-            for (int jj = 0; jj < bsz; ++jj)
-              yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), smem_val<W>(ysm, nmax, j0 + jj));
-            smem_put<W>(ysm, nmax, i, yi);
+          act[q] = i >= r0 && i < n;
+          if (act[q]) yq[q] = smem_val<W>(ysm, nmax, i);
+        }
+#pragma unroll 2
+        for (int jj = 0; jj < bsz; ++jj) {
+          const val<W> yj = smem_val<W>(ysm, nmax, j0 + jj);
+#pragma unroll
+          for (int q = 0; q < kSolveWRows; ++q) {
+            const int i = wt + q * 32 * kSolveWorkers;
+            if (act[q]) yq[q] = msub<W>(yq[q], load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), yj);
           }
         }
+#pragma unroll
+        for (int q = 0; q < kSolveWRows; ++q)
+          if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kSolveWorkers, yq[q]);
         __threadfence_block();
         __syncwarp();
         if (lane == 0) atomicAdd(&far_done[bk], 1);
@@ -413,17 +425,26 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const int j0 = bk * kSolveBs;
           const int bsz = min(kSolveBs, n - j0);
           const int rend = j0 - kSolveBs;          // rows [0, rend): blocks <= bk - 2
+          val<W> yq[kSolveWRows];
+          bool act[kSolveWRows];
 #pragma unroll
           for (int q = 0; q < kSolveWRows; ++q) {
             const int i = wt + q * 32 * kSolveWorkers;
-            if (i < rend) {
-              val<W> yi = smem_val<W>(ysm, nmax, i);
-#pragma unroll 4
-              for (int jj = bsz - 1; jj >= 0; --jj)
-                yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), smem_val<W>(ysm, nmax, j0 + jj));
-              smem_put<W>(ysm, nmax, i, yi);
+            act[q] = i < rend;
+            if (act[q]) yq[q] = smem_val<W>(ysm, nmax, i);
+          }
+#pragma unroll 2
+          for (int jj = bsz - 1; jj >= 0; --jj) {
+            const val<W> xj = smem_val<W>(ysm, nmax, j0 + jj);
+#pragma unroll
+            for (int q = 0; q < kSolveWRows; ++q) {
+              const int i = wt + q * 32 * kSolveWorkers;
+              if (act[q]) yq[q] = msub<W>(yq[q], load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), xj);
             }
           }
+#pragma unroll
+          for (int q = 0; q < kSolveWRows; ++q)
+            if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kSolveWorkers, yq[q]);
           __threadfence_block();
           __syncwarp();
           if (lane == 0) atomicAdd(&far_done[bk], 1);
@@ -508,10 +529,10 @@ k_bt_residual(int count, const int* __restrict__ nn, const int64_t* __restrict__
     if (!row_ok) continue;
     for (int c = 0; c < a_words; ++c) {
       const double a = __ldg(As + c * plane + (int64_t)j * n + i);
-      if (a == 0.0) continue;
+      if (zero_bits(a)) continue;
 #pragma unroll
       for (int d = 0; d < MW_LONG_WORDS; ++d)
-        if (d < x_words && xv[d] != 0.0) deposit_product(acc[lane], a, xv[d], 0, true);
+        if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], a, xv[d], 0, true);
     }
   }
   __syncthreads();
@@ -880,7 +901,7 @@ struct InnerSpec {
 };
 constexpr int kNumInner = 7;
 constexpr InnerSpec kInner[kNumInner] = {{0, 8}, {16, 8}, {0, 16}, {32, 8}, {48, 8}, {32, 16}, {0, 32}};
-constexpr int kPanelLeaf = 8;
+constexpr int kPanelLeafDefault = 8;   // MW_TUNE_BATCH_SPLIT_LEAF
 
 // tiles of an m x N product for every active system of one step
 static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool split, int bm, int bn,
@@ -1066,12 +1087,13 @@ static int upload_blocked(const BlockedPlanHost& bp, const std::vector<int>& n, 
 // the split path's panel: columns [k0 + c_off, k0 + c_off + w) factored
 // recursively -- left half, the right half's top rows solved, the rows below
 // updated by a split product, right half, then the right half's swaps on the
-// left half -- down to leaves of kPanelLeaf columns factored on the FP64 pipe
+// left half -- down to leaves of MW_TUNE_BATCH_SPLIT_LEAF columns (8, 16 or
+// 32; 8 by default) factored on the FP64 pipe
 template <int W>
 static int split_panel(const BatchPlanHost& p, const BatchView& bv, const BlockedPlanHost& bp, const BlockedDev& bd,
                        int st, int act, int k0, int c_off, int w, double* A, int64_t* piv, int64_t* info,
                        cudaStream_t s) {
-  if (w <= kPanelLeaf) return launch_bpanel<W>(bv, act, p.nmax, k0, c_off, w, A, piv, info, s);
+  if (w <= tune_get(MW_TUNE_BATCH_SPLIT_LEAF, 2)) return launch_bpanel<W>(bv, act, p.nmax, k0, c_off, w, A, piv, info, s);
   const int h = w / 2;
   int q = -1;
   for (int i = 0; i < kNumInner; ++i)

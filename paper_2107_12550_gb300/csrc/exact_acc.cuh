@@ -50,14 +50,18 @@ __device__ __forceinline__ void deposit128(u64* acc, u64 hi, u64 lo, int e, bool
   }
 }
 
+// +-0 tested on the bit pattern: a floating-point comparison would issue on
+// the FP64 pipe, which runs at 2 lanes per clock per SM on this part
+__device__ __forceinline__ bool zero_bits(double v) { return ((u64)__double_as_longlong(v) << 1) == 0ull; }
+
 __device__ __forceinline__ void deposit_double(u64* acc, double v, int extra_exp, bool negate) {
-  if (v == 0.0) return;
+  if (zero_bits(v)) return;
   const Dec d = decompose(v);
   deposit128(acc, 0ull, d.m, d.e + extra_exp, d.neg != negate);
 }
 
 __device__ __forceinline__ void deposit_product(u64* acc, double a, double b, int extra_exp, bool negate) {
-  if (a == 0.0 || b == 0.0) return;
+  if (zero_bits(a) || zero_bits(b)) return;
   const Dec da = decompose(a), db = decompose(b);
   const u64 lo = da.m * db.m;
   const u64 hi = __umul64hi(da.m, db.m);

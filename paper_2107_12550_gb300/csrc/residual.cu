@@ -47,10 +47,10 @@ k_residual(int64_t n, const double* __restrict__ A, int64_t lda, int64_t plane, 
     if (!row_ok) continue;
     for (int c = 0; c < a_words; ++c) {
       const double a = __ldg(A + c * plane + j * lda + i);
-      if (a == 0.0) continue;
+      if (zero_bits(a)) continue;
 #pragma unroll
       for (int d = 0; d < MW_LONG_WORDS; ++d)
-        if (d < x_words && xv[d] != 0.0) deposit_product(acc[lane], a, xv[d], 0, true);
+        if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], a, xv[d], 0, true);
     }
   }
   __syncthreads();

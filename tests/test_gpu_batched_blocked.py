@@ -129,6 +129,32 @@ def test_blocked_split_dd_backward_error_and_pivots():
         check_pivots_near_tie(mats[s], 2, pv[voff[s]: voff[s] + n], pivo)
 
 
+@pytest.mark.parametrize("leaf", [16, 32])
+def test_blocked_split_leaf_widths(leaf):
+    """Every leaf width the tuner may choose for the batched split panel
+    (MW_TUNE_BATCH_SPLIT_LEAF; 8 is the default, tested above): each system
+    keeps eta <= 1e-28 and pivots as the oracle's up to a near-tie."""
+    from paper_2107_12550_gb300 import _lib as L
+    lib = L.lib()
+    prev = lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, leaf)
+    try:
+        n_list = [65, 200, 300, 129, 513, 128, 257]
+        mats, vecs = _uniform_batch(2, n_list, seed=37)
+        A = dev(api().pack_matrices(mats, 2))
+        b = dev(api().pack_vectors(vecs, 2))
+        LU, piv, info = api().ludecomp_batched_blocked(A, n_list, 2, "split")
+        x = api().solve_batched(LU, piv, b, n_list, 2)
+        xs = api().unpack_vectors(host(x), n_list, 2)
+        _, voff = api().batch_offsets(n_list)
+        pv = host(piv)
+        for s, n in enumerate(n_list):
+            assert _eta(mats[s], vecs[s], xs[s]) <= 1e-28, (leaf, s, n)
+            _, pivo, _ = oracle.lu(2, mats[s])
+            check_pivots_near_tie(mats[s], 2, pv[voff[s]: voff[s] + n], pivo)
+    finally:
+        lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, prev)
+
+
 def test_blocked_split_close_to_plain_factors():
     """The batched split LU (U12 from the explicit inverse of L11 and both
     products on the tensor cores) stays within a few DD roundings of the

@@ -39,7 +39,11 @@ def test_knob_validation():
     assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, -1) == -3
     assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, 2) == 0
     assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE, 3, 0) == 2
-    assert lib.mw_set_tuning(L.MW_TUNE_GEMM_TILE + 1, 3, 0) == -1
+    assert lib.mw_get_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2) == 8
+    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 12) == -3
+    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 16) == 8
+    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 8) == 16
+    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF + 1, 3, 0) == -1
 
 
 def test_apply_from_cache(tmp_path):
@@ -55,6 +59,30 @@ def test_apply_from_cache(tmp_path):
     finally:
         lib.mw_set_tuning(0, 4, old[0])
         lib.mw_set_tuning(1, 4, old[1])
+
+
+def test_apply_split_knobs_and_packaged_overlay(tmp_path, monkeypatch):
+    B.build()
+    packaged = str(tmp_path / "packaged.json")
+    user = str(tmp_path / "user.json")
+    T.save_cache({T.key("FakeGPU", 2, "split_lu", 4096): {"split_leaf": 16, "rows_per_cta": 4},
+                  T.key("FakeGPU", 2, "batched_split", 1024): {"batch_split_leaf": 32}}, packaged)
+    T.save_cache({T.key("FakeGPU", 2, "split_lu", 4096): {"split_leaf": 32, "rows_per_cta": 8}}, user)
+    monkeypatch.setattr(T, "PACKAGED", packaged)
+    monkeypatch.setenv("MWLU_TUNE_CACHE", user)
+    lib = L.lib()
+    old = [lib.mw_get_tuning(p_, 2) for p_ in (L.MW_TUNE_SPLIT_PANEL_LEAF, L.MW_TUNE_PANEL_ROWS_PER_CTA,
+                                             L.MW_TUNE_BATCH_SPLIT_LEAF)]
+    try:
+        # the user's entry overrides the packaged one; other entries come from the package
+        assert T.apply(2, 4000, op="split_lu", gpu="FakeGPU") == {"split_leaf": 32, "rows_per_cta": 8}
+        assert lib.mw_get_tuning(L.MW_TUNE_SPLIT_PANEL_LEAF, 2) == 32
+        assert T.apply(2, 1000, op="batched_split", gpu="FakeGPU") == {"batch_split_leaf": 32}
+        assert lib.mw_get_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2) == 32
+        assert T.apply(2, 100, op="batched_split", gpu="FakeGPU") is None
+    finally:
+        for p_, v in zip((L.MW_TUNE_SPLIT_PANEL_LEAF, L.MW_TUNE_PANEL_ROWS_PER_CTA, L.MW_TUNE_BATCH_SPLIT_LEAF), old):
+            lib.mw_set_tuning(p_, 2, v)
 
 
 @pytest.mark.gpu
