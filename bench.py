@@ -198,6 +198,30 @@ def panel_sum_sq(n: int, nb: int = 64) -> int:
 
 
 
+DEFAULT_KNOBS = {"panel_width": 64, "rows_per_cta": 8, "ctas_per_sm": 2, "split_leaf": 0, "gemm_tile": 0,
+                 "batch_split_leaf": 8}
+
+
+def reset_knobs():
+    """Every tuning knob back to the library's default, for every precision."""
+    from paper_2107_12550_gb300 import _lib as L
+    params = {"panel_width": L.MW_TUNE_PANEL_WIDTH, "rows_per_cta": L.MW_TUNE_PANEL_ROWS_PER_CTA,
+              "ctas_per_sm": L.MW_TUNE_BATCH_CTAS_PER_SM, "split_leaf": L.MW_TUNE_SPLIT_PANEL_LEAF,
+              "gemm_tile": L.MW_TUNE_GEMM_TILE, "batch_split_leaf": L.MW_TUNE_BATCH_SPLIT_LEAF}
+    for name, prm in params.items():
+        for w in (2, 3, 4):
+            L.lib().mw_set_tuning(prm, w, DEFAULT_KNOBS[name])
+
+
+def tuned(prec: int, n: int, op: str) -> dict:
+    """The knobs of the tuning cache (the packaged GB300 table under the
+    user's cache) for this operation and size, applied over the defaults;
+    {} when the cache has no entry."""
+    from paper_2107_12550_gb300 import tune as T
+    reset_knobs()
+    return T.apply(prec, n, op=op) or {}
+
+
 def split_trail_mma_flops(n_list, nb: int = 64) -> int:
     """bf16 MMA flops of the trailing split updates of one blocked batched
     LU: per panel step and active system, ceil(m / 128) x ceil(m / 16) tiles
@@ -318,6 +342,7 @@ def single_system_td(peak_fp64, steps, sm_max_mhz):
     x = torch.empty((X_WORDS, N), dtype=torch.float64, device="cuda")
     work = api.workspace(L.MW_OP_REFINE, INNER, 0, N)
     stream = torch.cuda.current_stream()
+    knobs = tuned(INNER, N, "lu")
     f = lambda: api.refine(A, b, INNER, TARGET_BITS, x_words=X_WORDS, work=work, out=x)
     r = f()
     L.profile_read(reset=True)
@@ -331,7 +356,7 @@ def single_system_td(peak_fp64, steps, sm_max_mhz):
     achieved = instr / (gemm_ms * 1e-3) if gemm_ms > 0 else 0.0
     ceiling = FP64_LANES_PER_CLK * sm_max_mhz * 1e6 if sm_max_mhz else None
     lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain")) / steps
-    out = {"workload": "svd_kappa1e10_n2048_qd_stored_td_inner_plain_refine_to_2^-200",
+    out = {"workload": "svd_kappa1e10_n2048_qd_stored_td_inner_plain_refine_to_2^-200", "tuning": knobs,
            "solves_per_s": (1.0 if ok else 0.0) / (ms * 1e-3), "ms_per_solve": ms,
            "corrections": r.corrections, "residuals": r.residuals, "target_met": ok,
            "lu_ms": lu_ms, "lu_td_gops": (2.0 / 3.0) * N ** 3 / (lu_ms * 1e-3) / 1e9 if lu_ms else None,
@@ -343,6 +368,7 @@ def single_system_td(peak_fp64, steps, sm_max_mhz):
                         "traffic": GEMM_TD_TRAFFIC_PER_LAUNCH, "traffic_unit": "bytes per launch (ncu)",
                         "algorithmic_per_launch": instr / max(gemm_launches, 1)}}
     # the split-precision DD inner LU on the same system
+    reset_knobs()
     work2 = api.workspace(L.MW_OP_REFINE, 2, 1, N)
     g = lambda: api.refine(A, b, 2, TARGET_BITS, update="split", x_words=X_WORDS, work=work2, out=x)
     r2 = g()
@@ -439,7 +465,12 @@ def extras(steps, peak_fp64, peaks):
     n3 = 4096
     Au = torch.from_numpy(W.uniform_matrix(n3, 2, seed=0)).cuda()
     lu = {}
+    knobs3 = {}
     for upd, reps in (("plain", 1), ("split", 3)):
+        if upd == "split":
+            knobs3 = tuned(2, n3, "split_lu")
+        else:
+            reset_knobs()
         wk = api.workspace(L.MW_OP_LUDECOMP, 2, 1 if upd == "split" else 0, n3)
         g = lambda: api.ludecomp(Au, 2, upd, work=wk)
         g()
@@ -462,7 +493,7 @@ def extras(steps, peak_fp64, peaks):
     split_gemm_ms = lu["split"]["phase_ms"].get("gemm_split", 0.0)
     out["lu_dd_n4096"] = {
         "plain_dd_gops": lu["plain"]["dd_gops"], "split_dd_gops": lu["split"]["dd_gops"],
-        "plain_ms": lu["plain"]["ms"], "split_ms": lu["split"]["ms"],
+        "plain_ms": lu["plain"]["ms"], "split_ms": lu["split"]["ms"], "split_tuning": knobs3,
         "split_phase_ms": lu["split"]["phase_ms"],
         "split_gemm_roofline": {"bound": "tensor", "kernel": "k_split_gemm (bf16 tcgen05, TMEM)",
                                 "achieved": mma_flops / (split_gemm_ms * 1e-3) / 1e12 if split_gemm_ms else None,
@@ -479,6 +510,7 @@ def extras(steps, peak_fp64, peaks):
     # large DD LU, n = 8192, split update (the plain update would take ~11 s)
     n8 = 8192
     A8 = torch.from_numpy(W.uniform_matrix(n8, 2, seed=0)).cuda()
+    knobs8 = tuned(2, n8, "split_lu")
     wk8 = api.workspace(L.MW_OP_LUDECOMP, 2, 1, n8)
     g8 = lambda: api.ludecomp(A8, 2, "split", work=wk8)
     g8()
@@ -487,7 +519,8 @@ def extras(steps, peak_fp64, peaks):
     t8, (_, _, info8) = _time(g8, 1, stream)
     L.profile_enable(False)
     prof8 = L.profile_read(reset=True)
-    out["lu_dd_n8192_split"] = {"ms": t8, "dd_gops": (2.0 / 3.0) * n8 ** 3 / (t8 * 1e-3) / 1e9,
+    reset_knobs()
+    out["lu_dd_n8192_split"] = {"ms": t8, "dd_gops": (2.0 / 3.0) * n8 ** 3 / (t8 * 1e-3) / 1e9, "tuning": knobs8,
                                 "info": int(info8.item()),
                                 "phase_ms": {k: v[0] for k, v in prof8.items() if v[1]}}
     del A8, wk8
@@ -761,6 +794,7 @@ def main():
                                           work=work, out=x)
 
     peak_fp64 = api.peak_fp64()            # project microbenchmark, instructions/s
+    knobs = tuned(2, N_HI, "batched_split")
     for _ in range(max(args.warmup, 1)):
         _, stats = step()
     torch.cuda.synchronize()
@@ -880,6 +914,7 @@ def main():
                    "log10_kappa_range": [LOG10_KAPPA_LO, LOG10_KAPPA_HI], "global_batch": args.count * world,
                    "seq_len": 0, "parallelism": f"replicas{world}", "inner": "dd", "lu_update": "split",
                    "a_words": A_WORDS, "b_words": X_WORDS, "x_words": X_WORDS, "target_bits": TARGET_BITS,
+                   "tuning": {"op": "batched_split", "applied": knobs},
                    "l2": f"inputs_larger_than_l2 (A: {A_np.nbytes / 1e9:.1f} GB QD)"},
         "systems_met_per_step": met_per_step,
         "cuda_graph": {"replay_bitwise_equal_to_eager": graph_bitwise, "eager_ms_per_step": eager_ms},
