@@ -220,9 +220,13 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 // dynamic shared memory: 2 * W * nmax doubles
 // ---------------------------------------------------------------------------
 constexpr int kSolveBs = 32;
-constexpr int kSolveThreads = 512;                               // one CTA per SM
-constexpr int kSolveWorkers = kSolveThreads / 32 - 1;            // worker warps
-constexpr int kSolveWRows = (kBatchMaxN + 32 * kSolveWorkers - 1) / (32 * kSolveWorkers);  // rows per worker thread
+// The substitution's CTA size NT: 512 threads (one CTA per SM) or 256 (two
+// per SM, MW_TUNE_BATCH_SOLVE_CTAS); one leader warp, the rest workers
+template <int NT>
+struct SolveShape {
+  static constexpr int kWorkers = NT / 32 - 1;                                        // worker warps
+  static constexpr int kWRows = (kBatchMaxN + 32 * kWorkers - 1) / (32 * kWorkers);  // rows per worker thread
+};
 constexpr unsigned long long kSolveSpin = 1ull << 24;
 
 template <int W>
@@ -257,12 +261,14 @@ __device__ __forceinline__ bool solve_wait(P pred, volatile int* abort_flag, Bat
   return true;
 }
 
-template <int W>
-__global__ void __launch_bounds__(kSolveThreads, 1)
+template <int W, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
                 const int64_t* __restrict__ moff, const int64_t* __restrict__ voff,
                 const double* __restrict__ LU, const int64_t* __restrict__ piv, const double* b,
                 double* x, const BatchState* __restrict__ st, BatchCursor* cur, unsigned long long spin_limit) {
+  constexpr int kWorkers = SolveShape<NT>::kWorkers;
+  constexpr int kWRows = SolveShape<NT>::kWRows;
   extern __shared__ double bsm[];
   double* ysm = bsm;
   double* dsm = bsm + W * nmax;
@@ -286,18 +292,18 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
     const int64_t* pv = piv + voff[s];
     const double* bs = b + (int64_t)W * voff[s];
     double* xs = x + (int64_t)W * voff[s];
-    for (int i = tid; i < n; i += kSolveThreads)
+    for (int i = tid; i < n; i += NT)
 #pragma unroll
       for (int c = 0; c < W; ++c) ysm[c * nmax + i] = bs[c * n + i];
     // reciprocals of the diagonal, all j in parallel
-    for (int j = tid; j < n; j += kSolveThreads) {
+    for (int j = tid; j < n; j += NT) {
       val<W> one;
 #pragma unroll
       for (int c = 0; c < W; ++c) one.v[c] = 0.0;
       one.v[0] = 1.0;
       smem_put<W>(dsm, nmax, j, div<W>(one, load_ro<W>(a, plane, (int64_t)j * n + j)));
     }
-    for (int q = tid; q < nb + 2; q += kSolveThreads) far_done[q] = 0;
+    for (int q = tid; q < nb + 2; q += NT) far_done[q] = 0;
     if (tid == 0) {
       tri_done = -1;
       s_abort = 0;
@@ -321,7 +327,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
       for (int bk = 0; bk < nb; ++bk) {
         const int j0 = bk * kSolveBs;
         const int bsz = min(kSolveBs, n - j0);
-        if (bk >= 2 && !solve_wait([&] { return vfar[bk - 2] >= kSolveWorkers; }, vab, cur, spin_limit)) break;
+        if (bk >= 2 && !solve_wait([&] { return vfar[bk - 2] >= kWorkers; }, vab, cur, spin_limit)) break;
         const int i = j0 + lane;
         val<W> yi;
         if (lane < bsz) yi = smem_val<W>(ysm, nmax, i);
@@ -355,11 +361,11 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         // the thread's rows advance together, one column at a time, so their
         // independent multiply-subtract chains interleave (each row still
         // takes its updates in ascending column order)
-        val<W> yq[kSolveWRows];
-        bool act[kSolveWRows];
+        val<W> yq[kWRows];
+        bool act[kWRows];
 #pragma unroll
-        for (int q = 0; q < kSolveWRows; ++q) {
-          const int i = wt + q * 32 * kSolveWorkers;
+        for (int q = 0; q < kWRows; ++q) {
+          const int i = wt + q * 32 * kWorkers;
           act[q] = i >= r0 && i < n;
           if (act[q]) yq[q] = smem_val<W>(ysm, nmax, i);
         }
@@ -367,21 +373,21 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         for (int jj = 0; jj < bsz; ++jj) {
           const val<W> yj = smem_val<W>(ysm, nmax, j0 + jj);
 #pragma unroll
-          for (int q = 0; q < kSolveWRows; ++q) {
-            const int i = wt + q * 32 * kSolveWorkers;
+          for (int q = 0; q < kWRows; ++q) {
+            const int i = wt + q * 32 * kWorkers;
             if (act[q]) yq[q] = msub<W>(yq[q], load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), yj);
           }
         }
 #pragma unroll
-        for (int q = 0; q < kSolveWRows; ++q)
-          if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kSolveWorkers, yq[q]);
+        for (int q = 0; q < kWRows; ++q)
+          if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kWorkers, yq[q]);
         __threadfence_block();
         __syncwarp();
         if (lane == 0) atomicAdd(&far_done[bk], 1);
       }
     }
     __syncthreads();
-    for (int q = tid; q < nb + 2; q += kSolveThreads) far_done[q] = 0;
+    for (int q = tid; q < nb + 2; q += NT) far_done[q] = 0;
     if (tid == 0) tri_done = nb;
     __syncthreads();
     // ---- backward: upper U with the reciprocals ----
@@ -390,7 +396,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         for (int bk = nb - 1; bk >= 0; --bk) {
           const int j0 = bk * kSolveBs;
           const int bsz = min(kSolveBs, n - j0);
-          if (bk <= nb - 3 && !solve_wait([&] { return vfar[bk + 2] >= kSolveWorkers; }, vab, cur, spin_limit)) break;
+          if (bk <= nb - 3 && !solve_wait([&] { return vfar[bk + 2] >= kWorkers; }, vab, cur, spin_limit)) break;
           const int i = j0 + lane;
           val<W> yi, di;
           if (lane < bsz) {
@@ -425,11 +431,11 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const int j0 = bk * kSolveBs;
           const int bsz = min(kSolveBs, n - j0);
           const int rend = j0 - kSolveBs;          // rows [0, rend): blocks <= bk - 2
-          val<W> yq[kSolveWRows];
-          bool act[kSolveWRows];
+          val<W> yq[kWRows];
+          bool act[kWRows];
 #pragma unroll
-          for (int q = 0; q < kSolveWRows; ++q) {
-            const int i = wt + q * 32 * kSolveWorkers;
+          for (int q = 0; q < kWRows; ++q) {
+            const int i = wt + q * 32 * kWorkers;
             act[q] = i < rend;
             if (act[q]) yq[q] = smem_val<W>(ysm, nmax, i);
           }
@@ -437,14 +443,14 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           for (int jj = bsz - 1; jj >= 0; --jj) {
             const val<W> xj = smem_val<W>(ysm, nmax, j0 + jj);
 #pragma unroll
-            for (int q = 0; q < kSolveWRows; ++q) {
-              const int i = wt + q * 32 * kSolveWorkers;
+            for (int q = 0; q < kWRows; ++q) {
+              const int i = wt + q * 32 * kWorkers;
               if (act[q]) yq[q] = msub<W>(yq[q], load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), xj);
             }
           }
 #pragma unroll
-          for (int q = 0; q < kSolveWRows; ++q)
-            if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kSolveWorkers, yq[q]);
+          for (int q = 0; q < kWRows; ++q)
+            if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kWorkers, yq[q]);
           __threadfence_block();
           __syncwarp();
           if (lane == 0) atomicAdd(&far_done[bk], 1);
@@ -452,7 +458,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
       }
     }
     __syncthreads();
-    for (int i = tid; i < n; i += kSolveThreads)
+    for (int i = tid; i < n; i += NT)
 #pragma unroll
       for (int c = 0; c < W; ++c) xs[c * n + i] = ysm[c * nmax + i];
     __syncthreads();
@@ -713,12 +719,22 @@ static int solve_batched_launch(int count, int nmax, const int* order, const int
   BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
   MW_CUDA_CHECK(cudaMemsetAsync(&cur->next, 0, sizeof(cur->next), s));   // the error word stays
   const size_t shmem = sizeof(double) * 2 * W * (size_t)nmax;
-  int rc = set_smem(k_solve_batched<W>, shmem);
-  if (rc) return rc;
-  ProfScope ps(kPhBatchSolve, s);
-  const int grid = std::min(count, device_sm_count());
-  k_solve_batched<W><<<grid, kSolveThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x,
-                                                       static_cast<const BatchState*>(st), cur, wait_limit());
+  const int per_sm = tune_get(MW_TUNE_BATCH_SOLVE_CTAS, W) == 2 ? 2 : 1;
+  const int grid = std::min(count, per_sm * device_sm_count());
+  const BatchState* bst = static_cast<const BatchState*>(st);
+  if (per_sm == 2) {
+    int rc = set_smem(k_solve_batched<W, 256>, shmem);
+    if (rc) return rc;
+    ProfScope ps(kPhBatchSolve, s);
+    k_solve_batched<W, 256><<<grid, 256, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x, bst, cur,
+                                                     wait_limit());
+  } else {
+    int rc = set_smem(k_solve_batched<W, 512>, shmem);
+    if (rc) return rc;
+    ProfScope ps(kPhBatchSolve, s);
+    k_solve_batched<W, 512><<<grid, 512, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x, bst, cur,
+                                                     wait_limit());
+  }
   MW_LAUNCH_CHECK();
   return MW_OK;
 }

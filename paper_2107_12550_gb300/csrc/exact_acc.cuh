@@ -63,8 +63,15 @@ __device__ __forceinline__ void deposit_double(u64* acc, double v, int extra_exp
 __device__ __forceinline__ void deposit_product(u64* acc, double a, double b, int extra_exp, bool negate) {
   if (zero_bits(a) || zero_bits(b)) return;
   const Dec da = decompose(a), db = decompose(b);
-  const u64 lo = da.m * db.m;
-  const u64 hi = __umul64hi(da.m, db.m);
+  // the 106-bit product of the two 53-bit significands from 32 x 32-bit
+  // products (integer multiply-adds only)
+  const uint32_t al = (uint32_t)da.m, ah = (uint32_t)(da.m >> 32);
+  const uint32_t bl = (uint32_t)db.m, bh = (uint32_t)(db.m >> 32);
+  const u64 ll = (u64)al * bl;
+  const u64 mid = (u64)al * bh + (u64)ah * bl;      // < 2^54
+  const u64 hh = (u64)ah * bh;                       // < 2^42
+  const u64 lo = ll + (mid << 32);
+  const u64 hi = hh + (mid >> 32) + (lo < ll ? 1ull : 0ull);
   deposit128(acc, hi, lo, da.e + db.e + extra_exp, (da.neg != db.neg) != negate);
 }
 

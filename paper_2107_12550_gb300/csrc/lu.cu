@@ -873,11 +873,10 @@ k_bswap_apply(BatchView bv, int k0, int c_lo, int c_hi, double* __restrict__ A, 
   const int n = bv.n[sys];
   const int j0 = max(0, k0 + c_lo);
   const int j1 = min(n, k0 + c_hi);
+  const int64_t j = (int64_t)j0 + (int64_t)blockIdx.z * 8 + (threadIdx.x >> 5);
+  if (j >= j1) return;   // uniform per warp
   const int64_t plane = (int64_t)n * n;
-  // the CTAs of a system stride over its columns, 8 per round (one per
-  // warp), so the grid's depth stays small for uneven batches
-  for (int64_t j = (int64_t)j0 + (int64_t)blockIdx.z * 8 + (threadIdx.x >> 5); j < j1; j += (int64_t)gridDim.z * 8)
-    apply_swap_plan(A + (int64_t)W * bv.moff[sys] + blockIdx.y * plane + j * n, plans + blockIdx.x);
+  apply_swap_plan(A + (int64_t)W * bv.moff[sys] + blockIdx.y * plane + j * n, plans + blockIdx.x);
 }
 
 // inside the panel, block of 2H columns at column c0 = k0 + c_off: the top H
@@ -1174,7 +1173,7 @@ int launch_bswap_apply(const BatchView& bv, int act, int k0, int c_lo, int c_hi,
                        const SwapPlan* plans, cudaStream_t s) {
   if (act <= 0 || max_cols <= 0) return MW_OK;
   ProfScope ps(kPhLaswp, s);
-  k_bswap_apply<W><<<dim3((unsigned)act, W, (unsigned)std::min((max_cols + 7) / 8, 8)), 256, 0, s>>>(bv, k0, c_lo, c_hi, A,
+  k_bswap_apply<W><<<dim3((unsigned)act, W, (unsigned)((max_cols + 7) / 8)), 256, 0, s>>>(bv, k0, c_lo, c_hi, A,
                                                                                          plans);
   MW_LAUNCH_CHECK();
   return MW_OK;

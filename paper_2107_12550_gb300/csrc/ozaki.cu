@@ -158,7 +158,6 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
 // ---------------------------------------------------------------------------
 constexpr int kSliceRows = 16;   // rows (or columns) per CTA
 constexpr int kSliceThreads = kSliceRows * (kK / 8);
-constexpr int kSliceGridY = 8;   // batched slicing: CTAs per system, striding over its 16-row blocks
 
 // 8 entries (both words) of row or column r from k = kc*8; returns the
 // magnitude bits of max |hi| (integer operations, off the FP64 pipe)
@@ -662,7 +661,7 @@ __device__ __forceinline__ SplitOperands batch_operands(int geom, double* a, int
   return o;
 }
 
-// grid (act, <= kSliceGridY): the 16-row blocks y, y + gridDim.y, ... of system order[blockIdx.x]
+// grid (act, 8 * max_mt): 16 rows blockIdx.y of system order[blockIdx.x]
 __global__ void __launch_bounds__(kSliceThreads)
 k_bslice_rows(BatchView bv, int geom, int c_off, int h, const int2* __restrict__ bases, int k0,
               double* __restrict__ A, const double* __restrict__ aux, unsigned char* __restrict__ aslices,
@@ -672,19 +671,14 @@ k_bslice_rows(BatchView bv, int geom, int c_off, int h, const int2* __restrict__
   const int n = bv.n[sys];
   const SplitOperands o =
       batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK, c_off, h);
-  if (o.m <= 0 || o.N <= 0) return;   // uniform per CTA
-  const int64_t rows = (o.m + kTileM - 1) / kTileM * kTileM;
+  const int64_t rbase = (int64_t)blockIdx.y * kSliceRows;
+  if (o.m <= 0 || o.N <= 0 || rbase >= (o.m + kTileM - 1) / kTileM * kTileM) return;   // uniform per CTA
   const int abase = bases[pos].x;
-  // the CTAs of a system stride over its 16-row blocks, so the grid has a
-  // fixed small height instead of one CTA per block of the largest system
-  for (int64_t rbase = (int64_t)blockIdx.y * kSliceRows; rbase < rows; rbase += (int64_t)gridDim.y * kSliceRows) {
-    slice_rows16(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices + (int64_t)abase * kS * kASliceBytes,
-                 ea + (int64_t)abase * kTileM, rbase);
-    __syncthreads();   // the block maxima in shared memory are rewritten next round
-  }
+  slice_rows16(o.L, o.lrs, o.lks, o.planeL, o.m, o.K, aslices + (int64_t)abase * kS * kASliceBytes,
+               ea + (int64_t)abase * kTileM, rbase);
 }
 
-// grid (act, <= kSliceGridY): the 16-column blocks y, y + gridDim.y, ... of system order[blockIdx.x]
+// grid (act, 8 * max_cb): 16 columns blockIdx.y of system order[blockIdx.x]
 __global__ void __launch_bounds__(kSliceThreads)
 k_bslice_cols(BatchView bv, int geom, int c_off, int h, const int2* __restrict__ bases, int k0,
               double* __restrict__ A, const double* __restrict__ aux, unsigned char* __restrict__ bslices,
@@ -694,14 +688,11 @@ k_bslice_cols(BatchView bv, int geom, int c_off, int h, const int2* __restrict__
   const int n = bv.n[sys];
   const SplitOperands o =
       batch_operands(geom, A + 2 * bv.moff[sys], n, k0, aux + (int64_t)pos * 2 * kK * kK, c_off, h);
-  if (o.m <= 0 || o.N <= 0) return;   // uniform per CTA
-  const int64_t cols = (o.N + kTileN - 1) / kTileN * kTileN;
+  const int64_t jbase = (int64_t)blockIdx.y * kSliceRows;
+  if (o.m <= 0 || o.N <= 0 || jbase >= (o.N + kTileN - 1) / kTileN * kTileN) return;   // uniform per CTA
   const int bbase = bases[pos].y;
-  for (int64_t jbase = (int64_t)blockIdx.y * kSliceRows; jbase < cols; jbase += (int64_t)gridDim.y * kSliceRows) {
-    slice_cols16(o.U, o.uks, o.ujs, o.planeU, o.N, o.K, bslices + (int64_t)bbase * kS * kBSliceBytes,
-                 fb + (int64_t)bbase * kTileN, jbase);
-    __syncthreads();
-  }
+  slice_cols16(o.U, o.uks, o.ujs, o.planeU, o.N, o.K, bslices + (int64_t)bbase * kS * kBSliceBytes,
+               fb + (int64_t)bbase * kTileN, jbase);
 }
 
 __global__ void __launch_bounds__(kSplitThreads, 2)
@@ -933,12 +924,10 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
   int* fb = reinterpret_cast<int*>(ws + off);
   {
     ProfScope ps(kPhSplitAux, s);
-    const int ry = std::min(max_mt * kTileM / kSliceRows, kSliceGridY);
-    const int cy = std::min(max_cb * 128 / kSliceRows, kSliceGridY);
-    k_bslice_rows<<<dim3((unsigned)act, (unsigned)std::max(ry, 1)), kSliceThreads, 0, s>>>(
+    k_bslice_rows<<<dim3((unsigned)act, (unsigned)(max_mt * kTileM / kSliceRows)), kSliceThreads, 0, s>>>(
         bv, geom, c_off, h, bases, k0, A, aux, aslices, ea);
     MW_LAUNCH_CHECK();
-    k_bslice_cols<<<dim3((unsigned)act, (unsigned)std::max(cy, 1)), kSliceThreads, 0, s>>>(
+    k_bslice_cols<<<dim3((unsigned)act, (unsigned)(max_cb * 128 / kSliceRows)), kSliceThreads, 0, s>>>(
         bv, geom, c_off, h, bases, k0, A, aux, bslices, fb);
     MW_LAUNCH_CHECK();
   }
