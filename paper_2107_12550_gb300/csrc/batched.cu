@@ -528,17 +528,32 @@ k_bt_residual(int count, const int* __restrict__ nn, const int64_t* __restrict__
   __syncthreads();
   if (warp < b_words && row_ok) deposit_double(acc[lane], bs[warp * n + i], 0, false);
   constexpr int NWARP = kResThreads / 32;
-  for (int j = warp; j < n; j += NWARP) {
-    double xv[MW_LONG_WORDS];
+  // the next column's words are loaded before this column's deposits, so a
+  // warp keeps one column of A (and x) in flight while it accumulates
+  // (the residual is otherwise bound by the latency of these loads)
+  double xv[MW_LONG_WORDS], av[MW_LONG_WORDS], xn[MW_LONG_WORDS], an[MW_LONG_WORDS];
+  auto load_col = [&](int j, double (&xo)[MW_LONG_WORDS], double (&ao)[MW_LONG_WORDS]) {
 #pragma unroll
-    for (int d = 0; d < MW_LONG_WORDS; ++d) xv[d] = (d < x_words) ? __ldg(xs + d * n + j) : 0.0;
+    for (int d = 0; d < MW_LONG_WORDS; ++d) xo[d] = (d < x_words && j < n) ? __ldg(xs + d * n + j) : 0.0;
+    const double* col = As + (int64_t)j * n + i;
+#pragma unroll
+    for (int c = 0; c < MW_LONG_WORDS; ++c) ao[c] = (c < a_words && j < n && row_ok) ? __ldg(col + c * plane) : 0.0;
+  };
+  load_col(warp, xn, an);
+  for (int j = warp; j < n; j += NWARP) {
+#pragma unroll
+    for (int d = 0; d < MW_LONG_WORDS; ++d) {
+      xv[d] = xn[d];
+      av[d] = an[d];
+    }
+    load_col(j + NWARP, xn, an);
     if (!row_ok) continue;
-    for (int c = 0; c < a_words; ++c) {
-      const double a = __ldg(As + c * plane + (int64_t)j * n + i);
-      if (zero_bits(a)) continue;
+#pragma unroll
+    for (int c = 0; c < MW_LONG_WORDS; ++c) {
+      if (c >= a_words || zero_bits(av[c])) continue;
 #pragma unroll
       for (int d = 0; d < MW_LONG_WORDS; ++d)
-        if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], a, xv[d], 0, true);
+        if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], av[c], xv[d], 0, true);
     }
   }
   __syncthreads();
