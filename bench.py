@@ -67,10 +67,13 @@ SPLIT_TILE_FLOPS = 120 * 2 * 128 * 16 * 64
 # dram__bytes_write.sum over the 124 launches of one bench run, averaged per
 # launch.  Must be re-measured whenever k_gemm_plain changes.
 GEMM_TD_TRAFFIC_PER_LAUNCH = 40.40e6
-# DRAM bytes per multiword multiply-subtract of the batched substitution
-# (ncu, k_solve_batched on 64 systems of the headline distribution, scaled
-# by the units a launch processes); None until measured for this kernel
-SOLVE_BATCHED_TRAFFIC_PER_MSUB = None
+# DRAM bytes per multiword multiply-subtract of the batched substitution:
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_solve_batched<DD>
+# launch (the second solve of the 152-system mixed batch, n <= 1024, all 152
+# systems running: 998.5 + 4.5 MB) over its sum of n^2 (59.08 M); the
+# algorithmic figure is 16 bytes (each DD entry of L and U read once).  Must
+# be re-measured whenever k_solve_batched changes.
+SOLVE_BATCHED_TRAFFIC_PER_MSUB = 1003.0e6 / 59.08e6
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

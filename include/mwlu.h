@@ -431,10 +431,6 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
  *                                8), the wider inner updates as split
  *                                products; the results differ by roundings
  *                                only, within the split path's error bound
- *   MW_TUNE_BATCH_SOLVE_CTAS     CTAs per SM of the batched substitution: 1
- *                                (default: 512 threads, 15 worker warps per
- *                                system) or 2 (256 threads, 7 worker warps;
- *                                two systems share an SM); bitwise the same
  * mw_set_tuning returns the previous value, or -1 (param), -2 (prec) or
  * -3 (value) when invalid; mw_get_tuning returns the value or -1/-2.
  */
@@ -444,7 +440,6 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
 #define MW_TUNE_SPLIT_PANEL_LEAF 3
 #define MW_TUNE_GEMM_TILE 4
 #define MW_TUNE_BATCH_SPLIT_LEAF 5
-#define MW_TUNE_BATCH_SOLVE_CTAS 6
 int mw_set_tuning(int param, int prec, int value);
 int mw_get_tuning(int param, int prec);
 

@@ -220,13 +220,14 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 // dynamic shared memory: 2 * W * nmax doubles
 // ---------------------------------------------------------------------------
 constexpr int kSolveBs = 32;
-// The substitution's CTA size NT: 512 threads (one CTA per SM) or 256 (two
-// per SM, MW_TUNE_BATCH_SOLVE_CTAS); one leader warp, the rest workers
-template <int NT>
-struct SolveShape {
-  static constexpr int kWorkers = NT / 32 - 1;                                        // worker warps
-  static constexpr int kWRows = (kBatchMaxN + 32 * kWorkers - 1) / (32 * kWorkers);  // rows per worker thread
-};
+// The substitution's CTA: 512 threads, one per SM; one leader warp, the rest
+// workers.  Row groups of 32 (one row per lane) are dealt to the workers so
+// that each SM sub-partition holds a quarter of them (see the kernel).
+constexpr int kSolveThreads = 512;
+constexpr int kSolveWorkers = kSolveThreads / 32 - 1;                            // worker warps
+constexpr int kSolveMinSub = kSolveWorkers / 4;                                  // workers on sub-partition 0
+constexpr int kSolveWGroups = (kBatchMaxN / 32 / 4 + kSolveMinSub - 1) / kSolveMinSub;  // groups per worker
+static_assert(kBatchMaxN % 128 == 0, "row groups split evenly over the four sub-partitions");
 constexpr unsigned long long kSolveSpin = 1ull << 24;
 
 template <int W>
@@ -261,14 +262,15 @@ __device__ __forceinline__ bool solve_wait(P pred, volatile int* abort_flag, Bat
   return true;
 }
 
-template <int W, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT)
+template <int W>
+__global__ void __launch_bounds__(kSolveThreads, 1)
 k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* __restrict__ nn,
                 const int64_t* __restrict__ moff, const int64_t* __restrict__ voff,
                 const double* __restrict__ LU, const int64_t* __restrict__ piv, const double* b,
                 double* x, const BatchState* __restrict__ st, BatchCursor* cur, unsigned long long spin_limit) {
-  constexpr int kWorkers = SolveShape<NT>::kWorkers;
-  constexpr int kWRows = SolveShape<NT>::kWRows;
+  constexpr int NT = kSolveThreads;
+  constexpr int kWorkers = kSolveWorkers;
+  constexpr int kWRows = kSolveWGroups;
   extern __shared__ double bsm[];
   double* ysm = bsm;
   double* dsm = bsm + W * nmax;
@@ -279,7 +281,20 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
   volatile int* vtri = &tri_done;
   volatile int* vab = &s_abort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wt = tid - 32;                     // worker thread index (warp >= 1)
+  // Row group g (rows 32 g .. 32 g + 31, one per lane; the same as solve
+  // block g) belongs to a worker warp chosen so that the groups still active
+  // in any step, a contiguous range, spread evenly over the four SM
+  // sub-partitions (warp w issues on sub-partition w % 4): g goes to
+  // sub-partition 1, 2, 3, 0 for g % 4 = 0, 1, 2, 3 (0 also hosts the
+  // leader and has one worker fewer), and there to the worker of rank
+  // (g / 4) mod (its worker count).  A worker's groups are therefore
+  // g = 4 (rank + m nsub) + spos, m = 0, 1, ...  Ownership is fixed for the
+  // whole call, so each row's updates stay in program order on one warp.
+  const int sub = warp & 3;
+  const int spos = (sub + 3) & 3;                            // position of sub in (1, 2, 3, 0)
+  const int nsub = (sub == 0) ? kSolveMinSub : (NT / 32 - sub + 3) / 4;   // workers on sub
+  const int srank = (sub == 0) ? warp / 4 - 1 : (warp - sub) / 4;
+  auto group_row = [&](int q) { return (4 * (srank + q * nsub) + spos) * 32 + lane; };
   for (;;) {
     const int pos = next_system(cur, count);
     if (pos < 0) break;
@@ -365,7 +380,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         bool act[kWRows];
 #pragma unroll
         for (int q = 0; q < kWRows; ++q) {
-          const int i = wt + q * 32 * kWorkers;
+          const int i = group_row(q);
           act[q] = i >= r0 && i < n;
           if (act[q]) yq[q] = smem_val<W>(ysm, nmax, i);
         }
@@ -374,13 +389,13 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const val<W> yj = smem_val<W>(ysm, nmax, j0 + jj);
 #pragma unroll
           for (int q = 0; q < kWRows; ++q) {
-            const int i = wt + q * 32 * kWorkers;
+            const int i = group_row(q);
             if (act[q]) yq[q] = msub<W>(yq[q], load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), yj);
           }
         }
 #pragma unroll
         for (int q = 0; q < kWRows; ++q)
-          if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kWorkers, yq[q]);
+          if (act[q]) smem_put<W>(ysm, nmax, group_row(q), yq[q]);
         __threadfence_block();
         __syncwarp();
         if (lane == 0) atomicAdd(&far_done[bk], 1);
@@ -435,7 +450,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           bool act[kWRows];
 #pragma unroll
           for (int q = 0; q < kWRows; ++q) {
-            const int i = wt + q * 32 * kWorkers;
+            const int i = group_row(q);
             act[q] = i < rend;
             if (act[q]) yq[q] = smem_val<W>(ysm, nmax, i);
           }
@@ -444,13 +459,13 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
             const val<W> xj = smem_val<W>(ysm, nmax, j0 + jj);
 #pragma unroll
             for (int q = 0; q < kWRows; ++q) {
-              const int i = wt + q * 32 * kWorkers;
+              const int i = group_row(q);
               if (act[q]) yq[q] = msub<W>(yq[q], load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), xj);
             }
           }
 #pragma unroll
           for (int q = 0; q < kWRows; ++q)
-            if (act[q]) smem_put<W>(ysm, nmax, wt + q * 32 * kWorkers, yq[q]);
+            if (act[q]) smem_put<W>(ysm, nmax, group_row(q), yq[q]);
           __threadfence_block();
           __syncwarp();
           if (lane == 0) atomicAdd(&far_done[bk], 1);
@@ -528,32 +543,17 @@ k_bt_residual(int count, const int* __restrict__ nn, const int64_t* __restrict__
   __syncthreads();
   if (warp < b_words && row_ok) deposit_double(acc[lane], bs[warp * n + i], 0, false);
   constexpr int NWARP = kResThreads / 32;
-  // the next column's words are loaded before this column's deposits, so a
-  // warp keeps one column of A (and x) in flight while it accumulates
-  // (the residual is otherwise bound by the latency of these loads)
-  double xv[MW_LONG_WORDS], av[MW_LONG_WORDS], xn[MW_LONG_WORDS], an[MW_LONG_WORDS];
-  auto load_col = [&](int j, double (&xo)[MW_LONG_WORDS], double (&ao)[MW_LONG_WORDS]) {
-#pragma unroll
-    for (int d = 0; d < MW_LONG_WORDS; ++d) xo[d] = (d < x_words && j < n) ? __ldg(xs + d * n + j) : 0.0;
-    const double* col = As + (int64_t)j * n + i;
-#pragma unroll
-    for (int c = 0; c < MW_LONG_WORDS; ++c) ao[c] = (c < a_words && j < n && row_ok) ? __ldg(col + c * plane) : 0.0;
-  };
-  load_col(warp, xn, an);
   for (int j = warp; j < n; j += NWARP) {
+    double xv[MW_LONG_WORDS];
 #pragma unroll
-    for (int d = 0; d < MW_LONG_WORDS; ++d) {
-      xv[d] = xn[d];
-      av[d] = an[d];
-    }
-    load_col(j + NWARP, xn, an);
+    for (int d = 0; d < MW_LONG_WORDS; ++d) xv[d] = (d < x_words) ? __ldg(xs + d * n + j) : 0.0;
     if (!row_ok) continue;
-#pragma unroll
-    for (int c = 0; c < MW_LONG_WORDS; ++c) {
-      if (c >= a_words || zero_bits(av[c])) continue;
+    for (int c = 0; c < a_words; ++c) {
+      const double a = __ldg(As + c * plane + (int64_t)j * n + i);
+      if (zero_bits(a)) continue;
 #pragma unroll
       for (int d = 0; d < MW_LONG_WORDS; ++d)
-        if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], av[c], xv[d], 0, true);
+        if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], a, xv[d], 0, true);
     }
   }
   __syncthreads();
@@ -734,22 +734,13 @@ static int solve_batched_launch(int count, int nmax, const int* order, const int
   BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
   MW_CUDA_CHECK(cudaMemsetAsync(&cur->next, 0, sizeof(cur->next), s));   // the error word stays
   const size_t shmem = sizeof(double) * 2 * W * (size_t)nmax;
-  const int per_sm = tune_get(MW_TUNE_BATCH_SOLVE_CTAS, W) == 2 ? 2 : 1;
-  const int grid = std::min(count, per_sm * device_sm_count());
+  const int grid = std::min(count, device_sm_count());
   const BatchState* bst = static_cast<const BatchState*>(st);
-  if (per_sm == 2) {
-    int rc = set_smem(k_solve_batched<W, 256>, shmem);
-    if (rc) return rc;
-    ProfScope ps(kPhBatchSolve, s);
-    k_solve_batched<W, 256><<<grid, 256, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x, bst, cur,
-                                                     wait_limit());
-  } else {
-    int rc = set_smem(k_solve_batched<W, 512>, shmem);
-    if (rc) return rc;
-    ProfScope ps(kPhBatchSolve, s);
-    k_solve_batched<W, 512><<<grid, 512, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x, bst, cur,
-                                                     wait_limit());
-  }
+  int rc = set_smem(k_solve_batched<W>, shmem);
+  if (rc) return rc;
+  ProfScope ps(kPhBatchSolve, s);
+  k_solve_batched<W><<<grid, kSolveThreads, shmem, s>>>(count, nmax, order, nn, moff, voff, LU, piv, b, x, bst, cur,
+                                                        wait_limit());
   MW_LAUNCH_CHECK();
   return MW_OK;
 }

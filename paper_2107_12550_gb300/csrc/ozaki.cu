@@ -128,16 +128,20 @@ __device__ __forceinline__ __int128 scaled_floor(double v, int sh) {
 
 // 15 base-256 digits of X (|X| < 2^119), most significant first: the 14
 // low digits balanced in [-128, 127], the top digit the exact remainder,
-// within [-128, 128]
+// within [-128, 128].  With Y = X + sum_{p<14} 128 256^p, the low digits are
+// the bytes of Y minus 128 and the top digit is Y >> 112 (arithmetic): one
+// 128-bit addition and byte extractions instead of a 14-step carry loop
+// (balanced digits in [-128, 127] are unique, so both give the same digits)
 __device__ __forceinline__ void digits15(__int128 X, int (&a)[kS]) {
+  const unsigned __int128 bias = ((unsigned __int128)0x0000808080808080ull << 64) | 0x8080808080808080ull;
+  const __int128 Y = X + (__int128)bias;
+  const unsigned long long lo = (unsigned long long)Y;
+  const unsigned long long hi = (unsigned long long)(Y >> 64);
 #pragma unroll
-  for (int p = kS - 1; p >= 1; --p) {
-    int d = (int)(X & 0xff);
-    if (d >= 128) d -= 256;
-    a[p] = d;
-    X = (X - d) >> 8;
-  }
-  a[0] = (int)X;
+  for (int p = 0; p < 8; ++p) a[kS - 1 - p] = (int)((lo >> (8 * p)) & 0xffull) - 128;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) a[kS - 9 - p] = (int)((hi >> (8 * p)) & 0xffull) - 128;
+  a[0] = (int)((long long)hi >> 48);
 }
 
 __device__ __forceinline__ unsigned short bf16_bits_of_int(int d) {
@@ -165,13 +169,15 @@ __device__ __forceinline__ unsigned long long slice_load8(const double* __restri
                                               bool ok, int kvalid, int64_t r, int kc, double (&hv)[8],
                                               double (&lv)[8]) {
   unsigned long long mx = 0ull;
+  // the entry addresses by pointer increments: a 64 x 64-bit index product
+  // per entry would issue on the FP64 pipe
+  const double* px = X + (ok ? r * rs + (int64_t)(kc * 8) * ks : 0);
 #pragma unroll
-  for (int k8 = 0; k8 < 8; ++k8) {
+  for (int k8 = 0; k8 < 8; ++k8, px += ks) {
     const int k = kc * 8 + k8;
     if (ok && k < kvalid) {
-      const int64_t idx = r * rs + (int64_t)k * ks;
-      hv[k8] = X[idx];
-      lv[k8] = X[planeX + idx];
+      hv[k8] = px[0];
+      lv[k8] = px[planeX];
       const unsigned long long mb = mag_bits(hv[k8]);
       mx = (mb > mx) ? mb : mx;
     } else {

@@ -43,11 +43,8 @@ def test_knob_validation():
     assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 12) == -3
     assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 16) == 8
     assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 8) == 16
-    assert lib.mw_get_tuning(L.MW_TUNE_BATCH_SOLVE_CTAS, 2) == 1
-    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SOLVE_CTAS, 2, 3) == -3
-    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SOLVE_CTAS, 2, 2) == 1
-    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SOLVE_CTAS, 2, 1) == 2
-    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SOLVE_CTAS + 1, 3, 0) == -1
+    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF + 1, 3, 8) == -1
+    assert lib.mw_get_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF + 1, 3) == -1
 
 
 def test_apply_from_cache(tmp_path):
