@@ -202,7 +202,7 @@ def panel_sum_sq(n: int, nb: int = 64) -> int:
 
 
 DEFAULT_KNOBS = {"panel_width": 64, "rows_per_cta": 8, "ctas_per_sm": 2, "split_leaf": 0, "gemm_tile": 0,
-                 "batch_split_leaf": 8}
+                 "batch_split_leaf": 8, "lookahead": 1}
 
 
 def reset_knobs():
@@ -210,7 +210,8 @@ def reset_knobs():
     from paper_2107_12550_gb300 import _lib as L
     params = {"panel_width": L.MW_TUNE_PANEL_WIDTH, "rows_per_cta": L.MW_TUNE_PANEL_ROWS_PER_CTA,
               "ctas_per_sm": L.MW_TUNE_BATCH_CTAS_PER_SM, "split_leaf": L.MW_TUNE_SPLIT_PANEL_LEAF,
-              "gemm_tile": L.MW_TUNE_GEMM_TILE, "batch_split_leaf": L.MW_TUNE_BATCH_SPLIT_LEAF}
+              "gemm_tile": L.MW_TUNE_GEMM_TILE, "batch_split_leaf": L.MW_TUNE_BATCH_SPLIT_LEAF,
+              "lookahead": L.MW_TUNE_LOOKAHEAD}
     for name, prm in params.items():
         for w in (2, 3, 4):
             L.lib().mw_set_tuning(prm, w, DEFAULT_KNOBS[name])
@@ -864,12 +865,17 @@ def main():
     value = solved / (t_max * 1e-3)
 
     # ---- one profiled pass (not timed above): phases and kernel rooflines -
+    # Run with the serial schedule (MW_TUNE_LOOKAHEAD 0: bitwise the same
+    # results), so that no phase's events overlap another's and each phase
+    # time is its kernels' own duration.
+    la_prev = L.lib().mw_set_tuning(L.MW_TUNE_LOOKAHEAD, 2, 0)
     L.profile_read(reset=True)
     L.profile_enable(True)
     _, pst = step()
     torch.cuda.synchronize()
     L.profile_enable(False)
     prof = L.profile_read(reset=True)
+    L.lib().mw_set_tuning(L.MW_TUNE_LOOKAHEAD, 2, la_prev)
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz")
     roofs = headline_rooflines(prof, 1, n_list, pst.cpu().numpy(), peak_fp64, peaks, sm_max)
     dominant = max(roofs, key=lambda r: r["ms"]) if roofs else None

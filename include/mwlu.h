@@ -30,7 +30,13 @@
  *
  * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
  * enqueue work and return without synchronising, except mw_refine, which
- * reads a few status words back once per refinement step.
+ * reads a few status words back once per refinement step.  The LU calls
+ * (with MW_TUNE_LOOKAHEAD on) fork work onto a second stream the library
+ * creates once per device, and join it back into `stream` before
+ * returning, so all of a call's work is ordered before anything the caller
+ * enqueues on `stream` afterwards (inside a stream capture too: the fork
+ * and join become graph edges).  The first such call on a device must run
+ * outside a capture; a captured call before it runs the serial schedule.
  *
  * Return codes: MW_OK (0); a negative value -i when argument i (1-based) is
  * invalid; MW_ECUDA when a CUDA call failed (mw_last_cuda_error gives the
@@ -431,6 +437,14 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
  *                                8), the wider inner updates as split
  *                                products; the results differ by roundings
  *                                only, within the split path's error bound
+ *   MW_TUNE_LOOKAHEAD            1 (default): mw_ludecomp (and the LU inside
+ *                                mw_refine) updates the next panel's columns
+ *                                first and factors that panel on a second,
+ *                                higher-priority stream while the rest of
+ *                                the trailing matrix is updated; 0: one
+ *                                stream, panel after update.  Every entry
+ *                                receives the same operations in the same
+ *                                order either way: bitwise the same result.
  * mw_set_tuning returns the previous value, or -1 (param), -2 (prec) or
  * -3 (value) when invalid; mw_get_tuning returns the value or -1/-2.
  */
@@ -440,6 +454,7 @@ int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t lda, const i
 #define MW_TUNE_SPLIT_PANEL_LEAF 3
 #define MW_TUNE_GEMM_TILE 4
 #define MW_TUNE_BATCH_SPLIT_LEAF 5
+#define MW_TUNE_LOOKAHEAD 6
 int mw_set_tuning(int param, int prec, int value);
 int mw_get_tuning(int param, int prec);
 

@@ -22,6 +22,7 @@ MW_TUNE_PANEL_WIDTH, MW_TUNE_PANEL_ROWS_PER_CTA, MW_TUNE_BATCH_CTAS_PER_SM = 0, 
 MW_TUNE_SPLIT_PANEL_LEAF = 3
 MW_TUNE_GEMM_TILE = 4
 MW_TUNE_BATCH_SPLIT_LEAF = 5
+MW_TUNE_LOOKAHEAD = 6
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64

@@ -217,17 +217,19 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 // triangles overlap the workers' updates.  Each wait is bounded; a wait that
 // runs out records an error word and makes all warps leave the system.
 // Systems whose state is not "running" are skipped when st is given.
-// dynamic shared memory: 2 * W * nmax doubles
+// dynamic shared memory: W * (2 nmax + 4096) doubles (y, the reciprocals,
+// the leader's two tiles)
 // ---------------------------------------------------------------------------
 constexpr int kSolveBs = 32;
-// The substitution's CTA: 512 threads, one per SM; one leader warp, the rest
-// workers.  Row groups of 32 (one row per lane) are dealt to the workers so
-// that each SM sub-partition holds a quarter of them (see the kernel).
+// The substitution's CTA: 512 threads, one per SM.  Warp 0 leads and has SM
+// sub-partition 0 (warp w issues on sub-partition w % 4) to itself: its
+// triangles are the pipeline's serial chain, and sharing that
+// sub-partition's FP64 pipe with workers slowed the whole solve more than
+// their work gained (82.4 vs 89.7 ms for a 512-system refinement).  The
+// workers are the 12 warps on sub-partitions 1-3; warps 4, 8 and 12 idle.
 constexpr int kSolveThreads = 512;
-constexpr int kSolveWorkers = kSolveThreads / 32 - 1;                            // worker warps
-constexpr int kSolveMinSub = kSolveWorkers / 4;                                  // workers on sub-partition 0
-constexpr int kSolveWGroups = (kBatchMaxN / 32 / 4 + kSolveMinSub - 1) / kSolveMinSub;  // groups per worker
-static_assert(kBatchMaxN % 128 == 0, "row groups split evenly over the four sub-partitions");
+constexpr int kSolveWorkers = 12;                                                  // worker warps
+constexpr int kSolveWGroups = (kBatchMaxN / 32 + kSolveWorkers - 1) / kSolveWorkers;  // row groups per worker
 constexpr unsigned long long kSolveSpin = 1ull << 24;
 
 template <int W>
@@ -282,19 +284,41 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
   volatile int* vab = &s_abort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // Row group g (rows 32 g .. 32 g + 31, one per lane; the same as solve
-  // block g) belongs to a worker warp chosen so that the groups still active
-  // in any step, a contiguous range, spread evenly over the four SM
-  // sub-partitions (warp w issues on sub-partition w % 4): g goes to
-  // sub-partition 1, 2, 3, 0 for g % 4 = 0, 1, 2, 3 (0 also hosts the
-  // leader and has one worker fewer), and there to the worker of rank
-  // (g / 4) mod (its worker count).  A worker's groups are therefore
-  // g = 4 (rank + m nsub) + spos, m = 0, 1, ...  Ownership is fixed for the
-  // whole call, so each row's updates stay in program order on one warp.
-  const int sub = warp & 3;
-  const int spos = (sub + 3) & 3;                            // position of sub in (1, 2, 3, 0)
-  const int nsub = (sub == 0) ? kSolveMinSub : (NT / 32 - sub + 3) / 4;   // workers on sub
-  const int srank = (sub == 0) ? warp / 4 - 1 : (warp - sub) / 4;
-  auto group_row = [&](int q) { return (4 * (srank + q * nsub) + spos) * 32 + lane; };
+  // block g) belongs to worker g mod kWorkers, so the groups still active in
+  // any step (a contiguous range) are dealt round-robin; workers are
+  // numbered in warp order.  Ownership is fixed for the whole call, so each
+  // row's updates stay in program order on one warp.  wk < 0: not a worker.
+  const int wk = (warp & 3) ? (warp >> 2) * 3 + (warp & 3) - 1 : -1;
+  auto group_row = [&](int q) { return (wk + q * kWorkers) * 32 + lane; };
+  // The leader's two 32 x 64 tiles of the factor (rows of its block, the 64
+  // columns from c0), double-buffered in shared memory: tile bk goes to
+  // buffer bk & 1, word c of column c0 + cc, row j0 + lane, at
+  // [((buf * W + c) * 64 + cc) * 32 + lane].  Each lane copies and reads only
+  // its own row, so its own cp.async wait orders them; rows and columns
+  // outside the matrix are zero-filled (never read).
+  double* ltile = dsm + (size_t)W * nmax;
+  const double* a_cur = nullptr;
+  int n_cur = 0;
+  int64_t plane_cur = 0;
+  auto fetch_tile = [&](int bk, int c0) {
+    const int r = bk * kSolveBs + lane;
+    const bool rok = r < n_cur;
+    double* dst = ltile + (size_t)(bk & 1) * W * 64 * 32 + lane;
+    for (int cc = 0; cc < 64; ++cc) {
+      const int col = c0 + cc;
+      if (col < 0 || col >= n_cur) continue;           // warp-uniform
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        cp_async8(dst + (c * 64 + cc) * 32, a_cur + c * plane_cur + (int64_t)col * n_cur + (rok ? r : 0), rok);
+    }
+    cp_async_commit();
+  };
+  auto tile_val = [&](const double* tl, int cc) {
+    val<W> v;
+#pragma unroll
+    for (int c = 0; c < W; ++c) v.v[c] = tl[(c * 64 + cc) * 32];
+    return v;
+  };
   for (;;) {
     const int pos = next_system(cur, count);
     if (pos < 0) break;
@@ -304,9 +328,13 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
     const int nb = (n + kSolveBs - 1) / kSolveBs;
     const double* a = LU + (int64_t)W * moff[s];
     const int64_t plane = (int64_t)n * n;
+    a_cur = a;
+    n_cur = n;
+    plane_cur = plane;
     const int64_t* pv = piv + voff[s];
     const double* bs = b + (int64_t)W * voff[s];
     double* xs = x + (int64_t)W * voff[s];
+    if (warp == 0) fetch_tile(0, -kSolveBs);   // the leader's first tile, during the set-up
     for (int i = tid; i < n; i += NT)
 #pragma unroll
       for (int c = 0; c < W; ++c) ysm[c * nmax + i] = bs[c * n + i];
@@ -342,7 +370,12 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
       for (int bk = 0; bk < nb; ++bk) {
         const int j0 = bk * kSolveBs;
         const int bsz = min(kSolveBs, n - j0);
+        // block bk + 1's tile streams in while block bk is worked on
+        if (bk + 1 < nb) fetch_tile(bk + 1, j0);
+        else cp_async_commit();
         if (bk >= 2 && !solve_wait([&] { return vfar[bk - 2] >= kWorkers; }, vab, cur, spin_limit)) break;
+        cp_async_wait<1>();
+        const double* tl = ltile + (size_t)(bk & 1) * W * 64 * 32 + lane;   // column cc of word c: tl[(c*64+cc)*32]
         const int i = j0 + lane;
         val<W> yi;
         if (lane < bsz) yi = smem_val<W>(ysm, nmax, i);
@@ -354,20 +387,24 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const int jp = j0 - kSolveBs;
 #pragma unroll 4
           for (int jj = 0; jj < kSolveBs; ++jj)
-            yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(jp + jj) * n + i), smem_val<W>(ysm, nmax, jp + jj));
+            yi = msub<W>(yi, tile_val(tl, jj),
+                         smem_val<W>(ysm, nmax, jp + jj));
         }
         for (int jj = 0; jj < bsz - 1; ++jj) {
           val<W> yj;
 #pragma unroll
           for (int c = 0; c < W; ++c) yj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
-          if (lane > jj && lane < bsz) yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), yj);
+          if (lane > jj && lane < bsz)
+            yi = msub<W>(yi, tile_val(tl, kSolveBs + jj),
+                         yj);
         }
         if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
         __threadfence_block();
         __syncwarp();
         if (lane == 0) *vtri = bk;
       }
-    } else {
+      cp_async_wait<0>();
+    } else if (wk >= 0) {
       for (int bk = 0; bk < nb; ++bk) {
         if (!solve_wait([&] { return *vtri >= bk; }, vab, cur, spin_limit)) break;
         const int j0 = bk * kSolveBs;
@@ -408,10 +445,15 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
     // ---- backward: upper U with the reciprocals ----
     if (!*vab) {
       if (warp == 0) {
+        fetch_tile(nb - 1, (nb - 1) * kSolveBs);
         for (int bk = nb - 1; bk >= 0; --bk) {
           const int j0 = bk * kSolveBs;
           const int bsz = min(kSolveBs, n - j0);
+          if (bk >= 1) fetch_tile(bk - 1, j0 - kSolveBs);
+          else cp_async_commit();
           if (bk <= nb - 3 && !solve_wait([&] { return vfar[bk + 2] >= kWorkers; }, vab, cur, spin_limit)) break;
+          cp_async_wait<1>();
+          const double* tl = ltile + (size_t)(bk & 1) * W * 64 * 32 + lane;
           const int i = j0 + lane;
           val<W> yi, di;
           if (lane < bsz) {
@@ -426,21 +468,24 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
             const int bszn = min(kSolveBs, n - jn);
 #pragma unroll 4
             for (int jj = bszn - 1; jj >= 0; --jj)
-              yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(jn + jj) * n + i), smem_val<W>(ysm, nmax, jn + jj));
+              yi = msub<W>(yi, tile_val(tl, kSolveBs + jj),
+                           smem_val<W>(ysm, nmax, jn + jj));
           }
           for (int jj = bsz - 1; jj >= 0; --jj) {
             if (lane == jj) yi = mul<W>(yi, di);          // x_j = y_j d_j
             val<W> xj;
 #pragma unroll
             for (int c = 0; c < W; ++c) xj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
-            if (lane < jj) yi = msub<W>(yi, load_ro<W>(a, plane, (int64_t)(j0 + jj) * n + i), xj);
+            if (lane < jj)
+              yi = msub<W>(yi, tile_val(tl, jj), xj);
           }
           if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
           __threadfence_block();
           __syncwarp();
           if (lane == 0) *vtri = bk;
         }
-      } else {
+        cp_async_wait<0>();
+      } else if (wk >= 0) {
         for (int bk = nb - 1; bk >= 0; --bk) {
           if (!solve_wait([&] { return *vtri <= bk; }, vab, cur, spin_limit)) break;
           const int j0 = bk * kSolveBs;
@@ -733,7 +778,8 @@ static int solve_batched_launch(int count, int nmax, const int* order, const int
   if (count <= 0) return MW_OK;
   BatchCursor* cur = reinterpret_cast<BatchCursor*>(ws);
   MW_CUDA_CHECK(cudaMemsetAsync(&cur->next, 0, sizeof(cur->next), s));   // the error word stays
-  const size_t shmem = sizeof(double) * 2 * W * (size_t)nmax;
+  // y and the reciprocals (2 W nmax doubles), then the leader's two tiles
+  const size_t shmem = sizeof(double) * W * (2 * (size_t)nmax + 2 * 64 * 32);
   const int grid = std::min(count, device_sm_count());
   const BatchState* bst = static_cast<const BatchState*>(st);
   int rc = set_smem(k_solve_batched<W>, shmem);
@@ -902,6 +948,8 @@ static int upload_plan(const BatchPlanHost& p, int count, char* ws, BatchPlanDev
 struct GeomPlanHost {
   std::vector<int> max_mt, max_cb;   // per step: slicing grid extents (split)
   std::vector<int64_t> toff, boff;   // per step: first tile, first base (nsteps + 1 entries)
+  std::vector<int64_t> tnext;        // trail, per step: tiles touching the next panel's 64 columns,
+                                     // listed first among the step's tiles
   std::vector<TileEntry> tiles;
   std::vector<int2> bases;           // split: {first A-slice tile, first B-slice tile} per (step, pos)
   int64_t a_tiles = 0, b_tiles = 0;  // split: slice tiles of the largest step
@@ -928,7 +976,8 @@ constexpr int kPanelLeafDefault = 8;   // MW_TUNE_BATCH_SPLIT_LEAF
 // tiles of an m x N product for every active system of one step
 static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool split, int bm, int bn,
                           int (*dims)(int n, int k0, int c_off, int h, int* N), int k0, int c_off = 0,
-                          int h = 0) {
+                          int h = 0, bool next_first = false) {
+  const size_t t_begin = g.tiles.size();
   int64_t at = 0, btl = 0;
   int max_m = 0, max_n = 0;
   for (int pos = 0; pos < act; ++pos) {
@@ -943,6 +992,13 @@ static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool
       for (int ti = 0; ti < mt; ++ti) g.tiles.push_back(TileEntry{pos, ti, tj, 0});
     at += mt;
     btl += nt;
+  }
+  if (next_first) {
+    // the tiles holding any of the first kBatchNb columns first (the next
+    // panel's columns, updated before that panel is factored)
+    auto mid = std::stable_partition(g.tiles.begin() + (std::ptrdiff_t)t_begin, g.tiles.end(),
+                                     [&](const TileEntry& t) { return t.tj * bn < kBatchNb; });
+    g.tnext.push_back((int64_t)(mid - (g.tiles.begin() + (std::ptrdiff_t)t_begin)));
   }
   g.max_mt.push_back((max_m + kSplitTileM - 1) / kSplitTileM);
   g.max_cb.push_back(((max_n + kSplitTileN - 1) / kSplitTileN * kSplitTileN + 127) / 128);
@@ -995,7 +1051,7 @@ static void make_blocked_plan(const BatchPlanHost& p, int W, int update, Blocked
     const int m0 = p.n[p.order[0]] - k0 - kBatchNb;          // largest trailing order
     bp.max_cb_trsm.push_back(m0 > 0 ? (m0 + 7) / 8 : 0);
     bp.max_cols.push_back(std::max(m0, 0));
-    add_geom_step(bp.trail, p, act, split, bm, bn, dims_trail, k0);
+    add_geom_step(bp.trail, p, act, split, bm, bn, dims_trail, k0, 0, 0, true);
     if (split) {
       add_geom_step(bp.tinv, p, act, true, kSplitTileM, kSplitTileN, dims_tinv, k0);
       for (int q = 0; q < kNumInner; ++q)
@@ -1024,7 +1080,19 @@ static int64_t max_b_tiles(const BlockedPlanHost& bp) {
   return t;
 }
 
-// [trail | tinv | pinner tiles and bases | swap plans | aux | split scratch]
+static int64_t inner_a_tiles(const BlockedPlanHost& bp) {
+  int64_t t = 0;
+  for (const auto& g : bp.pinner) t = std::max(t, g.a_tiles);
+  return t;
+}
+static int64_t inner_b_tiles(const BlockedPlanHost& bp) {
+  int64_t t = 0;
+  for (const auto& g : bp.pinner) t = std::max(t, g.b_tiles);
+  return t;
+}
+
+// [trail | tinv | pinner tiles and bases | swap plans | aux | split scratch |
+//  the look-ahead panel's split scratch]
 static size_t blocked_extra_bytes(const BlockedPlanHost& bp) {
   size_t b = geom_bytes(bp.trail) + geom_bytes(bp.tinv);
   for (const auto& g : bp.pinner) b += geom_bytes(g);
@@ -1032,6 +1100,7 @@ static size_t blocked_extra_bytes(const BlockedPlanHost& bp) {
   if (bp.update == MW_UPDATE_SPLIT) {
     b += align256(sizeof(double) * 2 * kBatchNb * kBatchNb * (size_t)std::max<int64_t>(1, blocked_count(bp)));
     b += split_batched_workspace_bytes(max_a_tiles(bp), max_b_tiles(bp));
+    b += split_batched_workspace_bytes(inner_a_tiles(bp), inner_b_tiles(bp));   // the look-ahead panel's
   }
   return b;
 }
@@ -1048,6 +1117,9 @@ struct BlockedDev {
   char* split_ws;
   size_t split_bytes;
   int64_t a_tiles, b_tiles;
+  char* panel_ws;                  // the look-ahead panel's split scratch
+  size_t panel_bytes;
+  int64_t pa_tiles, pb_tiles;
   DeviceStatus* status;   // the call's error word (in the batch cursor)
 };
 
@@ -1096,12 +1168,21 @@ static int upload_blocked(const BlockedPlanHost& bp, const std::vector<int>& n, 
   d.split_bytes = 0;
   d.a_tiles = max_a_tiles(bp);
   d.b_tiles = max_b_tiles(bp);
+  d.panel_ws = nullptr;
+  d.panel_bytes = 0;
+  d.pa_tiles = d.pb_tiles = 0;
   if (bp.update == MW_UPDATE_SPLIT) {
     d.aux = reinterpret_cast<double*>(base + off);
     off += align256(sizeof(double) * 2 * kBatchNb * kBatchNb * (size_t)std::max<int64_t>(1, blocked_count(bp)));
     d.split_ws = base + off;
     d.split_bytes = split_batched_workspace_bytes(d.a_tiles, d.b_tiles);
+    off += d.split_bytes;
     MW_CUDA_CHECK(cudaMemsetAsync(d.split_ws, 0, 256, s));
+    d.pa_tiles = inner_a_tiles(bp);
+    d.pb_tiles = inner_b_tiles(bp);
+    d.panel_ws = base + off;
+    d.panel_bytes = split_batched_workspace_bytes(d.pa_tiles, d.pb_tiles);
+    MW_CUDA_CHECK(cudaMemsetAsync(d.panel_ws, 0, 256, s));
   }
   return MW_OK;
 }
@@ -1111,26 +1192,27 @@ static int upload_blocked(const BlockedPlanHost& bp, const std::vector<int>& n, 
 // updated by a split product, right half, then the right half's swaps on the
 // left half -- down to leaves of MW_TUNE_BATCH_SPLIT_LEAF columns (8, 16 or
 // 32; 8 by default) factored on the FP64 pipe
+// (on the scratch `ws` laid out for pa x pb slice tiles)
 template <int W>
 static int split_panel(const BatchPlanHost& p, const BatchView& bv, const BlockedPlanHost& bp, const BlockedDev& bd,
                        int st, int act, int k0, int c_off, int w, double* A, int64_t* piv, int64_t* info,
-                       cudaStream_t s) {
+                       char* ws, size_t ws_bytes, int64_t pa, int64_t pb, cudaStream_t s) {
   if (w <= tune_get(MW_TUNE_BATCH_SPLIT_LEAF, 2)) return launch_bpanel<W>(bv, act, p.nmax, k0, c_off, w, A, piv, info, s);
   const int h = w / 2;
   int q = -1;
   for (int i = 0; i < kNumInner; ++i)
     if (kInner[i].c_off == c_off && kInner[i].h == h) q = i;
   if (q < 0) return MW_EUNSUPPORTED;
-  int rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off, h, A, piv, info, s);
+  int rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off, h, A, piv, info, ws, ws_bytes, pa, pb, s);
   if (rc) return rc;
   rc = launch_btrsm_sub<W>(bv, act, k0, c_off, h, A, piv, s);
   if (rc) return rc;
   const GeomPlanHost& g = bp.pinner[q];
   rc = split_bupdate_dd(bv, kGeomPanelInner, c_off, h, act, g.max_mt[st], g.max_cb[st], bd.pinner[q].tiles + g.toff[st],
-                        g.toff[st + 1] - g.toff[st], bd.pinner[q].bases + g.boff[st], bd.a_tiles, bd.b_tiles, k0, A,
-                        bd.aux, bd.split_ws, bd.split_bytes, bd.status, s);
+                        g.toff[st + 1] - g.toff[st], bd.pinner[q].bases + g.boff[st], pa, pb, k0, A,
+                        bd.aux, ws, ws_bytes, bd.status, s);
   if (rc) return rc;
-  rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off + h, w - h, A, piv, info, s);
+  rc = split_panel<W>(p, bv, bp, bd, st, act, k0, c_off + h, w - h, A, piv, info, ws, ws_bytes, pa, pb, s);
   if (rc) return rc;
   return launch_bswap<W>(bv, act, k0, c_off + h, c_off + w, c_off, c_off + h, h, A, piv, s);
 }
@@ -1139,26 +1221,59 @@ static int split_panel(const BatchPlanHost& p, const BatchView& bv, const Blocke
 // every element sees the unblocked order.  Split update (DD): the recursive
 // panel above, the swaps left and right, M = -(L11^-1) strictly lower, then
 // U12 -= M U12 and A22 -= L21 U12 as split tensor-core products.
+// Look-ahead (MW_TUNE_LOOKAHEAD, as in the single-system LU): the trailing
+// tiles that hold the next panel's columns are updated first, then the next
+// panel is factored on the side stream while the caller's stream updates
+// the other tiles; the caller's stream joins the panel before the next
+// swaps.  The panel touches only its own columns (its inner split products
+// use a scratch of their own), the other tiles only columns right of it, and
+// each entry gets the same operations in the same order: bitwise the same.
 template <int W>
 static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d, const BlockedPlanHost& bp,
                                   const BlockedDev& bd, double* A, int64_t* piv, int64_t* info, cudaStream_t s) {
   const BatchView bv{d.order, d.n, d.moff, d.voff};
   const bool split = bp.update == MW_UPDATE_SPLIT;
   if (split && W != 2) return MW_EUNSUPPORTED;
+  if (bp.nsteps <= 0) return MW_OK;
   constexpr int kFar = 1 << 29;
+  SideStream la;
+  bool ahead = false;
+  if (tune_get(MW_TUNE_LOOKAHEAD, W) == 1 && (!split || bd.panel_ws)) {
+    int rc = la.open(s, &ahead);
+    if (rc) return rc;
+  }
+  // panel of step st on stream q (the look-ahead panel on its own scratch)
+  auto panel = [&](int st, cudaStream_t q, bool own) -> int {
+    const int k0 = st * kBatchNb;
+    if (split)
+      return own ? split_panel<W>(p, bv, bp, bd, st, bp.act[st], k0, 0, kBatchNb, A, piv, info, bd.panel_ws,
+                                  bd.panel_bytes, bd.pa_tiles, bd.pb_tiles, q)
+                 : split_panel<W>(p, bv, bp, bd, st, bp.act[st], k0, 0, kBatchNb, A, piv, info, bd.split_ws,
+                                  bd.split_bytes, bd.a_tiles, bd.b_tiles, q);
+    return launch_bpanel<W>(bv, bp.act[st], p.nmax, k0, 0, kBatchNb, A, piv, info, q);
+  };
+  // trailing tiles [t0, t1) of step st (within the step's list)
+  auto trail = [&](int st, int64_t t0, int64_t t1) -> int {
+    if (t1 <= t0) return MW_OK;
+    const int k0 = st * kBatchNb;
+    const TileEntry* tl = bd.trail.tiles + bp.trail.toff[st] + t0;
+    if (split)
+      return split_bgemm_dd(bv, kGeomTrail, 0, 0, tl, t1 - t0, bd.trail.bases + bp.trail.boff[st], bd.a_tiles,
+                            bd.b_tiles, k0, A, bd.aux, bd.split_ws, bd.split_bytes, bd.status, s);
+    return launch_bgemm_plain<W>(bv, tl, t1 - t0, k0, A, s);
+  };
+  int rc = panel(0, s, false);
+  if (rc) return rc;
   for (int st = 0; st < bp.nsteps; ++st) {
     const int k0 = st * kBatchNb;
     const int act = bp.act[st];
     const int64_t nt = bp.trail.toff[st + 1] - bp.trail.toff[st];
-    int rc;
     if (split) {
-      rc = split_panel<W>(p, bv, bp, bd, st, act, k0, 0, kBatchNb, A, piv, info, s);
-      if (rc) return rc;
       rc = launch_bswap_plan(bv, act, k0, 0, kBatchNb, piv, bd.plans, s);
       if (rc) return rc;
       rc = launch_bswap_apply<W>(bv, act, k0, -k0, 0, k0, A, bd.plans, s);   // left of the panel
       if (rc) return rc;
-      if (bp.max_cols[st] <= 0) continue;
+      if (bp.max_cols[st] <= 0) continue;   // no system has columns right of this panel: the last step
       rc = launch_bswap_apply<W>(bv, act, k0, kBatchNb, kFar, bp.max_cols[st], A, bd.plans, s);   // right
       if (rc) return rc;
       rc = split_binv_l11(bv, act, k0, A, bd.aux, s);
@@ -1168,21 +1283,42 @@ static int lu_blocked_batched_run(const BatchPlanHost& p, const BatchPlanDev& d,
                             bd.tinv.bases + bp.tinv.boff[st], bd.a_tiles, bd.b_tiles, k0, A, bd.aux, bd.split_ws,
                             bd.split_bytes, bd.status, s);
       if (rc) return rc;
-      rc = split_bupdate_dd(bv, kGeomTrail, 0, 0, act, bp.trail.max_mt[st], bp.trail.max_cb[st],
-                            bd.trail.tiles + bp.trail.toff[st], nt, bd.trail.bases + bp.trail.boff[st], bd.a_tiles,
-                            bd.b_tiles, k0, A, bd.aux, bd.split_ws, bd.split_bytes, bd.status, s);
-    } else {
-      rc = launch_bpanel<W>(bv, act, p.nmax, k0, 0, kBatchNb, A, piv, info, s);
+      rc = split_bslice_dd(bv, kGeomTrail, 0, 0, act, bp.trail.max_mt[st], bp.trail.max_cb[st],
+                           bd.trail.bases + bp.trail.boff[st], bd.a_tiles, bd.b_tiles, k0, A, bd.aux, bd.split_ws,
+                           bd.split_bytes, s);
       if (rc) return rc;
+    } else {
       if (k0 > 0) {
         rc = launch_bswap_plan(bv, act, k0, 0, kBatchNb, piv, bd.plans, s);
         if (rc) return rc;
         rc = launch_bswap_apply<W>(bv, act, k0, -k0, 0, k0, A, bd.plans, s);   // left of the panel
         if (rc) return rc;
       }
+      if (st + 1 >= bp.nsteps) break;
       rc = launch_btrsm<W>(bv, act, bp.max_cb_trsm[st], k0, A, piv, s);
       if (rc) return rc;
-      rc = launch_bgemm_plain<W>(bv, bd.trail.tiles + bp.trail.toff[st], nt, k0, A, s);
+    }
+    if (st + 1 >= bp.nsteps) {
+      rc = trail(st, 0, nt);
+      if (rc) return rc;
+      continue;
+    }
+    const int64_t tn = bp.trail.tnext[st];
+    if (ahead && tn < nt) {
+      rc = trail(st, 0, tn);
+      if (rc) return rc;
+      cudaStream_t s2;
+      rc = la.fork(&s2);
+      if (rc) return rc;
+      rc = panel(st + 1, s2, split);
+      if (rc) return rc;
+      rc = trail(st, tn, nt);
+      if (rc) return rc;
+      rc = la.join();
+    } else {
+      rc = trail(st, 0, nt);
+      if (rc) return rc;
+      rc = panel(st + 1, s, false);
     }
     if (rc) return rc;
   }

@@ -69,15 +69,15 @@ extern "C" void mw_internal_set_cuda_error(int e) { g_last_cuda_error = e; }
 static bool prec_ok(int p) { return p == MW_DD || p == MW_TD || p == MW_QD; }
 
 // tuning table: [param][prec - 2]
-static int g_tune[6][3] = {{64, 64, 64}, {8, 8, 8}, {2, 2, 2}, {0, 0, 0}, {0, 0, 0}, {8, 8, 8}};
+static int g_tune[7][3] = {{64, 64, 64}, {8, 8, 8}, {2, 2, 2}, {0, 0, 0}, {0, 0, 0}, {8, 8, 8}, {1, 1, 1}};
 
 int mw::tune_get(int param, int prec) {
-  if (param < 0 || param > MW_TUNE_BATCH_SPLIT_LEAF || !prec_ok(prec)) return -1;
+  if (param < 0 || param > MW_TUNE_LOOKAHEAD || !prec_ok(prec)) return -1;
   return g_tune[param][prec - 2];
 }
 
 extern "C" int mw_set_tuning(int param, int prec, int value) {
-  if (param < MW_TUNE_PANEL_WIDTH || param > MW_TUNE_BATCH_SPLIT_LEAF) return -1;
+  if (param < MW_TUNE_PANEL_WIDTH || param > MW_TUNE_LOOKAHEAD) return -1;
   if (!prec_ok(prec)) return -2;
   bool ok = false;
   switch (param) {
@@ -86,6 +86,7 @@ extern "C" int mw_set_tuning(int param, int prec, int value) {
     case MW_TUNE_SPLIT_PANEL_LEAF: ok = value == 0 || value == 8 || value == 16 || value == 32; break;
     case MW_TUNE_GEMM_TILE: ok = value >= 0 && value <= 3; break;
     case MW_TUNE_BATCH_SPLIT_LEAF: ok = value == 8 || value == 16 || value == 32; break;
+    case MW_TUNE_LOOKAHEAD: ok = value == 0 || value == 1; break;
     default: ok = value >= 1 && value <= 8; break;
   }
   if (!ok) return -3;
@@ -95,14 +96,12 @@ extern "C" int mw_set_tuning(int param, int prec, int value) {
 }
 
 extern "C" int mw_get_tuning(int param, int prec) {
-  if (param < MW_TUNE_PANEL_WIDTH || param > MW_TUNE_BATCH_SPLIT_LEAF) return -1;
+  if (param < MW_TUNE_PANEL_WIDTH || param > MW_TUNE_LOOKAHEAD) return -1;
   if (!prec_ok(prec)) return -2;
   return g_tune[param][prec - 2];
 }
 
-static size_t lu_ws_bytes(int update, int64_t n) {
-  return mw::kWsSplit + (update == MW_UPDATE_SPLIT ? mw::split_workspace_bytes(n, mw::kDefaultNb) : 0);
-}
+static size_t lu_ws_bytes(int update, int64_t n) { return mw::lu_workspace_bytes(update, n); }
 
 extern "C" int mw_workspace_size(int op, int prec, int update, int64_t n, size_t* bytes) {
   if (op < MW_OP_LUDECOMP || op > MW_OP_GEMM) return -1;

@@ -17,6 +17,7 @@
 // rounded multiply and subtraction, so the plain form is bitwise identical
 // to unblocked elimination.
 #include <algorithm>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "mw_arith.cuh"
@@ -520,17 +521,6 @@ k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0
 // 16 x 16 threads, micro-tile TM x TN per thread, K chunks of KT staged in
 // shared memory with coalesced loads of each word plane.
 // ---------------------------------------------------------------------------
-// 8-byte asynchronous copy global -> shared; ok == false fills zeros (no read)
-__device__ __forceinline__ void cp_async8(void* smem_dst, const double* gsrc, bool ok) {
-  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(gsrc), "r"(ok ? 8 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // K chunks of KT staged in shared memory, double-buffered: the copies of
 // chunk t+1 (cp.async, zero-filled outside the matrix) run while chunk t is
@@ -1041,28 +1031,125 @@ static int split_panel_rec(double* A, int64_t lda, int64_t plane, int64_t n, int
   return swap_gather_range(A, lda, plane, kp + h, (int)(lim - kp - h), kp, kp + h, piv, ws, s);
 }
 
+// Blocked look-ahead: once panel k's block row U12 is known, the next
+// panel's columns are updated first; that panel is then factored on the
+// side stream while the caller's stream updates the rest of the trailing
+// matrix, and the caller's stream waits for the panel before the next row
+// swaps.  The panel only touches its own columns (and the pivots, the
+// candidate records and its own split product area), the trailing update
+// only the columns right of it, and every entry receives the same
+// operations in the same order as in the serial schedule, so the result is
+// bitwise the same.  The side stream's priority places the panel's CTAs
+// ahead of the update's queued CTAs; the panel's grid-wide waits are bounded
+// like every other wait.
+namespace {
+struct SideSlot {
+  std::mutex mu;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kSideDevices = 64;
+SideSlot g_side[kSideDevices];
+}  // namespace
+
+int SideStream::open(cudaStream_t s, bool* ready) {
+  *ready = false;
+  s_ = s;
+  MW_CUDA_CHECK(cudaGetDevice(&dev_));
+  if (dev_ < 0 || dev_ >= kSideDevices) return MW_OK;
+  SideSlot& slot = g_side[dev_];
+  slot.mu.lock();
+  if (!slot.s2) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      slot.mu.unlock();
+      dev_ = -1;
+      if (e != cudaSuccess) MW_CUDA_CHECK(e);
+      return MW_OK;
+    }
+    int lo = 0, hi = 0;
+    cudaError_t ce = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&slot.s2, cudaStreamNonBlocking, hi);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&slot.fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&slot.join, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      if (slot.fork) cudaEventDestroy(slot.fork);
+      if (slot.s2) cudaStreamDestroy(slot.s2);
+      slot.s2 = nullptr;
+      slot.fork = nullptr;
+      slot.join = nullptr;
+      slot.mu.unlock();
+      dev_ = -1;
+      MW_CUDA_CHECK(ce);
+    }
+  }
+  s2_ = slot.s2;
+  fork_ = slot.fork;
+  join_ = slot.join;
+  *ready = true;
+  return MW_OK;
+}
+
+int SideStream::fork(cudaStream_t* s2) {
+  MW_CUDA_CHECK(cudaEventRecord(fork_, s_));
+  MW_CUDA_CHECK(cudaStreamWaitEvent(s2_, fork_, 0));
+  open_ = true;
+  *s2 = s2_;
+  return MW_OK;
+}
+
+int SideStream::join() {
+  open_ = false;
+  MW_CUDA_CHECK(cudaEventRecord(join_, s2_));
+  MW_CUDA_CHECK(cudaStreamWaitEvent(s_, join_, 0));
+  return MW_OK;
+}
+
+SideStream::~SideStream() {
+  if (open_) {
+    cudaEventRecord(join_, s2_);
+    cudaStreamWaitEvent(s_, join_, 0);
+  }
+  if (dev_ >= 0 && s2_) g_side[dev_].mu.unlock();
+}
+
+size_t lu_workspace_bytes(int update, int64_t n) {
+  if (update != MW_UPDATE_SPLIT) return kWsSplit;
+  return kWsSplit + split_workspace_bytes(n, kDefaultNb) + split_product_bytes(n, kDefaultNb);
+}
+
 static int lu_split_dd(int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info, char* ws, size_t ws_bytes,
                        cudaStream_t s) {
   const int64_t plane = lda * n;
   char* sws = ws + kWsSplit;
   const size_t sbytes = ws_bytes > kWsSplit ? ws_bytes - kWsSplit : 0;
   if (sbytes < split_workspace_bytes(n, kDefaultNb)) return MW_EUNSUPPORTED;
+  // the look-ahead panel's own product area, after the trailing update's
+  char* pws = sws + split_workspace_bytes(n, kDefaultNb);
+  const size_t pbytes = split_product_bytes(n, kDefaultNb);
+  SideStream la;
+  bool ahead = false;
+  if (ws_bytes >= lu_workspace_bytes(MW_UPDATE_SPLIT, n) && tune_get(MW_TUNE_LOOKAHEAD, 2) == 1) {
+    int rc = la.open(s, &ahead);
+    if (rc) return rc;
+  }
   double* aux = split_aux(sws, n);
   MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand + 2 * kCandParity, s));
   MW_CUDA_CHECK(cudaMemsetAsync(sws, 0, 256, s));
+  if (ahead) MW_CUDA_CHECK(cudaMemsetAsync(pws, 0, 256, s));
   MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
   constexpr int NB = kDefaultNb;
   const int leaf = tune_get(MW_TUNE_SPLIT_PANEL_LEAF, 2);
+  auto panel = [&](int64_t kp, int w, char* xws, size_t xbytes, cudaStream_t st) -> int {
+    if (leaf > 0) return split_panel_rec(A, lda, plane, n, kp, w, leaf, piv, info, ws, xws, xbytes, st);
+    ProfScope ps(kPhPanel, st);
+    return launch_panel<2>(A, lda, plane, n, kp, w, piv, info, ws, st);
+  };
+  int rc = panel(0, (int)std::min<int64_t>(NB, n), sws, sbytes, s);
+  if (rc) return rc;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int kb = (int)std::min<int64_t>(NB, n - k0);
-    int rc;
-    if (leaf > 0) {
-      rc = split_panel_rec(A, lda, plane, n, k0, kb, leaf, piv, info, ws, sws, sbytes, s);
-    } else {
-      ProfScope ps(kPhPanel, s);
-      rc = launch_panel<2>(A, lda, plane, n, k0, kb, piv, info, ws, s);
-    }
-    if (rc) return rc;
     rc = swap_gather(A, lda, plane, 2, n, k0, kb, piv, ws, k0 > 0, k0 + kb < n, s);
     if (rc) return rc;
     if (k0 + kb >= n) break;
@@ -1087,7 +1174,24 @@ static int lu_split_dd(int64_t n, double* A, int64_t lda, int64_t* piv, int64_t*
     o.K = NB;
     rc = split_product_dd(o, sws, sbytes, kPhTrsm, s);
     if (rc) return rc;
-    rc = split_update_dd(A, lda, plane, r0, n - r0, r0, n - r0, k0, NB, sws, sbytes, s);
+    const int kb1 = (int)std::min<int64_t>(NB, n - r0);   // the next panel
+    const int64_t rest = n - r0 - kb1;                     // columns right of it
+    if (ahead && rest > 0) {
+      rc = split_update_dd(A, lda, plane, r0, n - r0, r0, kb1, k0, NB, sws, sbytes, s);
+      if (rc) return rc;
+      cudaStream_t s2;
+      rc = la.fork(&s2);
+      if (rc) return rc;
+      rc = panel(r0, kb1, pws, pbytes, s2);
+      if (rc) return rc;
+      rc = split_update_dd(A, lda, plane, r0, n - r0, r0 + kb1, rest, k0, NB, sws, sbytes, s);
+      if (rc) return rc;
+      rc = la.join();
+    } else {
+      rc = split_update_dd(A, lda, plane, r0, n - r0, r0, n - r0, k0, NB, sws, sbytes, s);
+      if (rc) return rc;
+      rc = panel(r0, kb1, sws, sbytes, s);
+    }
     if (rc) return rc;
   }
   return MW_OK;
@@ -1100,31 +1204,55 @@ int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int6
   const int64_t plane = lda * n;
   MW_CUDA_CHECK(cudaMemsetAsync(ws, 0, kWsCand + 2 * kCandParity, s));
   MW_CUDA_CHECK(cudaMemsetAsync(info, 0, sizeof(int64_t), s));
+  if (n <= 0) return MW_OK;
+  SideStream la;
+  bool ahead = false;
+  if (tune_get(MW_TUNE_LOOKAHEAD, W) == 1) {
+    int rc = la.open(s, &ahead);
+    if (rc) return rc;
+  }
+  auto panel = [&](int64_t kp, int w, cudaStream_t st) -> int {
+    ProfScope ps(kPhPanel, st);
+    return launch_panel<W>(A, lda, plane, n, kp, w, piv, info, ws, st);
+  };
+  auto gemm = [&](int64_t r0, int64_t c0, int64_t N, int64_t k0, int kb) -> int {
+    ProfScope ps(kPhGemmPlain, s);
+    return launch_gemm_plain<W>(A, lda, plane, r0, n - r0, c0, N, k0, kb, s);
+  };
+  int rc = panel(0, (int)std::min<int64_t>(nb, n), s);
+  if (rc) return rc;
   for (int64_t k0 = 0; k0 < n; k0 += nb) {
     const int kb = (int)std::min<int64_t>(nb, n - k0);
-    int rc;
-    {
-      ProfScope ps(kPhPanel, s);
-      rc = launch_panel<W>(A, lda, plane, n, k0, kb, piv, info, ws, s);
-    }
-    if (rc) return rc;
     if (k0 > 0) {
       rc = swap_gather(A, lda, plane, W, n, k0, kb, piv, ws, true, false, s);
       if (rc) return rc;
     }
-    if (k0 + kb < n) {
-      {
-        ProfScope ps(kPhTrsm, s);
-        rc = launch_trsm<W>(A, lda, plane, n, k0, kb, piv, s);
-      }
-      if (rc) return rc;
-      const int64_t r0 = k0 + kb;
-      {
-        ProfScope ps(kPhGemmPlain, s);
-        rc = launch_gemm_plain<W>(A, lda, plane, r0, n - r0, r0, n - r0, k0, kb, s);
-      }
-      if (rc) return rc;
+    if (k0 + kb >= n) break;
+    {
+      ProfScope ps(kPhTrsm, s);
+      rc = launch_trsm<W>(A, lda, plane, n, k0, kb, piv, s);
     }
+    if (rc) return rc;
+    const int64_t r0 = k0 + kb;
+    const int kb1 = (int)std::min<int64_t>(nb, n - r0);   // the next panel
+    const int64_t rest = n - r0 - kb1;                     // columns right of it
+    if (ahead && rest > 0) {
+      rc = gemm(r0, r0, kb1, k0, kb);
+      if (rc) return rc;
+      cudaStream_t s2;
+      rc = la.fork(&s2);
+      if (rc) return rc;
+      rc = panel(r0, kb1, s2);
+      if (rc) return rc;
+      rc = gemm(r0, r0 + kb1, rest, k0, kb);
+      if (rc) return rc;
+      rc = la.join();
+    } else {
+      rc = gemm(r0, r0, n - r0, k0, kb);
+      if (rc) return rc;
+      rc = panel(r0, kb1, s);
+    }
+    if (rc) return rc;
   }
   return MW_OK;
 }

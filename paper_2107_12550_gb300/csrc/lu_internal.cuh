@@ -49,6 +49,35 @@ constexpr int64_t kMaxOrder = (int64_t)1 << 31;
 // tuning knobs (capi.cu): value of `param` (MW_TUNE_*) for precision prec
 int tune_get(int param, int prec);
 
+// The look-ahead's second stream (lu.cu): one per device, of the device's
+// highest priority, with a fork and a join event; created by the first call
+// that asks for it outside a stream capture.  A call holds the device's
+// lock from open() until it is destroyed, so the forks and joins of calls
+// from different host threads never interleave; the destructor joins a
+// fork left open by an early error return, so none of the call's work runs
+// after the caller's stream has passed the call.
+class SideStream {
+ public:
+  SideStream() = default;
+  SideStream(const SideStream&) = delete;
+  SideStream& operator=(const SideStream&) = delete;
+  ~SideStream();
+  // for a call on stream s: *ready is false (with MW_OK) when the side
+  // stream does not exist yet and s is capturing (the call then runs its
+  // serial schedule)
+  int open(cudaStream_t s, bool* ready);
+  // the side stream, ordered after everything enqueued on s so far
+  int fork(cudaStream_t* s2);
+  // s waits for everything enqueued on the side stream so far
+  int join();
+
+ private:
+  int dev_ = -1;
+  cudaStream_t s_ = nullptr, s2_ = nullptr;
+  cudaEvent_t fork_ = nullptr, join_ = nullptr;
+  bool open_ = false;
+};
+
 template <int W>
 int lu_blocked(int update, int64_t n, double* A, int64_t lda, int64_t* piv, int64_t* info,
                char* ws, size_t ws_bytes, int nb, cudaStream_t s);
@@ -82,6 +111,12 @@ int split_update_dd(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t
                     int64_t col0, int64_t N, int64_t k0, int nb, char* ws, size_t ws_bytes,
                     cudaStream_t s);
 size_t split_workspace_bytes(int64_t n, int nb);
+// work bytes of one split_product_dd with m rows and N columns
+size_t split_product_bytes(int64_t m, int64_t N);
+// work bytes of one LU of order n (lu_blocked): the header, and for the split
+// update the trailing-update area plus a second product area that the
+// look-ahead panel uses while the trailing update runs
+size_t lu_workspace_bytes(int update, int64_t n);
 // C -= L U (plus: C += L U) for one 64-wide slab of the inner dimension
 int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
                       int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
@@ -163,6 +198,15 @@ int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, i
                      const TileEntry* tiles,
                      int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
                      const double* aux, char* ws, size_t ws_bytes, DeviceStatus* status, cudaStream_t s);
+// the two halves of split_bupdate_dd: the slices of every active system's
+// operands, then the products of the tiles given (any subset of the step's
+// tiles, in any order, once the slices are in place)
+int split_bslice_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
+                    const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A, const double* aux,
+                    char* ws, size_t ws_bytes, cudaStream_t s);
+int split_bgemm_dd(const BatchView& bv, int geom, int c_off, int h, const TileEntry* tiles, int64_t ntiles,
+                   const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A, const double* aux,
+                   char* ws, size_t ws_bytes, DeviceStatus* status, cudaStream_t s);
 int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s);
 
 // Strassen's recursion over the block matrix product (strassen.cu): C = A B,

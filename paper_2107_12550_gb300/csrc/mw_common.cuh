@@ -106,6 +106,20 @@ inline cudaError_t ensure_smem_limit(K* kernel, size_t bytes) {
 // the current device's SM count (cached per device; 1 if it cannot be read)
 int device_sm_count();
 
+#ifdef __CUDACC__
+// 8-byte asynchronous copy global -> shared; ok == false fills zeros (no read)
+__device__ __forceinline__ void cp_async8(void* smem_dst, const double* gsrc, bool ok) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(gsrc), "r"(ok ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+#endif
+
 }  // namespace mw
 
 // record the last CUDA error of the library for mw_last_cuda_error()

@@ -841,6 +841,12 @@ size_t split_workspace_bytes(int64_t n, int nb) {
 
 double* split_aux(char* ws, int64_t n) { return reinterpret_cast<double*>(ws + split_slices_bytes(n)); }
 
+size_t split_product_bytes(int64_t m, int64_t N) {
+  const int64_t mt = (m + kTileM - 1) / kTileM, nt = (N + kTileN - 1) / kTileN;
+  return 256 + align256((size_t)mt * kS * kASliceBytes) + align256((size_t)nt * kS * kBSliceBytes) +
+         align256(sizeof(int) * (size_t)mt * kTileM) + align256(sizeof(int) * (size_t)nt * kTileN);
+}
+
 // C (m x N) -= L (m x K) * U (K x N) with the strides of `o` (K <= 64)
 int split_product_dd(const SplitOperands& o, char* ws, size_t ws_bytes, int phase, cudaStream_t s) {
   if (o.m <= 0 || o.N <= 0 || o.K <= 0) return MW_OK;
@@ -914,38 +920,68 @@ size_t split_batched_workspace_bytes(int64_t a_tiles, int64_t b_tiles) {
          align256(sizeof(int) * (size_t)a_tiles * kTileM) + align256(sizeof(int) * (size_t)b_tiles * kTileN);
 }
 
-int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
-                     const TileEntry* tiles,
-                     int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A,
-                     const double* aux, char* ws, size_t ws_bytes, DeviceStatus* status, cudaStream_t s) {
-  if (act <= 0 || ntiles <= 0) return MW_OK;
-  if (split_batched_workspace_bytes(a_tiles, b_tiles) > ws_bytes) return MW_EUNSUPPORTED;
+namespace {
+struct BSliceArea {
+  unsigned char* aslices;
+  unsigned char* bslices;
+  int* ea;
+  int* fb;
+};
+BSliceArea bslice_area(char* ws, int64_t a_tiles, int64_t b_tiles) {
+  BSliceArea r;
   size_t off = 256;
-  unsigned char* aslices = reinterpret_cast<unsigned char*>(ws + off);
+  r.aslices = reinterpret_cast<unsigned char*>(ws + off);
   off += align256((size_t)a_tiles * kS * kASliceBytes);
-  unsigned char* bslices = reinterpret_cast<unsigned char*>(ws + off);
+  r.bslices = reinterpret_cast<unsigned char*>(ws + off);
   off += align256((size_t)b_tiles * kS * kBSliceBytes);
-  int* ea = reinterpret_cast<int*>(ws + off);
+  r.ea = reinterpret_cast<int*>(ws + off);
   off += align256(sizeof(int) * (size_t)a_tiles * kTileM);
-  int* fb = reinterpret_cast<int*>(ws + off);
-  {
-    ProfScope ps(kPhSplitAux, s);
-    k_bslice_rows<<<dim3((unsigned)act, (unsigned)(max_mt * kTileM / kSliceRows)), kSliceThreads, 0, s>>>(
-        bv, geom, c_off, h, bases, k0, A, aux, aslices, ea);
-    MW_LAUNCH_CHECK();
-    k_bslice_cols<<<dim3((unsigned)act, (unsigned)(max_cb * 128 / kSliceRows)), kSliceThreads, 0, s>>>(
-        bv, geom, c_off, h, bases, k0, A, aux, bslices, fb);
-    MW_LAUNCH_CHECK();
-  }
-  {
-    ProfScope ps(geom == kGeomTrsmInv ? kPhTrsm : (geom == kGeomPanelInner ? kPhPanelInner : kPhGemmSplit), s);
-    const size_t shmem = split_smem_bytes();
-    MW_CUDA_CHECK(ensure_smem_limit(k_bsplit_gemm, shmem));
-    k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, geom, c_off, h, tiles, bases, k0, A, aux,
-                                                                aslices, bslices, ea, fb, status);
-    MW_LAUNCH_CHECK();
-  }
+  r.fb = reinterpret_cast<int*>(ws + off);
+  return r;
+}
+}  // namespace
+
+int split_bslice_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
+                    const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A, const double* aux,
+                    char* ws, size_t ws_bytes, cudaStream_t s) {
+  if (act <= 0) return MW_OK;
+  if (split_batched_workspace_bytes(a_tiles, b_tiles) > ws_bytes) return MW_EUNSUPPORTED;
+  const BSliceArea z = bslice_area(ws, a_tiles, b_tiles);
+  ProfScope ps(kPhSplitAux, s);
+  k_bslice_rows<<<dim3((unsigned)act, (unsigned)(max_mt * kTileM / kSliceRows)), kSliceThreads, 0, s>>>(
+      bv, geom, c_off, h, bases, k0, A, aux, z.aslices, z.ea);
+  MW_LAUNCH_CHECK();
+  k_bslice_cols<<<dim3((unsigned)act, (unsigned)(max_cb * 128 / kSliceRows)), kSliceThreads, 0, s>>>(
+      bv, geom, c_off, h, bases, k0, A, aux, z.bslices, z.fb);
+  MW_LAUNCH_CHECK();
   return MW_OK;
+}
+
+int split_bgemm_dd(const BatchView& bv, int geom, int c_off, int h, const TileEntry* tiles, int64_t ntiles,
+                   const int2* bases, int64_t a_tiles, int64_t b_tiles, int k0, double* A, const double* aux,
+                   char* ws, size_t ws_bytes, DeviceStatus* status, cudaStream_t s) {
+  if (ntiles <= 0) return MW_OK;
+  if (split_batched_workspace_bytes(a_tiles, b_tiles) > ws_bytes) return MW_EUNSUPPORTED;
+  const BSliceArea z = bslice_area(ws, a_tiles, b_tiles);
+  ProfScope ps(geom == kGeomTrsmInv ? kPhTrsm : (geom == kGeomPanelInner ? kPhPanelInner : kPhGemmSplit), s);
+  const size_t shmem = split_smem_bytes();
+  MW_CUDA_CHECK(ensure_smem_limit(k_bsplit_gemm, shmem));
+  k_bsplit_gemm<<<(unsigned)ntiles, kSplitThreads, shmem, s>>>(bv, geom, c_off, h, tiles, bases, k0, A, aux,
+                                                              z.aslices, z.bslices, z.ea, z.fb, status);
+  MW_LAUNCH_CHECK();
+  return MW_OK;
+}
+
+int split_bupdate_dd(const BatchView& bv, int geom, int c_off, int h, int act, int max_mt, int max_cb,
+                     const TileEntry* tiles, int64_t ntiles, const int2* bases, int64_t a_tiles, int64_t b_tiles,
+                     int k0, double* A, const double* aux, char* ws, size_t ws_bytes, DeviceStatus* status,
+                     cudaStream_t s) {
+  if (act <= 0 || ntiles <= 0) return MW_OK;
+  int rc = split_bslice_dd(bv, geom, c_off, h, act, max_mt, max_cb, bases, a_tiles, b_tiles, k0, A, aux, ws,
+                           ws_bytes, s);
+  if (rc) return rc;
+  return split_bgemm_dd(bv, geom, c_off, h, tiles, ntiles, bases, a_tiles, b_tiles, k0, A, aux, ws, ws_bytes,
+                        status, s);
 }
 
 int split_binv_l11(const BatchView& bv, int act, int k0, const double* A, double* aux, cudaStream_t s) {

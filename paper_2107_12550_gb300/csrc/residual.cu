@@ -274,7 +274,7 @@ static RefineMap refine_map(int inner, int update, int64_t n, int64_t lda) {
   RefineMap m;
   size_t off = 0;
   m.lu_ws = off;
-  off += align256(kWsSplit + (update == MW_UPDATE_SPLIT ? split_workspace_bytes(n, kDefaultNb) : 0));
+  off += align256(lu_workspace_bytes(update, n));
   m.solve_ws = off;
   off += align256(solve_workspace_bytes(inner, n));
   m.lu = off;

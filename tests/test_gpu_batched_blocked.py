@@ -324,3 +324,31 @@ def test_batched_refinement_in_one_cuda_graph(update):
             assert torch.equal(x, x_ref) and torch.equal(st, st_ref), update
     finally:
         api().batch_plan_cache(prev)
+
+
+@pytest.mark.parametrize("w,update", [(2, "plain"), (3, "plain"), (2, "split")])
+def test_blocked_lookahead_bitwise_equal_to_serial(w, update):
+    """With the look-ahead (MW_TUNE_LOOKAHEAD) the tiles holding the next
+    panel's columns are updated first and that panel is factored on a second
+    stream beside the other tiles; the factors, pivots and info are bit for
+    bit those of the serial schedule (orders around the panel and tile
+    edges, and a ragged mix up to 700)."""
+    from paper_2107_12550_gb300 import _lib as L
+    lib = L.lib()
+    n_list = EDGE_N + [int(v) for v in W.batch_sizes(40, 1, 700, seed=90 + w)]
+    mats, _ = _uniform_batch(w, n_list, seed=30 * w)
+    prev = lib.mw_get_tuning(L.MW_TUNE_LOOKAHEAD, w)
+    out = {}
+    try:
+        for la in (0, 1, 1):
+            lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, w, la)
+            A = dev(api().pack_matrices(mats, w))
+            LU, piv, info = api().ludecomp_batched_blocked(A, n_list, w, update)
+            out.setdefault(la, []).append((host(LU), host(piv), host(info)))
+    finally:
+        lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, w, prev)
+    ref = out[0][0]
+    for LU, piv, info in out[1]:
+        assert np.array_equal(info, ref[2])
+        assert np.array_equal(piv, ref[1])
+        assert np.array_equal(LU.view(np.uint64), ref[0].view(np.uint64))

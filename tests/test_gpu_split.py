@@ -333,3 +333,32 @@ def test_lu_split_recursive_panel(leaf):
             check_pivots_near_tie(s.A, 2, host(pivs), pivo)
     finally:
         lib.mw_set_tuning(L.MW_TUNE_SPLIT_PANEL_LEAF, 2, prev)
+
+
+@pytest.mark.parametrize("update,w,n,leaf", [("plain", 2, 300, 0), ("plain", 3, 700, 0), ("plain", 4, 257, 0),
+                                             ("split", 2, 1000, 0), ("split", 2, 1000, 16),
+                                             ("split", 2, 2048, 32)])
+def test_lu_lookahead_bitwise_equal_to_serial(update, w, n, leaf):
+    """The blocked look-ahead (MW_TUNE_LOOKAHEAD: the next panel factored on
+    a second stream while the rest of the trailing matrix is updated) gives
+    the serial schedule's factors and pivots bit for bit: every entry gets the
+    same operations in the same order.  Ragged last panels included."""
+    lib = L.lib()
+    s = W.uniform_system(n, words=w, seed=70 + n, b_words=w)
+    prev_la = lib.mw_get_tuning(L.MW_TUNE_LOOKAHEAD, w)
+    prev_leaf = lib.mw_get_tuning(L.MW_TUNE_SPLIT_PANEL_LEAF, 2)
+    out = {}
+    try:
+        lib.mw_set_tuning(L.MW_TUNE_SPLIT_PANEL_LEAF, 2, leaf)
+        for la in (0, 1, 1):
+            lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, w, la)
+            LU, piv, info = api().ludecomp(dev(s.A), w, update)
+            out.setdefault(la, []).append((host(LU), host(piv), int(info.item())))
+    finally:
+        lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, w, prev_la)
+        lib.mw_set_tuning(L.MW_TUNE_SPLIT_PANEL_LEAF, 2, prev_leaf)
+    ref = out[0][0]
+    for LU, piv, info in out[1]:
+        assert info == ref[2]
+        assert np.array_equal(piv, ref[1])
+        assert np.array_equal(LU.view(np.uint64), ref[0].view(np.uint64))

@@ -43,8 +43,12 @@ def test_knob_validation():
     assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 12) == -3
     assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 16) == 8
     assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF, 2, 8) == 16
-    assert lib.mw_set_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF + 1, 3, 8) == -1
-    assert lib.mw_get_tuning(L.MW_TUNE_BATCH_SPLIT_LEAF + 1, 3) == -1
+    assert lib.mw_get_tuning(L.MW_TUNE_LOOKAHEAD, 3) == 1
+    assert lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, 3, 2) == -3
+    assert lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, 3, 0) == 1
+    assert lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, 3, 1) == 0
+    assert lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD + 1, 3, 1) == -1
+    assert lib.mw_get_tuning(L.MW_TUNE_LOOKAHEAD + 1, 3) == -1
 
 
 def test_apply_from_cache(tmp_path):
