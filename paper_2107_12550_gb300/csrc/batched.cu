@@ -566,13 +566,27 @@ __global__ void k_bt_init_state(int count, const int64_t* __restrict__ info, Bat
   st[s] = z;
 }
 
-// r = b - A x exactly (running systems only); one CTA per 32-row block
+// r = b - A x exactly (running systems only); one CTA per 32-row block.
+// Warp w takes the columns j = w, w + 8, ...  Each column's A words (one
+// per lane's row) and x words are copied into a ring of kResStages stages
+// of the warp's shared memory by cp.async, kResStages - 1 columns ahead, so
+// the loads of later columns are in flight while a column's products are
+// deposited (one column's loads at a time left the kernel bound by their
+// latency).  dynamic shared memory: 8 warps x kResStages x
+// (32 a_words + x_words) doubles (res_stage_bytes)
+constexpr int kResStages = 3;
+constexpr int kResWarps = kResThreads / 32;
+inline size_t res_stage_bytes(int a_words, int x_words) {
+  return sizeof(double) * (size_t)kResWarps * kResStages * (size_t)(32 * a_words + x_words);
+}
+
 __global__ void __launch_bounds__(kResThreads)
 k_bt_residual(int count, const int* __restrict__ nn, const int64_t* __restrict__ moff,
               const int64_t* __restrict__ voff, const int64_t* __restrict__ rbstart, const double* __restrict__ A,
               int a_words, const double* __restrict__ b, int b_words, const double* __restrict__ x, int x_words,
               double* __restrict__ r, int r_words, const BatchState* __restrict__ st) {
   __shared__ u64 acc[kRowsPerCta][kNL];
+  extern __shared__ double rstage[];
   const int s = find_system(rbstart, count, blockIdx.x);
   if (st[s].done) return;
   const int n = nn[s];
@@ -587,20 +601,42 @@ k_bt_residual(int count, const int* __restrict__ nn, const int64_t* __restrict__
   for (int e = threadIdx.x; e < kRowsPerCta * kNL; e += blockDim.x) (&acc[0][0])[e] = 0ull;
   __syncthreads();
   if (warp < b_words && row_ok) deposit_double(acc[lane], bs[warp * n + i], 0, false);
-  constexpr int NWARP = kResThreads / 32;
-  for (int j = warp; j < n; j += NWARP) {
-    double xv[MW_LONG_WORDS];
-#pragma unroll
-    for (int d = 0; d < MW_LONG_WORDS; ++d) xv[d] = (d < x_words) ? __ldg(xs + d * n + j) : 0.0;
-    if (!row_ok) continue;
-    for (int c = 0; c < a_words; ++c) {
-      const double a = __ldg(As + c * plane + (int64_t)j * n + i);
-      if (zero_bits(a)) continue;
-#pragma unroll
-      for (int d = 0; d < MW_LONG_WORDS; ++d)
-        if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], a, xv[d], 0, true);
+  const int per = 32 * a_words + x_words;                 // doubles per stage
+  double* ring = rstage + (size_t)warp * kResStages * per;
+  // column t of this warp (j = warp + 8 t) into stage t % kResStages; rows
+  // beyond n are zero-filled (never used); always one commit group
+  auto issue = [&](int t) {
+    const int j = warp + t * kResWarps;
+    if (j < n) {
+      double* dst = ring + (t % kResStages) * per;
+      for (int c = 0; c < a_words; ++c)
+        cp_async8(dst + c * 32 + lane, As + c * plane + (int64_t)j * n + (row_ok ? i : 0), row_ok);
+      if (lane < x_words) cp_async8(dst + 32 * a_words + lane, xs + (int64_t)lane * n + j, true);
     }
+    cp_async_commit();
+  };
+  const int ncols = (n > warp) ? (n - warp + kResWarps - 1) / kResWarps : 0;
+  for (int t = 0; t < kResStages - 1; ++t) issue(t);
+  for (int t = 0; t < ncols; ++t) {
+    issue(t + kResStages - 1);
+    cp_async_wait<kResStages - 1>();
+    __syncwarp();   // the x words copied by lanes 0 .. x_words-1 are visible to the warp
+    const double* src = ring + (t % kResStages) * per;
+    if (row_ok) {
+      double xv[MW_LONG_WORDS];
+#pragma unroll
+      for (int d = 0; d < MW_LONG_WORDS; ++d) xv[d] = (d < x_words) ? src[32 * a_words + d] : 0.0;
+      for (int c = 0; c < a_words; ++c) {
+        const double a = src[c * 32 + lane];
+        if (zero_bits(a)) continue;
+#pragma unroll
+        for (int d = 0; d < MW_LONG_WORDS; ++d)
+          if (d < x_words && !zero_bits(xv[d])) deposit_product(acc[lane], a, xv[d], 0, true);
+      }
+    }
+    __syncwarp();   // every lane is done with this stage before it is refilled
   }
+  cp_async_wait<0>();
   __syncthreads();
   if (warp == 0 && row_ok) {
     for (int c = 0; c < r_words; ++c) rs[c * n + i] = acc_take(acc[lane]);
@@ -1451,14 +1487,16 @@ static int refine_batched_impl(int count, const BatchPlanHost& p, const BatchPla
   prof_count(kPhRefineAux);
   k_bt_take_vec<<<(unsigned)((p.sum_n + 255) / 256), 256, 0, s>>>(count, d.voff, d.n, p.sum_n, z, W, x, x_words);
   MW_LAUNCH_CHECK();
+  MW_CUDA_CHECK(ensure_smem_limit(k_bt_residual, res_stage_bytes(a_words, x_words),
+                                  sizeof(u64) * kRowsPerCta * kNL));   // + the accumulators
   // one refinement step, in two halves: the exact residual and the tests,
   // then the correction solve, the exact update and the correction test
   // (every kernel skips the systems that are no longer running)
   auto residual_and_check = [&](cudaStream_t q) -> int {
     {
       ProfScope ps(kPhResidual, q);
-      k_bt_residual<<<(unsigned)nrb, kResThreads, 0, q>>>(count, d.n, d.moff, d.voff, d.rb, A, a_words, b, b_words,
-                                                          x, x_words, r, x_words, st);
+      k_bt_residual<<<(unsigned)nrb, kResThreads, res_stage_bytes(a_words, x_words), q>>>(
+          count, d.n, d.moff, d.voff, d.rb, A, a_words, b, b_words, x, x_words, r, x_words, st);
       MW_LAUNCH_CHECK();
     }
     prof_count(kPhRefineAux);

@@ -13,8 +13,8 @@
 #include "lu_internal.cuh"
 
 namespace mw {
-cudaError_t ensure_smem_limit(const void* kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes, size_t static_bytes) {
+  if (bytes + static_bytes <= 48 * 1024) return cudaSuccess;
   struct Entry {
     const void* k;
     int dev;

@@ -94,13 +94,15 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DeviceStatus* status
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? MW_OK : MW_ECUDA; }
 
 // Raises a kernel's dynamic shared memory limit to at least `bytes` on the
-// current device, once per (kernel, device) and size: the attribute belongs
-// to the device's context, so every GPU a process uses needs its own call.
-// Safe for concurrent callers.  Returns a cudaError_t.
-cudaError_t ensure_smem_limit(const void* kernel, size_t bytes);
+// current device, once per (kernel, device) and size, when the dynamic bytes
+// and the kernel's static shared memory (static_bytes) exceed the default
+// 48 KB: the attribute belongs to the device's context, so every GPU a
+// process uses needs its own call.  Safe for concurrent callers.  Returns a
+// cudaError_t.
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes, size_t static_bytes = 0);
 template <typename K>
-inline cudaError_t ensure_smem_limit(K* kernel, size_t bytes) {
-  return ensure_smem_limit(reinterpret_cast<const void*>(kernel), bytes);
+inline cudaError_t ensure_smem_limit(K* kernel, size_t bytes, size_t static_bytes = 0) {
+  return ensure_smem_limit(reinterpret_cast<const void*>(kernel), bytes, static_bytes);
 }
 
 // the current device's SM count (cached per device; 1 if it cannot be read)
