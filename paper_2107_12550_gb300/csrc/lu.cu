@@ -716,7 +716,7 @@ int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64
 // column (argmax, swap inside the panel, multipliers, in-panel update)
 // dynamic shared memory: pivot row [W][kBatchNb] and multipliers [W][nmax]
 template <int W>
-__global__ void __launch_bounds__(kPanelThreads)
+__global__ void __launch_bounds__(kPanelThreads, 4)
 k_bpanel(BatchView bv, int nmax, int kp, int width, double* __restrict__ A, int64_t* __restrict__ piv,
          int64_t* __restrict__ info) {
   extern __shared__ double bsm[];
