@@ -70,10 +70,10 @@ GEMM_TD_TRAFFIC_PER_LAUNCH = 40.40e6
 # DRAM bytes per multiword multiply-subtract of the batched substitution:
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_solve_batched<DD>
 # launch (the second solve of the 152-system mixed batch, n <= 1024, all 152
-# systems running: 998.5 + 4.5 MB) over its sum of n^2 (59.08 M); the
+# systems running: 1031.9 + 4.4 MB) over its sum of n^2 (59.08 M); the
 # algorithmic figure is 16 bytes (each DD entry of L and U read once).  Must
 # be re-measured whenever k_solve_batched changes.
-SOLVE_BATCHED_TRAFFIC_PER_MSUB = 1003.0e6 / 59.08e6
+SOLVE_BATCHED_TRAFFIC_PER_MSUB = 1036.3e6 / 59.08e6
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -332,6 +332,31 @@ def _time(fn, reps, stream):
     return e0.elapsed_time(e1) / reps, out
 
 
+def serial_profile(fn, reps):
+    """Per-phase library profile of `reps` calls of fn, run with the serial
+    schedule (MW_TUNE_LOOKAHEAD 0 for every precision: bitwise the same
+    results).  Under the look-ahead a panel runs beside the trailing update,
+    so each phase's events would also hold the other's time; wall-clock
+    numbers are taken apart, with the look-ahead on."""
+    import torch
+    from paper_2107_12550_gb300 import _lib as L
+    lib = L.lib()
+    prev = {w: lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, w, 0) for w in (2, 3, 4)}
+    try:
+        torch.cuda.synchronize()
+        L.profile_read(reset=True)
+        L.profile_enable(True)
+        out = None
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        L.profile_enable(False)
+        return L.profile_read(reset=True), out
+    finally:
+        for w, v in prev.items():
+            lib.mw_set_tuning(L.MW_TUNE_LOOKAHEAD, w, v)
+
+
 def single_system_td(peak_fp64, steps, sm_max_mhz):
     """The plain FP64-core form on one system: n = 2048, kappa ~ 1e10, QD
     stored, TD LU with the plain trailing update, refined to 2^-200; with the
@@ -349,12 +374,9 @@ def single_system_td(peak_fp64, steps, sm_max_mhz):
     knobs = tuned(INNER, N, "lu")
     f = lambda: api.refine(A, b, INNER, TARGET_BITS, x_words=X_WORDS, work=work, out=x)
     r = f()
-    L.profile_read(reset=True)
-    L.profile_enable(True)
     ms, r = _time(f, steps, stream)
-    L.profile_enable(False)
-    prof = L.profile_read(reset=True)
     ok = r.converged and exact_ok(x.cpu().numpy(), N)
+    prof, _ = serial_profile(f, steps)
     gemm_ms, gemm_launches = prof["gemm_plain"]
     instr = panel_sum_sq(N) * FP64_PER_MSUB[INNER] * steps
     achieved = instr / (gemm_ms * 1e-3) if gemm_ms > 0 else 0.0
@@ -402,12 +424,9 @@ def batch_comparators(A, b, A_np, b_np, n_list, peak_fp64, sm_max_mhz):
     work = api.batch_blocked_workspace(L.MW_OP_REFINE, 2, "plain", n_list)
     f = lambda: api.refine_batched_blocked(A, A_WORDS, b, X_WORDS, n_list, 2, "plain", TARGET_BITS, work=work, out=x)
     f()
-    L.profile_read(reset=True)
-    L.profile_enable(True)
     ms, (_, stats) = _time(f, 1, stream)
-    L.profile_enable(False)
-    prof = L.profile_read(reset=True)
     met = batch_target_met(x.cpu().numpy(), n_list)
+    prof, _ = serial_profile(f, 1)
     lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain"))
     pm, tm = blocked_batch_msubs(n_list)
     ph = {k: v[0] for k, v in prof.items() if v[1]}
@@ -478,11 +497,8 @@ def extras(steps, peak_fp64, peaks):
         wk = api.workspace(L.MW_OP_LUDECOMP, 2, 1 if upd == "split" else 0, n3)
         g = lambda: api.ludecomp(Au, 2, upd, work=wk)
         g()
-        L.profile_read(reset=True)
-        L.profile_enable(True)
         t, _ = _time(g, reps, stream)
-        L.profile_enable(False)
-        prof = L.profile_read(reset=True)
+        prof, _ = serial_profile(g, reps)
         lu[upd] = {"ms": t, "dd_gops": (2.0 / 3.0) * n3 ** 3 / (t * 1e-3) / 1e9,
                    "phase_ms": {k: v[0] / reps for k, v in prof.items() if v[1]}}
     # tensor-pipe roofline of the split GEMM: bf16 MMA flops issued per LU
@@ -518,11 +534,8 @@ def extras(steps, peak_fp64, peaks):
     wk8 = api.workspace(L.MW_OP_LUDECOMP, 2, 1, n8)
     g8 = lambda: api.ludecomp(A8, 2, "split", work=wk8)
     g8()
-    L.profile_read(reset=True)
-    L.profile_enable(True)
     t8, (_, _, info8) = _time(g8, 1, stream)
-    L.profile_enable(False)
-    prof8 = L.profile_read(reset=True)
+    prof8, _ = serial_profile(g8, 1)
     reset_knobs()
     out["lu_dd_n8192_split"] = {"ms": t8, "dd_gops": (2.0 / 3.0) * n8 ** 3 / (t8 * 1e-3) / 1e9, "tuning": knobs8,
                                 "info": int(info8.item()),
@@ -868,14 +881,7 @@ def main():
     # Run with the serial schedule (MW_TUNE_LOOKAHEAD 0: bitwise the same
     # results), so that no phase's events overlap another's and each phase
     # time is its kernels' own duration.
-    la_prev = L.lib().mw_set_tuning(L.MW_TUNE_LOOKAHEAD, 2, 0)
-    L.profile_read(reset=True)
-    L.profile_enable(True)
-    _, pst = step()
-    torch.cuda.synchronize()
-    L.profile_enable(False)
-    prof = L.profile_read(reset=True)
-    L.lib().mw_set_tuning(L.MW_TUNE_LOOKAHEAD, 2, la_prev)
+    prof, (_, pst) = serial_profile(step, 1)
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz")
     roofs = headline_rooflines(prof, 1, n_list, pst.cpu().numpy(), peak_fp64, peaks, sm_max)
     dominant = max(roofs, key=lambda r: r["ms"]) if roofs else None
@@ -884,27 +890,66 @@ def main():
     lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain", "gemm_split", "split_aux", "panel_inner"))
 
     # ---- end to end through the public API with host buffers -------------
+    # Every step copies its inputs (A, b) from pinned host memory and reads x
+    # and the per-system statistics back.  Two input buffers, each with its
+    # own captured graph, let step k+1's host-to-device copy run on a copy
+    # stream while step k computes; the copy into a buffer waits until the
+    # step that last read it has finished.
     A_h = torch.from_numpy(A_np).pin_memory()
     b_h = torch.from_numpy(b_np).pin_memory()
-    x_h = torch.empty_like(x, device="cpu").pin_memory()
-    s_h = torch.empty((args.count, 4), dtype=torch.int64).pin_memory()
-    e2e_steps = 2
+    A2, b2 = torch.empty_like(A), torch.empty_like(b)
+    A2.copy_(A)
+    b2.copy_(b)
+    x2, st2 = torch.empty_like(x), torch.empty_like(st_buf)
+
+    def step_into2():
+        _, s_ = api.refine_batched_blocked(A2, A_WORDS, b2, X_WORDS, n_list, 2, "split", TARGET_BITS,
+                                           work=work, out=x2)
+        st2.copy_(s_)
+
+    step_into2()
+    torch.cuda.synchronize()
+    graph2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph2):
+        step_into2()
+    bufs = [(A, b, x, st_buf, graph), (A2, b2, x2, st2, graph2)]
+    x_h = [torch.empty_like(x, device="cpu").pin_memory() for _ in range(2)]
+    s_h = [torch.empty((args.count, 4), dtype=torch.int64).pin_memory() for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_used = [torch.cuda.Event(), torch.cuda.Event()]
+    e2e_steps = max(4, args.steps // 2)
+
+    def load(k):
+        i = k % 2
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(ev_used[i])
+            bufs[i][0].copy_(A_h, non_blocking=True)
+            bufs[i][1].copy_(b_h, non_blocking=True)
+            ev_in[i].record(copy_stream)
+
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(e2e_steps):
-        A.copy_(A_h, non_blocking=True)
-        b.copy_(b_h, non_blocking=True)
-        graph.replay()
-        x_h.copy_(x, non_blocking=True)
-        s_h.copy_(st_buf, non_blocking=True)
+    copy_stream.wait_event(f0)
+    load(0)
+    for k in range(e2e_steps):
+        i = k % 2
+        if k + 1 < e2e_steps:
+            load(k + 1)
+        stream.wait_event(ev_in[i])
+        bufs[i][4].replay()
+        ev_used[i].record(stream)
+        x_h[i].copy_(bufs[i][2], non_blocking=True)
+        s_h[i].copy_(bufs[i][3], non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    e2e_met = int(sum(batch_target_met(x_h.numpy(), n_list)))
+    e2e_met = min(int(sum(batch_target_met(x_h[i].numpy(), n_list))) for i in range(2))
     e2e_val = e2e_met / (e2e_ms * 1e-3) * world
-    del A_h
+    del A_h, A2, b2, x2, graph2
 
     line = {
         "metric": "solves/s at 2^-200 rel. error",
@@ -936,9 +981,11 @@ def main():
         "rooflines": roofs,
         "gpu_launches": launches * args.steps,
         "clocks": clk,
-        "e2e": {"value": e2e_val, "unit": "solves/s",
+        "e2e": {"value": e2e_val, "unit": "solves/s", "steps": e2e_steps, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(A_np.nbytes + b_np.nbytes),
-                "d2h_bytes_per_step": int(x.numel() * 8 + args.count * 4 * 8)},
+                "d2h_bytes_per_step": int(x.numel() * 8 + args.count * 4 * 8),
+                "overlap": "two input buffers and graphs: step k+1's host-to-device copy runs on a copy "
+                           "stream during step k"},
     }
     if rank == 0 and world == 1 and not args.no_extras:
         ex = {"comparators": batch_comparators(A, b, A_np, b_np, n_list, peak_fp64, sm_max)}
