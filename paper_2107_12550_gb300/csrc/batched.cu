@@ -221,14 +221,11 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 // the leader's two tiles)
 // ---------------------------------------------------------------------------
 constexpr int kSolveBs = 32;
-// The substitution's CTA: 512 threads, one per SM.  Warp 0 leads and has SM
-// sub-partition 0 (warp w issues on sub-partition w % 4) to itself: its
-// triangles are the pipeline's serial chain, and sharing that
-// sub-partition's FP64 pipe with workers slowed the whole solve more than
-// their work gained (82.4 vs 89.7 ms for a 512-system refinement).  The
-// workers are the 12 warps on sub-partitions 1-3; warps 4, 8 and 12 idle.
+// The substitution's CTA: 512 threads, one per SM: warp 0 leads, warps
+// 1 .. 15 work (measured: fewer workers were slower, 12 gave 77.2 ms and
+// 15 gave 75.0 ms for a 512-system refinement, 8 gave 89 ms).
 constexpr int kSolveThreads = 512;
-constexpr int kSolveWorkers = 12;                                                  // worker warps
+constexpr int kSolveWorkers = kSolveThreads / 32 - 1;                            // worker warps
 constexpr int kSolveWGroups = (kBatchMaxN / 32 + kSolveWorkers - 1) / kSolveWorkers;  // row groups per worker
 constexpr unsigned long long kSolveSpin = 1ull << 24;
 
@@ -288,7 +285,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
   // any step (a contiguous range) are dealt round-robin; workers are
   // numbered in warp order.  Ownership is fixed for the whole call, so each
   // row's updates stay in program order on one warp.  wk < 0: not a worker.
-  const int wk = (warp & 3) ? (warp >> 2) * 3 + (warp & 3) - 1 : -1;
+  const int wk = warp - 1;   // worker index (-1: the leader)
   auto group_row = [&](int q) { return (wk + q * kWorkers) * 32 + lane; };
   // The leader's two 32 x 64 tiles of the factor (rows of its block, the 64
   // columns from c0), double-buffered in shared memory: tile bk goes to
@@ -387,16 +384,14 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const int jp = j0 - kSolveBs;
 #pragma unroll 4
           for (int jj = 0; jj < kSolveBs; ++jj)
-            yi = msub<W>(yi, tile_val(tl, jj),
-                         smem_val<W>(ysm, nmax, jp + jj));
+            yi = msub<W>(yi, tile_val(tl, jj), smem_val<W>(ysm, nmax, jp + jj));
         }
         for (int jj = 0; jj < bsz - 1; ++jj) {
           val<W> yj;
 #pragma unroll
           for (int c = 0; c < W; ++c) yj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
           if (lane > jj && lane < bsz)
-            yi = msub<W>(yi, tile_val(tl, kSolveBs + jj),
-                         yj);
+            yi = msub<W>(yi, tile_val(tl, kSolveBs + jj), yj);
         }
         if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
         __threadfence_block();
@@ -404,7 +399,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
         if (lane == 0) *vtri = bk;
       }
       cp_async_wait<0>();
-    } else if (wk >= 0) {
+    } else {
       for (int bk = 0; bk < nb; ++bk) {
         if (!solve_wait([&] { return *vtri >= bk; }, vab, cur, spin_limit)) break;
         const int j0 = bk * kSolveBs;
@@ -468,8 +463,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
             const int bszn = min(kSolveBs, n - jn);
 #pragma unroll 4
             for (int jj = bszn - 1; jj >= 0; --jj)
-              yi = msub<W>(yi, tile_val(tl, kSolveBs + jj),
-                           smem_val<W>(ysm, nmax, jn + jj));
+              yi = msub<W>(yi, tile_val(tl, kSolveBs + jj), smem_val<W>(ysm, nmax, jn + jj));
           }
           for (int jj = bsz - 1; jj >= 0; --jj) {
             if (lane == jj) yi = mul<W>(yi, di);          // x_j = y_j d_j
@@ -485,7 +479,7 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           if (lane == 0) *vtri = bk;
         }
         cp_async_wait<0>();
-      } else if (wk >= 0) {
+      } else {
         for (int bk = nb - 1; bk >= 0; --bk) {
           if (!solve_wait([&] { return *vtri <= bk; }, vab, cur, spin_limit)) break;
           const int j0 = bk * kSolveBs;

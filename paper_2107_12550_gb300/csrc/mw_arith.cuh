@@ -39,14 +39,109 @@ __device__ __forceinline__ double fmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double fdiv(double a, double b) { return __ddiv_rn(a, b); }
 
-// s + e = a + b exactly, s = RN(a + b)
-__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+// Knuth's TwoSum as six FP64 operations: s = RN(a + b), e = a + b - s
+// exactly (for finite a, b without overflow)
+__device__ __forceinline__ void two_sum_fp64(double a, double b, double& s, double& e) {
   s = fadd(a, b);
   const double a_virt = fsub(s, b);
   const double b_virt = fsub(s, a_virt);
   const double a_err = fsub(a, a_virt);
   const double b_err = fsub(b, b_virt);
   e = fadd(a_err, b_err);
+}
+
+namespace eft_int {
+typedef unsigned long long u64;
+constexpr u64 kMan = (1ull << 52) - 1;
+constexpr u64 kHid = 1ull << 52;
+constexpr u64 kSign = 1ull << 63;
+__device__ __forceinline__ u64 bits(double x) { return (u64)__double_as_longlong(x); }
+__device__ __forceinline__ double dbl(u64 b) { return __longlong_as_double((long long)b); }
+
+// the double |r| 2^(E - 1075) with sign bit sg (r < 2^64, exactly
+// representable); false when it would be subnormal or overflow
+__device__ __forceinline__ bool pack(u64 r, int E, u64 sg, double& out) {
+  const int L = 64 - __clzll((long long)r);
+  const int Ee = E + (L - 53);
+  if (Ee < 1 || Ee > 2046) return false;
+  const u64 m = (L >= 53) ? (r >> (L - 53)) : (r << (53 - L));
+  out = dbl(sg | ((u64)Ee << 52) | (m & kMan));
+  return true;
+}
+
+// s = RN(a + b), e = a + b - s for the bit patterns A, B of two doubles with
+// |a| >= |b|; false (and the caller falls back) outside the normal range
+__device__ __forceinline__ bool sum_ordered(u64 A, u64 B, double& s, double& e) {
+  const u64 ua = A & ~kSign, ub = B & ~kSign;
+  const int ea = (int)(ua >> 52), eb = (int)(ub >> 52);
+  if (eb == 0 || ea == 2047) return false;   // b zero or subnormal; a infinite or NaN
+  const int d = ea - eb;
+  if (d > 54) {                              // |b| < ulp(a) / 4: RN(a + b) = a, exactly b left over
+    s = dbl(A);
+    e = dbl(B);
+    return true;
+  }
+  const u64 sa = A & kSign;
+  const u64 ma = (ua & kMan) | kHid, mb = (ub & kMan) | kHid;
+  // M = ma 2^d +- mb (< 2^108) in (hi, lo); a + b = M 2^(eb - 1075) with a's sign
+  u64 lo = ma << d;
+  u64 hi = d ? (ma >> (64 - d)) : 0ull;
+  if ((A ^ B) & kSign) {
+    const u64 l2 = lo - mb;
+    hi -= (l2 > lo) ? 1ull : 0ull;
+    lo = l2;
+  } else {
+    const u64 l2 = lo + mb;
+    hi += (l2 < lo) ? 1ull : 0ull;
+    lo = l2;
+  }
+  if ((hi | lo) == 0ull) {                   // a = -b: +0, +0
+    s = 0.0;
+    e = 0.0;
+    return true;
+  }
+  const int L = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  if (L <= 53) {                             // the sum is exact: e = +0
+    e = 0.0;
+    return pack(lo, eb, sa, s);
+  }
+  const int sh = L - 53;                     // 1 .. 55 bits below s's last place
+  u64 q = (lo >> sh) | (hi << (64 - sh));
+  const u64 r = lo & ((1ull << sh) - 1ull);
+  const u64 half = 1ull << (sh - 1);
+  const bool up = (r > half) || (r == half && (q & 1ull));   // to nearest, ties to even
+  int Es = eb + sh;
+  const long long rem = (long long)r - (up ? (long long)(1ull << sh) : 0ll);
+  if (up && ++q == (1ull << 53)) {
+    q >>= 1;
+    Es += 1;
+  }
+  if (Es > 2046) return false;
+  s = dbl(sa | ((u64)Es << 52) | (q & kMan));
+  if (rem == 0) {
+    e = 0.0;
+    return true;
+  }
+  return pack((u64)(rem < 0 ? -rem : rem), eb, rem < 0 ? (sa ^ kSign) : sa, e);
+}
+}  // namespace eft_int
+
+// TwoSum: s = RN(a + b) and e = a + b - s exactly (Knuth).  Both values are
+// fixed by a and b alone, so they are computed here on the integer pipes,
+// which run at 32 times the FP64 pipe's lane rate on this GPU: the two
+// significands are aligned into a 128-bit integer and added exactly, the sum
+// is rounded to nearest-even, and the remainder is e.  Operands or results
+// outside the normal range (zeros, subnormals, infinities, NaNs, overflow)
+// take the six-operation FP64 sequence, which gives the same values wherever
+// both apply; either way the bits are those of the FP64 sequence.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  eft_int::u64 A = eft_int::bits(a), B = eft_int::bits(b);
+  if ((A << 1) < (B << 1)) {
+    const eft_int::u64 t = A;
+    A = B;
+    B = t;
+  }
+  if (!eft_int::sum_ordered(A, B, s, e)) two_sum_fp64(a, b, s, e);
 }
 
 // x != 0 (either sign) tested on the bit pattern, off the FP64 pipe

@@ -73,6 +73,59 @@ def test_arith_bitwise(w):
             assert np.array_equal(got, ref, equal_nan=True), (op, np.argwhere(got != ref)[:5])
 
 
+def _twosum_edge_inputs(rng, w, cnt):
+    """Pairs aimed at every branch of the integer TwoSum: leading-word
+    exponent gaps 0..70 (the s = a, e = b cut at a gap of 55), exact and
+    near cancellation, halfway cases (ties to even, also below a power of
+    two), zeros of both signs, subnormals, and sums near overflow."""
+    x = _rand_mw(rng, w, cnt)
+    y = _rand_mw(rng, w, cnt)
+    q = cnt // 8
+    k = np.arange(cnt)
+    gap = rng.integers(0, 71, cnt)
+    sel = k < q                                               # exponent gaps
+    y[0, sel] = np.ldexp(rng.uniform(0.5, 1.0, q) * rng.choice([-1.0, 1.0], q), np.frexp(x[0, sel])[1] - gap[sel])
+    sel = (k >= q) & (k < 2 * q)                              # exact cancellation in any word
+    y[:, sel] = -x[:, sel]
+    sel = (k >= 2 * q) & (k < 3 * q)                          # a few ulps apart, opposite signs
+    y[0, sel] = -np.nextafter(x[0, sel], np.where(rng.random(q) < 0.5, np.inf, -np.inf))
+    sel = (k >= 3 * q) & (k < 4 * q)                          # halfway: y0 = +-ulp(x0) / 2 (+ tail)
+    ulp = np.spacing(np.abs(x[0, sel]))
+    y[0, sel] = ulp / 2 * rng.choice([-1.0, 1.0], q)
+    y[1:, sel] = 0.0
+    sel = (k >= 4 * q) & (k < 5 * q)                          # powers of two minus tiny values
+    x[0, sel] = np.ldexp(1.0, rng.integers(-20, 20, q)) * rng.choice([-1.0, 1.0], q)
+    y[0, sel] = -np.sign(x[0, sel]) * np.spacing(np.abs(x[0, sel])) * rng.choice([0.25, 0.5, 0.75, 1.0], q)
+    sel = (k >= 5 * q) & (k < 6 * q)                          # signed zeros anywhere
+    z = rng.choice([0.0, -0.0], (w, q))
+    m = rng.random((w, q)) < 0.5
+    y[:, sel] = np.where(m, z, y[:, sel])
+    sel = (k >= 6 * q) & (k < 7 * q)                          # subnormal and tiny words
+    x[:, sel] = rng.choice([5e-324, -5e-324, 2.2250738585072014e-308, -1.1e-308, 3e-310], (w, q))
+    y[:, sel] = rng.choice([5e-324, -2.2250738585072014e-308, 1e-309, -4e-323], (w, q))
+    sel = k >= 7 * q                                          # near overflow
+    r = cnt - 7 * q
+    x[0, sel] = rng.choice([1.7e308, -1.7e308, 8.9e307], r)
+    y[0, sel] = rng.choice([1.7e308, 8.98846567431158e307, -1.0], r)
+    x[1:, sel] = 0.0
+    y[1:, sel] = 0.0
+    return x, y
+
+
+@pytest.mark.parametrize("w", [2, 3, 4])
+def test_arith_twosum_edge_cases(w):
+    """Addition, multiplication and division on inputs aimed at the integer
+    TwoSum's branches and fallbacks: every result bitwise equal to the
+    oracle's FP64 TwoSum arithmetic (NaNs compared as NaNs)."""
+    rng = np.random.default_rng(91 + w)
+    x, y = _twosum_edge_inputs(rng, w, 16000)
+    for op in range(4):
+        got = host(api().arith(op, w, dev(x), dev(y)))
+        ref = oracle.arith(op, w, x, y)
+        same_bits = (got.view(np.uint64) == ref.view(np.uint64)) | (np.isnan(got) & np.isnan(ref))
+        assert same_bits.all(), (op, np.argwhere(~same_bits)[:5])
+
+
 @pytest.mark.parametrize("w", [2, 3, 4])
 def test_cmpabs_special_values(w):
     """The magnitude comparison of the pivot search on signed zeros,
