@@ -173,7 +173,7 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
       for (int i = k + 1 + tid; i < n; i += kBatchThreads) {
         val<W> l = load<W>(a, plane, (int64_t)k * n + i);
         if (!zero) {
-          l = div<W>(l, akk);
+          l = div<W, false>(l, akk);
           store<W>(a, plane, (int64_t)k * n + i, l);
         }
 #pragma unroll
@@ -193,7 +193,7 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
         }
         const int64_t idx = (int64_t)j * n + i;
         val<W> x = load<W>(a, plane, idx);
-        x = msub<W>(x, l, u);
+        x = msub<W, false>(x, l, u);
         store<W>(a, plane, idx, x);
       }
       __syncthreads();
@@ -223,7 +223,9 @@ k_lu_batched(int count, int nmax, const int* __restrict__ order, const int* __re
 constexpr int kSolveBs = 32;
 // The substitution's CTA: 512 threads, one per SM: warp 0 leads, warps
 // 1 .. 15 work (measured: fewer workers were slower, 12 gave 77.2 ms and
-// 15 gave 75.0 ms for a 512-system refinement, 8 gave 89 ms).
+// 15 gave 75.0 ms for a 512-system refinement, 8 gave 89 ms).  The
+// leader's serial chain takes TwoSum's FP64 form, the workers' loops the
+// integer form (63.2 ms; the other three combinations 75.0-86.3 ms).
 constexpr int kSolveThreads = 512;
 constexpr int kSolveWorkers = kSolveThreads / 32 - 1;                            // worker warps
 constexpr int kSolveWGroups = (kBatchMaxN / 32 + kSolveWorkers - 1) / kSolveWorkers;  // row groups per worker
@@ -384,14 +386,14 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
           const int jp = j0 - kSolveBs;
 #pragma unroll 4
           for (int jj = 0; jj < kSolveBs; ++jj)
-            yi = msub<W>(yi, tile_val(tl, jj), smem_val<W>(ysm, nmax, jp + jj));
+            yi = msub<W, false>(yi, tile_val(tl, jj), smem_val<W>(ysm, nmax, jp + jj));
         }
         for (int jj = 0; jj < bsz - 1; ++jj) {
           val<W> yj;
 #pragma unroll
           for (int c = 0; c < W; ++c) yj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
           if (lane > jj && lane < bsz)
-            yi = msub<W>(yi, tile_val(tl, kSolveBs + jj), yj);
+            yi = msub<W, false>(yi, tile_val(tl, kSolveBs + jj), yj);
         }
         if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
         __threadfence_block();
@@ -463,15 +465,15 @@ k_solve_batched(int count, int nmax, const int* __restrict__ order, const int* _
             const int bszn = min(kSolveBs, n - jn);
 #pragma unroll 4
             for (int jj = bszn - 1; jj >= 0; --jj)
-              yi = msub<W>(yi, tile_val(tl, kSolveBs + jj), smem_val<W>(ysm, nmax, jn + jj));
+              yi = msub<W, false>(yi, tile_val(tl, kSolveBs + jj), smem_val<W>(ysm, nmax, jn + jj));
           }
           for (int jj = bsz - 1; jj >= 0; --jj) {
-            if (lane == jj) yi = mul<W>(yi, di);          // x_j = y_j d_j
+            if (lane == jj) yi = mul<W, false>(yi, di);   // x_j = y_j d_j
             val<W> xj;
 #pragma unroll
             for (int c = 0; c < W; ++c) xj.v[c] = __shfl_sync(0xffffffffu, yi.v[c], jj);
             if (lane < jj)
-              yi = msub<W>(yi, tile_val(tl, jj), xj);
+              yi = msub<W, false>(yi, tile_val(tl, jj), xj);
           }
           if (lane < bsz) smem_put<W>(ysm, nmax, i, yi);
           __threadfence_block();

@@ -306,7 +306,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
     for (int64_t i = ilo + tid; i < r1; i += kPanelThreads) {
       val<W> a = pr.get(i, kk);
       if (!zero) {
-        a = div<W>(a, akk);
+        a = div<W, false>(a, akk);
         pr.put(i, kk, a);
       }
 #pragma unroll
@@ -327,7 +327,7 @@ k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k
           u.v[c] = su[c * nb + j];
         }
         val<W> a = pr.get(i, j);
-        a = msub<W>(a, l, u);
+        a = msub<W, false>(a, l, u);
         pr.put(i, j, a);
       }
     }
@@ -442,7 +442,7 @@ static int swap_gather(double* A, int64_t lda, int64_t plane, int W, int64_t n, 
 // (g = tid / 8).  Step t: the owner of row t publishes u_tj through shared
 // memory; every thread then updates its rows r > t.
 // ---------------------------------------------------------------------------
-template <int W, int NB>
+template <int W, int NB, bool I = true>
 __device__ __forceinline__ void trsm_cols(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n,
                                           int64_t k0, const int64_t* __restrict__ piv, int64_t cblock) {
   constexpr int TC = 8;
@@ -495,7 +495,7 @@ __device__ __forceinline__ void trsm_cols(double* __restrict__ A, int64_t lda, i
         const int r = q * NG + g;
         if (q >= qt && r > t && r < NB) {
           const val<W> l = load_ro<W>(A, plane, lcol + r);
-          a[q] = msub<W>(a[q], l, u);
+          a[q] = msub<W, I>(a[q], l, u);
         }
       }
     }
@@ -513,7 +513,7 @@ template <int W, int NB>
 __global__ void __launch_bounds__(256)
 k_trsm(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0,
        const int64_t* __restrict__ piv) {
-  trsm_cols<W, NB>(A, lda, plane, n, k0, piv, blockIdx.x);
+  trsm_cols<W, NB, false>(A, lda, plane, n, k0, piv, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -22,7 +22,10 @@
 //
 // Additions are issued as fma(a, 1, b): one rounding of a + b, hence the same
 // bits as an add, and the fused pipe issues faster than the add pipe on this
-// GPU's FP64 units.
+// GPU's FP64 units.  TwoSum's two results are fixed by its operands, so by
+// default they are computed on the integer pipes (exact integer sum of the
+// aligned significands, then round to nearest-even); every operation gives
+// the same bits with either form (template argument I).
 #pragma once
 #include <cstdint>
 
@@ -134,7 +137,17 @@ __device__ __forceinline__ bool sum_ordered(u64 A, u64 B, double& s, double& e) 
 // outside the normal range (zeros, subnormals, infinities, NaNs, overflow)
 // take the six-operation FP64 sequence, which gives the same values wherever
 // both apply; either way the bits are those of the FP64 sequence.
+// I = false: Knuth's FP64 sequence itself.  The integer form costs more
+// issue slots and a longer dependency chain but 6 fewer FP64 instructions:
+// it wins where many warps share the FP64 pipe (throughput loops) and loses
+// on a lone serial chain, so the multiword operations below take I as a
+// template argument (default: the integer form).
+template <bool I = true>
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  if constexpr (!I) {
+    two_sum_fp64(a, b, s, e);
+    return;
+  }
   eft_int::u64 A = eft_int::bits(a), B = eft_int::bits(b);
   if ((A << 1) < (B << 1)) {
     const eft_int::u64 t = A;
@@ -164,10 +177,11 @@ __device__ __forceinline__ void two_prod(double a, double b, double& p, double& 
 // ---------------------------------------------------------------------------
 // W = 2
 // ---------------------------------------------------------------------------
+template <bool I = true>
 __device__ __forceinline__ val<2> dd_add(const val<2>& x, const val<2>& y) {
   double sh, sl, th, tl, vh, vl;
-  two_sum(x.v[0], y.v[0], sh, sl);
-  two_sum(x.v[1], y.v[1], th, tl);
+  two_sum<I>(x.v[0], y.v[0], sh, sl);
+  two_sum<I>(x.v[1], y.v[1], th, tl);
   const double c = fadd(sl, th);
   quick_two_sum(sh, c, vh, vl);
   const double w = fadd(tl, vl);
@@ -206,14 +220,14 @@ __device__ __forceinline__ val<2> dd_div(const val<2>& x, const val<2>& y) {
 // ---------------------------------------------------------------------------
 // Renormalisation of M terms into W words (W = 3, 4)
 // ---------------------------------------------------------------------------
-template <int W, int M>
+template <int W, int M, bool I = true>
 __device__ __forceinline__ val<W> renormalise(double (&t)[M]) {
   // bottom-up exact cascade
   double s = t[M - 1];
 #pragma unroll
   for (int i = M - 2; i >= 0; --i) {
     double hi, lo;
-    two_sum(t[i], s, hi, lo);
+    two_sum<I>(t[i], s, hi, lo);
     s = hi;
     t[i + 1] = lo;
   }
@@ -228,7 +242,7 @@ __device__ __forceinline__ val<W> renormalise(double (&t)[M]) {
   for (int i = 1; i < M; ++i) {
     if (k < W - 1) {
       double hi, lo;
-      two_sum(s, t[i], hi, lo);
+      two_sum<I>(s, t[i], hi, lo);
       if (nonzero(lo)) {
 #pragma unroll
         for (int j = 0; j < W - 1; ++j) z.v[j] = (k == j) ? hi : z.v[j];
@@ -254,11 +268,11 @@ __device__ __forceinline__ val<W> renormalise(double (&t)[M]) {
   return z;
 }
 
-template <int W>
+template <int W, bool I = true>
 __device__ __forceinline__ val<W> gen_add(const val<W>& x, const val<W>& y) {
   double s[W], e[W];
 #pragma unroll
-  for (int i = 0; i < W; ++i) two_sum(x.v[i], y.v[i], s[i], e[i]);
+  for (int i = 0; i < W; ++i) two_sum<I>(x.v[i], y.v[i], s[i], e[i]);
   double t[2 * W - 1];
   t[0] = s[0];
 #pragma unroll
@@ -266,9 +280,10 @@ __device__ __forceinline__ val<W> gen_add(const val<W>& x, const val<W>& y) {
     t[2 * i - 1] = s[i];
     t[2 * i] = e[i - 1];
   }
-  return renormalise<W, 2 * W - 1>(t);
+  return renormalise<W, 2 * W - 1, I>(t);
 }
 
+template <bool I = true>
 __device__ __forceinline__ val<3> td_mul(const val<3>& x, const val<3>& y) {
   double p00, q00, p01, q01, p10, q10;
   two_prod(x.v[0], y.v[0], p00, q00);
@@ -280,9 +295,10 @@ __device__ __forceinline__ val<3> td_mul(const val<3>& x, const val<3>& y) {
   c = fadd(c, q01);
   c = fadd(c, q10);
   double t[5] = {p00, q00, p01, p10, c};
-  return renormalise<3, 5>(t);
+  return renormalise<3, 5, I>(t);
 }
 
+template <bool I = true>
 __device__ __forceinline__ val<4> qd_mul(const val<4>& x, const val<4>& y) {
   double p00, q00, p01, q01, p10, q10, p02, q02, p11, q11, p20, q20;
   two_prod(x.v[0], y.v[0], p00, q00);
@@ -299,10 +315,10 @@ __device__ __forceinline__ val<4> qd_mul(const val<4>& x, const val<4>& y) {
   c = fadd(c, q11);
   c = fadd(c, q20);
   double t[10] = {p00, q00, p01, p10, q01, q10, p02, p11, p20, c};
-  return renormalise<4, 10>(t);
+  return renormalise<4, 10, I>(t);
 }
 
-template <int W>
+template <int W, bool I = true>
 __device__ __forceinline__ val<W> gen_mul_d(const val<W>& x, double d) {
   double p[W], q[W];
 #pragma unroll
@@ -315,7 +331,7 @@ __device__ __forceinline__ val<W> gen_mul_d(const val<W>& x, double d) {
     t[2 * i - 1] = p[i];
     t[2 * i] = q[i - 1];
   }
-  return renormalise<W, 2 * W - 1>(t);
+  return renormalise<W, 2 * W - 1, I>(t);
 }
 
 template <int W>
@@ -326,45 +342,49 @@ __device__ __forceinline__ val<W> neg(const val<W>& x) {
   return z;
 }
 
-template <int W>
+template <int W, bool I = true>
 __device__ __forceinline__ val<W> gen_div(const val<W>& x, const val<W>& y) {
   double q[W + 1];
   q[0] = fdiv(x.v[0], y.v[0]);
   val<W> r = x;
 #pragma unroll
   for (int i = 1; i <= W; ++i) {
-    r = gen_add<W>(r, neg<W>(gen_mul_d<W>(y, q[i - 1])));
+    r = gen_add<W, I>(r, neg<W>(gen_mul_d<W, I>(y, q[i - 1])));
     q[i] = fdiv(r.v[0], y.v[0]);
   }
-  return renormalise<W, W + 1>(q);
+  return renormalise<W, W + 1, I>(q);
 }
 
 // ---------------------------------------------------------------------------
 // Precision-generic entry points
 // ---------------------------------------------------------------------------
-template <int W> __device__ __forceinline__ val<W> add(const val<W>& x, const val<W>& y);
-template <> __device__ __forceinline__ val<2> add<2>(const val<2>& x, const val<2>& y) { return dd_add(x, y); }
-template <> __device__ __forceinline__ val<3> add<3>(const val<3>& x, const val<3>& y) { return gen_add<3>(x, y); }
-template <> __device__ __forceinline__ val<4> add<4>(const val<4>& x, const val<4>& y) { return gen_add<4>(x, y); }
+template <int W, bool I = true>
+__device__ __forceinline__ val<W> add(const val<W>& x, const val<W>& y) {
+  if constexpr (W == 2) return dd_add<I>(x, y);
+  else return gen_add<W, I>(x, y);
+}
 
-template <int W>
-__device__ __forceinline__ val<W> sub(const val<W>& x, const val<W>& y) { return add<W>(x, neg<W>(y)); }
+template <int W, bool I = true>
+__device__ __forceinline__ val<W> sub(const val<W>& x, const val<W>& y) { return add<W, I>(x, neg<W>(y)); }
 
-template <int W> __device__ __forceinline__ val<W> mul(const val<W>& x, const val<W>& y);
-template <> __device__ __forceinline__ val<2> mul<2>(const val<2>& x, const val<2>& y) { return dd_mul(x, y); }
-template <> __device__ __forceinline__ val<3> mul<3>(const val<3>& x, const val<3>& y) { return td_mul(x, y); }
-template <> __device__ __forceinline__ val<4> mul<4>(const val<4>& x, const val<4>& y) { return qd_mul(x, y); }
+template <int W, bool I = true>
+__device__ __forceinline__ val<W> mul(const val<W>& x, const val<W>& y) {
+  if constexpr (W == 2) return dd_mul(x, y);
+  else if constexpr (W == 3) return td_mul<I>(x, y);
+  else return qd_mul<I>(x, y);
+}
 
-template <int W> __device__ __forceinline__ val<W> div(const val<W>& x, const val<W>& y);
-template <> __device__ __forceinline__ val<2> div<2>(const val<2>& x, const val<2>& y) { return dd_div(x, y); }
-template <> __device__ __forceinline__ val<3> div<3>(const val<3>& x, const val<3>& y) { return gen_div<3>(x, y); }
-template <> __device__ __forceinline__ val<4> div<4>(const val<4>& x, const val<4>& y) { return gen_div<4>(x, y); }
+template <int W, bool I = true>
+__device__ __forceinline__ val<W> div(const val<W>& x, const val<W>& y) {
+  if constexpr (W == 2) return dd_div(x, y);
+  else return gen_div<W, I>(x, y);
+}
 
 // c - a*b as a rounded multiply followed by a rounded subtraction (the
 // per-element step of the elimination and of the substitutions)
-template <int W>
+template <int W, bool I = true>
 __device__ __forceinline__ val<W> msub(const val<W>& c, const val<W>& a, const val<W>& b) {
-  return sub<W>(c, mul<W>(a, b));
+  return sub<W, I>(c, mul<W, I>(a, b));
 }
 
 // |x| vs |y| on the sign-adjusted words (|x0|, s x1, s x2, ...): -1, 0, +1,

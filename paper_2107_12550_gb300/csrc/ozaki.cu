@@ -800,7 +800,7 @@ k_inv_l11_cols(const double* __restrict__ A, int64_t lda, int64_t plane, int k0,
       l.v[1] = ls[P + t * kK + i];
       u.v[0] = xt[0];
       u.v[1] = xt[1];
-      x = msub<2>(x, l, u);
+      x = msub<2, false>(x, l, u);
     }
   }
   const bool below = i > c;

@@ -88,7 +88,7 @@ __global__ void k_solve_prep(const double* __restrict__ LU, int64_t lda, int64_t
 #pragma unroll
     for (int c = 0; c < W; ++c) one.v[c] = 0.0;
     one.v[0] = 1.0;
-    const val<W> dj = div<W>(one, load_ro<W>(LU, plane, q * lda + q));
+    const val<W> dj = div<W, false>(one, load_ro<W>(LU, plane, q * lda + q));
     store<W>(d, n, q, dj);
 #pragma unroll
     for (int c = 0; c < W; ++c) {
@@ -183,7 +183,7 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
         }
         for (int jj = done; jj < done + k; ++jj) {
           const val<W> yj = shfl_val<W>(v, jj);
-          if (row_ok) acc = msub<W>(acc, load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i), yj);
+          if (row_ok) acc = msub<W, false>(acc, load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i), yj);
         }
         done += k;
       }
@@ -195,7 +195,7 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
         for (int c = 0; c < W; ++c) __stcg(y + c * n + i, acc.v[c]);
       }
       const val<W> yj = shfl_val<W>(acc, jj);
-      if (lane > jj && lane < jb) acc = msub<W>(acc, load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i), yj);
+      if (lane > jj && lane < jb) acc = msub<W, false>(acc, load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i), yj);
     }
     yr[q] = acc;
   }
@@ -224,7 +224,7 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
         }
         for (int jj = done - 1; jj >= done - k; --jj) {
           const val<W> xj = shfl_val<W>(v, jj);
-          if (row_ok) acc = msub<W>(acc, load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i), xj);
+          if (row_ok) acc = msub<W, false>(acc, load_ro<W>(LU, plane, (J * kSolveBlock + jj) * lda + i), xj);
         }
         done -= k;
       }
@@ -232,12 +232,12 @@ k_solve(const double* __restrict__ LU, int64_t lda, int64_t plane, int64_t n,
     const int jb = (int)((n - I * kSolveBlock < kSolveBlock) ? n - I * kSolveBlock : kSolveBlock);
     for (int jj = jb - 1; jj >= 0; --jj) {
       if (lane == jj) {
-        acc = mul<W>(acc, load_ro<W>(d, n, i));
+        acc = mul<W, false>(acc, load_ro<W>(d, n, i));
 #pragma unroll
         for (int c = 0; c < W; ++c) __stcg(xb + c * n + i, acc.v[c]);
       }
       const val<W> xj = shfl_val<W>(acc, jj);
-      if (lane < jj) acc = msub<W>(acc, load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i), xj);
+      if (lane < jj) acc = msub<W, false>(acc, load_ro<W>(LU, plane, (I * kSolveBlock + jj) * lda + i), xj);
     }
     if (row_ok) {
 #pragma unroll
