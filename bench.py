@@ -52,8 +52,13 @@ INNER = 3                 # TD
 
 # FP64 instructions of one multiword multiply + subtraction (the elimination
 # step), counted from the algorithms in csrc/mw_arith.cuh on their typical
-# (all error terms non-zero) path
+# (all error terms non-zero) path: with TwoSum's FP64 sequence (the serial
+# chains: single-system panel, TRSM and solve, the substitution's leader) and
+# with TwoSum on the integer pipes (the throughput loops: the GEMMs, the
+# batched panel leaves, the substitution's workers), where each TwoSum's six
+# FP64 instructions leave the FP64 pipe
 FP64_PER_MSUB = {2: 29, 3: 117, 4: 196}
+FP64_PER_MSUB_INT = {2: 17, 3: 27, 4: 46}
 # FP64 thread instructions per clock of the whole GB300 (ncu: the
 # peak_sustained of sm__sass_thread_inst_executed_op_dfma_pred_on.sum,
 # 2 per SM per clock over 152 SMs)
@@ -378,7 +383,7 @@ def single_system_td(peak_fp64, steps, sm_max_mhz):
     ok = r.converged and exact_ok(x.cpu().numpy(), N)
     prof, _ = serial_profile(f, steps)
     gemm_ms, gemm_launches = prof["gemm_plain"]
-    instr = panel_sum_sq(N) * FP64_PER_MSUB[INNER] * steps
+    instr = panel_sum_sq(N) * FP64_PER_MSUB_INT[INNER] * steps
     achieved = instr / (gemm_ms * 1e-3) if gemm_ms > 0 else 0.0
     ceiling = FP64_LANES_PER_CLK * sm_max_mhz * 1e6 if sm_max_mhz else None
     lu_ms = sum(prof[p][0] for p in ("panel", "laswp", "trsm", "gemm_plain")) / steps
@@ -433,8 +438,8 @@ def batch_comparators(A, b, A_np, b_np, n_list, peak_fp64, sm_max_mhz):
     out["plain_dd_batched_refine"] = {
         "ms_per_batch": ms, "systems_met": int(sum(met)), "solves_per_s": int(sum(met)) / (ms * 1e-3),
         "lu_ms": lu_ms, "lu_dd_gops": ops / (lu_ms * 1e-3) / 1e9 if lu_ms else None, "phase_ms": ph,
-        "panel_fp64_frac_msub_only": pm * FP64_PER_MSUB[2] / (ph["panel"] * 1e-3) / peak_fp64 if ph.get("panel") else None,
-        "trsm_fp64_frac_msub_only": tm * FP64_PER_MSUB[2] / (ph["trsm"] * 1e-3) / peak_fp64 if ph.get("trsm") else None}
+        "panel_fp64_frac_msub_only": pm * FP64_PER_MSUB_INT[2] / (ph["panel"] * 1e-3) / peak_fp64 if ph.get("panel") else None,
+        "trsm_fp64_frac_msub_only": tm * FP64_PER_MSUB_INT[2] / (ph["trsm"] * 1e-3) / peak_fp64 if ph.get("trsm") else None}
     del work, x
     sample = stratified_sample(n_list, 16)
     sn = [n_list[s] for s in sample]
@@ -524,7 +529,7 @@ def extras(steps, peak_fp64, peaks):
     }
     pg = lu["plain"]["phase_ms"].get("gemm_plain", 0.0)
     if pg:
-        instr = panel_sum_sq(n3) * FP64_PER_MSUB[2]
+        instr = panel_sum_sq(n3) * FP64_PER_MSUB_INT[2]
         out["lu_dd_n4096"]["plain_gemm_fp64_frac"] = instr / (pg * 1e-3) / peak_fp64
     del Au
     # large DD LU, n = 8192, split update (the plain update would take ~11 s)
@@ -728,7 +733,7 @@ def headline_rooflines(prof, reps, n_list, stats, peak_fp64, peaks, sm_max_mhz):
     (reps calls): the batched substitution and the panel phase against the
     FP64 pipe, the trailing split update against the bf16 tensor pipe, the
     exact residual in exact products per second.  Work per unit:
-    substitution n^2 multiword multiply-subtracts per solve (FP64_PER_MSUB
+    substitution n^2 multiword multiply-subtracts per solve (FP64_PER_MSUB_INT
     FP64 instructions each); split update SPLIT_TILE_FLOPS bf16 flops per
     128 x 16 tile; residual n^2 * 4 * 8 word products per evaluation."""
     ceiling = FP64_LANES_PER_CLK * sm_max_mhz * 1e6 if sm_max_mhz else None
@@ -736,14 +741,14 @@ def headline_rooflines(prof, reps, n_list, stats, peak_fp64, peaks, sm_max_mhz):
     solves = sum((1 + int(stats[s, 0])) * n_list[s] ** 2 for s in range(len(n_list)))
     t = prof["batch_solve"][0] / reps
     if t > 0:
-        a = solves * FP64_PER_MSUB[2] / (t * 1e-3)
+        a = solves * FP64_PER_MSUB_INT[2] / (t * 1e-3)
         out.append({"kernel": "k_solve_batched<DD>", "ms": t, "bound": "alu", "pipe": "fp64",
                     "achieved": a / 1e12, "peak": peak_fp64 / 1e12, "unit": "T FP64 instr/s",
                     "frac": a / peak_fp64, "peak_source": "measured: mw_peak_fp64 in this run",
                     "frac_of_fp64_issue_ceiling": a / ceiling if ceiling else None,
                     "traffic": (SOLVE_BATCHED_TRAFFIC_PER_MSUB * solves / max(prof["batch_solve"][1] / reps, 1)
                                 if SOLVE_BATCHED_TRAFFIC_PER_MSUB else None),
-                    "algorithmic_per_launch": solves * FP64_PER_MSUB[2] / max(prof["batch_solve"][1] / reps, 1),
+                    "algorithmic_per_launch": solves * FP64_PER_MSUB_INT[2] / max(prof["batch_solve"][1] / reps, 1),
                     "unit_of_work": "n^2 DD multiply-subtracts per system and solve"})
     t = prof["gemm_split"][0] / reps
     if t > 0:
@@ -758,7 +763,7 @@ def headline_rooflines(prof, reps, n_list, stats, peak_fp64, peaks, sm_max_mhz):
     t = prof["panel"][0] / reps
     if t > 0:
         pm = split_panel_fp64_msubs(n_list)
-        a = pm * FP64_PER_MSUB[2] / (t * 1e-3)
+        a = pm * FP64_PER_MSUB_INT[2] / (t * 1e-3)
         out.append({"kernel": "panel phase on the FP64 pipe (k_bpanel 8-column leaves, k_btrsm_sub)", "ms": t,
                     "bound": "alu", "pipe": "fp64", "achieved": a / 1e12, "peak": peak_fp64 / 1e12,
                     "unit": "T FP64 instr/s", "frac": a / peak_fp64,
