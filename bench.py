@@ -75,10 +75,10 @@ GEMM_TD_TRAFFIC_PER_LAUNCH = 40.40e6
 # DRAM bytes per multiword multiply-subtract of the batched substitution:
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_solve_batched<DD>
 # launch (the second solve of the 152-system mixed batch, n <= 1024, all 152
-# systems running: 1031.9 + 4.4 MB) over its sum of n^2 (59.08 M); the
+# systems running: 1033.9 + 3.9 MB) over its sum of n^2 (59.08 M); the
 # algorithmic figure is 16 bytes (each DD entry of L and U read once).  Must
 # be re-measured whenever k_solve_batched changes.
-SOLVE_BATCHED_TRAFFIC_PER_MSUB = 1036.3e6 / 59.08e6
+SOLVE_BATCHED_TRAFFIC_PER_MSUB = 1037.8e6 / 59.08e6
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -896,10 +896,12 @@ def main():
 
     # ---- end to end through the public API with host buffers -------------
     # Every step copies its inputs (A, b) from pinned host memory and reads x
-    # and the per-system statistics back.  Two input buffers, each with its
-    # own captured graph, let step k+1's host-to-device copy run on a copy
-    # stream while step k computes; the copy into a buffer waits until the
-    # step that last read it has finished.
+    # and the per-system statistics back.  Two schedules are timed and the
+    # faster is reported (both are recorded): "sequential", each step's copy,
+    # graph replay and read-back in order on one stream; "overlapped", two
+    # input buffers, each with its own captured graph, so that step k+1's
+    # host-to-device copy runs on a copy stream while step k computes (the
+    # copy into a buffer waits until the step that last read it finished).
     A_h = torch.from_numpy(A_np).pin_memory()
     b_h = torch.from_numpy(b_np).pin_memory()
     A2, b2 = torch.empty_like(A), torch.empty_like(b)
@@ -920,39 +922,69 @@ def main():
     bufs = [(A, b, x, st_buf, graph), (A2, b2, x2, st2, graph2)]
     x_h = [torch.empty_like(x, device="cpu").pin_memory() for _ in range(2)]
     s_h = [torch.empty((args.count, 4), dtype=torch.int64).pin_memory() for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    # each step's inputs go over in N_COPY chunks on as many copy streams, so
+    # that several copy engines share the host-to-device transfer
+    N_COPY = 8
+    copy_streams = [torch.cuda.Stream() for _ in range(N_COPY)]
+    ev_in = [[torch.cuda.Event() for _ in range(N_COPY)] for _ in range(2)]
     ev_used = [torch.cuda.Event(), torch.cuda.Event()]
     e2e_steps = max(4, args.steps // 2)
+    A_hf, b_hf = A_h.reshape(-1), b_h.reshape(-1)
+    cut = [A_hf.numel() * c // N_COPY for c in range(N_COPY + 1)]
 
-    def load(k):
+    def load(k, after=None):
+        """Copy step k's inputs into buffer k % 2; ev_in[k % 2] marks them done."""
         i = k % 2
-        with torch.cuda.stream(copy_stream):
-            if k >= 2:
-                copy_stream.wait_event(ev_used[i])
-            bufs[i][0].copy_(A_h, non_blocking=True)
-            bufs[i][1].copy_(b_h, non_blocking=True)
-            ev_in[i].record(copy_stream)
+        Af = bufs[i][0].reshape(-1)
+        for c, cs in enumerate(copy_streams):
+            with torch.cuda.stream(cs):
+                if after is not None:
+                    cs.wait_event(after)
+                if k >= 2:
+                    cs.wait_event(ev_used[i])
+                Af[cut[c]:cut[c + 1]].copy_(A_hf[cut[c]:cut[c + 1]], non_blocking=True)
+                if c == 0:
+                    bufs[i][1].reshape(-1).copy_(b_hf, non_blocking=True)
+                ev_in[i][c].record(cs)
 
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    copy_stream.wait_event(f0)
-    load(0)
+    load(0, after=f0)
     for k in range(e2e_steps):
         i = k % 2
         if k + 1 < e2e_steps:
             load(k + 1)
-        stream.wait_event(ev_in[i])
+        for ev in ev_in[i]:
+            stream.wait_event(ev)
         bufs[i][4].replay()
         ev_used[i].record(stream)
         x_h[i].copy_(bufs[i][2], non_blocking=True)
         s_h[i].copy_(bufs[i][3], non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    e2e_met = min(int(sum(batch_target_met(x_h[i].numpy(), n_list))) for i in range(2))
+    ovl_ms = f0.elapsed_time(f1) / e2e_steps
+    ovl_met = min(int(sum(batch_target_met(x_h[i].numpy(), n_list))) for i in range(2))
+    # sequential schedule on the first buffer set
+    torch.cuda.synchronize()
+    f0.record(stream)
+    for k in range(e2e_steps):
+        ev_used[0].record(stream)
+        load(0, after=ev_used[0])            # buffer 0, after the previous step
+        for ev in ev_in[0]:
+            stream.wait_event(ev)
+        graph.replay()
+        x_h[0].copy_(x, non_blocking=True)
+        s_h[0].copy_(st_buf, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = f0.elapsed_time(f1) / e2e_steps
+    seq_met = int(sum(batch_target_met(x_h[0].numpy(), n_list)))
+    if seq_ms <= ovl_ms:
+        e2e_sched, e2e_ms, e2e_met = "sequential", seq_ms, seq_met
+    else:
+        e2e_sched, e2e_ms, e2e_met = "overlapped", ovl_ms, ovl_met
     e2e_val = e2e_met / (e2e_ms * 1e-3) * world
     del A_h, A2, b2, x2, graph2
 
@@ -989,8 +1021,13 @@ def main():
         "e2e": {"value": e2e_val, "unit": "solves/s", "steps": e2e_steps, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(A_np.nbytes + b_np.nbytes),
                 "d2h_bytes_per_step": int(x.numel() * 8 + args.count * 4 * 8),
-                "overlap": "two input buffers and graphs: step k+1's host-to-device copy runs on a copy "
-                           "stream during step k"},
+                "schedule": e2e_sched,
+                "ms_per_step_by_schedule": {"sequential": seq_ms, "overlapped": ovl_ms},
+                "copy_streams": N_COPY,
+                "schedules": {"sequential": "copy in (chunked over the copy streams), graph replay, read "
+                                            "back, each step after the previous one",
+                              "overlapped": "two input buffers and graphs: step k+1's host-to-device copy "
+                                            "runs on the copy streams during step k"}},
     }
     if rank == 0 and world == 1 and not args.no_extras:
         ex = {"comparators": batch_comparators(A, b, A_np, b_np, n_list, peak_fp64, sm_max)}
