@@ -77,7 +77,13 @@ __device__ __forceinline__ bool pack(u64 r, int E, u64 sg, double& out) {
 __device__ __forceinline__ bool sum_ordered(u64 A, u64 B, double& s, double& e) {
   const u64 ua = A & ~kSign, ub = B & ~kSign;
   const int ea = (int)(ua >> 52), eb = (int)(ub >> 52);
-  if (eb == 0 || ea == 2047) return false;   // b zero or subnormal; a infinite or NaN
+  if (ea == 2047) return false;              // a infinite or NaN
+  if (ub == 0ull) {                          // b = +-0: s = a + b, e = +0 (both zero: -0 only if both are)
+    s = dbl(ua ? A : (A & B & kSign));
+    e = 0.0;
+    return true;
+  }
+  if (eb == 0) return false;                 // b subnormal
   const int d = ea - eb;
   if (d > 54) {                              // |b| < ulp(a) / 4: RN(a + b) = a, exactly b left over
     s = dbl(A);

@@ -43,7 +43,11 @@ def sum_ordered(A, B):
     """(s, e) for bit patterns with |a| >= |b|, or None (fall back)."""
     ua, ub = A & ~SIGN, B & ~SIGN
     ea, eb = ua >> 52, ub >> 52
-    if eb == 0 or ea == 2047:
+    if ea == 2047:
+        return None
+    if ub == 0:
+        return dbl(A if ua else (A & B & SIGN)), 0.0
+    if eb == 0:
         return None
     d = ea - eb
     if d > 54:
@@ -102,8 +106,10 @@ def _cases(rng, cnt):
         elif k == 3:                                    # halfway cases, also below a power of two
             a = math.copysign(2.0 ** rng.randrange(-20, 20), rng.choice([-1, 1])) if rng.random() < 0.5 else a
             b = rng.choice([-1, 1]) * math.ulp(a) * rng.choice([0.25, 0.5, 0.75, 1.0, 1.5])
-        elif k == 4:                                    # zeros and exact cancellation
+        elif k == 4:                                    # zeros (either side, both signs) and exact cancellation
             b = rng.choice([0.0, -0.0, -a])
+            if rng.random() < 0.3:
+                a = rng.choice([0.0, -0.0])
         elif k == 5:                                    # subnormal words
             a = rng.choice([5e-324, -5e-324, 2.2250738585072014e-308, 1e-310])
             b = rng.choice([-5e-324, 3e-310, -2.2250738585072014e-308])
