@@ -37,6 +37,8 @@
  * enqueues on `stream` afterwards (inside a stream capture too: the fork
  * and join become graph edges).  The first such call on a device must run
  * outside a capture; a captured call before it runs the serial schedule.
+ * That stream does not survive cudaDeviceReset: after a reset, set
+ * MW_TUNE_LOOKAHEAD to 0 or the LU calls return MW_ECUDA.
  *
  * Return codes: MW_OK (0); a negative value -i when argument i (1-based) is
  * invalid; MW_ECUDA when a CUDA call failed (mw_last_cuda_error gives the
