@@ -68,10 +68,12 @@ FP64_LANES_PER_CLK = 304
 SPLIT_TILE_FLOPS = 120 * 2 * 128 * 16 * 64
 
 # DRAM bytes (read + write) per launch of the TD plain trailing update in the
-# n = 2048 single-system workload: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum over the 124 launches of one bench run, averaged per
-# launch.  Must be re-measured whenever k_gemm_plain changes.
-GEMM_TD_TRAFFIC_PER_LAUNCH = 40.40e6
+# n = 2048 single-system workload with the packaged tuning (panel 32 x 16
+# rows; with the look-ahead, two update launches per panel step): ncu
+# dram__bytes_read.sum + dram__bytes_write.sum over the LU's 125 launches
+# (2266.1 + 234.5 MB), averaged per launch.  Must be re-measured whenever
+# k_gemm_plain changes.
+GEMM_TD_TRAFFIC_PER_LAUNCH = 20.0e6
 # DRAM bytes per multiword multiply-subtract of the batched substitution:
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_solve_batched<DD>
 # launch (the second solve of the 152-system mixed batch, n <= 1024, all 152
