@@ -4,8 +4,8 @@ Full-size plain factorisations: the first columns against the oracle's
 first elimination steps (first_columns_bitwise).
 
 Results of the split (tensor-core) LU, which is not bitwise equal to the
-oracle (only the plain path is), follow the survey's parity rules for the
-split path:
+oracle (only the plain path is), follow these parity rules for the split
+path:
 
 * Pivots: identical to the reference sequence (the oracle's, or the plain
   GPU path's, which the parity tests pin bitwise to the oracle) up to the
