@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmwlu.so")
-SOURCES = ["lu.cu", "solve.cu", "residual.cu", "ozaki.cu", "capi.cu", "profile.cu", "noalloc.cu", "batched.cu",
+SOURCES = ["lu.cu", "gemm_plain.cu", "solve.cu", "residual.cu", "ozaki.cu", "capi.cu", "profile.cu", "noalloc.cu", "batched.cu",
            "strassen.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",

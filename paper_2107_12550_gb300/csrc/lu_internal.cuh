@@ -121,6 +121,11 @@ size_t lu_workspace_bytes(int update, int64_t n);
 int split_gemm_sub_dd(int64_t m, int64_t N, double* C, int64_t ldc, int64_t planeC, const double* L,
                       int64_t ldl, int64_t planeL, const double* U, int64_t ldu, int64_t planeU,
                       char* ws, size_t ws_bytes, cudaStream_t s, bool plus = false);
+// the plain trailing update A22 -= L21 U12 in place (gemm_plain.cu): rows
+// [row0, row0 + m) of columns [col0, col0 + N), inner columns [k0, k0 + nb)
+template <int W>
+int launch_gemm_plain(double* A, int64_t lda, int64_t plane, int64_t row0, int64_t m,
+                      int64_t col0, int64_t N, int64_t k0, int nb, cudaStream_t s);
 // C -= L U (add: C += L U) in plain multiword arithmetic, any K
 template <int W>
 int launch_gemm_plain_ptr(int64_t m, int64_t N, int K, double* C, int64_t ldc, int64_t planeC,
