@@ -1003,7 +1003,6 @@ struct InnerSpec {
 };
 constexpr int kNumInner = 7;
 constexpr InnerSpec kInner[kNumInner] = {{0, 8}, {16, 8}, {0, 16}, {32, 8}, {48, 8}, {32, 16}, {0, 32}};
-constexpr int kPanelLeafDefault = 8;   // MW_TUNE_BATCH_SPLIT_LEAF
 
 // tiles of an m x N product for every active system of one step
 static void add_geom_step(GeomPlanHost& g, const BatchPlanHost& p, int act, bool split, int bm, int bn,
