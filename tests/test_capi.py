@@ -122,3 +122,12 @@ def test_status_and_wait_limit_arguments(lib):
     prev = lib.mw_set_wait_limit(1000)
     assert prev == 0
     assert lib.mw_set_wait_limit(prev) == 1000
+
+
+def test_build_compiles_every_translation_unit():
+    """Every .cu file of the library is in the build's source list (a file
+    left out would leave its kernels' symbols undefined only at load time)."""
+    import os
+    from paper_2107_12550_gb300 import build as B
+    on_disk = sorted(f for f in os.listdir(B.CSRC) if f.endswith(".cu"))
+    assert sorted(B.SOURCES) == on_disk
