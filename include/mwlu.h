@@ -349,7 +349,8 @@ int mw_batch_plan_reset(void);
  *   op 0: z = x + y   1: z = x - y   2: z = x * y   3: z = x / y
  *   op 4: z plane 0 = sign(|x| - |y|) in the pivot order (-1, 0, +1),
  *         other planes 0.
- * x, y, z: device, prec planes of cnt doubles.  Asynchronous on `stream`.
+ * x, y, z: device, prec planes of cnt doubles, 0 <= cnt <= 256 (2^31 - 1)
+ * (-3 otherwise, on the host).  Asynchronous on `stream`.
  * Returns MW_OK, -i or MW_ECUDA.
  */
 int mw_arith(int op, int prec, int64_t cnt, const double* x, const double* y, double* z,

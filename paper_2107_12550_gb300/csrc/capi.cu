@@ -324,7 +324,8 @@ extern "C" int mw_arith(int op, int prec, int64_t cnt, const double* x, const do
                         void* stream) {
   if (op < 0 || op > 4) return -1;
   if (!prec_ok(prec)) return -2;
-  if (cnt < 0) return -3;
+  // one thread per element; the grid's x extent stops at 2^31 - 1 blocks
+  if (cnt < 0 || cnt > 256 * (int64_t)INT32_MAX) return -3;
   if (cnt > 0 && (!x)) return -4;
   if (cnt > 0 && (!y)) return -5;
   if (cnt > 0 && (!z)) return -6;

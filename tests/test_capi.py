@@ -111,6 +111,10 @@ def test_huge_orders_rejected_before_any_size_arithmetic(lib):
     stats = (ctypes.c_int64 * 4)()
     assert lib.mw_refine(big, 8, big, 2, 8, 2, 3, 0, 200, 5, 1, 0.0, 0.0, 8, 8, stats, 8, 1 << 30, None) == -1
     assert lib.mw_gemm_sub(2, 0, big, 4, 4, 8, big, 8, big, 8, 4, None, 0, None) == -3
+    # element counts whose grid would not fit the launch's x extent
+    assert lib.mw_arith(0, 2, big, 8, 8, 8, None) == -3
+    assert lib.mw_arith(0, 2, 256 * (2**31 - 1) + 1, 8, 8, 8, None) == -3
+    assert lib.mw_arith(0, 2, 2**63 - 1, 8, 8, 8, None) == -3
 
 
 def test_status_and_wait_limit_arguments(lib):
