@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kPanelThreads)
 k_panel(double* __restrict__ A, int64_t lda, int64_t plane, int64_t n, int64_t k0, int nb,
         int64_t* __restrict__ piv, int64_t* __restrict__ info, char* __restrict__ ws,
         unsigned long long spin_limit) {
-  GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + kWsBarrier);
+  GridAbort* bar = reinterpret_cast<GridAbort*>(ws + kWsAbort);
   DeviceStatus* status = reinterpret_cast<DeviceStatus*>(ws + kWsStatus);
 
   const int G = gridDim.x;

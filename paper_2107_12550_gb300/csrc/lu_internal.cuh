@@ -16,12 +16,12 @@ constexpr int kDefaultNb = 64;          // panel width of the blocked LU
 constexpr int kMaxNb = 128;
 constexpr size_t kPanelResidentMax = 200 * 1024;   // shared memory for panel rows kept resident
 
-// LU work buffer: [barrier | status | panel candidates | split-update scratch]
+// LU work buffer: [abort word | status | panel candidates | split-update scratch]
 // The candidate area holds, for two column parities, one record per CTA
 // (a ready tag, the candidate value, its row index and a copy of the whole
 // candidate row of the panel) and a copy of the old row k.  It is cleared at
 // the start of every factorisation.
-constexpr size_t kWsBarrier = 0;
+constexpr size_t kWsAbort = 0;
 constexpr size_t kWsStatus = 64;
 constexpr size_t kWsCand = 256;
 constexpr size_t kCandStride = 8 * (1 + 4 + 1 + 4 * kMaxNb);         // one record, in bytes

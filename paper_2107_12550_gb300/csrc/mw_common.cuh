@@ -15,15 +15,13 @@ struct DeviceStatus {
   unsigned int where;       // which wait (kernel-specific tag)
 };
 
-// Software grid barrier for cooperative launches.  All CTAs of the grid are
-// co-resident (the launch is cooperative), so every wait ends; still, each
-// wait spins at most kSpinLimit times, after which it records the tag in
-// `status`, sets `abort` and returns false so that the kernel can leave.
-struct GridBarrier {
-  unsigned int count;
-  unsigned int generation;
+// The abort word shared by the CTAs of one cooperative launch.  Each of
+// their waits spins at most a bounded number of times; a CTA whose wait
+// gives up records the wait's tag in `status` and sets `abort`, and the
+// waits of the other CTAs see it and leave as well.
+struct GridAbort {
   unsigned int abort;
-  unsigned int pad;
+  unsigned int pad[3];
 };
 
 constexpr unsigned long long kSpinLimit = 1ull << 26;  // ~seconds at worst
@@ -51,44 +49,6 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// Returns true when every CTA arrived; false if the wait gave up (or another
-// CTA gave up earlier).  Must be called by all threads of every CTA.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DeviceStatus* status, unsigned int tag) {
-  __shared__ int ok_shared;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
-    __threadfence();
-    const unsigned int gen = ld_acquire_u32(&bar->generation);
-    if (ld_acquire_u32(&bar->abort)) {
-      ok = 0;
-    } else if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->generation, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (ld_acquire_u32(&bar->generation) == gen) {
-        if (ld_acquire_u32(&bar->abort) || ++spins > kSpinLimit) {
-          atomicExch(&bar->abort, 1u);
-          if (status) {
-            atomicExch(&status->timeout, 1u);
-            atomicExch(&status->where, tag);
-          }
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    ok_shared = ok;
-  }
-  __syncthreads();
-  return ok_shared != 0;
 }
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? MW_OK : MW_ECUDA; }
