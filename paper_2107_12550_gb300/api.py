@@ -39,9 +39,39 @@ def _check_mat(A: torch.Tensor, name: str):
         raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape (w, n, lda)")
 
 
-def _check_vec(v: torch.Tensor, name: str):
-    if not (v.is_cuda and v.dtype == torch.float64 and v.dim() == 2 and v.is_contiguous()):
-        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape (w, n)")
+def _check_vec(v: torch.Tensor, name: str, n: Optional[int] = None):
+    if not (v.is_cuda and v.dtype == torch.float64 and v.dim() == 2 and v.is_contiguous()
+            and (n is None or v.shape[1] == n)):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape (w, n)"
+                         + ("" if n is None else f" with n = {n}"))
+
+
+# Every tensor below reaches the library as a raw device address with no
+# extent attached, so the binding checks each one before any allocation or
+# library call: a host tensor, another GPU's, the wrong element type or too
+# few elements would otherwise become an out-of-bounds device access.
+
+def _check_dev(t: torch.Tensor, name: str, device, dtype=torch.float64, numel: int = 0):
+    """t: a contiguous CUDA tensor of `dtype` on `device` with at least
+    `numel` elements."""
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() >= numel
+            and (device is None or t.device == device)):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor on {device} "
+                         f"with at least {numel} elements")
+
+
+def _same_device(device, *named):
+    for t, name in named:
+        if t.device != device:
+            raise ValueError(f"{name} is on {t.device}, the operands on {device}")
+
+
+def _work_bytes(work: torch.Tensor, device) -> int:
+    """A caller's work buffer (any element type): contiguous, on `device`;
+    its size in bytes (the library checks it against what the call needs)."""
+    if not (work.is_cuda and work.is_contiguous() and (device is None or work.device == device)):
+        raise ValueError(f"work must be a contiguous CUDA tensor on {device}")
+    return work.numel() * work.element_size()
 
 
 def workspace(op: int, prec: int, update: int, n: int, device=None) -> torch.Tensor:
@@ -58,6 +88,8 @@ def ludecomp(A: torch.Tensor, prec="dd", update="plain", *, work: Optional[torch
     w = _prec(prec)
     u = UPDATE[update]
     n, lda = A.shape[1], A.shape[2]
+    if work is not None:
+        _work_bytes(work, A.device)
     if inplace:
         if A.shape[0] != w:
             raise ValueError("in-place factorisation needs exactly `prec` planes")
@@ -71,7 +103,7 @@ def ludecomp(A: torch.Tensor, prec="dd", update="plain", *, work: Optional[torch
     if work is None:
         work = workspace(L.MW_OP_LUDECOMP, w, u, n, A.device)
     L.check("mw_ludecomp", L.lib().mw_ludecomp(w, u, n, _ptr(LU), lda, _ptr(piv), _ptr(info),
-                                               _ptr(work), work.numel(), _stream(stream)))
+                                               _ptr(work), _work_bytes(work, A.device), _stream(stream)))
     return LU, piv[:n], info
 
 
@@ -82,7 +114,15 @@ def solve(LU: torch.Tensor, piv: torch.Tensor, b: torch.Tensor, prec=None, *,
     _check_mat(LU, "LU")
     w = _prec(prec) if prec is not None else LU.shape[0]
     n, lda = LU.shape[1], LU.shape[2]
-    _check_vec(b, "b")
+    if LU.shape[0] < w:
+        raise ValueError("LU must hold at least `prec` planes")
+    _check_dev(piv, "piv", LU.device, torch.int64, n)
+    _check_vec(b, "b", n)
+    _same_device(LU.device, (b, "b"))
+    if out is not None:
+        _check_dev(out, "out", LU.device, numel=w * n)
+    if work is not None:
+        _work_bytes(work, LU.device)
     if b.shape[0] != w:
         bb = torch.zeros((w, n), dtype=torch.float64, device=LU.device)
         k = min(w, b.shape[0])
@@ -92,7 +132,7 @@ def solve(LU: torch.Tensor, piv: torch.Tensor, b: torch.Tensor, prec=None, *,
     if work is None:
         work = workspace(L.MW_OP_SOLVE, w, 0, n, LU.device)
     L.check("mw_solve", L.lib().mw_solve(w, n, _ptr(LU), lda, _ptr(piv), _ptr(b), _ptr(x),
-                                         _ptr(work), work.numel(), _stream(stream)))
+                                         _ptr(work), _work_bytes(work, LU.device), _stream(stream)))
     return x
 
 
@@ -100,9 +140,12 @@ def residual(A: torch.Tensor, b: torch.Tensor, x: torch.Tensor, r_words: int = 8
              out: Optional[torch.Tensor] = None):
     """r = b - A x exactly, rounded greedily to r_words words."""
     _check_mat(A, "A")
-    _check_vec(b, "b")
-    _check_vec(x, "x")
     n, lda = A.shape[1], A.shape[2]
+    _check_vec(b, "b", n)
+    _check_vec(x, "x", n)
+    _same_device(A.device, (b, "b"), (x, "x"))
+    if out is not None:
+        _check_dev(out, "out", A.device, numel=r_words * n)
     r = out if out is not None else torch.empty((r_words, n), dtype=torch.float64, device=A.device)
     L.check("mw_residual", L.lib().mw_residual(n, _ptr(A), lda, A.shape[0], _ptr(b), b.shape[0],
                                                _ptr(x), x.shape[0], _ptr(r), r_words, _stream(stream)))
@@ -129,17 +172,22 @@ def refine(A: torch.Tensor, b: torch.Tensor, inner_prec="td", target_bits: int =
     """Mixed precision iterative refinement (Listing 1).  Returns a
     RefineResult; x has x_words planes (8 = 424 bits)."""
     _check_mat(A, "A")
-    _check_vec(b, "b")
     w = _prec(inner_prec)
     u = UPDATE[update]
     n, lda = A.shape[1], A.shape[2]
+    _check_vec(b, "b", n)
+    _same_device(A.device, (b, "b"))
+    if out is not None:
+        _check_dev(out, "out", A.device, numel=x_words * n)
+    if work is not None:
+        _work_bytes(work, A.device)
     x = out if out is not None else torch.empty((x_words, n), dtype=torch.float64, device=A.device)
     if work is None:
         work = workspace(L.MW_OP_REFINE, w, u, n, A.device)
     stats = (ctypes.c_int64 * 4)()
     rc = L.lib().mw_refine(n, _ptr(A), lda, A.shape[0], _ptr(b), b.shape[0], w, u, target_bits,
                            max_iter, stop_mode, rtol, atol, _ptr(x), x_words, stats, _ptr(work),
-                           work.numel(), _stream(stream))
+                           _work_bytes(work, A.device), _stream(stream))
     L.check("mw_refine", rc, ok=(L.MW_OK, L.MW_ENOTCONV, L.MW_ESINGULAR))
     return RefineResult(x, rc, int(stats[0]), int(stats[1]), int(stats[2]))
 
@@ -147,15 +195,22 @@ def refine(A: torch.Tensor, b: torch.Tensor, inner_prec="td", target_bits: int =
 def _gemm(name: str, C, A, B, m, prec, update, work, stream):
     for t, nm in ((C, "C"), (A, "A"), (B, "B")):
         _check_mat(t, nm)
+    _same_device(C.device, (A, "A"), (B, "B"))
     w = _prec(prec) if prec is not None else C.shape[0]
     u = UPDATE[update]
     N, ldc = C.shape[1], C.shape[2]
     K, lda = A.shape[1], A.shape[2]
     ldb = B.shape[2]
+    if min(C.shape[0], A.shape[0], B.shape[0]) < w:
+        raise ValueError("C, A and B must hold at least `prec` planes each")
+    if B.shape[1] != N:
+        raise ValueError("B must have the N columns of C: shape (w, N, ldb)")
+    if work is not None:
+        _work_bytes(work, C.device)
     if work is None:
         work = workspace(L.MW_OP_GEMM, w, u, max(m, N), C.device)
     L.check(name, getattr(L.lib(), name)(w, u, m, N, K, _ptr(C), ldc, _ptr(A), lda, _ptr(B), ldb,
-                                         _ptr(work), work.numel(), _stream(stream)))
+                                         _ptr(work), _work_bytes(work, C.device), _stream(stream)))
     return C
 
 
@@ -187,6 +242,11 @@ def gemm_strassen(A: torch.Tensor, B: torch.Tensor, prec=None, update="plain", l
     n = A.shape[1]
     if B.shape[1] != n or A.shape[0] < w or B.shape[0] < w:
         raise ValueError("A and B must be n x n with at least `prec` planes each")
+    _same_device(A.device, (B, "B"))
+    if out is not None:
+        _same_device(A.device, (out, "out"))
+    if work is not None:
+        _work_bytes(work, A.device)
     if out is None:
         out = torch.empty((w, n, max(n, 1)), dtype=torch.float64, device=A.device)
     _check_mat(out, "out")
@@ -198,8 +258,8 @@ def gemm_strassen(A: torch.Tensor, B: torch.Tensor, prec=None, update="plain", l
                 L.lib().mw_gemm_strassen_workspace_size(w, u, levels, n, ctypes.byref(nbytes)))
         work = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=A.device)
     L.check("mw_gemm_strassen", L.lib().mw_gemm_strassen(w, u, levels, n, _ptr(A), A.shape[2], _ptr(B), B.shape[2],
-                                                         _ptr(out), out.shape[2], _ptr(work), work.numel(),
-                                                         _stream(stream)))
+                                                         _ptr(out), out.shape[2], _ptr(work),
+                                                         _work_bytes(work, A.device), _stream(stream)))
     return out
 
 
@@ -209,6 +269,9 @@ def gemm(A: torch.Tensor, B: torch.Tensor, m: int, prec=None, update="plain", *,
     _check_mat(A, "A")
     _check_mat(B, "B")
     w = _prec(prec) if prec is not None else A.shape[0]
+    if A.shape[0] < w or B.shape[0] < w:
+        raise ValueError("A and B must hold at least `prec` planes each")
+    _same_device(A.device, (B, "B"))
     C = torch.zeros((w, B.shape[1], max(m, 1)), dtype=torch.float64, device=A.device)
     return gemm_add(C, A, B, m, w, update, work=work, stream=stream)
 
@@ -273,6 +336,13 @@ def _n_host(n_list):
     return arr
 
 
+def _batch_extent(n_list):
+    """(sum of n, sum of n^2): the entries per word of the packed vectors and
+    matrices (the library rejects orders outside its range itself)."""
+    ns = [int(v) for v in n_list]
+    return sum(ns), sum(v * v for v in ns)
+
+
 def batch_workspace(op: int, prec: int, n_list, device=None) -> torch.Tensor:
     out = ctypes.c_size_t(0)
     L.check("mw_batch_workspace_size",
@@ -283,6 +353,10 @@ def batch_workspace(op: int, prec: int, n_list, device=None) -> torch.Tensor:
 def ludecomp_batched(A: torch.Tensor, n_list, prec="dd", *, work=None, stream=None, inplace=False):
     """Batched LU (packed layout, `prec` words).  Returns (LU, piv, info)."""
     w = _prec(prec)
+    _, sum_n2 = _batch_extent(n_list)
+    _check_dev(A, "A", None, numel=w * sum_n2)
+    if work is not None:
+        _work_bytes(work, A.device)
     LU = A if inplace else A.clone()
     total_n = int(sum(n_list))
     piv = torch.empty(max(total_n, 1), dtype=torch.int64, device=A.device)
@@ -290,20 +364,30 @@ def ludecomp_batched(A: torch.Tensor, n_list, prec="dd", *, work=None, stream=No
     if work is None:
         work = batch_workspace(L.MW_OP_LUDECOMP, w, n_list, A.device)
     L.check("mw_ludecomp_batched", L.lib().mw_ludecomp_batched(
-        w, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(info), _ptr(work), work.numel(),
-        _stream(stream)))
+        w, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(info), _ptr(work),
+        _work_bytes(work, A.device), _stream(stream)))
     return LU, piv, info
 
 
 def solve_batched(LU: torch.Tensor, piv: torch.Tensor, b: torch.Tensor, n_list, prec="dd", *, work=None,
                   out=None, stream=None):
+    """Batched substitution: x (`prec` words per entry, packed like b) from
+    the factors and pivots of ludecomp_batched or ludecomp_batched_blocked."""
     w = _prec(prec)
+    sum_n, sum_n2 = _batch_extent(n_list)
+    _check_dev(LU, "LU", None, numel=w * sum_n2)
+    _check_dev(piv, "piv", LU.device, torch.int64, sum_n)
+    _check_dev(b, "b", LU.device, numel=w * sum_n)
+    if out is not None:
+        _check_dev(out, "out", LU.device, numel=w * sum_n)
+    if work is not None:
+        _work_bytes(work, LU.device)
     x = out if out is not None else torch.empty_like(b)
     if work is None:
         work = batch_workspace(L.MW_OP_SOLVE, w, n_list, LU.device)
     L.check("mw_solve_batched", L.lib().mw_solve_batched(
-        w, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(b), _ptr(x), _ptr(work), work.numel(),
-        _stream(stream)))
+        w, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(b), _ptr(x), _ptr(work),
+        _work_bytes(work, LU.device), _stream(stream)))
     return x
 
 
@@ -313,15 +397,27 @@ def refine_batched(A: torch.Tensor, a_words: int, b: torch.Tensor, b_words: int,
     """Batched refinement; returns (x, stats) with stats an int64 tensor
     (count, 4): corrections, residuals, LU info, status."""
     w = _prec(inner_prec)
-    total_n = int(sum(n_list))
+    total_n, sum_n2 = _batch_extent(n_list)
+    _check_batch_refine(A, a_words, b, b_words, x_words, total_n, sum_n2, out, work)
     x = out if out is not None else torch.empty(x_words * total_n, dtype=torch.float64, device=A.device)
     stats = torch.zeros((len(n_list), 4), dtype=torch.int64, device=A.device)
     if work is None:
         work = batch_workspace(L.MW_OP_REFINE, w, n_list, A.device)
     L.check("mw_refine_batched", L.lib().mw_refine_batched(
         len(n_list), _n_host(n_list), _ptr(A), a_words, _ptr(b), b_words, w, target_bits, max_iter, _ptr(x),
-        x_words, _ptr(stats), _ptr(work), work.numel(), _stream(stream)))
+        x_words, _ptr(stats), _ptr(work), _work_bytes(work, A.device), _stream(stream)))
     return x, stats
+
+
+def _check_batch_refine(A, a_words, b, b_words, x_words, total_n, sum_n2, out, work):
+    if min(a_words, b_words, x_words) < 1:
+        raise ValueError("a_words, b_words and x_words must be at least 1")
+    _check_dev(A, "A", None, numel=a_words * sum_n2)
+    _check_dev(b, "b", A.device, numel=b_words * total_n)
+    if out is not None:
+        _check_dev(out, "out", A.device, numel=x_words * total_n)
+    if work is not None:
+        _work_bytes(work, A.device)
 
 
 def _update(update) -> int:
@@ -348,6 +444,10 @@ def ludecomp_batched_blocked(A: torch.Tensor, n_list, prec="dd", update="plain",
     Returns (LU, piv, info)."""
     w = _prec(prec)
     u = _update(update)
+    _, sum_n2 = _batch_extent(n_list)
+    _check_dev(A, "A", None, numel=w * sum_n2)
+    if work is not None:
+        _work_bytes(work, A.device)
     LU = A if inplace else A.clone()
     total_n = int(sum(n_list))
     piv = torch.empty(max(total_n, 1), dtype=torch.int64, device=A.device)
@@ -355,8 +455,8 @@ def ludecomp_batched_blocked(A: torch.Tensor, n_list, prec="dd", update="plain",
     if work is None:
         work = batch_blocked_workspace(L.MW_OP_LUDECOMP, w, u, n_list, A.device)
     L.check("mw_ludecomp_batched_blocked", L.lib().mw_ludecomp_batched_blocked(
-        w, u, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(info), _ptr(work), work.numel(),
-        _stream(stream)))
+        w, u, len(n_list), _n_host(n_list), _ptr(LU), _ptr(piv), _ptr(info), _ptr(work),
+        _work_bytes(work, A.device), _stream(stream)))
     return LU, piv, info
 
 
@@ -366,14 +466,15 @@ def refine_batched_blocked(A: torch.Tensor, a_words: int, b: torch.Tensor, b_wor
     """refine_batched with the inner LU factored by the blocked batched LU."""
     w = _prec(inner_prec)
     u = _update(update)
-    total_n = int(sum(n_list))
+    total_n, sum_n2 = _batch_extent(n_list)
+    _check_batch_refine(A, a_words, b, b_words, x_words, total_n, sum_n2, out, work)
     x = out if out is not None else torch.empty(x_words * total_n, dtype=torch.float64, device=A.device)
     stats = torch.zeros((len(n_list), 4), dtype=torch.int64, device=A.device)
     if work is None:
         work = batch_blocked_workspace(L.MW_OP_REFINE, w, u, n_list, A.device)
     L.check("mw_refine_batched_blocked", L.lib().mw_refine_batched_blocked(
         len(n_list), _n_host(n_list), _ptr(A), a_words, _ptr(b), b_words, w, u, target_bits, max_iter,
-        _ptr(x), x_words, _ptr(stats), _ptr(work), work.numel(), _stream(stream)))
+        _ptr(x), x_words, _ptr(stats), _ptr(work), _work_bytes(work, A.device), _stream(stream)))
     return x, stats
 
 
@@ -390,6 +491,9 @@ def arith(op: int, prec, x: torch.Tensor, y: torch.Tensor, *, stream=None) -> to
     w = _prec(prec)
     _check_vec(x, "x")
     _check_vec(y, "y")
+    if y.shape != x.shape or x.shape[0] < w:
+        raise ValueError("x and y must have the same shape (planes >= prec, cnt)")
+    _same_device(x.device, (y, "y"))
     z = torch.empty_like(x)
     L.check("mw_arith", L.lib().mw_arith(op, w, x.shape[1], _ptr(x), _ptr(y), _ptr(z), _stream(stream)))
     return z
@@ -405,6 +509,7 @@ def peak_fp64() -> float:
 def work_status(op: int, update, work: torch.Tensor, *, stream=None) -> int:
     """MW_OK or MW_ETIMEOUT for the last call that used this single-system
     work buffer (synchronises the stream; mw_work_status)."""
+    _work_bytes(work, None)
     return L.check("mw_work_status", L.lib().mw_work_status(op, UPDATE[update], _ptr(work), _stream(stream)),
                    ok=(L.MW_OK, L.MW_ETIMEOUT))
 
@@ -412,6 +517,7 @@ def work_status(op: int, update, work: torch.Tensor, *, stream=None) -> int:
 def batch_work_status(work: torch.Tensor, *, stream=None) -> int:
     """MW_OK or MW_ETIMEOUT for the last batched call that used this work
     buffer (synchronises the stream; mw_batch_work_status)."""
+    _work_bytes(work, None)
     return L.check("mw_batch_work_status", L.lib().mw_batch_work_status(_ptr(work), _stream(stream)),
                    ok=(L.MW_OK, L.MW_ETIMEOUT))
 
