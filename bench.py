@@ -44,7 +44,13 @@ BATCH = 512
 N_LO, N_HI = 64, 1024
 LOG10_KAPPA_LO, LOG10_KAPPA_HI = 4.0, 20.0
 A_WORDS = 4
-WORKLOAD = "mixed_batch_512_svd_n64-1024_kappa1e4-1e20_qd_stored_split_dd_inner_refine_to_2^-200"
+
+
+def workload_name(count: int) -> str:
+    return (f"mixed_batch_{count}_svd_n{N_LO}-{N_HI}_kappa1e{LOG10_KAPPA_LO:g}-1e{LOG10_KAPPA_HI:g}"
+            f"_qd_stored_split_dd_inner_refine_to_2^-{TARGET_BITS}")
+
+
 # the single-system comparator (plain TD LU)
 N = 2048
 LOG10_KAPPA = 10.0
@@ -314,7 +320,7 @@ def run_reference(args, world, rank):
             "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(secs) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "systems": args.count, "n_range": [N_LO, N_HI],
+            "config": {"workload": workload_name(args.count), "systems": args.count, "n_range": [N_LO, N_HI],
                        "log10_kappa_range": [LOG10_KAPPA_LO, LOG10_KAPPA_HI], "global_batch": args.count,
                        "seq_len": 0, "parallelism": "cpu-oracle", "inner": "dd", "target_bits": TARGET_BITS,
                        "l2": "inputs_larger_than_l2"},
@@ -1003,7 +1009,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "systems": args.count, "n_range": [N_LO, N_HI],
+        "config": {"workload": workload_name(args.count), "systems": args.count, "n_range": [N_LO, N_HI],
                    "log10_kappa_range": [LOG10_KAPPA_LO, LOG10_KAPPA_HI], "global_batch": args.count * world,
                    "seq_len": 0, "parallelism": f"replicas{world}", "inner": "dd", "lu_update": "split",
                    "a_words": A_WORDS, "b_words": X_WORDS, "x_words": X_WORDS, "target_bits": TARGET_BITS,
