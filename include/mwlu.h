@@ -44,8 +44,9 @@
  * invalid; MW_ECUDA when a CUDA call failed (mw_last_cuda_error gives the
  * cudaError_t); MW_ETIMEOUT when a bounded device wait gave up;
  * MW_ESINGULAR / MW_ENOTCONV as documented per call.  Inputs with NaN or
- * Inf give unspecified (but memory-safe) results.  Orders (and GEMM
- * dimensions) above 2^31 are rejected as invalid arguments.
+ * Inf give unspecified (but memory-safe) results.  Orders, leading
+ * dimensions and GEMM dimensions above 2^28 are rejected as invalid
+ * arguments, before any size is computed.
  *
  * Bounded waits.  Kernels whose threads wait for other threads (the
  * substitution's ready values, the panel's candidate records, the split

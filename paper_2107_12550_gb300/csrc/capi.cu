@@ -124,7 +124,7 @@ extern "C" int mw_ludecomp(int prec, int update, int64_t n, double* A, int64_t l
   if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
   if (n < 0 || n > mw::kMaxOrder) return -3;
   if (n > 0 && !A) return -4;
-  if (lda < (n > 1 ? n : 1)) return -5;
+  if (lda < (n > 1 ? n : 1) || lda > mw::kMaxOrder) return -5;
   if (n > 0 && !piv) return -6;
   if (!info) return -7;
   if (!work) return -8;
@@ -149,7 +149,7 @@ extern "C" int mw_solve(int prec, int64_t n, const double* LU, int64_t lda, cons
   if (!prec_ok(prec)) return -1;
   if (n < 0 || n > mw::kMaxOrder) return -2;
   if (n > 0 && !LU) return -3;
-  if (lda < (n > 1 ? n : 1)) return -4;
+  if (lda < (n > 1 ? n : 1) || lda > mw::kMaxOrder) return -4;
   if (n > 0 && !piv) return -5;
   if (n > 0 && !b) return -6;
   if (n > 0 && !x) return -7;
@@ -169,7 +169,7 @@ extern "C" int mw_residual(int64_t n, const double* A, int64_t lda, int a_words,
                            void* stream) {
   if (n < 0 || n > mw::kMaxOrder) return -1;
   if (n > 0 && !A) return -2;
-  if (lda < (n > 1 ? n : 1)) return -3;
+  if (lda < (n > 1 ? n : 1) || lda > mw::kMaxOrder) return -3;
   if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
   if (n > 0 && !b) return -5;
   if (b_words < 1 || b_words > MW_LONG_WORDS) return -6;
@@ -187,7 +187,7 @@ extern "C" int mw_refine(int64_t n, const double* A, int64_t lda, int a_words, c
                          int64_t* stats, void* work, size_t work_bytes, void* stream) {
   if (n < 0 || n > mw::kMaxOrder) return -1;
   if (n > 0 && !A) return -2;
-  if (lda < (n > 1 ? n : 1)) return -3;
+  if (lda < (n > 1 ? n : 1) || lda > mw::kMaxOrder) return -3;
   if (a_words < 1 || a_words > MW_LONG_WORDS) return -4;
   if (n > 0 && !b) return -5;
   if (b_words < 1 || b_words > MW_LONG_WORDS) return -6;
@@ -218,11 +218,11 @@ static int gemm_impl(int prec, int update, int64_t m, int64_t N, int64_t K, doub
   if (N < 0 || N > mw::kMaxOrder) return -4;
   if (K < 0 || K > mw::kMaxOrder) return -5;
   if (m > 0 && N > 0 && !C) return -6;
-  if (ldc < (m > 1 ? m : 1)) return -7;
+  if (ldc < (m > 1 ? m : 1) || ldc > mw::kMaxOrder) return -7;
   if (m > 0 && K > 0 && !A) return -8;
-  if (lda < (m > 1 ? m : 1)) return -9;
+  if (lda < (m > 1 ? m : 1) || lda > mw::kMaxOrder) return -9;
   if (K > 0 && N > 0 && !B) return -10;
-  if (ldb < (K > 1 ? K : 1)) return -11;
+  if (ldb < (K > 1 ? K : 1) || ldb > mw::kMaxOrder) return -11;
   const int64_t nmax = m > N ? m : N;
   const size_t need = 256 + (update == MW_UPDATE_SPLIT ? mw::split_workspace_bytes(nmax, mw::kDefaultNb) : 0);
   if (update == MW_UPDATE_SPLIT && !work) return -12;
@@ -263,7 +263,7 @@ static int strassen_check(int prec, int update, int levels, int64_t n) {
   if (!prec_ok(prec)) return -1;
   if (update != MW_UPDATE_PLAIN && update != MW_UPDATE_SPLIT) return -2;
   if (levels < 0 || levels > 8) return -3;
-  if (n < 0) return -4;
+  if (n < 0 || n > mw::kMaxOrder) return -4;
   if (n % ((int64_t)1 << levels) != 0) return MW_EUNSUPPORTED;
   if (update == MW_UPDATE_SPLIT && (prec != MW_DD || (n >> levels) % 64 != 0)) return MW_EUNSUPPORTED;
   return MW_OK;
@@ -283,11 +283,11 @@ extern "C" int mw_gemm_strassen(int prec, int update, int levels, int64_t n, con
   int rc = strassen_check(prec, update, levels, n);
   if (rc) return rc;
   if (n > 0 && !A) return -5;
-  if (lda < (n > 1 ? n : 1)) return -6;
+  if (lda < (n > 1 ? n : 1) || lda > mw::kMaxOrder) return -6;
   if (n > 0 && !B) return -7;
-  if (ldb < (n > 1 ? n : 1)) return -8;
+  if (ldb < (n > 1 ? n : 1) || ldb > mw::kMaxOrder) return -8;
   if (n > 0 && !C) return -9;
-  if (ldc < (n > 1 ? n : 1)) return -10;
+  if (ldc < (n > 1 ? n : 1) || ldc > mw::kMaxOrder) return -10;
   if (n > 0 && !work) return -11;
   if (work_bytes < mw::strassen_workspace_bytes(prec, update, levels, n)) return -12;
   if (n == 0) return MW_OK;

@@ -42,9 +42,14 @@ static_assert(kWsSwapPlan + sizeof(SwapPlan) <= kWsSplit, "swap plan inside the 
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Largest order any single-system entry point accepts; every size computed
-// from an order up to this bound fits in size_t without overflow.
-constexpr int64_t kMaxOrder = (int64_t)1 << 31;
+// Largest order (and leading dimension, and GEMM dimension) any
+// single-system entry point accepts.  Every size computed from values up to
+// this bound fits without overflow: plane strides ld * n <= 2^56 in int64,
+// the refinement's LU copy 8 * 4 * n^2 <= 2^61 bytes and Strassen's
+// temporaries (9 w (n/2)^2 doubles per level, summed) below 2^63 bytes in
+// size_t.  An n x n multiword matrix at this order would already hold 2^56
+// entries per word, far beyond any device.
+constexpr int64_t kMaxOrder = (int64_t)1 << 28;
 
 // tuning knobs (capi.cu): value of `param` (MW_TUNE_*) for precision prec
 int tune_get(int param, int prec);

@@ -61,7 +61,7 @@ extern "C" int mw_solve_noalloc(int prec, int64_t n, const double* LU, int64_t l
   if (n < 0 || n > kNoallocMaxOrder) return -2;                               // before any size arithmetic
   if (mw::solve_workspace_bytes(prec, n) > kNoallocScratchBytes) return -2;  // beyond the fixed scratch
   if (n > 0 && !LU) return -3;
-  if (lda < (n > 1 ? n : 1)) return -4;
+  if (lda < (n > 1 ? n : 1) || lda > mw::kMaxOrder) return -4;
   if (n > 0 && !piv) return -5;
   if (n > 0 && !b) return -6;
   if (n > 0 && !x) return -7;

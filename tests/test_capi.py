@@ -117,6 +117,36 @@ def test_huge_orders_rejected_before_any_size_arithmetic(lib):
     assert lib.mw_arith(0, 2, 2**63 - 1, 8, 8, 8, None) == -3
 
 
+def test_order_bound_keeps_every_size_exact(lib):
+    """Orders and leading dimensions are bounded by 2^28: just above it every
+    entry point rejects the call on the host; at it, the byte counts that
+    grow with n^2 (the refinement's LU copy, Strassen's temporaries) are
+    still exact, not wrapped around size_t."""
+    top = 1 << 28
+    out = ctypes.c_size_t(0)
+    assert lib.mw_workspace_size(L.MW_OP_REFINE, 4, 0, top + 1, ctypes.byref(out)) == -4
+    assert lib.mw_workspace_size(L.MW_OP_REFINE, 4, 0, top, ctypes.byref(out)) == 0
+    assert out.value >= 8 * 4 * top * top                  # the QD LU copy alone
+    for bad in (top + 2, 1 << 62):
+        assert lib.mw_gemm_strassen_workspace_size(4, 0, 1, bad, ctypes.byref(out)) == -4
+        assert lib.mw_gemm_strassen(4, 0, 1, bad, 8, bad, 8, bad, 8, bad, 8, 1 << 30, None) == -4
+    assert lib.mw_gemm_strassen_workspace_size(4, 0, 1, top, ctypes.byref(out)) == 0
+    assert out.value >= 8 * 9 * 4 * (top // 2) ** 2        # one level of temporaries
+    # leading dimensions above the bound, with small orders
+    ld = top + 1
+    stats = (ctypes.c_int64 * 4)()
+    assert lib.mw_ludecomp(2, 0, 8, 8, ld, 8, 8, 8, 1 << 30, None) == -5
+    assert lib.mw_solve(2, 8, 8, ld, 8, 8, 8, 8, 1 << 30, None) == -4
+    assert lib.mw_solve_noalloc(2, 8, 8, ld, 8, 8, 8, None) == -4
+    assert lib.mw_residual(8, 8, ld, 1, 8, 1, 8, 1, 8, 1, None) == -3
+    assert lib.mw_refine(8, 8, ld, 2, 8, 2, 3, 0, 200, 5, 1, 0.0, 0.0, 8, 8, stats, 8, 1 << 30, None) == -3
+    assert lib.mw_gemm_sub(2, 0, 8, 8, 8, 8, ld, 8, 8, 8, 8, None, 0, None) == -7
+    assert lib.mw_gemm_sub(2, 0, 8, 8, 8, 8, 8, 8, ld, 8, 8, None, 0, None) == -9
+    assert lib.mw_gemm_sub(2, 0, 8, 8, 8, 8, 8, 8, 8, 8, ld, None, 0, None) == -11
+    assert lib.mw_gemm_strassen(2, 0, 1, 64, 8, ld, 8, 64, 8, 64, 8, 1 << 30, None) == -6
+    assert lib.mw_gemm_strassen(2, 0, 1, 64, 8, 64, 8, 64, 8, ld, 8, 1 << 30, None) == -10
+
+
 def test_status_and_wait_limit_arguments(lib):
     assert lib.mw_work_status(7, 0, 8, None) == -1
     assert lib.mw_work_status(L.MW_OP_SOLVE, 5, 8, None) == -2
