@@ -150,6 +150,61 @@ def pin_stagnation_exit():
     return (st, corr, nres, info) == (2, 2, 2, 0) and x[0, 0] == 37 / 16 and not np.any(x[1:, 0])
 
 
+def _rel_bound(w, op):
+    """The relative error bounds the arithmetic is held to: DD multiply 5u^2
+    and divide 15u^2 (Joldes, Muller and Popescu 2017), TD/QD 4u^w."""
+    if w == 2:
+        return (5 if op == oracle.OP_MUL else 15) * U ** 2
+    return 4 * U ** w
+
+
+def pin_rel(op, w):
+    def f():
+        rng = np.random.default_rng(20 + w)
+        x, y = _rand_mw(rng, w, 200), _rand_mw(rng, w, 200)
+        z = oracle.arith(op, w, x, y)
+        for i in range(200):
+            a, b = X.words_to_frac(x[:, i]), X.words_to_frac(y[:, i])
+            ex = a * b if op == oracle.OP_MUL else a / b
+            if abs(X.words_to_frac(z[:, i]) - ex) > _rel_bound(w, op) * abs(ex):
+                return False
+        return True
+    return f
+
+
+def pin_cmpabs(w):
+    """The pivot order on |x| against the exact order, with near ties in the
+    last word, exact ties and random signs."""
+    def f():
+        rng = np.random.default_rng(30 + w)
+        x = _rand_mw(rng, w, 400)
+        y = x.copy()
+        y[w - 1] += np.where(rng.random(400) < 0.5, 1, -1) * np.abs(x[w - 1]) * 2.0 ** -10
+        flip = rng.random(400) < 0.5
+        y[:, flip] = -y[:, flip]
+        x[:, rng.random(400) < 0.5] *= -1
+        y[:, ::7] = x[:, ::7]
+        r = oracle.arith(oracle.OP_CMPABS, w, x, y)
+        for i in range(400):
+            a, b = abs(X.words_to_frac(x[:, i])), abs(X.words_to_frac(y[:, i]))
+            if r[i] != (a > b) - (a < b):
+                return False
+        return True
+    return f
+
+
+def pin_singular_info():
+    """A zero column at position 2 (0-based) of a 5 x 5 matrix: the first
+    exactly zero pivot is at step 3 in the 1-based count that info uses
+    (LAPACK getrf)."""
+    rng = np.random.default_rng(7)
+    A = np.zeros((2, 5, 5))
+    A[0] = rng.uniform(-1, 1, (5, 5))
+    A[:, 2, :] = 0.0
+    _, _, info = oracle.lu(2, A)
+    return info == 3
+
+
 MUTATIONS = [
     ("dd_mul drops the cross terms", "    cl3 = cl1 + cl2;\n", "    cl3 = cl1;\n", pin_dd_mul),
     ("dd_add wrong sign", "    c = sl + th;\n", "    c = sl - th;\n", pin_add(2)),
@@ -172,6 +227,20 @@ MUTATIONS = [
      pin_stagnation_exit),
     ("stagnation test starts a correction late", "if (corrections >= 2 && corr > 0.5 * prev)",
      "if (corrections >= 3 && corr > 0.5 * prev)", pin_stagnation_exit),
+    ("DD division drops its correction quotient", "    fast_two_sum(q0, q1, &z[0], &z[1]);\n",
+     "    fast_two_sum(q0, 0.0 * q1, &z[0], &z[1]);\n", pin_rel(oracle.OP_DIV, 2)),
+    ("DD division ignores the divisor's low word", "    pl = fma(y[1], q0, pl);", "    pl = fma(0.0 * y[1], q0, pl);",
+     pin_rel(oracle.OP_DIV, 2)),
+    ("TD multiplication drops x1*y1", "        c = x[1] * y[1];\n", "        c = 0.0 * x[1] * y[1];\n",
+     pin_rel(oracle.OP_MUL, 3)),
+    ("QD multiplication drops an order-2 product error", "        c = c + q11;\n", "        c = c + 0.0 * q11;\n",
+     pin_rel(oracle.OP_MUL, 4)),
+    ("long division's remainder loses the product errors", "        t[m++] = q[i - 1];\n",
+     "        t[m++] = 0.0 * q[i - 1];\n", pin_rel(oracle.OP_DIV, 3)),
+    ("magnitude order without the sign adjustment", "        double a = sx * x[c], b = sy * y[c];\n",
+     "        double a = x[c], b = y[c];\n", pin_cmpabs(2)),
+    ("zero pivot reported 0-based", "            if (*info == 0) *info = k + 1;\n",
+     "            if (*info == 0) *info = k;\n", pin_singular_info),
 ]
 
 
