@@ -205,6 +205,26 @@ def pin_singular_info():
     return info == 3
 
 
+def pin_eq2_first_exit():
+    """Stop mode 0 (Eq. (2)) stops at the first iterate that meets
+    ||r||_2 <= sqrt(n) rtol ||A||_F ||x||_2.  rtol is placed so that after one
+    correction ||r|| lies halfway (a factor 2 either side) between
+    rtol ||A|| ||x|| and sqrt(n) rtol ||A|| ||x|| (n = 16), from exact
+    residuals: the loop must stop after exactly one correction."""
+    import math
+    s = W.svd_system(16, 8.0, seed=4)
+    n = 16
+    _, x1, c1, _, _ = oracle.refine(s.A, s.b, 2, stop_mode=0, rtol=0.0, max_iter=1)
+    Af = X.mat_to_frac(s.A, n)
+    r = X.residual(Af, X.vec_to_frac(s.b), X.vec_to_frac(x1))
+    nr2 = sum(v * v for v in r)
+    nA2 = sum(a * a for row in Af for a in row)
+    nx2 = sum(v * v for v in X.vec_to_frac(x1))
+    ratio = math.sqrt(float(nr2 / (nA2 * nx2)))
+    st, x, corr, nres, info = oracle.refine(s.A, s.b, 2, stop_mode=0, rtol=ratio / 2)
+    return c1 == 1 and st == 0 and corr == 1
+
+
 MUTATIONS = [
     ("dd_mul drops the cross terms", "    cl3 = cl1 + cl2;\n", "    cl3 = cl1;\n", pin_dd_mul),
     ("dd_add wrong sign", "    c = sl + th;\n", "    c = sl - th;\n", pin_add(2)),
@@ -241,6 +261,10 @@ MUTATIONS = [
      "        double a = x[c], b = y[c];\n", pin_cmpabs(2)),
     ("zero pivot reported 0-based", "            if (*info == 0) *info = k + 1;\n",
      "            if (*info == 0) *info = k;\n", pin_singular_info),
+    ("Eq. (2) without its sqrt(n) factor", "            double rhs = sqrt((double)n) * rtol;\n",
+     "            double rhs = rtol;\n", pin_eq2_first_exit),
+    ("Eq. (2) without the norm of x", "            rhs = rhs * nx;\n", "            rhs = rhs * 1.0;\n",
+     pin_eq2_first_exit),
 ]
 
 
