@@ -81,6 +81,23 @@ def pin_lu_factors():
     return info == 0 and np.array_equal(got, ref) and np.all(LU[1] == 0)
 
 
+def pin_lu_pivoted_factors():
+    """A = P L U with |l_ij| <= 3/8 and small integer U: partial pivoting
+    must undo P, and with dyadic entries every operation is exact, so the
+    stored factors are exactly L (strictly lower part, in the pivoted row
+    order) and U, with zero low words.  This needs the row interchanges to
+    carry the multipliers already stored left of the pivot column."""
+    rng = np.random.default_rng(8)
+    n = 6
+    Lm = np.eye(n) + np.tril(rng.integers(-3, 4, (n, n)) / 8.0, -1)
+    Um = np.triu(rng.integers(-9, 10, (n, n)).astype(float), 1) + \
+        np.diag(rng.choice([-1, 1], n) * rng.integers(12, 20, n))
+    A = np.zeros((2, n, n))
+    A[0] = (Lm @ Um)[rng.permutation(n)].T
+    LU, piv, info = oracle.lu(2, A)
+    return info == 0 and np.array_equal(LU[0].T, np.tril(Lm, -1) + Um) and np.all(LU[1] == 0)
+
+
 def pin_residual():
     rng = np.random.default_rng(5)
     n = 5
@@ -265,6 +282,9 @@ MUTATIONS = [
      "            double rhs = rtol;\n", pin_eq2_first_exit),
     ("Eq. (2) without the norm of x", "            rhs = rhs * nx;\n", "            rhs = rhs * 1.0;\n",
      pin_eq2_first_exit),
+    ("row interchange skips the multipliers left of the pivot",
+     "        if (p != k) {\n            for (j = 0; j < n; ++j) {\n",
+     "        if (p != k) {\n            for (j = k; j < n; ++j) {\n", pin_lu_pivoted_factors),
 ]
 
 
