@@ -98,6 +98,24 @@ def pin_lu_pivoted_factors():
     return info == 0 and np.array_equal(LU[0].T, np.tril(Lm, -1) + Um) and np.all(LU[1] == 0)
 
 
+def pin_solve_exact():
+    """A = P L U with |l_ij| <= 3/8, small integer U with a power-of-two
+    diagonal, and an integer x*: every step of the substitution is exact
+    (the reciprocals 1/u_jj included), so x = x* with zero low words."""
+    rng = np.random.default_rng(9)
+    n = 6
+    Lm = np.eye(n) + np.tril(rng.integers(-3, 4, (n, n)) / 8.0, -1)
+    Um = np.triu(rng.integers(-9, 10, (n, n)).astype(float), 1) + \
+        np.diag(rng.choice([-16.0, -8.0, 8.0, 16.0], n))
+    xs = rng.integers(-5, 6, n).astype(float)
+    M = (Lm @ Um)[rng.permutation(n)]
+    A = np.zeros((2, n, n)); A[0] = M.T
+    b = np.zeros((2, n)); b[0] = M @ xs
+    LU, piv, info = oracle.lu(2, A)
+    x = oracle.solve(2, LU, piv, b)
+    return info == 0 and np.array_equal(x[0], xs) and np.all(x[1] == 0)
+
+
 def pin_residual():
     rng = np.random.default_rng(5)
     n = 5
@@ -285,6 +303,12 @@ MUTATIONS = [
     ("row interchange skips the multipliers left of the pivot",
      "        if (p != k) {\n            for (j = 0; j < n; ++j) {\n",
      "        if (p != k) {\n            for (j = k; j < n; ++j) {\n", pin_lu_pivoted_factors),
+    ("forward substitution also updates the diagonal row",
+     "        for (i = j + 1; i < n; ++i) {\n            double l[4], yi[4], prod[4], res[4];\n",
+     "        for (i = j; i < n; ++i) {\n            double l[4], yi[4], prod[4], res[4];\n", pin_solve_exact),
+    ("back substitution skips row 0",
+     "        for (i = 0; i < j; ++i) {\n            double u[4], yi[4], prod[4], res[4];\n",
+     "        for (i = 1; i < j; ++i) {\n            double u[4], yi[4], prod[4], res[4];\n", pin_solve_exact),
 ]
 
 
