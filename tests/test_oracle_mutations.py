@@ -132,6 +132,15 @@ def pin_rn_ties():
         oracle.exact_sum([1.0, 3 * 2.0 ** -53], 1)[0] == 1.0 + 2.0 ** -51
 
 
+def pin_rn_sticky():
+    """Above the halfway point by less than the last place's half: the bits
+    below the rounding bit decide, so 1 + 2^-53 + 2^-80 rounds up to
+    1 + 2^-52 (and its negative down), even though 1 is the even neighbour."""
+    up = oracle.exact_sum([1.0, 2.0 ** -53, 2.0 ** -80], 1)[0]
+    down = oracle.exact_sum([-1.0, -2.0 ** -53, -2.0 ** -80], 1)[0]
+    return up == 1.0 + 2.0 ** -52 and down == -(1.0 + 2.0 ** -52)
+
+
 def pin_solve_pivots():
     n = 5
     perm = [3, 0, 4, 1, 2]
@@ -309,6 +318,13 @@ MUTATIONS = [
     ("back substitution skips row 0",
      "        for (i = 0; i < j; ++i) {\n            double u[4], yi[4], prod[4], res[4];\n",
      "        for (i = 1; i < j; ++i) {\n            double u[4], yi[4], prod[4], res[4];\n", pin_solve_exact),
+    ("greedy rounding keeps the rounded word in the accumulator",
+     "        acc_add_u128(a, 1, (unsigned __int128)q, lsb);\n",
+     "        acc_add_u128(a, 1, (unsigned __int128)0, lsb);\n", pin_residual),
+    ("carries taken with an unsigned shift",
+     "        int64_t c = a->d[k] >> 32;  /* arithmetic shift = floor division */\n",
+     "        int64_t c = (int64_t)((uint64_t)a->d[k] >> 32);\n", pin_residual),
+    ("rounding ignores the sticky bits", "(acc_any_below(a, lsb - 1) || (q & 1u))", "((q & 1u))", pin_rn_sticky),
 ]
 
 
