@@ -56,6 +56,26 @@ def pin_twoprod():
                for x, y, pp, ee in zip(a, b, p, e))
 
 
+def pin_twosum():
+    """TwoSum is exact for any pair: s + e = a + b, with s = RN(a + b); the
+    pairs span exponent gaps in both orders."""
+    rng = np.random.default_rng(11)
+    a = rng.uniform(-1, 1, 500) * 2.0 ** rng.integers(-60, 60, 500)
+    b = rng.uniform(-1, 1, 500) * 2.0 ** rng.integers(-60, 60, 500)
+    s, e = oracle.eft(oracle.EFT_TWOSUM, a, b)
+    return all(Fraction(x) + Fraction(y) == Fraction(ss) + Fraction(ee) and ss == x + y
+               for x, y, ss, ee in zip(a, b, s, e))
+
+
+def pin_fasttwosum():
+    """FastTwoSum is exact when the exponent of a is at least that of b."""
+    rng = np.random.default_rng(12)
+    a = rng.uniform(1, 2, 500) * 2.0 ** rng.integers(0, 40, 500)
+    b = rng.uniform(-1, 1, 500)
+    s, e = oracle.eft(oracle.EFT_FASTTWOSUM, a, b)
+    return all(Fraction(x) + Fraction(y) == Fraction(ss) + Fraction(ee) for x, y, ss, ee in zip(a, b, s, e))
+
+
 def pin_lu_ties():
     A = np.zeros((2, 3, 3))
     M = [[1.0, 2.0, 3.0], [-1.0, 5.0, 1.0], [1.0, 1.0, 7.0]]
@@ -325,6 +345,8 @@ MUTATIONS = [
      "        int64_t c = a->d[k] >> 32;  /* arithmetic shift = floor division */\n",
      "        int64_t c = (int64_t)((uint64_t)a->d[k] >> 32);\n", pin_residual),
     ("rounding ignores the sticky bits", "(acc_any_below(a, lsb - 1) || (q & 1u))", "((q & 1u))", pin_rn_sticky),
+    ("TwoSum drops the error of b", "    *e = da + db;\n", "    *e = da;\n", pin_twosum),
+    ("FastTwoSum error with the wrong sign", "    *e = b - z;\n", "    *e = z - b;\n", pin_fasttwosum),
 ]
 
 
