@@ -1,5 +1,7 @@
 """Pins of the oracle's block matrix product and its Strassen form
 (Section 2: BNCmatmul and its Strassen variant) against exact results."""
+import os
+import types
 from fractions import Fraction
 
 import numpy as np
@@ -90,3 +92,41 @@ def test_product_accumulates_from_c0():
                 p = oracle.arith(oracle.OP_MUL, w, A[:, t, i][:, None], B[:, j, t][:, None])
                 c = oracle.arith(oracle.OP_ADD, w, c, p)
             assert np.array_equal(got[:, j, i], c[:, 0])
+
+
+def _strassen_variant(old: str, new: str):
+    """A copy of the Strassen oracle with one planted mistake, loaded as a
+    module of the oracle package."""
+    path = os.path.join(os.path.dirname(S.__file__), "strassen.py")
+    src = open(path).read()
+    assert src.count(old) == 1, old
+    mod = types.ModuleType("oracle.strassen_variant")
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(old, new), path + " (variant)", "exec"), mod.__dict__)
+    return mod
+
+
+def _exact_one_level(model):
+    n = 8
+    A = _int_mat(2, n, 51)
+    B = _int_mat(2, n, 52)
+    ref = (A[0].T.astype(np.int64) @ B[0].T.astype(np.int64)).T
+    return np.array_equal(model.strassen(2, A, B, 1)[0], ref.astype(float))
+
+
+STRASSEN_MUTATIONS = [
+    ("C12 and C21 written to each other's quadrant",
+     "    C[:, h:n, 0:h] = add(M3, M5)                        # C12 (block row 0, block column 1)\n"
+     "    C[:, 0:h, h:n] = add(M2, M4)                        # C21\n",
+     "    C[:, 0:h, h:n] = add(M3, M5)\n    C[:, h:n, 0:h] = add(M2, M4)\n"),
+    ("M6 with its difference reversed", "    M6 = rec(sub(A21, A11), add(B11, B12))\n",
+     "    M6 = rec(sub(A11, A21), add(B11, B12))\n"),
+    ("C11 without M7", "    C[:, 0:h, 0:h] = add(sub(add(M1, M4), M5), M7)      # C11\n",
+     "    C[:, 0:h, 0:h] = sub(add(M1, M4), M5)\n"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", STRASSEN_MUTATIONS, ids=[m[0] for m in STRASSEN_MUTATIONS])
+def test_planted_strassen_mistake_is_caught(name, old, new):
+    assert _exact_one_level(S), "the pin must pass on the unmodified oracle"
+    assert not _exact_one_level(_strassen_variant(old, new)), name
