@@ -2,13 +2,11 @@
 step, through the C ABI.  Each system's factors, pivots, solutions and
 refined solutions must be bitwise identical to the CPU oracle's
 single-system results (sampled systems at the full batch sizes)."""
-from fractions import Fraction
 
 import numpy as np
 import pytest
 
 import oracle
-from oracle import exact as X
 from paper_2107_12550_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu

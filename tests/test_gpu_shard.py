@@ -4,7 +4,6 @@ unsharded blocked batched refinement's, bitwise."""
 import os
 import socket
 
-import numpy as np
 import pytest
 
 from paper_2107_12550_gb300 import workloads as W

@@ -1,7 +1,6 @@
 """mpmath interoperability (host conversions): the greedy round-to-nearest
 word expansion against the oracle's, exact round trips, special values; on
 the GPU, refinement of an mpmath system to 2^-200."""
-import math
 import random
 from fractions import Fraction
 

@@ -2,7 +2,6 @@
 plausible error (a dropped term, a wrong sign, a wrong index or tie rule)
 and shows that a pin rejects it, while the unmodified oracle passes the
 same pin.  Mistakes are planted in the oracle only, on the CPU."""
-import os
 from fractions import Fraction
 
 import numpy as np

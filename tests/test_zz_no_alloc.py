@@ -4,7 +4,6 @@ pool owns the GPU, or hooks that must not touch an allocator), checked
 through the C ABI against mw_solve, which takes a caller-provided work
 buffer.  Two calls in a row must both match, since every call reuses the
 same fixed scratch.  Collected last on purpose."""
-import ctypes
 
 import numpy as np
 import pytest
