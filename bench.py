@@ -275,7 +275,9 @@ def oracle_batch_sample(systems, inner: int = 2):
     inner precision, exact residual, refinement to 2^-200) on whole systems,
     all host cores: (systems solved to 2^-200, seconds, threads)."""
     import oracle
-    threads = oracle.set_threads(0)
+    # every core the process may run on (torchrun sets OMP_NUM_THREADS=1 for
+    # its ranks, which would leave rank 0's oracle on one core)
+    threads = oracle.set_threads(len(os.sched_getaffinity(0)))
     met = 0
     t0 = time.perf_counter()
     for A, b in systems:

@@ -20,11 +20,17 @@ def _bench_module():
     return mod
 
 
+ARGS = ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0", "--count", "32"]
+
+
 def _run(extra_env=None):
     env = dict(os.environ)
     env.update(extra_env or {})
-    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                           "--count", "32"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return subprocess.run([sys.executable, *ARGS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def _lines(out):
+    return [json.loads(l) for l in out.splitlines() if l.startswith("{")]
 
 
 def test_reference_line_keeps_the_contract():
@@ -54,3 +60,22 @@ def test_reference_arm_other_ranks_exit_quietly():
     p = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0
     assert not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_reference_arm_under_torchrun_prints_once_on_all_cores():
+    single = _lines(_run().stdout)
+    p = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), *ARGS, "--gpus", "2"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = _lines(p.stdout)
+    assert len(lines) == 1 and len(single) == 1
+    assert lines[0]["n_gpus"] == 2
+    assert lines[0]["cpu_baseline"]["cores"] == single[0]["cpu_baseline"]["cores"]
