@@ -44,6 +44,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    # one build at a time: the ranks of a multi-process launch share this
+    # tree, and the first to take the lock builds while the others wait and
+    # then find the library up to date
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and up_to_date():
+            return LIB
+        return _compile_and_link(verbose)
+
+
+def _compile_and_link(verbose: bool) -> str:
     cc = nvcc()
     procs = []
     objs = []
