@@ -46,9 +46,12 @@ def _free_port() -> int:
         return s.getsockname()[1]
 
 
-def _batch():
-    n_list = [12, 30, 7, 25, 18, 33, 9, 21]
-    kap = [4.0, 12.0, 6.0, 16.0, 8.0, 20.0, 5.0, 10.0]
+BATCH_8 = ([12, 30, 7, 25, 18, 33, 9, 21], [4.0, 12.0, 6.0, 16.0, 8.0, 20.0, 5.0, 10.0])
+BATCH_2 = ([12, 30], [4.0, 12.0])
+
+
+def _batch(spec):
+    n_list, kap = list(spec[0]), list(spec[1])
     A, b = W.svd_batch(n_list, kap, seed=7, processes=1)
     return n_list, A, b
 
@@ -60,7 +63,7 @@ def _system(A, b, n_list, s):
     return (A[4 * moff: 4 * (moff + n * n)].reshape(4, n, n).copy(), b[8 * voff: 8 * (voff + n)].reshape(8, n).copy())
 
 
-def _rank_main(rank, world, port, out):
+def _rank_main(rank, world, port, out, spec=BATCH_8):
     import torch.distributed as dist
     sys.path.insert(0, ROOT)
     import oracle
@@ -69,7 +72,7 @@ def _rank_main(rank, world, port, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        n_list, A, b = _batch()
+        n_list, A, b = _batch(spec)
         assignment = S.lpt_assign(n_list, world)
         ids = assignment[rank]
         sub_n = [n_list[s] for s in ids]
@@ -114,3 +117,21 @@ def test_sharded_batch_gathers_every_system_over_two_gloo_ranks():
         assert p.exitcode == 0
     got = dict(out.get(timeout=10) for _ in range(2))
     assert got == {"checked": True, "other": True}
+
+
+@pytest.mark.timeout(180)
+def test_more_ranks_than_systems_leaves_a_rank_empty():
+    """Three ranks, two systems: LPT gives the third rank nothing, its
+    gathered parts are empty, and rank 0 still gets every system."""
+    assert shard.lpt_assign(BATCH_2[0], 3) == [[1], [0], []]
+    ctx = torch.multiprocessing.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 3, port, out, BATCH_2)) for r in range(3)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=150)
+        assert p.exitcode == 0
+    got = sorted(out.get(timeout=10) for _ in range(3))
+    assert got == [("checked", True), ("other", True), ("other", True)]
