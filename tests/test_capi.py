@@ -147,6 +147,45 @@ def test_order_bound_keeps_every_size_exact(lib):
     assert lib.mw_gemm_strassen(2, 0, 1, 64, 8, 64, 8, 64, 8, ld, 8, 1 << 30, None) == -10
 
 
+def test_batched_arguments_checked_on_the_host(lib):
+    """The batched entry points check their arguments, orders included
+    (1 <= n <= 1024), before any device work; an empty batch is a no-op."""
+    def orders(*ns):
+        return (ctypes.c_int * len(ns))(*ns)
+    out = ctypes.c_size_t(0)
+    ok2, bad_hi, bad_lo = orders(3, 5), orders(3, 1025), orders(0, 5)
+    # sizes
+    assert lib.mw_batch_workspace_size(L.MW_OP_SOLVE, 2, 2, ok2, ctypes.byref(out)) == 0 and out.value > 0
+    assert lib.mw_batch_workspace_size(9, 2, 2, ok2, ctypes.byref(out)) == -1
+    assert lib.mw_batch_workspace_size(L.MW_OP_SOLVE, 5, 2, ok2, ctypes.byref(out)) == -2
+    assert lib.mw_batch_workspace_size(L.MW_OP_SOLVE, 2, -1, ok2, ctypes.byref(out)) == -3
+    assert lib.mw_batch_workspace_size(L.MW_OP_SOLVE, 2, 2, bad_hi, ctypes.byref(out)) == -4
+    assert lib.mw_batch_workspace_size(L.MW_OP_SOLVE, 2, 2, bad_lo, ctypes.byref(out)) == -4
+    assert lib.mw_batch_workspace_size(L.MW_OP_SOLVE, 2, 2, ok2, None) == -5
+    assert lib.mw_batch_blocked_workspace_size(L.MW_OP_REFINE, 2, 1, 2, ok2, ctypes.byref(out)) == 0
+    assert lib.mw_batch_blocked_workspace_size(L.MW_OP_LUDECOMP, 3, 1, 2, ok2, ctypes.byref(out)) \
+        == L.MW_EUNSUPPORTED                                   # split update is DD only
+    assert lib.mw_batch_blocked_workspace_size(L.MW_OP_LUDECOMP, 2, 0, 2, bad_hi, ctypes.byref(out)) == -5
+    # factorisation, substitution, refinement
+    big = 1 << 30
+    assert lib.mw_ludecomp_batched(2, 0, None, None, None, None, None, 0, None) == 0
+    assert lib.mw_ludecomp_batched(2, 2, bad_hi, 8, 8, 8, 8, big, None) == -3
+    assert lib.mw_ludecomp_batched_blocked(2, 0, 2, bad_lo, 8, 8, 8, 8, big, None) == -4
+    assert lib.mw_ludecomp_batched_blocked(3, 1, 2, ok2, 8, 8, 8, 8, big, None) == L.MW_EUNSUPPORTED
+    assert lib.mw_ludecomp_batched_blocked(2, 0, 2, ok2, 8, 8, 8, 8, 0, None) == -9
+    assert lib.mw_solve_batched(2, 2, bad_lo, 8, 8, 8, 8, 8, big, None) == -3
+    assert lib.mw_solve_batched(2, 2, ok2, 8, 8, 8, 8, 8, 0, None) == -9
+    assert lib.mw_refine_batched(2, ok2, 8, 9, 8, 8, 2, 200, 30, 8, 8, 8, 8, big, None) == -4
+    assert lib.mw_refine_batched(2, ok2, 8, 4, 8, 8, 3, 200, 30, 8, 2, 8, 8, big, None) == -11
+    assert lib.mw_refine_batched(2, bad_hi, 8, 4, 8, 8, 2, 200, 30, 8, 8, 8, 8, big, None) == -2
+    assert lib.mw_refine_batched(2, ok2, 8, 4, 8, 8, 2, 200, 30, 8, 8, 8, 8, 0, None) == -14
+    assert lib.mw_refine_batched_blocked(2, ok2, 8, 4, 8, 8, 3, 1, 200, 30, 8, 8, 8, 8, big, None) \
+        == L.MW_EUNSUPPORTED
+    assert lib.mw_refine_batched_blocked(2, bad_hi, 8, 4, 8, 8, 2, 1, 200, 30, 8, 8, 8, 8, big, None) == -2
+    assert lib.mw_refine_batched_blocked(2, ok2, 8, 4, 8, 8, 2, 1, 0, 30, 8, 8, 8, 8, big, None) == -9
+    assert lib.mw_refine_batched_blocked(2, ok2, 8, 4, 8, 8, 2, 1, 200, 30, 8, 8, 8, 8, 0, None) == -15
+
+
 def test_status_and_wait_limit_arguments(lib):
     assert lib.mw_work_status(7, 0, 8, None) == -1
     assert lib.mw_work_status(L.MW_OP_SOLVE, 5, 8, None) == -2
