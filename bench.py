@@ -999,6 +999,10 @@ def main():
     e2e_t_max, e2e_solved = combine_ranks(e2e_ms, e2e_met, "cuda")
     e2e_val = e2e_solved / (e2e_t_max * 1e-3)
     del A_h, A2, b2, x2, graph2
+    # every graph is captured; the comparisons below make eager calls with
+    # work buffers of their own, which must not be taken for resident plans
+    # (a freed buffer's address can come back for a new one)
+    api.batch_plan_cache(False)
 
     line = {
         "metric": "solves/s at 2^-200 rel. error",
