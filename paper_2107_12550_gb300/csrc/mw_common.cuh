@@ -1,5 +1,5 @@
-// mw_common.cuh -- status codes, launch checks and the bounded grid barrier
-// shared by the library's kernels.
+// mw_common.cuh -- status codes, launch checks, the bounded-wait helpers and
+// the cp.async wrappers shared by the library's kernels.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
